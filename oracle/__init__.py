@@ -1,0 +1,235 @@
+"""FP64 CPU oracle for the registration hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product path (``paper_2509_25044_gb300``)
+never imports, links or executes anything in here, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, OpenMP over
+z-planes with a fixed summation order).  This module loads it through ctypes
+and composes the per-step functions into one registration iteration by the
+chain rule, in the paper's order (Sec. 1 Eq. image-reg; Fig. 1b): warp ->
+similarity -> its adjoint -> sampler adjoint -> regulariser -> Adam.
+
+Conventions: volumes ``[nz, ny, nx]`` (x fastest), displacement ``u`` is
+``[3, nz, ny, nx]`` with channels (x, y, z) in voxel units, phi(p) = p + u(p).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import build as _build_lib, lib_path
+
+PAD_BORDER = 0
+PAD_ZEROS = 1
+LOSS_LNCC = 0
+LOSS_MI = 1
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            _build_lib()
+        lib = ctypes.CDLL(path)
+        lib.or_warp.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.or_warp.restype = None
+        lib.or_lncc.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, _dp, _dp]
+        lib.or_lncc.restype = ctypes.c_double
+        lib.or_lncc_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, _dp]
+        lib.or_lncc_grad.restype = ctypes.c_double
+        lib.or_bspline3.argtypes = [ctypes.c_double]
+        lib.or_bspline3.restype = ctypes.c_double
+        lib.or_bspline3_deriv.argtypes = [ctypes.c_double]
+        lib.or_bspline3_deriv.restype = ctypes.c_double
+        lib.or_mi.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, _dp]
+        lib.or_mi.restype = ctypes.c_double
+        lib.or_mi_grad.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, _dp]
+        lib.or_mi_grad.restype = ctypes.c_double
+        lib.or_diffusion.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        lib.or_diffusion.restype = ctypes.c_double
+        lib.or_bf16_round.argtypes = [ctypes.c_double]
+        lib.or_bf16_round.restype = ctypes.c_double
+        lib.or_adam.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.or_adam.restype = None
+        lib.or_jacdet.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        lib.or_jacdet.restype = None
+        _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _dims(vol: np.ndarray):
+    nz, ny, nx = vol.shape
+    return nx, ny, nz
+
+
+# --------------------------------------------------------------------------
+# per-step functions
+# --------------------------------------------------------------------------
+def warp(M, u, pad: int = PAD_BORDER, with_grad: bool = False):
+    """J = M o (id+u) (trilinear) and optionally dJ/dphi [3, nz, ny, nx]."""
+    M = _f64(M)
+    u = _f64(u)
+    assert u.shape == (3,) + M.shape
+    nx, ny, nz = _dims(M)
+    J = np.empty_like(M)
+    dJ = np.empty_like(u) if with_grad else None
+    _load().or_warp(_ptr(M), _ptr(u), nx, ny, nz, int(pad), _ptr(J), _ptr(dJ))
+    return (J, dJ) if with_grad else J
+
+
+def lncc(F, J, win: int, eps: float, per_voxel: bool = False):
+    """S = mean_i n_i (LNCC similarity); the loss is 1 - S."""
+    F = _f64(F)
+    J = _f64(J)
+    nx, ny, nz = _dims(F)
+    n = np.empty_like(F) if per_voxel else None
+    S = _load().or_lncc(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps), _ptr(n), None)
+    return (S, n) if per_voxel else S
+
+
+def lncc_grad(F, J, win: int, eps: float):
+    """(S, dL/dJ) for L = 1 - S."""
+    F = _f64(F)
+    J = _f64(J)
+    nx, ny, nz = _dims(F)
+    g = np.empty_like(F)
+    S = _load().or_lncc_grad(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps), _ptr(g))
+    return S, g
+
+
+def bspline3(t: float) -> float:
+    return _load().or_bspline3(float(t))
+
+
+def bspline3_deriv(t: float) -> float:
+    return _load().or_bspline3_deriv(float(t))
+
+
+def mi(Fh, Jh, bins: int, with_hist: bool = False):
+    """Parzen MI of intensities already mapped to [0,1]."""
+    Fh = _f64(Fh).ravel()
+    Jh = _f64(Jh).ravel()
+    p = np.empty((bins, bins), dtype=np.float64) if with_hist else None
+    v = _load().or_mi(_ptr(Fh), _ptr(Jh), Fh.size, int(bins), _ptr(p))
+    return (v, p) if with_hist else v
+
+
+def mi_grad(Fh, Jh, bins: int):
+    """(MI, dL/dJh) for L = -MI."""
+    shape = np.shape(Jh)
+    Fh = _f64(Fh).ravel()
+    Jh = _f64(Jh).ravel()
+    g = np.empty_like(Jh)
+    v = _load().or_mi_grad(_ptr(Fh), _ptr(Jh), Fh.size, int(bins), _ptr(g))
+    return v, g.reshape(shape)
+
+
+def normalize(v, lo: float, hi: float):
+    """Map intensities to [0,1]: vh = clamp((v-lo)/(hi-lo), 0, 1), and dvh/dv."""
+    v = _f64(v)
+    t = (v - lo) / (hi - lo)
+    d = np.where((t >= 0.0) & (t <= 1.0), 1.0 / (hi - lo), 0.0)
+    return np.clip(t, 0.0, 1.0), d
+
+
+def diffusion(u, with_grad: bool = True):
+    u = _f64(u)
+    nx, ny, nz = _dims(u[0])
+    g = np.empty_like(u) if with_grad else None
+    R = _load().or_diffusion(_ptr(u), nx, ny, nz, _ptr(g))
+    return (R, g) if with_grad else R
+
+
+def bf16_round(a):
+    a = _f64(a)
+    f = _load().or_bf16_round
+    return np.vectorize(f, otypes=[np.float64])(a) if a.size else a.copy()
+
+
+def adam(u, m, v, g, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+         eps: float = 1e-8, grad_scale: float = 1.0, bf16_moments: bool = False):
+    """Returns (u', m', v') after one Adam step (inputs are not modified)."""
+    u = _f64(u).copy()
+    m = _f64(m).copy()
+    v = _f64(v).copy()
+    g = _f64(g)
+    _load().or_adam(_ptr(u), _ptr(m), _ptr(v), _ptr(g), u.size, float(lr), float(beta1), float(beta2),
+                    float(eps), float(grad_scale), int(t), int(bool(bf16_moments)))
+    return u, m, v
+
+
+def jacdet(u):
+    u = _f64(u)
+    nx, ny, nz = _dims(u[0])
+    d = np.empty(u.shape[1:], dtype=np.float64)
+    _load().or_jacdet(_ptr(u), nx, ny, nz, _ptr(d))
+    return d
+
+
+# --------------------------------------------------------------------------
+# one iteration, composed by the chain rule
+# --------------------------------------------------------------------------
+@dataclass
+class LossSpec:
+    kind: int = LOSS_LNCC
+    window: int = 7
+    eps: float = 1e-5
+    bins: int = 32
+    f_range: tuple = (0.0, 1.0)
+    m_range: tuple = (0.0, 1.0)
+
+
+def similarity_and_grad(F, M, u, spec: LossSpec, pad: int = PAD_BORDER, need_grad: bool = True):
+    """Returns (similarity, dC/du or None) with C = 1 - S (LNCC) or -MI (MI)."""
+    J, dJ = warp(M, u, pad, with_grad=True)
+    if spec.kind == LOSS_LNCC:
+        if not need_grad:
+            return lncc(F, J, spec.window, spec.eps), None
+        S, gJ = lncc_grad(F, J, spec.window, spec.eps)
+        return S, gJ[None] * dJ
+    Fh, _ = normalize(F, *spec.f_range)
+    Jh, dJh = normalize(J, *spec.m_range)
+    if not need_grad:
+        return mi(Fh, Jh, spec.bins), None
+    v, gJh = mi_grad(Fh, Jh, spec.bins)
+    return v, (gJh * dJh)[None] * dJ
+
+
+def objective(F, M, u, spec: LossSpec, lam: float, pad: int = PAD_BORDER):
+    """Returns dict(sim, R, loss, total, grad) for C(F, M o (id+u)) + lam R(u)."""
+    sim, g = similarity_and_grad(F, M, u, spec, pad)
+    R, gR = diffusion(u)
+    loss = 1.0 - sim if spec.kind == LOSS_LNCC else -sim
+    return dict(sim=sim, R=R, loss=loss, total=loss + lam * R, grad=g + lam * gR)
+
+
+def iterate(F, M, u, m, v, t: int, spec: LossSpec, lam: float, lr: float, beta1=0.9, beta2=0.999,
+            eps=1e-8, grad_scale=None, bf16_moments=False, pad: int = PAD_BORDER):
+    """One full iteration; grad_scale defaults to N (the Adam input is N * grad)."""
+    obj = objective(F, M, u, spec, lam, pad)
+    if grad_scale is None:
+        grad_scale = float(np.prod(np.shape(F)))
+    u2, m2, v2 = adam(u, m, v, obj["grad"], t, lr, beta1, beta2, eps, grad_scale, bf16_moments)
+    obj.update(u=u2, m=m2, v=v2)
+    return obj

@@ -1,0 +1,517 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for one iteration of dense 3-D deformable
+ * registration, argmin_u C(F, M o (id+u)) + lambda R(u)  (Sec. 1, Eq. image-reg).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no source, header, table or helper with the
+ * CUDA library in paper_2509_25044_gb300/csrc.
+ *
+ * Every function follows the paper's definition as written, in the obvious
+ * order, in double precision.  Global sums are taken per z-plane (serially in
+ * x-fastest order) and then over planes in increasing z, so results do not
+ * depend on the number of OpenMP threads.
+ *
+ * Layout conventions (the paper is silent on them):
+ *   volumes   [nz][ny][nx], x fastest, voxel spacing 1;
+ *   u         structure of arrays [3][nz][ny][nx]; channel 0,1,2 = x,y,z
+ *             displacement in voxel units; phi(p) = p + u(p).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PAD_BORDER 0
+#define OR_PAD_ZEROS 1
+
+static long lin(int x, int y, int z, int nx, int ny) { return ((long)z * ny + y) * nx + x; }
+
+/* ------------------------------------------------------------------------ */
+/* Trilinear warp J = M o (id + u).                                          */
+/* Follows the d-linear interpolation formula of the ring-sampler appendix   */
+/* (Eq. interp): J = sum_{b in {0,1}^3} prod_k (1-a_k)^(1-b_k) a_k^b_k       */
+/* M[i+b], i_k = floor(phi_k), a_k = phi_k - i_k; and Algorithm gridsampler  */
+/* (one sample per target voxel, identity grid implicit).                    */
+/* Padding: ZEROS = corners outside the volume contribute 0 (Algorithm       */
+/* gridsampler).  BORDER = the sample point is first clamped into            */
+/* [0, n_k - 1] per axis; the cell index is then min(floor(q), n_k - 2).     */
+/* dJ (optional, 3N) receives dJ/dphi_k.  In BORDER mode the derivative      */
+/* along k is 0 where phi_k lies outside [0, n_k - 1] (the clamp is flat).   */
+/* ------------------------------------------------------------------------ */
+void or_warp(const double *M, const double *u, int nx, int ny, int nz, int pad,
+             double *J, double *dJ)
+{
+    const long N = (long)nx * ny * nz;
+    const int n[3] = {nx, ny, nz};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const long p = lin(x, y, z, nx, ny);
+                const int pc[3] = {x, y, z};
+                long i[3];
+                double a[3];
+                double slope_ok[3];
+                for (int k = 0; k < 3; ++k) {
+                    double phi = (double)pc[k] + u[(long)k * N + p];
+                    if (pad == OR_PAD_BORDER) {
+                        double q = phi;
+                        slope_ok[k] = (phi >= 0.0 && phi <= (double)(n[k] - 1)) ? 1.0 : 0.0;
+                        if (q < 0.0) q = 0.0;
+                        if (q > (double)(n[k] - 1)) q = (double)(n[k] - 1);
+                        if (n[k] == 1) {
+                            i[k] = 0;
+                            a[k] = 0.0;
+                        } else {
+                            long f = (long)floor(q);
+                            if (f > n[k] - 2) f = n[k] - 2;
+                            i[k] = f;
+                            a[k] = q - (double)f;
+                        }
+                    } else {
+                        slope_ok[k] = 1.0;
+                        long f = (long)floor(phi);
+                        i[k] = f;
+                        a[k] = phi - (double)f;
+                    }
+                }
+                double val = 0.0;
+                double der[3] = {0.0, 0.0, 0.0};
+                for (int b = 0; b < 8; ++b) {
+                    const int bb[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+                    long c[3];
+                    int inside = 1;
+                    for (int k = 0; k < 3; ++k) {
+                        c[k] = i[k] + bb[k];
+                        if (c[k] < 0 || c[k] > n[k] - 1) inside = 0;
+                    }
+                    double mv = 0.0;
+                    if (inside) {
+                        mv = M[lin((int)c[0], (int)c[1], (int)c[2], nx, ny)];
+                    } else if (pad == OR_PAD_BORDER) {
+                        /* only reachable with zero weight (n_k == 1) */
+                        long cc[3];
+                        for (int k = 0; k < 3; ++k) cc[k] = c[k] > n[k] - 1 ? n[k] - 1 : c[k];
+                        mv = M[lin((int)cc[0], (int)cc[1], (int)cc[2], nx, ny)];
+                    }
+                    double w[3], dw[3];
+                    for (int k = 0; k < 3; ++k) {
+                        w[k] = bb[k] ? a[k] : 1.0 - a[k];
+                        dw[k] = bb[k] ? 1.0 : -1.0;
+                    }
+                    val += w[0] * w[1] * w[2] * mv;
+                    der[0] += dw[0] * w[1] * w[2] * mv;
+                    der[1] += w[0] * dw[1] * w[2] * mv;
+                    der[2] += w[0] * w[1] * dw[2] * mv;
+                }
+                J[p] = val;
+                if (dJ) {
+                    for (int k = 0; k < 3; ++k) dJ[(long)k * N + p] = der[k] * slope_ok[k];
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* LNCC value (App. fused LNCC, Eq. lncc-loss and Eqs. lncc-a .. lncc-c).    */
+/* The averaging filter w is a uniform box of side `win` (odd) centred at i; */
+/* at the volume border the box is truncated to the voxels inside the volume */
+/* and normalised by their count c_i (the paper does not say how borders are */
+/* handled).  Two-pass form: means first, then centred sums.                 */
+/*   A_i = sum_k w_ik (F_k - muF_i)(J_k - muJ_i), B_i, C_i likewise,          */
+/*   n_i = A_i^2 / (B_i C_i + eps), and n_i = 0 where B_i C_i + eps == 0.     */
+/* Returns S = (1/N) sum_i n_i; the loss is 1 - S.  n_out (optional, N).     */
+/* The per-window quantities (muF, muJ, A, B, C, c) go to win_out (optional, */
+/* 6N, [6][N]) for the gradient.                                             */
+/* ------------------------------------------------------------------------ */
+static void window_bounds(int c, int r, int n, int *lo, int *hi)
+{
+    *lo = c - r < 0 ? 0 : c - r;
+    *hi = c + r > n - 1 ? n - 1 : c + r;
+}
+
+double or_lncc(const double *F, const double *J, int nx, int ny, int nz, int win, double eps,
+               double *n_out, double *win_out)
+{
+    const long N = (long)nx * ny * nz;
+    const int r = win / 2;
+    double *plane_sum = (double *)calloc((size_t)nz, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z) {
+        double acc = 0.0;
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                int x0, x1, y0, y1, z0, z1;
+                window_bounds(x, r, nx, &x0, &x1);
+                window_bounds(y, r, ny, &y0, &y1);
+                window_bounds(z, r, nz, &z0, &z1);
+                double cnt = 0.0, sF = 0.0, sJ = 0.0;
+                for (int zz = z0; zz <= z1; ++zz)
+                    for (int yy = y0; yy <= y1; ++yy)
+                        for (int xx = x0; xx <= x1; ++xx) {
+                            long k = lin(xx, yy, zz, nx, ny);
+                            sF += F[k];
+                            sJ += J[k];
+                            cnt += 1.0;
+                        }
+                const double muF = sF / cnt, muJ = sJ / cnt;
+                double A = 0.0, B = 0.0, C = 0.0;
+                for (int zz = z0; zz <= z1; ++zz)
+                    for (int yy = y0; yy <= y1; ++yy)
+                        for (int xx = x0; xx <= x1; ++xx) {
+                            long k = lin(xx, yy, zz, nx, ny);
+                            const double df = F[k] - muF, dj = J[k] - muJ;
+                            A += df * dj;
+                            B += df * df;
+                            C += dj * dj;
+                        }
+                A /= cnt;
+                B /= cnt;
+                C /= cnt;
+                const double D = B * C + eps;
+                const double ni = D > 0.0 ? A * A / D : 0.0;
+                const long p = lin(x, y, z, nx, ny);
+                if (n_out) n_out[p] = ni;
+                if (win_out) {
+                    win_out[0 * N + p] = muF;
+                    win_out[1 * N + p] = muJ;
+                    win_out[2 * N + p] = A;
+                    win_out[3 * N + p] = B;
+                    win_out[4 * N + p] = C;
+                    win_out[5 * N + p] = cnt;
+                }
+                acc += ni;
+            }
+        }
+        plane_sum[z] = acc;
+    }
+    double S = 0.0;
+    for (int z = 0; z < nz; ++z) S += plane_sum[z];
+    free(plane_sum);
+    return S / (double)N;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the LNCC loss L = 1 - (1/N) sum_i n_i with respect to J.      */
+/* Differentiates the definition directly (App. fused LNCC, the chain rule  */
+/* of Eq. gradientcc-first written for the moving image), with              */
+/*   dn/dA = 2A/D,  dn/dC = -A^2 B / D^2,  D = B C + eps,                    */
+/*   dA_i/dJ_k = (F_k - muF_i)/c_i,  dC_i/dJ_k = 2 (J_k - muJ_i)/c_i          */
+/* for k inside window i, and dL/dn_i = -1/N.  Then                          */
+/*   gJ_k = sum_{i : k in W_i} dL/dn_i (dn/dA dA_i/dJ_k + dn/dC dC_i/dJ_k). */
+/* (The paper's printed coefficient A/(B^2 C) in Eq. gradientcc-first is     */
+/* read as A^2/(B^2 C), as in its next line; eps is kept.)                   */
+/* Returns S as or_lncc does.                                                */
+/* ------------------------------------------------------------------------ */
+double or_lncc_grad(const double *F, const double *J, int nx, int ny, int nz, int win, double eps,
+                    double *gJ)
+{
+    const long N = (long)nx * ny * nz;
+    const int r = win / 2;
+    double *wq = (double *)malloc(sizeof(double) * 6 * (size_t)N);
+    const double S = or_lncc(F, J, nx, ny, nz, win, eps, NULL, wq);
+    const double *muF = wq, *muJ = wq + N, *A = wq + 2 * N, *B = wq + 3 * N, *C = wq + 4 * N,
+                 *cnt = wq + 5 * N;
+    /* per-window coefficients alpha_i (multiplies F_k - muF_i) and beta_i (J_k - muJ_i) */
+    double *alpha = (double *)malloc(sizeof(double) * (size_t)N);
+    double *beta = (double *)malloc(sizeof(double) * (size_t)N);
+    const double dLdn = -1.0 / (double)N;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) {
+        const double D = B[i] * C[i] + eps;
+        if (D > 0.0) {
+            const double dndA = 2.0 * A[i] / D;
+            const double dndC = -A[i] * A[i] * B[i] / (D * D);
+            alpha[i] = dLdn * dndA / cnt[i];
+            beta[i] = dLdn * dndC * 2.0 / cnt[i];
+        } else {
+            alpha[i] = 0.0;
+            beta[i] = 0.0;
+        }
+    }
+    /* k lies in W_i  <=>  i inside the volume and |i - k|_inf <= r */
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const long k = lin(x, y, z, nx, ny);
+                int x0, x1, y0, y1, z0, z1;
+                window_bounds(x, r, nx, &x0, &x1);
+                window_bounds(y, r, ny, &y0, &y1);
+                window_bounds(z, r, nz, &z0, &z1);
+                double g = 0.0;
+                for (int zz = z0; zz <= z1; ++zz)
+                    for (int yy = y0; yy <= y1; ++yy)
+                        for (int xx = x0; xx <= x1; ++xx) {
+                            const long i = lin(xx, yy, zz, nx, ny);
+                            g += alpha[i] * (F[k] - muF[i]) + beta[i] * (J[k] - muJ[i]);
+                        }
+                gJ[k] = g;
+            }
+        }
+    }
+    free(alpha);
+    free(beta);
+    free(wq);
+    return S;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cubic B-spline Parzen kernel and its derivative (Sec. 2.2, Eq. mi, with   */
+/* the 3rd-order B-spline choice of kappa).                                  */
+/* ------------------------------------------------------------------------ */
+double or_bspline3(double t)
+{
+    const double a = fabs(t);
+    if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+    if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+    return 0.0;
+}
+
+double or_bspline3_deriv(double t)
+{
+    const double a = fabs(t);
+    const double s = t < 0.0 ? -1.0 : 1.0;
+    if (a < 1.0) return s * (-2.0 * a + 1.5 * a * a);
+    if (a < 2.0) return s * (-0.5 * (2.0 - a) * (2.0 - a));
+    return 0.0;
+}
+
+/* Bin coordinate of an intensity v in [0,1] for B bins: the B-spline of     */
+/* bin m is centred at s = m, and [0,1] maps onto [1, B-2] so that every     */
+/* intensity has its full kernel support inside the B bins.                  */
+static double bin_coord(double v, int B) { return v * (double)(B - 3) + 1.0; }
+
+/* ------------------------------------------------------------------------ */
+/* Parzen-window mutual information (Sec. 2.2, Eq. mi; App. fused MI).       */
+/* Inputs Fh, Jh are intensities already mapped to [0,1].                    */
+/*   p_IJ[m][n] = (1/N) sum_k kappa(sF_k - m) kappa(sJ_k - n)                */
+/*   p_I[m] = sum_n p_IJ[m][n],  p_J[n] = sum_m p_IJ[m][n]                   */
+/*   MI = sum_{m,n : p_IJ > 0} p_IJ log(p_IJ / (p_I p_J))   (natural log)     */
+/* p_out (optional, B*B, row m = fixed-image bin).                           */
+/* ------------------------------------------------------------------------ */
+double or_mi(const double *Fh, const double *Jh, long N, int B, double *p_out)
+{
+    const int BB = B * B;
+    /* one partial histogram per block of voxels, summed in block order */
+    const long blk = 4096;
+    const long nblk = (N + blk - 1) / blk;
+    double *part = (double *)calloc((size_t)nblk * BB, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (long b = 0; b < nblk; ++b) {
+        double *h = part + b * BB;
+        double wF[256], wJ[256];
+        const long k1 = (b + 1) * blk < N ? (b + 1) * blk : N;
+        for (long k = b * blk; k < k1; ++k) {
+            const double sF = bin_coord(Fh[k], B), sJ = bin_coord(Jh[k], B);
+            for (int m = 0; m < B; ++m) {
+                wF[m] = or_bspline3(sF - (double)m);
+                wJ[m] = or_bspline3(sJ - (double)m);
+            }
+            for (int m = 0; m < B; ++m)
+                for (int n = 0; n < B; ++n) h[m * B + n] += wF[m] * wJ[n];
+        }
+    }
+    double *p = (double *)calloc((size_t)BB, sizeof(double));
+    for (long b = 0; b < nblk; ++b)
+        for (int e = 0; e < BB; ++e) p[e] += part[b * BB + e];
+    free(part);
+    for (int e = 0; e < BB; ++e) p[e] /= (double)N;
+    double pI[256], pJ[256];
+    for (int m = 0; m < B; ++m) {
+        pI[m] = 0.0;
+        pJ[m] = 0.0;
+    }
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            pI[m] += p[m * B + n];
+            pJ[n] += p[m * B + n];
+        }
+    double mi = 0.0;
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            const double v = p[m * B + n];
+            if (v > 0.0) mi += v * log(v / (pI[m] * pJ[n]));
+        }
+    if (p_out) memcpy(p_out, p, sizeof(double) * (size_t)BB);
+    free(p);
+    return mi;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the MI loss L = -MI with respect to Jh (App. fused MI, Eq.    */
+/* gradientmi-threadn, with the marginals obtained from the joint).          */
+/* With MI = sum p log p - sum p_I log p_I - sum p_J log p_J and the        */
+/* marginals taken as row/column sums of the joint,                          */
+/*   dMI/dp_IJ[m][n] = log(p_IJ[m][n] / (p_I[m] p_J[n])) - 1,                */
+/* and the -1 drops out because sum_{m,n} dp_IJ/dJh_k = 0 (the kernel is a   */
+/* partition of unity).  So G[m][n] = log(p_IJ / (p_I p_J)), 0 where         */
+/* p_IJ = 0 (no voxel then has a non-zero derivative there).  Then           */
+/*   dL/dJh_k = -(1/N) (B-3) sum_{m,n} G[m][n] kappa(sF_k - m) kappa'(sJ_k - n). */
+/* Returns MI.                                                               */
+/* ------------------------------------------------------------------------ */
+double or_mi_grad(const double *Fh, const double *Jh, long N, int B, double *gJh)
+{
+    const int BB = B * B;
+    double *p = (double *)malloc(sizeof(double) * (size_t)BB);
+    const double mi = or_mi(Fh, Jh, N, B, p);
+    double pI[256], pJ[256];
+    for (int m = 0; m < B; ++m) {
+        pI[m] = 0.0;
+        pJ[m] = 0.0;
+    }
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            pI[m] += p[m * B + n];
+            pJ[n] += p[m * B + n];
+        }
+    double *G = (double *)malloc(sizeof(double) * (size_t)BB);
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            const double v = p[m * B + n];
+            G[m * B + n] = v > 0.0 ? log(v / (pI[m] * pJ[n])) : 0.0;
+        }
+    const double scale = -(double)(B - 3) / (double)N;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < N; ++k) {
+        double wF[256], dJ[256];
+        const double sF = bin_coord(Fh[k], B), sJ = bin_coord(Jh[k], B);
+        for (int m = 0; m < B; ++m) {
+            wF[m] = or_bspline3(sF - (double)m);
+            dJ[m] = or_bspline3_deriv(sJ - (double)m);
+        }
+        double g = 0.0;
+        for (int m = 0; m < B; ++m)
+            for (int n = 0; n < B; ++n) g += G[m * B + n] * wF[m] * dJ[n];
+        gJh[k] = scale * g;
+    }
+    free(G);
+    free(p);
+    return mi;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diffusion regulariser (Sec. 1 lists the Sobolev norm of the gradient as  */
+/* a common R; this is its first-order, squared form):                       */
+/*   R(u) = (1/N) sum_c sum_d sum_{p : p+e_d inside} (u_c(p+e_d) - u_c(p))^2  */
+/* grad (optional, 3N, overwritten) = dR/du, by the chain rule of each       */
+/* squared difference.                                                       */
+/* ------------------------------------------------------------------------ */
+double or_diffusion(const double *u, int nx, int ny, int nz, double *grad)
+{
+    const long N = (long)nx * ny * nz;
+    if (grad) memset(grad, 0, sizeof(double) * 3 * (size_t)N);
+    const int step_ok[3] = {nx > 1, ny > 1, nz > 1};
+    double R = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double *uc = u + (long)c * N;
+        double *gc = grad ? grad + (long)c * N : NULL;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long p = lin(x, y, z, nx, ny);
+                    const int q[3][3] = {{x + 1, y, z}, {x, y + 1, z}, {x, y, z + 1}};
+                    for (int d = 0; d < 3; ++d) {
+                        if (!step_ok[d]) continue;
+                        if (q[d][0] >= nx || q[d][1] >= ny || q[d][2] >= nz) continue;
+                        const long pn = lin(q[d][0], q[d][1], q[d][2], nx, ny);
+                        const double diff = uc[pn] - uc[p];
+                        R += diff * diff;
+                        if (gc) {
+                            gc[pn] += 2.0 * diff / (double)N;
+                            gc[p] -= 2.0 * diff / (double)N;
+                        }
+                    }
+                }
+    }
+    return R / (double)N;
+}
+
+/* ------------------------------------------------------------------------ */
+/* bfloat16 round-to-nearest-even of a value, through its FP32 bit pattern   */
+/* (bfloat16 keeps the top 16 bits of an IEEE-754 binary32).                */
+/* ------------------------------------------------------------------------ */
+double or_bf16_round(double x)
+{
+    float f = (float)x;
+    uint32_t bits;
+    memcpy(&bits, &f, 4);
+    if ((bits & 0x7f800000u) == 0x7f800000u) { /* inf / nan pass through */
+        if (bits & 0x007fffffu) bits |= 0x00400000u;
+        bits &= 0xffff0000u;
+    } else {
+        const uint32_t lsb = (bits >> 16) & 1u;
+        bits = bits + 0x7fffu + lsb;
+        bits &= 0xffff0000u;
+    }
+    float out;
+    memcpy(&out, &bits, 4);
+    return (double)out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Adam step (the optimiser state m1, m2 of Sec. 3.1), with bias         */
+/* correction, on n elements:                                                */
+/*   gs = grad_scale * g;  m = b1 m + (1-b1) gs;  v = b2 v + (1-b2) gs^2;     */
+/*   u -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).                  */
+/* bf16_moments: the update uses the new m, v as computed; the stored m, v   */
+/* are then rounded to bfloat16 (round to nearest even).                     */
+/* ------------------------------------------------------------------------ */
+void or_adam(double *u, double *m, double *v, const double *g, long n, double lr, double b1,
+             double b2, double eps, double grad_scale, int t, int bf16_moments)
+{
+    const double bc1 = 1.0 - pow(b1, (double)t);
+    const double bc2 = 1.0 - pow(b2, (double)t);
+    for (long i = 0; i < n; ++i) {
+        const double gs = grad_scale * g[i];
+        const double mn = b1 * m[i] + (1.0 - b1) * gs;
+        const double vn = b2 * v[i] + (1.0 - b2) * gs * gs;
+        u[i] -= lr * (mn / bc1) / (sqrt(vn / bc2) + eps);
+        m[i] = bf16_moments ? or_bf16_round(mn) : mn;
+        v[i] = bf16_moments ? or_bf16_round(vn) : vn;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobian determinant of phi = id + u: det(I + grad u), with central       */
+/* differences in the interior and one-sided differences at the border      */
+/* (0 along an axis of length 1).  Row c = displacement component, column d */
+/* = derivative axis.                                                        */
+/* ------------------------------------------------------------------------ */
+void or_jacdet(const double *u, int nx, int ny, int nz, double *det)
+{
+    const long N = (long)nx * ny * nz;
+    const int n[3] = {nx, ny, nz};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int pc[3] = {x, y, z};
+                double Jm[3][3];
+                for (int c = 0; c < 3; ++c) {
+                    const double *uc = u + (long)c * N;
+                    for (int d = 0; d < 3; ++d) {
+                        int lo[3] = {x, y, z}, hi[3] = {x, y, z};
+                        double h = 0.0;
+                        if (n[d] > 1) {
+                            if (pc[d] > 0) lo[d] = pc[d] - 1;
+                            if (pc[d] < n[d] - 1) hi[d] = pc[d] + 1;
+                            h = (double)(hi[d] - lo[d]);
+                        }
+                        double deriv = 0.0;
+                        if (h > 0.0)
+                            deriv = (uc[lin(hi[0], hi[1], hi[2], nx, ny)] -
+                                     uc[lin(lo[0], lo[1], lo[2], nx, ny)]) / h;
+                        Jm[c][d] = (c == d ? 1.0 : 0.0) + deriv;
+                    }
+                }
+                det[lin(x, y, z, nx, ny)] =
+                    Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
+                    Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
+                    Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+            }
+}
+
+int or_version(void) { return 1; }

@@ -1,0 +1,115 @@
+"""Pins for the oracle's LNCC value and gradient (App. fused LNCC: Eq.
+lncc-loss, Eqs. lncc-a..lncc-c, Eq. gradientcc-first).  CPU only."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _smooth(rng, shape):
+    from scipy.ndimage import gaussian_filter
+    return gaussian_filter(rng.standard_normal(shape), 1.5) + 0.05 * rng.standard_normal(shape)
+
+
+def test_self_similarity_is_one(rng):
+    F = _smooth(rng, (9, 10, 11))
+    S, n = O.lncc(F, F, 5, 0.0, per_voxel=True)
+    np.testing.assert_allclose(n, 1.0, atol=1e-12)
+    assert abs(S - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("a,b,c,d", [(2.5, -1.0, 1.0, 0.0), (-0.3, 4.0, 7.0, -2.0)])
+def test_affine_intensity_invariance(rng, a, b, c, d):
+    F = _smooth(rng, (8, 9, 10))
+    J = _smooth(rng, (8, 9, 10))
+    S0, n0 = O.lncc(F, J, 5, 0.0, per_voxel=True)
+    S1, n1 = O.lncc(c * F + d, a * J + b, 5, 0.0, per_voxel=True)
+    np.testing.assert_allclose(n1, n0, rtol=1e-9, atol=1e-12)
+
+
+def test_symmetry_and_bounds(rng):
+    F = _smooth(rng, (8, 9, 10))
+    J = _smooth(rng, (8, 9, 10))
+    S0, n0 = O.lncc(F, J, 7, 1e-3, per_voxel=True)
+    S1, n1 = O.lncc(J, F, 7, 1e-3, per_voxel=True)
+    np.testing.assert_allclose(n0, n1, rtol=1e-12)
+    assert (n0 >= 0).all() and (n0 <= 1.0).all()
+
+
+def test_closed_form_ramp_against_square():
+    """F = x, J = x^2 (constant along y, z).  Inside a window the x-offsets d
+    run over an integer range; with X = x + d:  A = cov(X, X^2), B = var(X),
+    C = var(X^2), so for the interior window d in {-r..r}:
+    n = 4 x^2 V / (4 x^2 V + W) with V = r(r+1)/3 and
+    W = var(d^2) = r(r+1)(3r^2+3r-1)/15 - V^2."""
+    nx, ny, nz = 20, 7, 7
+    r = 2
+    x = np.arange(nx, dtype=np.float64)
+    F = np.broadcast_to(x, (nz, ny, nx)).copy()
+    J = F ** 2
+    _, n = O.lncc(F, J, 2 * r + 1, 0.0, per_voxel=True)
+    V = r * (r + 1) / 3.0
+    W = r * (r + 1) * (3 * r * r + 3 * r - 1) / 15.0 - V * V
+    for xi in range(r, nx - r):
+        expect = 4 * xi * xi * V / (4 * xi * xi * V + W)
+        np.testing.assert_allclose(n[:, :, xi], expect, rtol=1e-11)
+    # truncated windows at the x border: moments of the clipped offset range,
+    # by direct enumeration of the few values X can take.
+    for xi in list(range(0, r)) + list(range(nx - r, nx)):
+        X = np.arange(max(0, xi - r), min(nx - 1, xi + r) + 1, dtype=np.float64)
+        cov = np.mean(X * X ** 2) - np.mean(X) * np.mean(X ** 2)
+        expect = cov ** 2 / (np.var(X) * np.var(X ** 2))
+        np.testing.assert_allclose(n[:, :, xi], expect, rtol=1e-10)
+
+
+def test_constant_window_gives_zero_with_eps_zero():
+    F = np.ones((5, 5, 5))
+    J = np.ones((5, 5, 5))
+    S, n = O.lncc(F, J, 3, 0.0, per_voxel=True)
+    assert S == 0.0 and (n == 0).all()
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-3])
+def test_gradient_wrt_J_matches_central_differences(rng, eps):
+    F = _smooth(rng, (7, 8, 9))
+    J = _smooth(rng, (7, 8, 9))
+    win = 5
+    S, g = O.lncc_grad(F, J, win, eps)
+    assert abs(S - O.lncc(F, J, win, eps)) < 1e-15
+    h = 1e-5
+    idx = [tuple(rng.integers(0, s) for s in F.shape) for _ in range(30)]
+    idx += [(0, 0, 0), (6, 7, 8), (3, 0, 4)]
+    for k in idx:
+        Jp = J.copy()
+        Jp[k] += h
+        Jm = J.copy()
+        Jm[k] -= h
+        fd = -(O.lncc(F, Jp, win, eps) - O.lncc(F, Jm, win, eps)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd) + 1e-11, (k, g[k], fd)
+
+
+def test_full_chain_gradient_wrt_u_matches_central_differences(rng):
+    """dC/du through warp + LNCC on a 16^3 volume, FP64, rel 1e-6."""
+    n = 16
+    F = _smooth(rng, (n, n, n))
+    M = _smooth(rng, (n, n, n))
+    u = rng.integers(-1, 2, (3, n, n, n)) + rng.uniform(0.1, 0.9, (3, n, n, n))
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=7, eps=1e-5)
+    S, g = O.similarity_and_grad(F, M, u, spec)
+    # h = 1e-4 keeps the FP64 cancellation error of the difference quotient
+    # (about 1e-16 |S| / h) well below 1e-6 of the smallest sampled entries;
+    # the O(h^2) truncation term is ~1e-9 relative here.
+    h = 1e-4
+    errs = []
+    for _ in range(24):
+        c = rng.integers(0, 3)
+        k = (c,) + tuple(rng.integers(2, n - 2, 3))
+        up = u.copy()
+        up[k] += h
+        um = u.copy()
+        um[k] -= h
+        Sp, _ = O.similarity_and_grad(F, M, up, spec, need_grad=False)
+        Sm, _ = O.similarity_and_grad(F, M, um, spec, need_grad=False)
+        fd = -(Sp - Sm) / (2 * h)
+        errs.append(abs(g[k] - fd) / max(abs(fd), 1e-9))
+    assert max(errs) < 1e-6, errs

@@ -1,0 +1,134 @@
+"""Pins for the oracle's Parzen mutual information (Sec. 2.2 Eq. mi; App.
+fused MI, Eq. gradientmi-threadn).  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+B = 32
+
+
+def _bin_value(s, bins=B):
+    """Intensity whose bin coordinate is s (the kernel of bin m is centred at s = m)."""
+    return (s - 1.0) / (bins - 3)
+
+
+def test_kernel_equals_scipy_cardinal_cubic_bspline():
+    from scipy.interpolate import BSpline
+    ref = BSpline.basis_element([0, 1, 2, 3, 4], extrapolate=False)
+    for t in np.linspace(-2.5, 2.5, 101):
+        expect = ref(t + 2.0)
+        expect = 0.0 if np.isnan(expect) else float(expect)
+        assert abs(O.bspline3(t) - expect) < 1e-14
+        d = ref.derivative()(t + 2.0)
+        d = 0.0 if np.isnan(d) else float(d)
+        assert abs(O.bspline3_deriv(t) - d) < 1e-12
+
+
+def test_kernel_is_partition_of_unity():
+    for s in np.linspace(1.0, B - 2.0, 77):
+        tot = sum(O.bspline3(s - m) for m in range(B))
+        dtot = sum(O.bspline3_deriv(s - m) for m in range(B))
+        assert abs(tot - 1.0) < 1e-14 and abs(dtot) < 1e-13
+
+
+def test_joint_histogram_sums_to_one(rng):
+    Fh = rng.random(5000)
+    Jh = rng.random(5000)
+    Fh[:3] = [0.0, 1.0, 0.5]
+    Jh[:3] = [1.0, 0.0, 0.0]
+    v, p = O.mi(Fh, Jh, B, with_hist=True)
+    assert abs(p.sum() - 1.0) < 1e-12
+    assert (p >= 0).all()
+
+
+def test_constant_moving_image_has_zero_mi(rng):
+    Fh = rng.random(4000)
+    assert abs(O.mi(Fh, np.full(4000, 0.37), B)) < 1e-14
+
+
+def test_symmetry_and_entropy_bound(rng):
+    Fh = rng.random(6000)
+    Jh = np.clip(Fh ** 2 + 0.1 * rng.standard_normal(6000), 0, 1)
+    v1, p = O.mi(Fh, Jh, B, with_hist=True)
+    v2 = O.mi(Jh, Fh, B)
+    assert abs(v1 - v2) < 1e-13
+    pI, pJ = p.sum(1), p.sum(0)
+    H = lambda q: -sum(x * math.log(x) for x in q if x > 0)
+    assert 0.0 <= v1 <= min(H(pI), H(pJ)) + 1e-13
+
+
+def test_closed_form_two_separated_modes_identical():
+    """F = J taking two values whose kernels do not overlap, half the voxels
+    each: p_IJ is 0.5 w w^T around each mode and p_I = p_J = 0.5 w there, so
+    p_IJ / (p_I p_J) = 2 on the support and MI = log 2 exactly."""
+    a, b = _bin_value(5.0), _bin_value(20.0)
+    Fh = np.array([a, b] * 500)
+    assert abs(O.mi(Fh, Fh, B) - math.log(2.0)) < 1e-13
+
+
+def test_closed_form_independent_modes():
+    """Four equally frequent combinations of two separated F modes and two
+    separated J modes: p_IJ = p_I p_J, so MI = 0."""
+    a, b = _bin_value(4.3), _bin_value(17.6)
+    c, d = _bin_value(8.2), _bin_value(24.9)
+    Fh = np.array([a, a, b, b] * 300)
+    Jh = np.array([c, d, c, d] * 300)
+    assert abs(O.mi(Fh, Jh, B)) < 1e-14
+
+
+def test_streaming_equals_materialised_parzen_block(rng):
+    """The O(1)-memory accumulation equals the vanilla form p = Psi_I Psi_J^T / N
+    with the Parzen blocks Psi(m, k) = kappa(s_k - m) materialised (Sec. 2.2)."""
+    N = 300
+    Fh, Jh = rng.random(N), rng.random(N)
+    sF, sJ = Fh * (B - 3) + 1, Jh * (B - 3) + 1
+    PF = np.array([[O.bspline3(sF[k] - m) for k in range(N)] for m in range(B)])
+    PJ = np.array([[O.bspline3(sJ[k] - m) for k in range(N)] for m in range(B)])
+    ref = PF @ PJ.T / N
+    _, p = O.mi(Fh, Jh, B, with_hist=True)
+    np.testing.assert_allclose(p, ref, atol=1e-15)
+
+
+def test_gradient_wrt_Jh_matches_central_differences(rng):
+    N = 2000
+    Fh = rng.uniform(0.02, 0.98, N)
+    Jh = np.clip(0.6 * Fh + 0.3 * rng.random(N), 0.01, 0.99)
+    v, g = O.mi_grad(Fh, Jh, B)
+    # the kernel is a cubic inside each knot interval, so the central
+    # difference has no truncation error there; h only trades rounding noise.
+    h = 1e-5
+    for k in rng.integers(0, N, 25):
+        Jp = Jh.copy()
+        Jp[k] += h
+        Jm = Jh.copy()
+        Jm[k] -= h
+        fd = -(O.mi(Fh, Jp, B) - O.mi(Fh, Jm, B)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd) + 1e-12, (k, g[k], fd)
+
+
+def test_full_chain_gradient_wrt_u_matches_central_differences(rng):
+    """dC/du through warp + normalisation + MI at 16^3, FP64, rel 1e-6."""
+    from scipy.ndimage import gaussian_filter
+    n = 16
+    F = gaussian_filter(rng.random((n, n, n)), 1.0)
+    M = np.cos(3 * F) + 0.05 * rng.random((n, n, n))
+    u = rng.integers(-1, 2, (3, n, n, n)) + rng.uniform(0.1, 0.9, (3, n, n, n))
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=B, f_range=(F.min(), F.max()),
+                      m_range=(M.min() - 0.01, M.max() + 0.01))
+    v, g = O.similarity_and_grad(F, M, u, spec)
+    h = 1e-4
+    errs = []
+    for _ in range(24):
+        k = (rng.integers(0, 3),) + tuple(rng.integers(2, n - 2, 3))
+        up = u.copy()
+        up[k] += h
+        um = u.copy()
+        um[k] -= h
+        vp, _ = O.similarity_and_grad(F, M, up, spec, need_grad=False)
+        vm, _ = O.similarity_and_grad(F, M, um, spec, need_grad=False)
+        fd = -(vp - vm) / (2 * h)
+        errs.append(abs(g[k] - fd) / max(abs(fd), 1e-9))
+    assert max(errs) < 1e-6, errs

@@ -1,0 +1,115 @@
+"""Pins for the oracle's diffusion regulariser, Adam step, bfloat16
+rounding and Jacobian determinant.  CPU only."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+
+
+def test_diffusion_constant_field_is_zero(rng):
+    u = np.ones((3, 5, 6, 7)) * np.array([0.3, -1.0, 2.0])[:, None, None, None]
+    R, g = O.diffusion(u)
+    assert R == 0.0 and not g.any()
+
+
+def test_diffusion_linear_field_closed_form():
+    nz, ny, nx = 5, 6, 7
+    a = 0.7
+    x = np.arange(nx, dtype=np.float64)
+    u = np.zeros((3, nz, ny, nx))
+    u[1] = a * x  # y-component varies along x only
+    R, _ = O.diffusion(u)
+    N = nx * ny * nz
+    assert abs(R - a * a * (nx - 1) * ny * nz / N) < 1e-14
+
+
+def test_diffusion_gradient_is_scaled_neumann_laplacian():
+    """u_c = x^2 along x: the interior second difference is 2, so
+    dR/du = -(2/N) * 2 in the interior; at x=0 the one-sided Neumann
+    stencil gives -(2/N)(u1 - u0) = -2/N, at x=n-1 +(2/N)(u_{n-1}-u_{n-2})."""
+    nz, ny, nx = 3, 4, 9
+    N = nx * ny * nz
+    x = np.arange(nx, dtype=np.float64)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = x ** 2
+    _, g = O.diffusion(u)
+    np.testing.assert_allclose(g[0][:, :, 1:-1], -4.0 / N, atol=1e-14)
+    np.testing.assert_allclose(g[0][:, :, 0], -(2.0 / N) * 1.0, atol=1e-14)
+    np.testing.assert_allclose(g[0][:, :, -1], (2.0 / N) * (64 - 49), atol=1e-14)
+    assert not g[1].any() and not g[2].any()
+
+
+def test_diffusion_gradient_matches_central_differences(rng):
+    u = rng.standard_normal((3, 4, 5, 6))
+    R, g = O.diffusion(u)
+    h = 1e-6
+    for _ in range(20):
+        k = tuple(rng.integers(0, s) for s in u.shape)
+        up = u.copy()
+        up[k] += h
+        um = u.copy()
+        um[k] -= h
+        fd = (O.diffusion(up, False) - O.diffusion(um, False)) / (2 * h)
+        assert abs(fd - g[k]) < 1e-8
+
+
+def test_adam_equals_torch_adam_step_for_step(rng):
+    n = 64
+    u0 = rng.standard_normal(n)
+    p = torch.tensor(u0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=0.1, betas=(0.9, 0.999), eps=1e-8)
+    u, m, v = u0.copy(), np.zeros(n), np.zeros(n)
+    for t in range(1, 6):
+        g = rng.standard_normal(n) * (1e-3 if t % 2 else 10.0)
+        p.grad = torch.tensor(g)
+        opt.step()
+        u, m, v = O.adam(u, m, v, g, t, lr=0.1)
+        np.testing.assert_allclose(u, p.detach().numpy(), rtol=1e-13, atol=1e-14)
+        st = opt.state[p]
+        np.testing.assert_allclose(m, st["exp_avg"].numpy(), rtol=1e-13)
+        np.testing.assert_allclose(v, st["exp_avg_sq"].numpy(), rtol=1e-13)
+
+
+def test_adam_grad_scale_is_input_scaling(rng):
+    n = 32
+    u0, g = rng.standard_normal(n), rng.standard_normal(n)
+    a = O.adam(u0, np.zeros(n), np.zeros(n), g, 1, 0.1, grad_scale=1000.0)
+    b = O.adam(u0, np.zeros(n), np.zeros(n), 1000.0 * g, 1, 0.1)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=1e-14)
+
+
+def test_bf16_round_equals_torch_conversion(rng):
+    x = np.concatenate([rng.standard_normal(500) * 10.0 ** rng.integers(-20, 20, 500),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 3e38, 1e-40]])
+    ref = torch.tensor(x, dtype=torch.float64).to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    np.testing.assert_array_equal(O.bf16_round(x), ref.numpy())
+
+
+def test_adam_bf16_moments_are_rounded_after_use(rng):
+    n = 50
+    u0, g = rng.standard_normal(n), rng.standard_normal(n)
+    uf, mf, vf = O.adam(u0, np.zeros(n), np.zeros(n), g, 1, 0.05)
+    ub, mb, vb = O.adam(u0, np.zeros(n), np.zeros(n), g, 1, 0.05, bf16_moments=True)
+    np.testing.assert_array_equal(ub, uf)
+    np.testing.assert_array_equal(mb, O.bf16_round(mf))
+    np.testing.assert_array_equal(vb, O.bf16_round(vf))
+
+
+def test_jacdet_identity_and_linear_maps(rng):
+    shape = (5, 6, 7)
+    assert (O.jacdet(np.zeros((3,) + shape)) == 1.0).all()
+    A = rng.uniform(-0.3, 0.3, (3, 3))
+    z, y, x = np.meshgrid(*[np.arange(s, dtype=np.float64) for s in shape], indexing="ij")
+    X = np.stack([x, y, z])
+    u = np.einsum("cd,dzyx->czyx", A, X)
+    d = O.jacdet(u)
+    np.testing.assert_allclose(d, np.linalg.det(np.eye(3) + A), rtol=1e-13)
+
+
+def test_jacdet_detects_folding():
+    u = np.zeros((3, 4, 4, 8))
+    x = np.arange(8, dtype=np.float64)
+    u[0] = -2.0 * x  # phi_x = -x : orientation reversed
+    assert (O.jacdet(u) < 0).all()
