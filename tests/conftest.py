@@ -12,7 +12,8 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
 
 
-@pytest.fixture(scope="session")
+@pytest.fixture
 def rng():
+    """A fresh, fixed-seed generator per test, so results do not depend on test order."""
     import numpy as np
     return np.random.default_rng(12345)

@@ -81,8 +81,9 @@ def test_adam_grad_scale_is_input_scaling(rng):
 
 
 def test_bf16_round_equals_torch_conversion(rng):
+    # includes exact ties with even (1 + 2^-8) and odd (1 + 2^-7 + 2^-8) last kept bit
     x = np.concatenate([rng.standard_normal(500) * 10.0 ** rng.integers(-20, 20, 500),
-                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 3e38, 1e-40]])
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, -1.01171875, 1.005859375, 3e38, 1e-40]])
     ref = torch.tensor(x, dtype=torch.float64).to(torch.float32).to(torch.bfloat16).to(torch.float64)
     np.testing.assert_array_equal(O.bf16_round(x), ref.numpy())
 

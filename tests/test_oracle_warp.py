@@ -130,3 +130,17 @@ def test_slope_matches_central_differences(rng, pad):
         ok = np.abs(coord - 0.0) > 1e-3
         ok &= np.abs(coord - (n - 1)) > 1e-3
         np.testing.assert_allclose(dJ[c][ok], fd[ok], atol=1e-7)
+
+
+def test_slope_on_knots_uses_the_upper_cell():
+    """On an integer sample point the slope is the forward difference
+    M[x+1] - M[x]; on the last knot (phi = n-1, not clamped) it is the
+    backward difference M[n-1] - M[n-2] (the cell index is min(floor, n-2))."""
+    rng = np.random.default_rng(7)
+    M = rng.standard_normal((4, 5, 6))
+    J, dJ = O.warp(M, np.zeros((3,) + M.shape), O.PAD_BORDER, with_grad=True)
+    fwd = np.diff(M, axis=2)
+    np.testing.assert_allclose(dJ[0][:, :, :-1], fwd, atol=1e-15)
+    np.testing.assert_allclose(dJ[0][:, :, -1], fwd[:, :, -1], atol=1e-15)
+    np.testing.assert_allclose(dJ[2][:-1], np.diff(M, axis=0), atol=1e-15)
+    np.testing.assert_allclose(dJ[2][-1], M[-1] - M[-2], atol=1e-15)
