@@ -1,0 +1,191 @@
+/*
+ * reg.h -- C ABI of the GB300 (sm_103a) registration hot path.
+ *
+ * One iteration of  argmin_u  C(F, M o (id + u)) + lambda R(u)   (Sec. 1,
+ * Eq. image-reg) on a dense 3-D displacement field u: trilinear warp of the
+ * moving image (Sec. 2.1), windowed LNCC (Sec. 2.3, App. fused LNCC) or
+ * Parzen mutual information (Sec. 2.2, App. fused MI), their hand-written
+ * adjoints back to dC/du, a diffusion regulariser and an Adam step.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Volumes are dense [nz][ny][nx] arrays, x fastest, voxel spacing 1.
+ *  - u (and every gradient) is FP32, structure of arrays [3][nz][ny][nx]:
+ *    channel 0, 1, 2 = x, y, z displacement in voxel units;
+ *    phi(p) = p + u(p) for integer voxel centres p.
+ *  - Every pointer argument is a DEVICE pointer unless stated otherwise, and
+ *    must be 16-byte aligned (REG_ERR_ALIGN otherwise).  Any nx, ny, nz >= 1
+ *    is accepted (no padding or pitch requirement).
+ *  - Ownership: the caller allocates and owns every buffer, including the
+ *    workspace; the library allocates no memory on these paths and keeps no
+ *    pointer after a call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls only enqueue work; outputs are valid once the stream
+ *    has been synchronised.
+ *  - Errors: arguments are validated on the host before anything is
+ *    launched; a failing check returns its code and enqueues nothing.  A
+ *    launch failure returns REG_ERR_CUDA.  Non-finite loss or regulariser
+ *    partials found on the device are latched in a device error word, read
+ *    (and cleared) by reg_get_device_error().  No kernel traps or asserts.
+ *  - Determinism: identical inputs give bitwise-identical outputs
+ *    (fixed-order FP64 reductions, integer MI histograms).
+ */
+#ifndef REG_H
+#define REG_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define REG_API __attribute__((visibility("default")))
+#else
+#define REG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum reg_status {
+    REG_OK = 0,
+    REG_ERR_INVALID_ARG = 1, /* null pointer, bad enum or out-of-range parameter */
+    REG_ERR_SHAPE = 2,       /* dims < 1, too large, or window/bins unsupported */
+    REG_ERR_DTYPE = 3,       /* unknown reg_dtype */
+    REG_ERR_ALIGN = 4,       /* a pointer is not 16-byte aligned */
+    REG_ERR_WORKSPACE = 5,   /* ws_bytes smaller than reg_workspace_size() */
+    REG_ERR_NONFINITE = 6,   /* device error word: a non-finite partial sum was seen */
+    REG_ERR_TIMEOUT = 7,     /* device error word: a bounded device wait expired */
+    REG_ERR_CUDA = 8,        /* a CUDA runtime call or kernel launch failed */
+    REG_ERR_UNSUPPORTED = 9  /* valid request this build does not implement */
+} reg_status;
+
+typedef enum reg_dtype { REG_F32 = 0, REG_BF16 = 1 } reg_dtype;
+
+/* Out-of-volume sampling.  BORDER: the sample point is clamped into the
+ * volume per axis (the slope along a clamped axis is 0).  ZEROS: voxels
+ * outside the volume read as 0 (Algorithm gridsampler). */
+typedef enum reg_pad { REG_PAD_BORDER = 0, REG_PAD_ZEROS = 1 } reg_pad;
+
+typedef struct reg_dims {
+    int nx, ny, nz;
+} reg_dims;
+
+typedef enum reg_loss_kind { REG_LOSS_LNCC = 0, REG_LOSS_MI = 1 } reg_loss_kind;
+
+/* Similarity description.
+ *   LNCC (App. fused LNCC, Eq. lncc-loss): `window` odd in [3, 15]; a uniform
+ *     box of that side centred at each voxel, truncated at the volume border
+ *     and normalised by the in-volume count; eps >= 0 is added to B_i C_i.
+ *     Similarity S = mean_i A_i^2 / (B_i C_i + eps); loss C = 1 - S.
+ *   MI (Sec. 2.2, Eq. mi): `bins` in [8, 64]; cubic B-spline Parzen kernel.
+ *     Intensities are mapped to [0,1] by (v - lo) / (hi - lo) and clamped;
+ *     the kernel of bin m sits at s = m with s = v (bins - 3) + 1.
+ *     Similarity = MI (natural log); loss C = -MI.
+ *     Requires f_hi > f_lo and m_hi > m_lo (the fixed / moving ranges). */
+typedef struct reg_loss_desc {
+    int kind;   /* reg_loss_kind */
+    int window; /* LNCC */
+    float eps;  /* LNCC */
+    int bins;   /* MI */
+    float f_lo, f_hi, m_lo, m_hi; /* MI intensity ranges */
+} reg_loss_desc;
+
+/* Adam (the optimiser state m1, m2 of Sec. 3.1), torch.optim.Adam semantics
+ * with bias correction.  The gradient fed to Adam is grad_scale * dL/du
+ * (use grad_scale = N = nx ny nz: C and R are voxel means, so dL/du is
+ * O(1/N) and eps would otherwise dominate).  moment_dtype: REG_F32 or
+ * REG_BF16 (m, v stored in bfloat16, round-to-nearest-even, updated in FP32). */
+typedef struct reg_adam_desc {
+    float lr, beta1, beta2, eps;
+    int moment_dtype; /* reg_dtype */
+    float grad_scale;
+} reg_adam_desc;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+REG_API int reg_version(void);
+
+/* Static description of a status code; never NULL. */
+REG_API const char *reg_status_string(reg_status s);
+
+/* Bytes of device workspace that reg_loss, reg_loss_grad, reg_regularize,
+ * reg_iterate and reg_jacdet_min need for these dims (loss may be NULL for
+ * the regulariser / det J alone).  *bytes is a HOST pointer. */
+REG_API reg_status reg_workspace_size(const reg_loss_desc *loss, reg_dims d, size_t *bytes);
+
+/* J = M o (id + u): trilinear warp of M (img_dt) by u (Sec. 2.1, the
+ * deformable part of fused_grid_sampler with A = I, t = 0, S = I;
+ * Algorithm gridsampler, forward).  J_out: FP32 N (overwritten).
+ * dJ_out: optional (may be NULL) FP32 [3][N] receiving dJ/dphi per axis. */
+REG_API reg_status reg_warp(const void *M, int img_dt, const float *u, reg_dims d, int pad, float *J_out,
+                    float *dJ_out, void *stream);
+
+/* Similarity of F and M o (id+u) (LNCC or MI per `loss`).  sim_out: device
+ * double[1], receives S (LNCC) or MI.  F and M share img_dt.  The warped
+ * image is recomputed on chip and never stored. */
+REG_API reg_status reg_loss(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u,
+                    reg_dims d, int pad, void *ws, size_t ws_bytes, double *sim_out, void *stream);
+
+/* As reg_loss, and grad_u (FP32 [3][N], overwritten) = dC/du of the loss
+ * C = 1 - S (LNCC) or -MI (MI): the similarity adjoint (LNCC: App. fused
+ * LNCC, Eq. gradientcc-first and its moving-image counterpart; MI: Eq.
+ * gradientmi-threadn) chained through the sampler slope (Algorithm
+ * gridsampler, backward: g_u = dv/dX g). */
+REG_API reg_status reg_loss_grad(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u,
+                         reg_dims d, int pad, void *ws, size_t ws_bytes, double *sim_out, float *grad_u,
+                         void *stream);
+
+/* Diffusion regulariser R(u) = (1/N) sum_c sum_d sum_{p, p+e_d inside}
+ * (u_c(p+e_d) - u_c(p))^2 (first-order Sobolev norm, listed among common
+ * choices of R in Sec. 1).  r_out: device double[1] receives R(u) (without
+ * lambda).  grad_u: FP32 [3][N], lambda * dR/du is ADDED to it (may be NULL). */
+REG_API reg_status reg_regularize(const float *u, reg_dims d, float lambda, void *ws, size_t ws_bytes, double *r_out,
+                          float *grad_u, void *stream);
+
+/* One Adam step on u (t >= 1 is the 1-based step count):
+ * u_out = u_in - lr * mhat / (sqrt(vhat) + eps).  u_out may equal u_in.
+ * m, v: [3][N] in adam->moment_dtype, updated in place. */
+REG_API reg_status reg_step(const float *u_in, float *u_out, void *m, void *v, const float *grad_u, reg_dims d,
+                    const reg_adam_desc *adam, int t, void *stream);
+
+/* One fused iteration: similarity + its gradient + lambda * diffusion
+ * gradient + Adam, in two sweeps over the volume (LNCC: window statistics,
+ * then adjoint + step; MI: joint histogram, then adjoint + step).
+ * u_out must not alias u_in (the stencils read neighbours of u_in).
+ * obj_out: device double[2] = {similarity, R(u_in)} at u_in.
+ * grad_out: optional FP32 [3][N] receiving the total gradient dL/du fed to
+ * Adam (before grad_scale); NULL skips the store. */
+REG_API reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u_in,
+                       float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
+                       const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
+                       float *grad_out, void *stream);
+
+/* Fold check of phi = id + u: min over voxels of det(I + grad u) (central
+ * differences, one-sided at the border) and the number of voxels with
+ * det <= 0.  min_out: device float[1]; nfold_out: device unsigned long long[1]. */
+REG_API reg_status reg_jacdet_min(const float *u, reg_dims d, void *ws, size_t ws_bytes, float *min_out,
+                          unsigned long long *nfold_out, void *stream);
+
+/* Synchronises `stream`, returns the device error word accumulated by
+ * earlier calls on this device (REG_OK, REG_ERR_NONFINITE or
+ * REG_ERR_TIMEOUT; the first latched code wins) and clears it. */
+REG_API reg_status reg_get_device_error(void *stream);
+
+/* Timing hook: the NEXT reg_iterate call on this host thread records the
+ * caller's CUDA events (cudaEvent_t passed as void*) on its stream:
+ * events[0] before the first sweep, events[1] between the sweeps (after the
+ * MI finalisation), events[2] after the second sweep; then the hook clears
+ * itself.  n must be 3 (or 0 with events == NULL to clear).  Lets a caller
+ * time each sweep inside a long run without synchronising. */
+REG_API reg_status reg_set_timing_events(void *const *events, int n);
+
+/* Test hook for failure detection: a one-thread kernel polls *flag (device
+ * unsigned) until it equals `expect` or `timeout_ns` nanoseconds of device
+ * time pass; on expiry it latches REG_ERR_TIMEOUT in the device error word
+ * and returns (no trap, the context stays usable).  Used to show that a
+ * device wait which never completes is reported, not hung. */
+REG_API reg_status reg_debug_wait_flag(const unsigned *flag, unsigned expect, unsigned long long timeout_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

@@ -47,6 +47,9 @@ def _load():
         lib.or_lncc_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, _dp]
         lib.or_lncc_grad.restype = ctypes.c_double
+        lib.or_lncc_grad_points.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.POINTER(ctypes.c_long), ctypes.c_int, _dp, _dp]
+        lib.or_lncc_grad_points.restype = None
         lib.or_bspline3.argtypes = [ctypes.c_double]
         lib.or_bspline3.restype = ctypes.c_double
         lib.or_bspline3_deriv.argtypes = [ctypes.c_double]
@@ -116,6 +119,20 @@ def lncc_grad(F, J, win: int, eps: float):
     g = np.empty_like(F)
     S = _load().or_lncc_grad(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps), _ptr(g))
     return S, g
+
+
+def lncc_grad_points(F, J, win: int, eps: float, points):
+    """(dL/dJ, n) at the listed voxels (linear indices), for L = 1 - S of the
+    whole volume; for volumes too large for lncc_grad."""
+    F = _f64(F)
+    J = _f64(J)
+    nx, ny, nz = _dims(F)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int64))
+    g = np.empty(pts.size, dtype=np.float64)
+    n = np.empty(pts.size, dtype=np.float64)
+    _load().or_lncc_grad_points(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps),
+                                pts.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), int(pts.size), _ptr(g), _ptr(n))
+    return g, n
 
 
 def bspline3(t: float) -> float:

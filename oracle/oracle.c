@@ -515,3 +515,84 @@ void or_jacdet(const double *u, int nx, int ny, int nz, double *det)
 }
 
 int or_version(void) { return 1; }
+
+/* ------------------------------------------------------------------------ */
+/* The same LNCC gradient as or_lncc_grad, evaluated only at listed voxels   */
+/* (linear indices pts[0..npts)), for volumes too large for the full field: */
+/* for each listed k, every window i with k in W_i is formed from its        */
+/* definition and contributes its chain-rule term.  N is the full voxel      */
+/* count (dL/dn_i = -1/N).  n_out (optional) receives n_k at the same        */
+/* voxels.                                                                   */
+/* ------------------------------------------------------------------------ */
+static void window_stats(const double *F, const double *J, int nx, int ny, int nz, int r, int x, int y, int z,
+                         double eps, double *muF, double *muJ, double *A, double *B, double *C, double *cnt)
+{
+    int x0, x1, y0, y1, z0, z1;
+    window_bounds(x, r, nx, &x0, &x1);
+    window_bounds(y, r, ny, &y0, &y1);
+    window_bounds(z, r, nz, &z0, &z1);
+    double c = 0.0, sF = 0.0, sJ = 0.0;
+    for (int zz = z0; zz <= z1; ++zz)
+        for (int yy = y0; yy <= y1; ++yy)
+            for (int xx = x0; xx <= x1; ++xx) {
+                const long k = lin(xx, yy, zz, nx, ny);
+                sF += F[k];
+                sJ += J[k];
+                c += 1.0;
+            }
+    const double mF = sF / c, mJ = sJ / c;
+    double a = 0.0, b = 0.0, cc = 0.0;
+    for (int zz = z0; zz <= z1; ++zz)
+        for (int yy = y0; yy <= y1; ++yy)
+            for (int xx = x0; xx <= x1; ++xx) {
+                const long k = lin(xx, yy, zz, nx, ny);
+                const double df = F[k] - mF, dj = J[k] - mJ;
+                a += df * dj;
+                b += df * df;
+                cc += dj * dj;
+            }
+    *muF = mF;
+    *muJ = mJ;
+    *A = a / c;
+    *B = b / c;
+    *C = cc / c;
+    *cnt = c;
+    (void)eps;
+}
+
+void or_lncc_grad_points(const double *F, const double *J, int nx, int ny, int nz, int win, double eps,
+                         const long *pts, int npts, double *gJ_out, double *n_out)
+{
+    const long N = (long)nx * ny * nz;
+    const int r = win / 2;
+    const double dLdn = -1.0 / (double)N;
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < npts; ++s) {
+        const long k = pts[s];
+        const int x = (int)(k % nx), y = (int)((k / nx) % ny), z = (int)(k / ((long)nx * ny));
+        int x0, x1, y0, y1, z0, z1;
+        window_bounds(x, r, nx, &x0, &x1);
+        window_bounds(y, r, ny, &y0, &y1);
+        window_bounds(z, r, nz, &z0, &z1);
+        double g = 0.0;
+        for (int zz = z0; zz <= z1; ++zz)
+            for (int yy = y0; yy <= y1; ++yy)
+                for (int xx = x0; xx <= x1; ++xx) {
+                    double mF, mJ, A, B, C, c;
+                    window_stats(F, J, nx, ny, nz, r, xx, yy, zz, eps, &mF, &mJ, &A, &B, &C, &c);
+                    const double D = B * C + eps;
+                    if (D > 0.0) {
+                        const double dndA = 2.0 * A / D;
+                        const double dndC = -A * A * B / (D * D);
+                        g += dLdn * (dndA * (F[k] - mF) / c + dndC * 2.0 * (J[k] - mJ) / c);
+                    }
+                }
+        gJ_out[s] = g;
+        if (n_out) {
+            double mF, mJ, A, B, C, c;
+            window_stats(F, J, nx, ny, nz, r, x, y, z, eps, &mF, &mJ, &A, &B, &C, &c);
+            const double D = B * C + eps;
+            n_out[s] = D > 0.0 ? A * A / D : 0.0;
+        }
+    }
+}

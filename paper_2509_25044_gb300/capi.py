@@ -1,0 +1,264 @@
+"""ctypes binding of the C ABI in include/reg.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks dtypes / shapes of torch tensors, passes
+their device pointers, the current CUDA stream and the descriptor structs,
+and turns a non-zero reg_status into a RegError.  All compute runs in
+libreg_gb300.so; if that library is missing the import fails loudly (there is
+no CPU or PyTorch fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libreg_gb300.so")
+
+REG_OK = 0
+REG_F32, REG_BF16 = 0, 1
+REG_PAD_BORDER, REG_PAD_ZEROS = 0, 1
+REG_LOSS_LNCC, REG_LOSS_MI = 0, 1
+STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR_DTYPE", 4: "REG_ERR_ALIGN",
+          5: "REG_ERR_WORKSPACE", 6: "REG_ERR_NONFINITE", 7: "REG_ERR_TIMEOUT", 8: "REG_ERR_CUDA",
+          9: "REG_ERR_UNSUPPORTED"}
+
+# every C entry point declared in include/reg.h
+EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
+           "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
+           "reg_debug_wait_flag", "reg_set_timing_events")
+
+
+class RegError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().reg_status_string(status).decode()})")
+
+
+class RegDims(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class RegLossDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("window", ctypes.c_int), ("eps", ctypes.c_float), ("bins", ctypes.c_int),
+                ("f_lo", ctypes.c_float), ("f_hi", ctypes.c_float), ("m_lo", ctypes.c_float),
+                ("m_hi", ctypes.c_float)]
+
+
+class RegAdamDesc(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("moment_dtype", ctypes.c_int), ("grad_scale", ctypes.c_float)]
+
+
+_L = None
+_vp = ctypes.c_void_p
+_st = ctypes.c_int
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2509_25044_gb300.build.build() "
+                              "(nvcc, sm_103a); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        L.reg_version.restype = ctypes.c_int
+        L.reg_status_string.argtypes = [_st]
+        L.reg_status_string.restype = ctypes.c_char_p
+        L.reg_workspace_size.argtypes = [ctypes.POINTER(RegLossDesc), RegDims, ctypes.POINTER(ctypes.c_size_t)]
+        L.reg_warp.argtypes = [_vp, ctypes.c_int, _vp, RegDims, ctypes.c_int, _vp, _vp, _vp]
+        L.reg_loss.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims, ctypes.c_int, _vp,
+                               ctypes.c_size_t, _vp, _vp]
+        L.reg_loss_grad.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims, ctypes.c_int,
+                                    _vp, ctypes.c_size_t, _vp, _vp, _vp]
+        L.reg_regularize.argtypes = [_vp, RegDims, ctypes.c_float, _vp, ctypes.c_size_t, _vp, _vp, _vp]
+        L.reg_step.argtypes = [_vp, _vp, _vp, _vp, _vp, RegDims, ctypes.POINTER(RegAdamDesc), ctypes.c_int, _vp]
+        L.reg_iterate.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
+                                  ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, _vp,
+                                  ctypes.c_size_t, _vp, _vp, _vp]
+        L.reg_jacdet_min.argtypes = [_vp, RegDims, _vp, ctypes.c_size_t, _vp, _vp, _vp]
+        L.reg_get_device_error.argtypes = [_vp]
+        L.reg_debug_wait_flag.argtypes = [_vp, ctypes.c_uint, ctypes.c_ulonglong, _vp]
+        L.reg_set_timing_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        for name in EXPORTS:
+            if name not in ("reg_version", "reg_status_string"):
+                getattr(L, name).restype = _st
+        _L = L
+    return _L
+
+
+def load():
+    """Load the library (raises ImportError if it has not been built)."""
+    return _lib()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _check(status: int, where: str):
+    if status != REG_OK:
+        raise RegError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(t=None):
+    if t is not None and t.device.type == "cuda":
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _img_dtype(t) -> int:
+    if t.dtype == torch.float32:
+        return REG_F32
+    if t.dtype == torch.bfloat16:
+        return REG_BF16
+    raise TypeError(f"image dtype must be float32 or bfloat16, got {t.dtype}")
+
+
+def dims_of(vol) -> RegDims:
+    nz, ny, nx = vol.shape[-3:]
+    return RegDims(int(nx), int(ny), int(nz))
+
+
+def _need(t, shape, dtype, name):
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} shape {tuple(t.shape)} != {tuple(shape)}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} dtype {t.dtype} != {dtype}")
+
+
+def lncc_desc(window: int = 7, eps: float = 1e-5) -> RegLossDesc:
+    return RegLossDesc(REG_LOSS_LNCC, int(window), float(eps), 0, 0.0, 1.0, 0.0, 1.0)
+
+
+def mi_desc(f_range, m_range, bins: int = 32) -> RegLossDesc:
+    return RegLossDesc(REG_LOSS_MI, 0, 0.0, int(bins), float(f_range[0]), float(f_range[1]), float(m_range[0]),
+                       float(m_range[1]))
+
+
+def adam_desc(lr: float, beta1=0.9, beta2=0.999, eps=1e-8, moment_dtype=REG_F32, grad_scale=1.0) -> RegAdamDesc:
+    return RegAdamDesc(float(lr), float(beta1), float(beta2), float(eps), int(moment_dtype), float(grad_scale))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def reg_version() -> int:
+    return _lib().reg_version()
+
+
+def reg_status_string(status: int) -> str:
+    return _lib().reg_status_string(int(status)).decode()
+
+
+def reg_workspace_size(loss: RegLossDesc | None, dims: RegDims) -> int:
+    out = ctypes.c_size_t(0)
+    _check(_lib().reg_workspace_size(ctypes.byref(loss) if loss is not None else None, dims, ctypes.byref(out)),
+           "reg_workspace_size")
+    return int(out.value)
+
+
+def workspace(loss, vol) -> torch.Tensor:
+    """Allocate (with torch) a workspace sized by reg_workspace_size."""
+    n = reg_workspace_size(loss, dims_of(vol))
+    return torch.empty(n, dtype=torch.uint8, device=vol.device)
+
+
+def reg_warp(M, u, pad: int = REG_PAD_BORDER, J=None, dJ=None, with_slope: bool = False):
+    d = dims_of(M)
+    _need(u, (3,) + tuple(M.shape), torch.float32, "u")
+    if J is None:
+        J = torch.empty(M.shape, dtype=torch.float32, device=M.device)
+    if with_slope and dJ is None:
+        dJ = torch.empty_like(u)
+    _check(_lib().reg_warp(_ptr(M), _img_dtype(M), _ptr(u), d, int(pad), _ptr(J), _ptr(dJ), _stream(M)), "reg_warp")
+    return (J, dJ) if dJ is not None else J
+
+
+def reg_loss(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None):
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _need(u, (3,) + tuple(F.shape), torch.float32, "u")
+    if sim is None:
+        sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    _check(_lib().reg_loss(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d, int(pad), _ptr(ws),
+                           ws.numel(), _ptr(sim), _stream(F)), "reg_loss")
+    return sim
+
+
+def reg_loss_grad(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None, grad=None):
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _need(u, (3,) + tuple(F.shape), torch.float32, "u")
+    if sim is None:
+        sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    if grad is None:
+        grad = torch.empty_like(u)
+    _check(_lib().reg_loss_grad(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d, int(pad), _ptr(ws),
+                                ws.numel(), _ptr(sim), _ptr(grad), _stream(F)), "reg_loss_grad")
+    return sim, grad
+
+
+def reg_regularize(u, lam: float, ws, r=None, grad=None):
+    d = dims_of(u)
+    if r is None:
+        r = torch.empty(1, dtype=torch.float64, device=u.device)
+    _check(_lib().reg_regularize(_ptr(u), d, float(lam), _ptr(ws), ws.numel(), _ptr(r), _ptr(grad), _stream(u)),
+           "reg_regularize")
+    return r
+
+
+def reg_step(u_in, u_out, m, v, grad, adam: RegAdamDesc, t: int):
+    d = dims_of(u_in)
+    _check(_lib().reg_step(_ptr(u_in), _ptr(u_out), _ptr(m), _ptr(v), _ptr(grad), d, ctypes.byref(adam), int(t),
+                           _stream(u_in)), "reg_step")
+    return u_out
+
+
+def reg_iterate(loss: RegLossDesc, F, M, u_in, u_out, m, v, lam: float, adam: RegAdamDesc, t: int, ws,
+                pad: int = REG_PAD_BORDER, obj=None, grad=None):
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _need(u_in, (3,) + tuple(F.shape), torch.float32, "u_in")
+    _need(u_out, (3,) + tuple(F.shape), torch.float32, "u_out")
+    if obj is None:
+        obj = torch.empty(2, dtype=torch.float64, device=F.device)
+    _check(_lib().reg_iterate(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u_in), _ptr(u_out), _ptr(m),
+                              _ptr(v), d, int(pad), float(lam), ctypes.byref(adam), int(t), _ptr(ws), ws.numel(),
+                              _ptr(obj), _ptr(grad), _stream(F)), "reg_iterate")
+    return obj
+
+
+def reg_jacdet_min(u, out_min=None, out_nfold=None):
+    d = dims_of(u)
+    if out_min is None:
+        out_min = torch.empty(4, dtype=torch.float32, device=u.device)
+    if out_nfold is None:
+        out_nfold = torch.empty(2, dtype=torch.int64, device=u.device)
+    _check(_lib().reg_jacdet_min(_ptr(u), d, None, 0, _ptr(out_min), _ptr(out_nfold), _stream(u)), "reg_jacdet_min")
+    return out_min[:1], out_nfold[:1]
+
+
+def reg_get_device_error(stream_of=None) -> int:
+    """Synchronises the stream and returns (and clears) the device error code."""
+    return int(_lib().reg_get_device_error(_stream(stream_of)))
+
+
+def reg_debug_wait_flag(flag, expect: int, timeout_ns: int):
+    _check(_lib().reg_debug_wait_flag(_ptr(flag), int(expect), int(timeout_ns), _stream(flag)), "reg_debug_wait_flag")
+
+
+def reg_set_timing_events(events):
+    """Arm the timing hook with three torch.cuda.Event objects (or None to clear)."""
+    if events is None:
+        _check(_lib().reg_set_timing_events(None, 0), "reg_set_timing_events")
+        return
+    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(_lib().reg_set_timing_events(arr, 3), "reg_set_timing_events")

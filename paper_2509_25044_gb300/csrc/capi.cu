@@ -1,0 +1,364 @@
+// capi.cu -- the C ABI of include/reg.h: host-side validation, workspace
+// layout and kernel sequencing.  Every entry point validates all arguments
+// before enqueueing anything and allocates no memory.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "kernels.h"
+
+using namespace regk;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// workspace layout (caller-owned, 256-byte aligned sections)
+// ---------------------------------------------------------------------------
+constexpr size_t WS_HIST = 0;                                        // u64[64*64]
+constexpr size_t WS_COUNTERS = WS_HIST + sizeof(unsigned long long) * MAX_BINS * MAX_BINS;  // u32[64]
+constexpr size_t WS_ZERO_BYTES = WS_COUNTERS + 256;                  // zeroed by every call
+constexpr size_t WS_GTAB = WS_ZERO_BYTES;                            // f32[64*64]
+constexpr size_t WS_SCRATCH = WS_GTAB + sizeof(float) * MAX_BINS * MAX_BINS;  // f64[32]
+constexpr size_t WS_PARTIALS = WS_SCRATCH + 256;                     // f64[max blocks]
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+reg_status check_dims(reg_dims d) {
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return REG_ERR_SHAPE;
+    if (d.nx > (1 << 20) || d.ny > (1 << 19) || d.nz > (1 << 16)) return REG_ERR_SHAPE;
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    if (n > (1LL << 36)) return REG_ERR_SHAPE;
+    return REG_OK;
+}
+
+reg_status check_loss(const reg_loss_desc *L) {
+    if (!L) return REG_ERR_INVALID_ARG;
+    if (L->kind == REG_LOSS_LNCC) {
+        if (L->window < 3 || L->window > 2 * MAX_RADIUS + 1 || (L->window & 1) == 0) return REG_ERR_SHAPE;
+        if (!(L->eps >= 0.0f) || !isfinite(L->eps)) return REG_ERR_INVALID_ARG;
+        return REG_OK;
+    }
+    if (L->kind == REG_LOSS_MI) {
+        if (L->bins < 8 || L->bins > MAX_BINS) return REG_ERR_SHAPE;
+        if (!isfinite(L->f_lo) || !isfinite(L->f_hi) || !isfinite(L->m_lo) || !isfinite(L->m_hi))
+            return REG_ERR_INVALID_ARG;
+        if (!(L->f_hi > L->f_lo) || !(L->m_hi > L->m_lo)) return REG_ERR_INVALID_ARG;
+        return REG_OK;
+    }
+    return REG_ERR_INVALID_ARG;
+}
+
+reg_status check_adam(const reg_adam_desc *A, int t) {
+    if (!A) return REG_ERR_INVALID_ARG;
+    if (t < 1) return REG_ERR_INVALID_ARG;
+    if (!(A->lr > 0.0f) || !isfinite(A->lr)) return REG_ERR_INVALID_ARG;
+    if (!(A->beta1 >= 0.0f && A->beta1 < 1.0f) || !(A->beta2 >= 0.0f && A->beta2 < 1.0f)) return REG_ERR_INVALID_ARG;
+    if (!(A->eps >= 0.0f) || !isfinite(A->eps)) return REG_ERR_INVALID_ARG;
+    if (!(A->grad_scale > 0.0f) || !isfinite(A->grad_scale)) return REG_ERR_INVALID_ARG;
+    if (A->moment_dtype != REG_F32 && A->moment_dtype != REG_BF16) return REG_ERR_DTYPE;
+    return REG_OK;
+}
+
+long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
+    long long nb = diffusion_grid(g).blocks();
+    const long long mi = mi_sweep_grid(g).blocks();
+    if (mi > nb) nb = mi;
+    if (L && L->kind == REG_LOSS_LNCC) {
+        const long long ln = lncc_grid(g, L->window / 2).blocks();
+        if (ln > nb) nb = ln;
+    }
+    return nb;
+}
+
+size_t workspace_bytes(const Dims &g, const reg_loss_desc *L) {
+    size_t bytes = align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L));
+    if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 3 * (size_t)g.n);
+    return bytes;
+}
+
+struct Ws {
+    unsigned long long *hist;
+    unsigned *counters;
+    float *gtab;
+    double *scratch;
+    double *partials;
+    float *coef;
+};
+
+Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
+    char *b = (char *)ws;
+    Ws w;
+    w.hist = (unsigned long long *)(b + WS_HIST);
+    w.counters = (unsigned *)(b + WS_COUNTERS);
+    w.gtab = (float *)(b + WS_GTAB);
+    w.scratch = (double *)(b + WS_SCRATCH);
+    w.partials = (double *)(b + WS_PARTIALS);
+    w.coef = (float *)(b + align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L)));
+    return w;
+}
+
+MiParams mi_params(const reg_loss_desc *L) {
+    MiParams P;
+    P.f_lo = L->f_lo;
+    P.f_scale = (float)(1.0 / ((double)L->f_hi - (double)L->f_lo));
+    P.m_lo = L->m_lo;
+    P.m_scale = (float)(1.0 / ((double)L->m_hi - (double)L->m_lo));
+    P.bins = L->bins;
+    return P;
+}
+
+StepParams step_params(const reg_adam_desc *A, int t, float lam, const Dims &g) {
+    StepParams S;
+    S.lam = lam;
+    S.two_over_n = (float)(2.0 / (double)g.n);
+    const double bc1 = 1.0 - pow((double)A->beta1, (double)t);
+    const double bc2 = 1.0 - pow((double)A->beta2, (double)t);
+    S.lr_bc1 = (float)((double)A->lr / bc1);
+    S.rsqrt_bc2 = (float)(1.0 / sqrt(bc2));
+    S.b1 = A->beta1;
+    S.b2 = A->beta2;
+    S.eps = A->eps;
+    S.gscale = A->grad_scale;
+    return S;
+}
+
+thread_local cudaEvent_t t_events[3] = {nullptr, nullptr, nullptr};
+thread_local bool t_events_armed = false;
+
+cudaError_t mark(int i, cudaStream_t s) {
+    if (!t_events_armed || !t_events[i]) return cudaSuccess;
+    return cudaEventRecord(t_events[i], s);
+}
+
+reg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? REG_OK : REG_ERR_CUDA; }
+
+#define REG_TRY(expr)                            \
+    do {                                         \
+        const reg_status _s = (expr);            \
+        if (_s != REG_OK) return _s;             \
+    } while (0)
+
+#define REG_CUDA(expr)                                 \
+    do {                                               \
+        const cudaError_t _e = (expr);                 \
+        if (_e != cudaSuccess) return REG_ERR_CUDA;    \
+    } while (0)
+
+reg_status check_ptr(const void *p) {
+    if (!p) return REG_ERR_INVALID_ARG;
+    if (!aligned16(p)) return REG_ERR_ALIGN;
+    return REG_OK;
+}
+reg_status check_opt_ptr(const void *p) { return p ? check_ptr(p) : REG_OK; }
+
+reg_status check_common(const reg_loss_desc *L, const void *F, const void *M, int img_dt, const float *u,
+                        reg_dims d, int pad, void *ws, size_t ws_bytes) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_loss(L));
+    if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(F));
+    REG_TRY(check_ptr(M));
+    REG_TRY(check_ptr(u));
+    REG_TRY(check_ptr(ws));
+    if (ws_bytes < workspace_bytes(make_dims(d), L)) return REG_ERR_WORKSPACE;
+    return REG_OK;
+}
+
+// sweep 1 of either loss: similarity into sim_out (+ LNCC coefficient fields)
+reg_status run_sweep1(const reg_loss_desc *L, const void *F, const void *M, int img_dt, const float *u,
+                      const Dims &g, int pad, const Ws &w, double *sim_out, bool need_grad, cudaStream_t s) {
+    REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
+    if (L->kind == REG_LOSS_LNCC) {
+        LnccParams P{L->window / 2, L->eps};
+        REG_CUDA(launch_lncc_stats(F, M, img_dt, u, g, pad, P, need_grad ? w.coef : nullptr, w.partials,
+                                   w.counters + 0, sim_out, s));
+    } else {
+        const MiParams P = mi_params(L);
+        REG_CUDA(launch_mi_hist(F, M, img_dt, u, g, pad, P, w.hist, s));
+        REG_CUDA(launch_mi_finalize(w.hist, P, g.n, w.gtab, sim_out, s));
+    }
+    return REG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int reg_version(void) { return 100; }
+
+const char *reg_status_string(reg_status s) {
+    switch (s) {
+        case REG_OK: return "ok";
+        case REG_ERR_INVALID_ARG: return "invalid argument";
+        case REG_ERR_SHAPE: return "unsupported shape, window or bin count";
+        case REG_ERR_DTYPE: return "unknown dtype";
+        case REG_ERR_ALIGN: return "pointer not 16-byte aligned";
+        case REG_ERR_WORKSPACE: return "workspace too small";
+        case REG_ERR_NONFINITE: return "non-finite value in a loss or regulariser reduction";
+        case REG_ERR_TIMEOUT: return "bounded device wait expired";
+        case REG_ERR_CUDA: return "CUDA runtime error";
+        case REG_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+reg_status reg_workspace_size(const reg_loss_desc *loss, reg_dims d, size_t *bytes) {
+    if (!bytes) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_dims(d));
+    if (loss) REG_TRY(check_loss(loss));
+    *bytes = workspace_bytes(make_dims(d), loss);
+    return REG_OK;
+}
+
+reg_status reg_warp(const void *M, int img_dt, const float *u, reg_dims d, int pad, float *J_out, float *dJ_out,
+                    void *stream) {
+    REG_TRY(check_dims(d));
+    if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(M));
+    REG_TRY(check_ptr(u));
+    REG_TRY(check_ptr(J_out));
+    REG_TRY(check_opt_ptr(dJ_out));
+    return cuda_status(launch_warp(M, img_dt, u, make_dims(d), pad, J_out, dJ_out, (cudaStream_t)stream));
+}
+
+reg_status reg_loss(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u, reg_dims d,
+                    int pad, void *ws, size_t ws_bytes, double *sim_out, void *stream) {
+    REG_TRY(check_common(loss, F, M, img_dt, u, d, pad, ws, ws_bytes));
+    REG_TRY(check_ptr(sim_out));
+    const Dims g = make_dims(d);
+    const Ws w = carve(ws, g, loss);
+    return run_sweep1(loss, F, M, img_dt, u, g, pad, w, sim_out, false, (cudaStream_t)stream);
+}
+
+reg_status reg_loss_grad(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u,
+                         reg_dims d, int pad, void *ws, size_t ws_bytes, double *sim_out, float *grad_u,
+                         void *stream) {
+    REG_TRY(check_common(loss, F, M, img_dt, u, d, pad, ws, ws_bytes));
+    REG_TRY(check_ptr(sim_out));
+    REG_TRY(check_ptr(grad_u));
+    const Dims g = make_dims(d);
+    const Ws w = carve(ws, g, loss);
+    const cudaStream_t s = (cudaStream_t)stream;
+    REG_TRY(run_sweep1(loss, F, M, img_dt, u, g, pad, w, sim_out, true, s));
+    StepParams S{};
+    if (loss->kind == REG_LOSS_LNCC) {
+        LnccParams P{loss->window / 2, loss->eps};
+        REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u, g, pad, P, w.coef, grad_u, false, nullptr, nullptr, nullptr,
+                                    REG_F32, S, w.partials, w.counters + 1, w.scratch, s));
+    } else {
+        REG_CUDA(launch_mi_sweep2(F, M, img_dt, u, g, pad, mi_params(loss), w.gtab, grad_u, false, nullptr, nullptr,
+                                  nullptr, REG_F32, S, w.partials, w.counters + 1, w.scratch, s));
+    }
+    return REG_OK;
+}
+
+reg_status reg_regularize(const float *u, reg_dims d, float lambda, void *ws, size_t ws_bytes, double *r_out,
+                          float *grad_u, void *stream) {
+    REG_TRY(check_dims(d));
+    if (!isfinite(lambda)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(u));
+    REG_TRY(check_ptr(ws));
+    REG_TRY(check_ptr(r_out));
+    REG_TRY(check_opt_ptr(grad_u));
+    const Dims g = make_dims(d);
+    if (ws_bytes < workspace_bytes(g, nullptr)) return REG_ERR_WORKSPACE;
+    const Ws w = carve(ws, g, nullptr);
+    const cudaStream_t s = (cudaStream_t)stream;
+    REG_CUDA(cudaMemsetAsync(w.counters, 0, 256, s));
+    return cuda_status(launch_diffusion(u, g, lambda, grad_u, w.partials, w.counters + 2, r_out, s));
+}
+
+reg_status reg_step(const float *u_in, float *u_out, void *m, void *v, const float *grad_u, reg_dims d,
+                    const reg_adam_desc *adam, int t, void *stream) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_adam(adam, t));
+    REG_TRY(check_ptr(u_in));
+    REG_TRY(check_ptr(u_out));
+    REG_TRY(check_ptr(m));
+    REG_TRY(check_ptr(v));
+    REG_TRY(check_ptr(grad_u));
+    const Dims g = make_dims(d);
+    const StepParams S = step_params(adam, t, 0.0f, g);
+    return cuda_status(launch_adam(u_in, u_out, m, v, adam->moment_dtype, grad_u, 3 * g.n, S, (cudaStream_t)stream));
+}
+
+reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u_in,
+                       float *u_out, void *m, void *v, reg_dims d, int pad, float lambda, const reg_adam_desc *adam,
+                       int t, void *ws, size_t ws_bytes, double *obj_out, float *grad_out, void *stream) {
+    REG_TRY(check_common(loss, F, M, img_dt, u_in, d, pad, ws, ws_bytes));
+    REG_TRY(check_adam(adam, t));
+    if (!isfinite(lambda)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(u_out));
+    REG_TRY(check_ptr(m));
+    REG_TRY(check_ptr(v));
+    REG_TRY(check_ptr(obj_out));
+    REG_TRY(check_opt_ptr(grad_out));
+    const Dims g = make_dims(d);
+    {
+        const uintptr_t a0 = (uintptr_t)u_in, a1 = a0 + sizeof(float) * 3 * (size_t)g.n;
+        const uintptr_t b0 = (uintptr_t)u_out, b1 = b0 + sizeof(float) * 3 * (size_t)g.n;
+        if (a0 < b1 && b0 < a1) return REG_ERR_INVALID_ARG;  // u_out must not overlap u_in
+    }
+    const Ws w = carve(ws, g, loss);
+    const cudaStream_t s = (cudaStream_t)stream;
+    REG_CUDA(mark(0, s));
+    REG_TRY(run_sweep1(loss, F, M, img_dt, u_in, g, pad, w, obj_out, true, s));
+    REG_CUDA(mark(1, s));
+    const StepParams S = step_params(adam, t, lambda, g);
+    if (loss->kind == REG_LOSS_LNCC) {
+        LnccParams P{loss->window / 2, loss->eps};
+        REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u_in, g, pad, P, w.coef, grad_out, true, u_out, m, v,
+                                    adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s));
+    } else {
+        REG_CUDA(launch_mi_sweep2(F, M, img_dt, u_in, g, pad, mi_params(loss), w.gtab, grad_out, true, u_out, m, v,
+                                  adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s));
+    }
+    REG_CUDA(mark(2, s));
+    t_events_armed = false;
+    return REG_OK;
+}
+
+reg_status reg_set_timing_events(void *const *events, int n) {
+    if (n == 0 && events == nullptr) {
+        t_events_armed = false;
+        return REG_OK;
+    }
+    if (n != 3 || !events) return REG_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i) t_events[i] = (cudaEvent_t)events[i];
+    t_events_armed = true;
+    return REG_OK;
+}
+
+reg_status reg_jacdet_min(const float *u, reg_dims d, void *ws, size_t ws_bytes, float *min_out,
+                          unsigned long long *nfold_out, void *stream) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_ptr(u));
+    REG_TRY(check_ptr(min_out));
+    REG_TRY(check_ptr(nfold_out));
+    (void)ws;
+    (void)ws_bytes;
+    return cuda_status(launch_jacdet(u, make_dims(d), min_out, nfold_out, (cudaStream_t)stream));
+}
+
+reg_status reg_get_device_error(void *stream) {
+    REG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned *word = error_word();
+    if (!word) return REG_ERR_CUDA;
+    unsigned v = 0;
+    REG_CUDA(cudaMemcpy(&v, word, sizeof(v), cudaMemcpyDeviceToHost));
+    REG_CUDA(cudaMemset(word, 0, sizeof(v)));
+    if (v == REG_ERR_NONFINITE || v == REG_ERR_TIMEOUT) return (reg_status)v;
+    return v == 0 ? REG_OK : REG_ERR_CUDA;
+}
+
+reg_status reg_debug_wait_flag(const unsigned *flag, unsigned expect, unsigned long long timeout_ns, void *stream) {
+    REG_TRY(check_ptr(flag));
+    if (timeout_ns > 10ull * 1000000000ull) return REG_ERR_INVALID_ARG;
+    return cuda_status(launch_wait_flag(flag, expect, timeout_ns, (cudaStream_t)stream));
+}
+
+}  // extern "C"

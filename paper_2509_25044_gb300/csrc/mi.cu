@@ -1,0 +1,290 @@
+// mi.cu -- Parzen-window mutual information (Sec. 2.2, Eq. mi; App. fused
+// MI) on sm_103a, in two sweeps plus a one-block finalisation:
+//
+//   sweep 1 (mi_hist_kernel): warp M on chip, map F and the warped value to
+//     bin coordinates, add the 4 x 4 cubic B-spline outer product of each
+//     voxel into a per-CTA joint histogram in shared memory.  Entries are
+//     unsigned 64-bit fixed point (2^-32 per unit weight), so the sums are
+//     exact integers and the histogram does not depend on the order of the
+//     atomics (deterministic).  Each CTA then adds its non-zero bins to the
+//     global histogram (integer atomics, order-free).  No N x B Parzen block
+//     is ever materialised (the memory the paper removes).
+//   finalise (mi_finalize_kernel): p = hist / (2^32 N) in FP64, marginals
+//     as row / column sums, MI = sum p log(p / (pI pJ)), and the FP32 table
+//     G'[m][n] = -(B-3) m_scale / N * log(p / (pI pJ)) of the adjoint.
+//   sweep 2 (mi_sweep2_kernel): warp again with slope, the adjoint
+//     dL/dJ = sum_{a,b} G'[mF+a][nJ+b] w_a(sF) w'_b(sJ) (Eq. gradientmi-
+//     threadn with the 16 non-zero kernel terms), chained through the
+//     sampler slope; optionally fused with the diffusion gradient and Adam.
+#include "kernels.h"
+
+namespace regk {
+
+// Cubic B-spline weights of the 4 bins around bin coordinate s in [1, B-2]:
+// bins i0-1 .. i0+2 with i0 = min(floor(s), B-3), fraction f = s - i0.
+__device__ __forceinline__ int bspline_weights(float s, int B, float w[4]) {
+    int i0 = (int)floorf(s);
+    i0 = min(max(i0, 1), B - 3);
+    const float f = s - (float)i0;
+    const float f2 = f * f, f3 = f2 * f, g = 1.0f - f;
+    w[0] = g * g * g * (1.0f / 6.0f);
+    w[1] = (3.0f * f3 - 6.0f * f2 + 4.0f) * (1.0f / 6.0f);
+    w[2] = (-3.0f * f3 + 3.0f * f2 + 3.0f * f + 1.0f) * (1.0f / 6.0f);
+    w[3] = f3 * (1.0f / 6.0f);
+    return i0;
+}
+
+// derivatives of the same 4 weights with respect to s
+__device__ __forceinline__ int bspline_dweights(float s, int B, float d[4]) {
+    int i0 = (int)floorf(s);
+    i0 = min(max(i0, 1), B - 3);
+    const float f = s - (float)i0;
+    const float g = 1.0f - f;
+    d[0] = -0.5f * g * g;
+    d[1] = 1.5f * f * f - 2.0f * f;
+    d[2] = -1.5f * f * f + f + 0.5f;
+    d[3] = 0.5f * f * f;
+    return i0;
+}
+
+__device__ __forceinline__ float to_bin(float v, float lo, float scale, int B) {
+    const float t = fminf(fmaxf((v - lo) * scale, 0.0f), 1.0f);
+    return fmaf(t, (float)(B - 3), 1.0f);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M,
+                                                               const float *__restrict__ u, Dims g, int pad,
+                                                               MiParams P, int zc,
+                                                               unsigned long long *__restrict__ hist) {
+    __shared__ unsigned long long sh[MAX_BINS * MAX_BINS];
+    const int B = P.bins, BB = B * B;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int i = tid; i < BB; i += TILE_THREADS) sh[i] = 0ull;
+    __syncthreads();
+
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(g.nz, z0 + zc);
+    if (x < g.nx && y < g.ny) {
+        for (int z = z0; z < z1; ++z) {
+            const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+            const float fv = ld_vox(F, p);
+            const float jv = sample(M, g, x, y, z, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p), pad);
+            float wf[4], wj[4];
+            const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
+            const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const unsigned long long q = __float2ull_rn(wf[a] * wj[b] * 4294967296.0f);
+                    if (q) atomicAdd(&sh[(iF + a) * B + iJ + b], q);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < BB; i += TILE_THREADS) {
+        const unsigned long long v = sh[i];
+        if (v) atomicAdd(hist + i, v);
+    }
+}
+
+__global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long long *__restrict__ hist, int B,
+                                                           double inv_total, double gscale,
+                                                           float *__restrict__ Gtab, double *__restrict__ sim_out,
+                                                           unsigned *err) {
+    __shared__ double p[MAX_BINS * MAX_BINS];
+    __shared__ double pI[MAX_BINS], pJ[MAX_BINS];
+    __shared__ double red[32];
+    const int BB = B * B;
+    for (int e = threadIdx.x; e < BB; e += blockDim.x) p[e] = (double)hist[e] * inv_total;
+    __syncthreads();
+    if (threadIdx.x < B) {
+        double s = 0.0;
+        for (int n = 0; n < B; ++n) s += p[threadIdx.x * B + n];
+        pI[threadIdx.x] = s;
+    } else if (threadIdx.x >= 64 && threadIdx.x < 64 + B) {
+        const int n = threadIdx.x - 64;
+        double s = 0.0;
+        for (int m = 0; m < B; ++m) s += p[m * B + n];
+        pJ[n] = s;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < BB; e += blockDim.x) {
+        const double v = p[e];
+        float gv = 0.0f;
+        if (v > 0.0) {
+            const double lr = log(v / (pI[e / B] * pJ[e % B]));
+            acc += v * lr;
+            gv = (float)(gscale * lr);
+        }
+        Gtab[e] = gv;
+    }
+    const double mi = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        if (!isfinite(mi)) latch_error(err, REG_ERR_NONFINITE);
+        sim_out[0] = mi;
+    }
+}
+
+template <typename T, typename MT, bool STEP>
+__global__ void __launch_bounds__(TILE_THREADS)
+    mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, int pad,
+                     MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
+                     float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
+                     double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
+                     unsigned *err) {
+    __shared__ float Gs[MAX_BINS * MAX_BINS];
+    __shared__ double red[32];
+    const int B = P.bins, BB = B * B;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int i = tid; i < BB; i += TILE_THREADS) Gs[i] = Gtab[i];
+    __syncthreads();
+
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(g.nz, z0 + zc);
+    float rpart = 0.0f;
+    if (x < g.nx && y < g.ny) {
+        const long long col = (long long)y * g.nx + x;
+        float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
+        {
+            const long long p = (long long)z0 * g.nxy + col;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cur[c] = __ldg(u + c * g.n + p);
+            if (STEP && z0 > 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) prv[c] = __ldg(u + c * g.n + p - g.nxy);
+            }
+        }
+        for (int z = z0; z < z1; ++z) {
+            const long long p = (long long)z * g.nxy + col;
+            if (z + 1 < g.nz) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(u + c * g.n + p + g.nxy);
+            }
+            const float fv = ld_vox(F, p);
+            float sx, sy, sz;
+            const float jv = sample_grad(M, g, x, y, z, cur[0], cur[1], cur[2], pad, sx, sy, sz);
+            float wf[4], dj[4];
+            const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
+            const float tj = (jv - P.m_lo) * P.m_scale;
+            const int iJ = bspline_dweights(to_bin(jv, P.m_lo, P.m_scale, B), B, dj) - 1;
+            float gj = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float *row = Gs + (iF + a) * B + iJ;
+                const float t = fmaf(row[0], dj[0], fmaf(row[1], dj[1], fmaf(row[2], dj[2], row[3] * dj[3])));
+                gj = fmaf(wf[a], t, gj);
+            }
+            if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
+            float gs[3] = {gj * sx, gj * sy, gj * sz};
+            if (STEP) {
+                float gR[3];
+                diffusion_at(u, g, x, y, z, p, cur, prv, nxt, gR, rpart);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    if (grad_out) grad_out[c * g.n + p] = gt;
+                    u_out[c * g.n + p] = adam_elem(cur[c], gt, m, v, c * g.n + p, S);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) grad_out[c * g.n + p] = gs[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+            }
+        }
+    }
+    if (STEP) {
+        const double bs = block_sum((double)rpart, red);
+        const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (tid == 0) partials[bid] = bs;
+        if (arrive_last(counter)) {
+            const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+            double acc = 0.0;
+            // fixed order: thread t sums blocks t, t+256, ... then a fixed tree
+            for (long long i = tid; i < nb; i += TILE_THREADS) acc += __ldcg(partials + i);
+            const double tot = block_sum(acc, red);
+            if (tid == 0) {
+                const double R = tot / (double)g.n;
+                if (!isfinite(R)) latch_error(err, REG_ERR_NONFINITE);
+                r_out[0] = R;
+                *counter = 0u;
+            }
+        }
+    }
+}
+
+MarchGrid mi_hist_grid(const Dims &g) { return march_grid(g, 2LL * num_sms() * 4, 1); }
+MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
+
+cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
+                           const MiParams &P, unsigned long long *hist, cudaStream_t s) {
+    const MarchGrid G = mi_hist_grid(g);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    if (dt == REG_BF16)
+        mi_hist_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)F, (const __nv_bfloat16 *)M,
+                                                              u, g, pad, P, G.zc, hist);
+    else
+        mi_hist_kernel<float><<<grid, block, 0, s>>>((const float *)F, (const float *)M, u, g, pad, P, G.zc, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
+                               double *sim_out, cudaStream_t s) {
+    const double inv_total = 1.0 / (4294967296.0 * (double)N);
+    const double gscale = -(double)(P.bins - 3) * (double)P.m_scale / (double)N;
+    mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, inv_total, gscale, Gtab, sim_out, error_word());
+    return cudaGetLastError();
+}
+
+template <typename T, typename MT>
+static void mi_sweep2_dispatch(bool step, dim3 grid, dim3 block, cudaStream_t s, const void *F, const void *M,
+                               const float *u, const Dims &g, int pad, const MiParams &P, int zc,
+                               const float *Gtab, float *grad_out, float *u_out, void *m, void *v,
+                               const StepParams &S, double *partials, unsigned *counter, double *r_out) {
+    if (step)
+        mi_sweep2_kernel<T, MT, true><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc, Gtab,
+                                                             grad_out, u_out, (MT *)m, (MT *)v, S, partials,
+                                                             counter, r_out, error_word());
+    else
+        mi_sweep2_kernel<T, MT, false><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc, Gtab,
+                                                              grad_out, u_out, (MT *)m, (MT *)v, S, partials,
+                                                              counter, r_out, error_word());
+}
+
+cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
+                             const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
+                             void *m, void *v, int mdt, const StepParams &S, double *partials,
+                             unsigned *counter, double *r_out, cudaStream_t s) {
+    const MarchGrid G = mi_sweep_grid(g);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    const bool mb = step && mdt == REG_BF16;
+    if (dt == REG_BF16) {
+        if (mb)
+            mi_sweep2_dispatch<__nv_bfloat16, __nv_bfloat16>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab,
+                                                             grad_out, u_out, m, v, S, partials, counter, r_out);
+        else
+            mi_sweep2_dispatch<__nv_bfloat16, float>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out,
+                                                     u_out, m, v, S, partials, counter, r_out);
+    } else {
+        if (mb)
+            mi_sweep2_dispatch<float, __nv_bfloat16>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out,
+                                                     u_out, m, v, S, partials, counter, r_out);
+        else
+            mi_sweep2_dispatch<float, float>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out, u_out,
+                                             m, v, S, partials, counter, r_out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace regk

@@ -1,0 +1,239 @@
+// regadam.cu -- diffusion regulariser, Adam step, Jacobian-determinant fold
+// check, the device error word and the bounded-wait test hook.
+#include "kernels.h"
+
+namespace regk {
+
+__device__ unsigned int g_reg_error = 0u;
+
+unsigned *error_word() {
+    static unsigned *cached[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cached[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_reg_error) != cudaSuccess) return nullptr;
+        cached[dev] = (unsigned *)p;
+    }
+    return cached[dev];
+}
+
+int num_sms() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            cached = n;
+        else
+            cached = 152;
+    }
+    return cached;
+}
+
+MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc) {
+    MarchGrid G;
+    G.tiles_x = (g.nx + TX - 1) / TX;
+    G.tiles_y = (g.ny + TY - 1) / TY;
+    const long long tiles = (long long)G.tiles_x * G.tiles_y;
+    long long chunks = (target_blocks + tiles - 1) / tiles;
+    const long long max_chunks = (g.nz + min_zc - 1) / min_zc;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    G.zc = (int)((g.nz + chunks - 1) / chunks);
+    G.chunks = (g.nz + G.zc - 1) / G.zc;
+    return G;
+}
+
+MarchGrid diffusion_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
+
+// ---------------------------------------------------------------------------
+// diffusion regulariser: value (FP64 fixed-order sum) and lambda * dR/du
+// added into grad (grad may be null)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE_THREADS)
+    diffusion_kernel(const float *__restrict__ u, Dims g, int zc, float scale, float *__restrict__ grad,
+                     double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
+                     unsigned *err) {
+    __shared__ double red[32];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    float rpart = 0.0f;
+    if (x < g.nx && y < g.ny) {
+        const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
+        const long long col = (long long)y * g.nx + x;
+        float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
+        const long long p0 = (long long)z0 * g.nxy + col;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cur[c] = __ldg(u + c * g.n + p0);
+            if (z0 > 0) prv[c] = __ldg(u + c * g.n + p0 - g.nxy);
+        }
+        for (int z = z0; z < z1; ++z) {
+            const long long p = (long long)z * g.nxy + col;
+            if (z + 1 < g.nz) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(u + c * g.n + p + g.nxy);
+            }
+            float gR[3];
+            diffusion_at(u, g, x, y, z, p, cur, prv, nxt, gR, rpart);
+            if (grad) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) grad[c * g.n + p] = fmaf(scale, gR[c], grad[c * g.n + p]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+            }
+        }
+    }
+    const double bs = block_sum((double)rpart, red);
+    const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (tid == 0) partials[bid] = bs;
+    if (arrive_last(counter)) {
+        const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+        double acc = 0.0;
+        for (long long i = tid; i < nb; i += TILE_THREADS) acc += __ldcg(partials + i);
+        const double tot = block_sum(acc, red);
+        if (tid == 0) {
+            const double R = tot / (double)g.n;
+            if (!isfinite(R)) latch_error(err, REG_ERR_NONFINITE);
+            r_out[0] = R;
+            *counter = 0u;
+        }
+    }
+}
+
+cudaError_t launch_diffusion(const float *u, const Dims &g, float lam, float *grad, double *partials,
+                             unsigned *counter, double *r_out, cudaStream_t s) {
+    const MarchGrid G = diffusion_grid(g);
+    const float scale = (float)((double)lam * 2.0 / (double)g.n);
+    diffusion_kernel<<<dim3(G.tiles_x, G.tiles_y, G.chunks), dim3(TX, TY), 0, s>>>(u, g, G.zc, scale, grad,
+                                                                                   partials, counter, r_out,
+                                                                                   error_word());
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adam over the 3N displacement components
+// ---------------------------------------------------------------------------
+template <typename MT>
+__global__ void __launch_bounds__(256) adam_kernel(const float *__restrict__ u_in, float *u_out, MT *m, MT *v,
+                                                  const float *__restrict__ grad, long long n3, StepParams S) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float uu = u_in[i];
+        u_out[i] = adam_elem(uu, __ldg(grad + i), m, v, i, S);
+    }
+}
+
+cudaError_t launch_adam(const float *u_in, float *u_out, void *m, void *v, int mdt, const float *grad, long long n3,
+                        const StepParams &S, cudaStream_t s) {
+    long long blocks = (n3 + 255) / 256;
+    const long long cap = 16LL * num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (mdt == REG_BF16)
+        adam_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(u_in, u_out, (__nv_bfloat16 *)m,
+                                                                     (__nv_bfloat16 *)v, grad, n3, S);
+    else
+        adam_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(u_in, u_out, (float *)m, (float *)v, grad, n3, S);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// det(I + grad u): central differences, one-sided at the border
+// ---------------------------------------------------------------------------
+__global__ void jacdet_init_kernel(float *min_out, unsigned long long *nfold) {
+    min_out[0] = __int_as_float(0x7f800000);  // +inf
+    nfold[0] = 0ull;
+}
+
+__device__ __forceinline__ void atomic_min_float(float *addr, float val) {
+    if (val >= 0.0f)
+        atomicMin((int *)addr, __float_as_int(val));
+    else
+        atomicMax((unsigned *)addr, __float_as_uint(val));
+}
+
+__device__ __forceinline__ float central(const float *uc, long long p, int coord, int n, long long stride) {
+    if (n == 1) return 0.0f;
+    const int lo = coord > 0 ? coord - 1 : coord;
+    const int hi = coord < n - 1 ? coord + 1 : coord;
+    const float a = __ldg(uc + p + (long long)(hi - coord) * stride);
+    const float b = __ldg(uc + p - (long long)(coord - lo) * stride);
+    return (a - b) / (float)(hi - lo);
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) jacdet_kernel(const float *__restrict__ u, Dims g, int zc,
+                                                              float *min_out, unsigned long long *nfold) {
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    float mn = __int_as_float(0x7f800000);
+    unsigned cnt = 0;
+    if (x < g.nx && y < g.ny) {
+        const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
+        for (int z = z0; z < z1; ++z) {
+            const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+            float Jm[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *uc = u + c * g.n;
+                Jm[c][0] = central(uc, p, x, g.nx, 1) + (c == 0 ? 1.0f : 0.0f);
+                Jm[c][1] = central(uc, p, y, g.ny, g.nx) + (c == 1 ? 1.0f : 0.0f);
+                Jm[c][2] = central(uc, p, z, g.nz, g.nxy) + (c == 2 ? 1.0f : 0.0f);
+            }
+            const float det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
+                              Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
+                              Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+            if (!(det > 0.0f)) ++cnt;
+            if (det == det) mn = fminf(mn, det);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_min_float(min_out, mn);
+        if (cnt) atomicAdd(nfold, (unsigned long long)cnt);
+    }
+}
+
+cudaError_t launch_jacdet(const float *u, const Dims &g, float *min_out, unsigned long long *nfold,
+                          cudaStream_t s) {
+    jacdet_init_kernel<<<1, 1, 0, s>>>(min_out, nfold);
+    const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
+    jacdet_kernel<<<dim3(G.tiles_x, G.tiles_y, G.chunks), dim3(TX, TY), 0, s>>>(u, g, G.zc, min_out, nfold);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// bounded device wait (failure-detection test hook)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void wait_flag_kernel(const unsigned *flag, unsigned expect, unsigned long long timeout_ns, unsigned *err) {
+    const unsigned long long t0 = global_ns();
+    // iteration cap as a second bound in case the timer does not advance
+    for (long long it = 0; it < (1LL << 24); ++it) {
+        if (*(volatile const unsigned *)flag == expect) return;
+        if (global_ns() - t0 > timeout_ns) break;
+        __nanosleep(1000);
+    }
+    latch_error(err, REG_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_flag(const unsigned *flag, unsigned expect, unsigned long long timeout_ns, cudaStream_t s) {
+    wait_flag_kernel<<<1, 1, 0, s>>>(flag, expect, timeout_ns, error_word());
+    return cudaGetLastError();
+}
+
+}  // namespace regk

@@ -1,0 +1,76 @@
+// step_common.cuh -- the per-voxel tail shared by the fused sweeps: the
+// diffusion regulariser's value / gradient at one voxel and the Adam update
+// of its three displacement components.
+#pragma once
+
+#include "reg_common.cuh"
+
+namespace regk {
+
+struct StepParams {
+    float lam;        // regulariser weight lambda
+    float two_over_n; // 2 / N (dR/du scale)
+    float lr_bc1;     // lr / (1 - beta1^t)
+    float rsqrt_bc2;  // 1 / sqrt(1 - beta2^t)
+    float b1, b2, eps, gscale;
+};
+
+__device__ __forceinline__ float ld_moment(const float *p, long long i) { return p[i]; }
+__device__ __forceinline__ float ld_moment(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void st_moment(float *p, long long i, float v) { p[i] = v; }
+__device__ __forceinline__ void st_moment(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
+
+// Adam on one element (torch.optim.Adam with bias correction; the update
+// uses the new moments in FP32, the stored moments are rounded to MT).
+template <typename MT>
+__device__ __forceinline__ float adam_elem(float u, float g, MT *m, MT *v, long long i, const StepParams &S) {
+    const float gs = S.gscale * g;
+    const float mn = fmaf(S.b1, ld_moment(m, i), (1.0f - S.b1) * gs);
+    const float vn = fmaf(S.b2, ld_moment(v, i), (1.0f - S.b2) * gs * gs);
+    st_moment(m, i, mn);
+    st_moment(v, i, vn);
+    const float denom = fmaf(sqrtf(vn), S.rsqrt_bc2, S.eps);
+    return u - S.lr_bc1 * (mn / denom);
+}
+
+// Diffusion regulariser at voxel (x,y,z) for all three channels.
+//   grad:  gR_c = (2/N) sum_d [ (u_c(p) - u_c(p+e_d)) [p+e_d inside]
+//                             + (u_c(p) - u_c(p-e_d)) [p-e_d inside] ]
+//   value: adds sum_c sum_d (u_c(p+e_d) - u_c(p))^2 over forward neighbours
+//          inside the volume (each pair is counted by its lower voxel).
+// cur/prv/nxt hold u at z, z-1, z+1 (prv/nxt ignored at the z borders);
+// the x and y neighbours are read through the read-only cache.
+__device__ __forceinline__ void diffusion_at(const float *__restrict__ u, const Dims &g, int x, int y, int z,
+                                             long long p, const float cur[3], const float prv[3],
+                                             const float nxt[3], float gR[3], float &rpart) {
+    const bool hxm = x > 0, hxp = x + 1 < g.nx;
+    const bool hym = y > 0, hyp = y + 1 < g.ny;
+    const bool hzm = z > 0, hzp = z + 1 < g.nz;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float *uc = u + (long long)c * g.n;
+        const float c0 = cur[c];
+        float acc = 0.0f;
+        if (hxp) {
+            const float d = __ldg(uc + p + 1) - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hxm) acc += c0 - __ldg(uc + p - 1);
+        if (hyp) {
+            const float d = __ldg(uc + p + g.nx) - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hym) acc += c0 - __ldg(uc + p - g.nx);
+        if (hzp) {
+            const float d = nxt[c] - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hzm) acc += c0 - prv[c];
+        gR[c] = acc;
+    }
+}
+
+}  // namespace regk

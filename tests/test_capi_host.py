@@ -1,0 +1,126 @@
+"""C-ABI library: builds, loads, exports every symbol of include/reg.h, and
+rejects bad arguments on the host before anything reaches a GPU.  CPU only:
+no call here passes arguments that would launch a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2509_25044_gb300 import build, capi
+    build.build()
+    capi.load()
+    return capi
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "reg.h")).read()
+    return sorted(set(re.findall(r"REG_API[^;(]*?\b(reg_\w+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    syms = header_symbols()
+    assert len(syms) >= 12
+    lib = ctypes.CDLL(capi.LIB_PATH)
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(capi.EXPORTS) == syms
+
+
+def test_version_and_status_strings(capi):
+    assert capi.reg_version() >= 100
+    for code in range(10):
+        assert capi.reg_status_string(code)
+    assert capi.reg_status_string(999) == "unknown status"
+
+
+def _lib(capi):
+    return capi.load()
+
+
+D = None
+
+
+def dims(nx=8, ny=8, nz=8):
+    from paper_2509_25044_gb300.capi import RegDims
+    return RegDims(nx, ny, nz)
+
+
+def test_workspace_size_host_only(capi):
+    lncc = capi.lncc_desc(7, 1e-5)
+    mi = capi.mi_desc((0, 1), (0, 1), 32)
+    a = capi.reg_workspace_size(lncc, dims(64, 64, 64))
+    b = capi.reg_workspace_size(mi, dims(64, 64, 64))
+    c = capi.reg_workspace_size(None, dims(64, 64, 64))
+    assert a >= 3 * 4 * 64 ** 3  # LNCC keeps three coefficient fields
+    assert b < a and c <= b
+    with pytest.raises(capi.RegError) as e:
+        capi.reg_workspace_size(capi.lncc_desc(8, 1e-5), dims())
+    assert e.value.status == 2
+    with pytest.raises(capi.RegError):
+        capi.reg_workspace_size(capi.mi_desc((1, 0), (0, 1), 32), dims())
+    with pytest.raises(capi.RegError):
+        capi.reg_workspace_size(capi.mi_desc((0, 1), (0, 1), 100), dims())
+    with pytest.raises(capi.RegError):
+        capi.reg_workspace_size(None, dims(0, 4, 4))
+
+
+FAKE = 0x10000  # 16-byte aligned, never dereferenced: validation fails first
+
+
+def test_warp_validation(capi):
+    L = _lib(capi)
+    vp = ctypes.c_void_p
+    assert L.reg_warp(vp(FAKE), 0, vp(FAKE), dims(0, 4, 4), 0, vp(FAKE), None, None) == 2
+    assert L.reg_warp(vp(FAKE), 7, vp(FAKE), dims(), 0, vp(FAKE), None, None) == 3
+    assert L.reg_warp(vp(FAKE), 0, vp(FAKE), dims(), 5, vp(FAKE), None, None) == 1
+    assert L.reg_warp(None, 0, vp(FAKE), dims(), 0, vp(FAKE), None, None) == 1
+    assert L.reg_warp(vp(FAKE + 4), 0, vp(FAKE), dims(), 0, vp(FAKE), None, None) == 4
+    assert L.reg_warp(vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), vp(FAKE + 8), None) == 4
+
+
+def test_loss_and_iterate_validation(capi):
+    L = _lib(capi)
+    vp = ctypes.c_void_p
+    lncc = capi.lncc_desc(7, 1e-5)
+    need = capi.reg_workspace_size(lncc, dims())
+    # workspace too small
+    assert L.reg_loss(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need - 1,
+                      vp(FAKE), None) == 5
+    # bad eps
+    bad = capi.lncc_desc(7, -1.0)
+    assert L.reg_loss(ctypes.byref(bad), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need,
+                      vp(FAKE), None) == 1
+    # null similarity output
+    assert L.reg_loss_grad(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need, None,
+                           vp(FAKE), None) == 1
+    adam = capi.adam_desc(0.1, grad_scale=512.0)
+    # u_out overlapping u_in
+    assert L.reg_iterate(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), vp(FAKE + 256), vp(FAKE), vp(FAKE),
+                         dims(), 0, 0.1, ctypes.byref(adam), 1, vp(FAKE), need, vp(FAKE), None, None) == 1
+    # step count must be >= 1
+    assert L.reg_iterate(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), vp(FAKE << 8), vp(FAKE), vp(FAKE),
+                         dims(), 0, 0.1, ctypes.byref(adam), 0, vp(FAKE), need, vp(FAKE), None, None) == 1
+    badadam = capi.adam_desc(0.1, beta1=1.0)
+    assert L.reg_step(vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), dims(), ctypes.byref(badadam), 1,
+                      None) == 1
+    bf = capi.adam_desc(0.1, moment_dtype=9)
+    assert L.reg_step(vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), dims(), ctypes.byref(bf), 1, None) == 3
+    assert L.reg_regularize(vp(FAKE), dims(), float("nan"), vp(FAKE), 1 << 20, vp(FAKE), None, None) == 1
+    assert L.reg_debug_wait_flag(vp(FAKE), 1, 11 * 10 ** 9, None) == 1
+
+
+def test_product_package_has_no_oracle_dependency():
+    """The product path must not import, link or execute the oracle."""
+    pkg = os.path.join(ROOT, "paper_2509_25044_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt and "oracle.c" not in txt, f

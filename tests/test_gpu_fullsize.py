@@ -1,0 +1,86 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench
+times (reg_iterate, one fused iteration): every output where the FP64 oracle
+can compute the whole field (64^3 LNCC, 192^3 MI), sampled voxels at 512^3."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from _util import GRAD_RTOL, GRAD_RTOL_BF16, LOSS_RTOL, assert_rel, rel_l2, to64
+from paper_2509_25044_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2509_25044_gb300 import build, capi
+    build.build()
+    capi.load()
+    return capi
+
+
+def _run(capi, loss, F, M, u, lam, mdt=0):
+    N = F.numel()
+    ud = u.to(DEV).contiguous()
+    uo = torch.empty_like(ud)
+    mt = torch.bfloat16 if mdt else torch.float32
+    m = torch.zeros(ud.shape, dtype=mt, device=DEV)
+    v = torch.zeros(ud.shape, dtype=mt, device=DEV)
+    g = torch.empty_like(ud)
+    ws = capi.workspace(loss, F)
+    adam = capi.adam_desc(0.1, moment_dtype=mdt, grad_scale=float(N))
+    obj = capi.reg_iterate(loss, F, M, ud, uo, m, v, lam, adam, 1, ws, grad=g)
+    torch.cuda.synchronize()
+    return obj.cpu().numpy(), g
+
+
+def test_c0_lncc_64(capi):
+    d = synth.make("c0")
+    u = 0.5 * d["u_true"]  # a mid-registration displacement
+    loss = capi.lncc_desc(7, 1e-5)
+    obj, g = _run(capi, loss, d["F"].to(DEV), d["M"].to(DEV), u, 0.1)
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=7, eps=1e-5)
+    ref = O.objective(to64(d["F"]), to64(d["M"]), to64(u), spec, 0.1)
+    assert_rel(obj[0], ref["sim"], LOSS_RTOL, "S")
+    assert_rel(obj[1], ref["R"], 1e-6, "R")
+    assert rel_l2(to64(g), ref["grad"]) <= GRAD_RTOL
+
+
+def test_c1_mi_192(capi):
+    d = synth.make("c1")
+    u = -0.5 * d["u_true"]
+    loss = capi.mi_desc(d["f_range"], d["m_range"], 32)
+    obj, g = _run(capi, loss, d["F"].to(DEV), d["M"].to(DEV), u, 0.05)
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=d["f_range"], m_range=d["m_range"])
+    ref = O.objective(to64(d["F"]), to64(d["M"]), to64(u), spec, 0.05)
+    assert_rel(obj[0], ref["sim"], LOSS_RTOL, "MI")
+    assert_rel(obj[1], ref["R"], 1e-6, "R")
+    assert rel_l2(to64(g), ref["grad"]) <= GRAD_RTOL
+
+
+def test_c2_lncc_bf16_512_sampled(capi):
+    d = synth.make("c2", device=DEV)
+    Fb = d["F"].to(torch.bfloat16).contiguous()
+    Mb = d["M"].to(torch.bfloat16).contiguous()
+    u = (0.5 * d["u_true"]).contiguous()
+    F32, M32 = to64(d["F"]), to64(d["M"])
+    del d
+    loss = capi.lncc_desc(9, 1e-5)
+    obj, g = _run(capi, loss, Fb, Mb, u, 0.0, mdt=1)
+    u64 = to64(u)
+    N = F32.size
+    rng = np.random.default_rng(2025)
+    pts = np.concatenate([[0, N - 1, N // 2], rng.integers(0, N, 45)])
+    ggpu = to64(g).reshape(3, -1)[:, pts]
+    # the stored BF16 values: the FP32 arithmetic bar
+    Fv, Mv = to64(Fb.float()), to64(Mb.float())
+    J, dJ = O.warp(Mv, u64, O.PAD_BORDER, with_grad=True)
+    gJ, _ = O.lncc_grad_points(Fv, J, 9, 1e-5, pts)
+    assert rel_l2(ggpu, gJ[None, :] * dJ.reshape(3, -1)[:, pts]) <= GRAD_RTOL
+    del J, dJ, Fv, Mv
+    # the FP32 images: the BF16 storage bar
+    J, dJ = O.warp(M32, u64, O.PAD_BORDER, with_grad=True)
+    gJ, _ = O.lncc_grad_points(F32, J, 9, 1e-5, pts)
+    assert rel_l2(ggpu, gJ[None, :] * dJ.reshape(3, -1)[:, pts]) <= GRAD_RTOL_BF16

@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on
+the same seeded inputs (element by element where the oracle computes every
+output, sampled at full size otherwise)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from _util import (GRAD_RTOL, GRAD_RTOL_BF16, LOSS_RTOL, LOSS_RTOL_BF16, WARP_TOL, assert_rel, bf16_values,
+                   field, mono_images, multimodal_images, rel_l2, to64)
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2509_25044_gb300 import build, capi
+    build.build()
+    capi.load()
+    return capi
+
+
+def _img(t, dtype):
+    return t.to(DEV).to(dtype).contiguous()
+
+
+def _oracle_img(t, dtype):
+    return to64(bf16_values(t) if dtype == torch.bfloat16 else t)
+
+
+# ---------------------------------------------------------------------------
+# warp
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(17, 20, 33), (1, 6, 9), (24, 1, 7), (64, 64, 64)])
+@pytest.mark.parametrize("pad", [0, 1])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_warp_matches_oracle(capi, shape, pad, dtype):
+    F, M = mono_images(shape, 3)
+    u = field(shape, 2.0, 4.0, 5)
+    u[0, :, :, :2] += 6.0  # push some samples across the x border
+    J, dJ = capi.reg_warp(_img(M, dtype), u.to(DEV), pad=pad, with_slope=True)
+    torch.cuda.synchronize()
+    Jr, dJr = O.warp(_oracle_img(M, dtype), to64(u), pad, with_grad=True)
+    rng = float(M.max() - M.min())
+    assert np.abs(to64(J) - Jr).max() <= WARP_TOL * rng
+    assert np.abs(to64(dJ) - dJr).max() <= 2 * WARP_TOL * rng
+
+
+def test_warp_zero_displacement_is_exact(capi):
+    _, M = mono_images((19, 21, 23), 4)
+    J = capi.reg_warp(M.to(DEV), torch.zeros((3,) + tuple(M.shape), device=DEV))
+    assert torch.equal(J.cpu(), M)
+
+
+# ---------------------------------------------------------------------------
+# LNCC
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,window", [((16, 16, 16), 7), ((21, 35, 40), 5), ((20, 17, 44), 9),
+                                          ((12, 13, 14), 15), ((1, 9, 40), 3), ((30, 30, 30), 3)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_lncc_matches_oracle(capi, shape, window, pad):
+    F, M = mono_images(shape, 7)
+    u = field(shape, 3.0, 2.5, 8)
+    loss = capi.lncc_desc(window, 1e-4)
+    ws = capi.workspace(loss, F.to(DEV))
+    Fd, Md, ud = F.to(DEV), M.to(DEV), u.to(DEV)
+    sim1 = capi.reg_loss(loss, Fd, Md, ud, ws, pad=pad)
+    sim, g = capi.reg_loss_grad(loss, Fd, Md, ud, ws, pad=pad)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=window, eps=1e-4)
+    Sr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec, pad)
+    assert_rel(sim1.item(), Sr, LOSS_RTOL, "S (reg_loss)")
+    assert_rel(sim.item(), Sr, LOSS_RTOL, "S (reg_loss_grad)")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL
+
+
+def test_lncc_bf16_storage(capi):
+    shape = (32, 40, 48)
+    F, M = mono_images(shape, 11)
+    u = field(shape, 3.0, 2.0, 12)
+    loss = capi.lncc_desc(9, 1e-4)
+    Fb, Mb = _img(F, torch.bfloat16), _img(M, torch.bfloat16)
+    ws = capi.workspace(loss, Fb)
+    sim, g = capi.reg_loss_grad(loss, Fb, Mb, u.to(DEV), ws)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=9, eps=1e-4)
+    # same stored values: FP32 arithmetic bars
+    Sb, gb = O.similarity_and_grad(_oracle_img(F, torch.bfloat16), _oracle_img(M, torch.bfloat16), to64(u), spec)
+    assert_rel(sim.item(), Sb, LOSS_RTOL, "S bf16 values")
+    assert rel_l2(to64(g), gb) <= GRAD_RTOL
+    # against the FP32 images: the BF16 storage bars
+    Sr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec)
+    assert_rel(sim.item(), Sr, LOSS_RTOL_BF16, "S bf16 vs f32")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL_BF16
+
+
+# ---------------------------------------------------------------------------
+# MI
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,bins", [((16, 16, 16), 32), ((33, 29, 40), 32), ((24, 26, 28), 8),
+                                        ((20, 22, 36), 64), ((1, 30, 41), 16)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_mi_matches_oracle(capi, shape, bins, pad):
+    F, M = multimodal_images(shape, 21)
+    u = field(shape, 3.0, 3.0, 22)
+    fr = (float(F.min()), float(F.max()))
+    mr = (float(M.min()), float(M.max()))
+    loss = capi.mi_desc(fr, mr, bins)
+    ws = capi.workspace(loss, F.to(DEV))
+    Fd, Md, ud = F.to(DEV), M.to(DEV), u.to(DEV)
+    sim1 = capi.reg_loss(loss, Fd, Md, ud, ws, pad=pad)
+    sim, g = capi.reg_loss_grad(loss, Fd, Md, ud, ws, pad=pad)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=bins, f_range=fr, m_range=mr)
+    vr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec, pad)
+    assert_rel(sim1.item(), vr, LOSS_RTOL, "MI (reg_loss)")
+    assert_rel(sim.item(), vr, LOSS_RTOL, "MI (reg_loss_grad)")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL
+
+
+def test_mi_bf16_storage(capi):
+    shape = (40, 36, 44)
+    F, M = multimodal_images(shape, 31)
+    u = field(shape, 3.0, 3.0, 32)
+    Fb, Mb = _img(F, torch.bfloat16), _img(M, torch.bfloat16)
+    fr = (float(Fb.min()), float(Fb.max()))
+    mr = (float(Mb.min()), float(Mb.max()))
+    loss = capi.mi_desc(fr, mr, 32)
+    ws = capi.workspace(loss, Fb)
+    sim, g = capi.reg_loss_grad(loss, Fb, Mb, u.to(DEV), ws)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=fr, m_range=mr)
+    vb, gb = O.similarity_and_grad(_oracle_img(F, torch.bfloat16), _oracle_img(M, torch.bfloat16), to64(u), spec)
+    assert_rel(sim.item(), vb, LOSS_RTOL, "MI bf16 values")
+    assert rel_l2(to64(g), gb) <= GRAD_RTOL
+    vr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec)
+    assert_rel(sim.item(), vr, LOSS_RTOL_BF16, "MI bf16 vs f32")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL_BF16
+
+
+# ---------------------------------------------------------------------------
+# regulariser, Adam, det J
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(9, 10, 37), (1, 5, 6), (40, 40, 40)])
+def test_regularizer_matches_oracle(capi, shape):
+    u = field(shape, 2.0, 3.0, 41)
+    ud = u.to(DEV)
+    ws = capi.workspace(None, ud[0])
+    base = torch.randn(ud.shape, device=DEV) * 1e-3
+    g = base.clone()
+    r = capi.reg_regularize(ud, 0.37, ws, grad=g)
+    torch.cuda.synchronize()
+    Rr, gr = O.diffusion(to64(u))
+    assert_rel(r.item(), Rr, 1e-6, "R")
+    assert rel_l2(to64(g - base), 0.37 * gr) <= 1e-5
+
+
+@pytest.mark.parametrize("mdt", [0, 1])
+@pytest.mark.parametrize("t", [1, 7])
+def test_adam_matches_oracle(capi, mdt, t):
+    n = (6, 7, 33)
+    gen = torch.Generator().manual_seed(5 + t)
+    u = torch.randn((3,) + n, generator=gen)
+    g = torch.randn((3,) + n, generator=gen) * 1e-3
+    m0 = torch.randn((3,) + n, generator=gen) * 0.5
+    v0 = torch.rand((3,) + n, generator=gen) * 0.3
+    mt = torch.bfloat16 if mdt else torch.float32
+    m, v = m0.to(mt).to(DEV), v0.to(mt).to(DEV)
+    adam = capi.adam_desc(0.05, moment_dtype=mdt, grad_scale=1000.0)
+    uo = torch.empty_like(u, device=DEV)
+    capi.reg_step(u.to(DEV), uo, m, v, g.to(DEV), adam, t)
+    torch.cuda.synchronize()
+    ur, mr, vr = O.adam(to64(u), to64(m0.to(mt)), to64(v0.to(mt)), to64(g), t, 0.05, grad_scale=1000.0,
+                        bf16_moments=bool(mdt))
+    np.testing.assert_allclose(to64(uo) - to64(u), ur - to64(u), atol=2e-6 * 0.05 * 10, rtol=1e-5)
+    if mdt:  # one bf16 ulp where FP32 and FP64 land on opposite sides of a rounding boundary
+        np.testing.assert_allclose(to64(m), mr, rtol=2 ** -7, atol=1e-30)
+        np.testing.assert_allclose(to64(v), vr, rtol=2 ** -7, atol=1e-30)
+    else:
+        np.testing.assert_allclose(to64(m), mr, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(to64(v), vr, rtol=1e-6, atol=1e-12)
+
+
+def test_jacdet_matches_oracle(capi):
+    shape = (20, 24, 28)
+    u = field(shape, 2.0, 4.0, 51)
+    mn, nf = capi.reg_jacdet_min(u.to(DEV))
+    torch.cuda.synchronize()
+    d = O.jacdet(to64(u))
+    assert abs(mn.item() - d.min()) <= 1e-5 * max(1.0, abs(d.min()))
+    near = np.abs(d) < 1e-5
+    assert abs(int(nf.item()) - int((d <= 0).sum())) <= int(near.sum())
+    u0 = torch.zeros((3,) + shape, device=DEV)
+    mn0, nf0 = capi.reg_jacdet_min(u0)
+    assert mn0.item() == 1.0 and nf0.item() == 0
+
+
+# ---------------------------------------------------------------------------
+# fused iteration
+# ---------------------------------------------------------------------------
+def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
+    if kind == "lncc":
+        F, M = mono_images(shape, seed)
+        loss = capi.lncc_desc(7, 1e-4)
+        spec = O.LossSpec(kind=O.LOSS_LNCC, window=7, eps=1e-4)
+    else:
+        F, M = multimodal_images(shape, seed)
+        fr = (float(F.min()), float(F.max()))
+        mr = (float(M.min()), float(M.max()))
+        loss = capi.mi_desc(fr, mr, 32)
+        spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=fr, m_range=mr)
+    u = field(shape, 3.0, 2.0, seed + 1)
+    N = int(np.prod(shape))
+    gen = torch.Generator().manual_seed(seed)
+    m0 = torch.randn((3,) + shape, generator=gen) * 1e-2
+    v0 = torch.rand((3,) + shape, generator=gen) * 1e-4
+    mt = torch.bfloat16 if mdt else torch.float32
+    Fd, Md = _img(F, dtype), _img(M, dtype)
+    m, v = m0.to(mt).to(DEV), v0.to(mt).to(DEV)
+    adam = capi.adam_desc(0.1, moment_dtype=mdt, grad_scale=float(N))
+    ws = capi.workspace(loss, Fd)
+    ud = u.to(DEV)
+    uo = torch.empty_like(ud)
+    g = torch.empty_like(ud)
+    obj = capi.reg_iterate(loss, Fd, Md, ud, uo, m, v, 0.1, adam, t, ws, grad=g)
+    torch.cuda.synchronize()
+    return dict(F=F, M=M, u=u, m0=m0.to(mt), v0=v0.to(mt), spec=spec, uo=uo, m=m, v=v, g=g, obj=obj, N=N,
+                dtype=dtype)
+
+
+@pytest.mark.parametrize("kind", ["lncc", "mi"])
+@pytest.mark.parametrize("shape", [(24, 20, 35), (48, 48, 48)])
+def test_iterate_matches_oracle(capi, kind, shape):
+    c = _iterate_case(capi, kind, shape, t=3)
+    ref = O.objective(to64(c["F"]), to64(c["M"]), to64(c["u"]), c["spec"], 0.1)
+    assert_rel(c["obj"][0].item(), ref["sim"], LOSS_RTOL, "similarity")
+    assert_rel(c["obj"][1].item(), ref["R"], 1e-6, "R")
+    assert rel_l2(to64(c["g"]), ref["grad"]) <= GRAD_RTOL
+    # Adam on the GPU's own gradient must agree elementwise with the oracle's Adam
+    ur, mr, vr = O.adam(to64(c["u"]), to64(c["m0"]), to64(c["v0"]), to64(c["g"]), 3, 0.1, grad_scale=c["N"])
+    np.testing.assert_allclose(to64(c["uo"]), ur, atol=1e-5, rtol=0)
+    np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("kind", ["lncc", "mi"])
+def test_iterate_is_deterministic(capi, kind):
+    a = _iterate_case(capi, kind, (40, 33, 37), seed=71)
+    b = _iterate_case(capi, kind, (40, 33, 37), seed=71)
+    for k in ("uo", "m", "v", "g", "obj"):
+        assert torch.equal(a[k], b[k]), k
+
+
+# ---------------------------------------------------------------------------
+# failure detection (host-visible device error word; no GPU fault)
+# ---------------------------------------------------------------------------
+def test_nonfinite_input_is_reported(capi):
+    shape = (16, 16, 16)
+    F, M = mono_images(shape, 81)
+    F[3, 4, 5] = float("nan")
+    loss = capi.lncc_desc(5, 1e-4)
+    Fd = F.to(DEV)
+    ws = capi.workspace(loss, Fd)
+    assert capi.reg_get_device_error() == 0
+    capi.reg_loss(loss, Fd, M.to(DEV), torch.zeros((3,) + shape, device=DEV), ws)
+    assert capi.reg_get_device_error() == 6  # REG_ERR_NONFINITE
+    assert capi.reg_get_device_error() == 0  # cleared
+
+
+def test_bounded_wait_times_out_and_context_survives(capi):
+    flag = torch.zeros(4, dtype=torch.int32, device=DEV)
+    capi.reg_debug_wait_flag(flag, 1, 2_000_000)  # nothing sets it: 2 ms limit
+    assert capi.reg_get_device_error() == 7  # REG_ERR_TIMEOUT
+    flag[0] = 1
+    capi.reg_debug_wait_flag(flag, 1, 2_000_000)
+    assert capi.reg_get_device_error() == 0
+    assert torch.ones(3, device=DEV).sum().item() == 3.0

@@ -116,3 +116,14 @@ def test_full_chain_gradient_wrt_u_matches_central_differences(rng):
         # that entries near zero are judged on the FD rounding noise scale
         errs.append(abs(g[k] - fd) / (abs(fd) + 0.1 * rms))
     assert max(errs) < 1e-6, errs
+
+
+def test_pointwise_gradient_equals_full_field(rng):
+    F = _smooth(rng, (9, 11, 10))
+    J = _smooth(rng, (9, 11, 10))
+    S, g = O.lncc_grad(F, J, 5, 1e-4)
+    _, n = O.lncc(F, J, 5, 1e-4, per_voxel=True)
+    pts = np.concatenate([[0, F.size - 1], rng.integers(0, F.size, 40)])
+    gp, npnt = O.lncc_grad_points(F, J, 5, 1e-4, pts)
+    np.testing.assert_allclose(gp, g.ravel()[pts], rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(npnt, n.ravel()[pts], rtol=1e-12)
