@@ -275,6 +275,11 @@ def run_ours(args):
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for trip in evs:  # torch creates the CUDA event on its first record
+        for e in trip:
+            e.record(stream)
+    start.record(stream)
+    end.record(stream)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)

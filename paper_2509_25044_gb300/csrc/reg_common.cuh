@@ -103,6 +103,9 @@ __device__ __forceinline__ float corner(const T *M, const Dims &g, const Axis &X
     return ld_vox(M, ((long long)iz * g.ny + iy) * g.nx + ix);
 }
 
+// (1-a) lo + a hi, exact at a = 0 and a = 1 (so u = 0 reproduces M bit for bit)
+__device__ __forceinline__ float lerp1(float a, float lo, float hi) { return fmaf(a, hi, (1.0f - a) * lo); }
+
 // value only
 template <typename T>
 __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
@@ -114,10 +117,10 @@ __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y,
     const float c010 = corner(M, g, X, Y, Z, 0, 1, 0), c110 = corner(M, g, X, Y, Z, 1, 1, 0);
     const float c001 = corner(M, g, X, Y, Z, 0, 0, 1), c101 = corner(M, g, X, Y, Z, 1, 0, 1);
     const float c011 = corner(M, g, X, Y, Z, 0, 1, 1), c111 = corner(M, g, X, Y, Z, 1, 1, 1);
-    const float e00 = fmaf(X.a, c100 - c000, c000), e10 = fmaf(X.a, c110 - c010, c010);
-    const float e01 = fmaf(X.a, c101 - c001, c001), e11 = fmaf(X.a, c111 - c011, c011);
-    const float f0 = fmaf(Y.a, e10 - e00, e00), f1 = fmaf(Y.a, e11 - e01, e01);
-    return fmaf(Z.a, f1 - f0, f0);
+    const float e00 = lerp1(X.a, c000, c100), e10 = lerp1(X.a, c010, c110);
+    const float e01 = lerp1(X.a, c001, c101), e11 = lerp1(X.a, c011, c111);
+    const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
+    return lerp1(Z.a, f0, f1);
 }
 
 // value and slope dJ/dphi
@@ -132,15 +135,15 @@ __device__ __forceinline__ float sample_grad(const T *M, const Dims &g, int x, i
     const float c001 = corner(M, g, X, Y, Z, 0, 0, 1), c101 = corner(M, g, X, Y, Z, 1, 0, 1);
     const float c011 = corner(M, g, X, Y, Z, 0, 1, 1), c111 = corner(M, g, X, Y, Z, 1, 1, 1);
     const float d00 = c100 - c000, d10 = c110 - c010, d01 = c101 - c001, d11 = c111 - c011;
-    const float e00 = fmaf(X.a, d00, c000), e10 = fmaf(X.a, d10, c010);
-    const float e01 = fmaf(X.a, d01, c001), e11 = fmaf(X.a, d11, c011);
-    const float f0 = fmaf(Y.a, e10 - e00, e00), f1 = fmaf(Y.a, e11 - e01, e01);
+    const float e00 = lerp1(X.a, c000, c100), e10 = lerp1(X.a, c010, c110);
+    const float e01 = lerp1(X.a, c001, c101), e11 = lerp1(X.a, c011, c111);
+    const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
     const float dy0 = e10 - e00, dy1 = e11 - e01;
     const float dx0 = fmaf(Y.a, d10 - d00, d00), dx1 = fmaf(Y.a, d11 - d01, d01);
     gz = (f1 - f0) * Z.slope;
     gy = fmaf(Z.a, dy1 - dy0, dy0) * Y.slope;
     gx = fmaf(Z.a, dx1 - dx0, dx0) * X.slope;
-    return fmaf(Z.a, f1 - f0, f0);
+    return lerp1(Z.a, f0, f1);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,17 +160,23 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+__device__ __forceinline__ int linear_tid() {
+    return (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+}
+
 // Fixed-order block sum of a double (every thread passes a value; the
-// result is valid in thread 0).  `sh` needs blockDim.x / 32 doubles.
+// result is valid in linear thread 0).  `sh` needs (threads / 32) doubles;
+// the block size must be a multiple of 32.
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int t = linear_tid();
+    const int w = t >> 5, l = t & 31;
     __syncthreads();
     if (l == 0) sh[w] = v;
     __syncthreads();
     double r = 0.0;
     if (w == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
+        const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
         r = l < nw ? sh[l] : 0.0;
         r = warp_sum(r);
     }
@@ -191,7 +200,7 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (linear_tid() == 0) {
         const unsigned prev = atomicAdd(counter, 1u);
         last = (prev == gridDim.x * gridDim.y * gridDim.z - 1);
     }

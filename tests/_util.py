@@ -12,6 +12,9 @@ GRAD_RTOL = 1e-4         # gradient, relative L2
 # BF16 storage vs the FP32-input oracle
 LOSS_RTOL_BF16 = 2e-3
 GRAD_RTOL_BF16 = 5e-3
+# drift of the gradient when FP32 images are stored as BF16 (input rounding,
+# not arithmetic; see the BF16 storage tests)
+GRAD_DRIFT_BF16 = 0.2
 
 
 def smooth_noise(shape, sigma, seed, scale=1.0):
