@@ -169,6 +169,31 @@ REG_API reg_status reg_jacdet_min(const float *u, reg_dims d, void *ws, size_t w
  * REG_ERR_TIMEOUT; the first latched code wins) and clears it. */
 REG_API reg_status reg_get_device_error(void *stream);
 
+/* MI similarity and (optionally) its gradient, like reg_loss_grad with an
+ * MI descriptor, but with no workspace argument: for callers that cannot
+ * allocate device memory -- a host application or framework that has
+ * reserved all GPU memory for its own pool and allows no other allocation,
+ * or a latency-critical loop that must never enter the allocator (cudaMalloc
+ * and cudaFree can synchronise the device).  The paper has no counterpart;
+ * this is a property of the library, not of the method.
+ *   - Scratch: a fixed 48 KiB array inside the library (joint histogram
+ *     u64[64*64] + adjoint table f32[64*64]), held by every GPU that loads
+ *     the library until the process exits.  bins must be in [8, 64]; larger
+ *     counts do not fit and return REG_ERR_SHAPE; a non-MI descriptor returns
+ *     REG_ERR_UNSUPPORTED.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - Every call shares the one array (it keeps the previous call's
+ *     contents; the histogram is cleared at the start of each call), so calls
+ *     that may overlap on the GPU -- different streams, or several host
+ *     threads -- race and must be serialised by the caller.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * sim_out: device double[1] (MI); grad_u: FP32 [3][N] or NULL (dC/du of
+ * C = -MI, overwritten).  Other arguments as reg_loss_grad. */
+REG_API reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                            const float *u, reg_dims d, int pad, double *sim_out, float *grad_u,
+                                            void *stream);
+
 /* Timing hook: the NEXT reg_iterate call on this host thread records the
  * caller's CUDA events (cudaEvent_t passed as void*) on its stream:
  * events[0] before the first sweep, events[1] between the sweeps (after the

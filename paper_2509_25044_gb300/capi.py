@@ -28,7 +28,7 @@ STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR
 # every C entry point declared in include/reg.h
 EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
-           "reg_debug_wait_flag", "reg_set_timing_events")
+           "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc")
 
 
 class RegError(RuntimeError):
@@ -82,6 +82,8 @@ def _lib():
         L.reg_get_device_error.argtypes = [_vp]
         L.reg_debug_wait_flag.argtypes = [_vp, ctypes.c_uint, ctypes.c_ulonglong, _vp]
         L.reg_set_timing_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        L.reg_mi_loss_grad_noalloc.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
+                                               ctypes.c_int, _vp, _vp, _vp]
         for name in EXPORTS:
             if name not in ("reg_version", "reg_status_string"):
                 getattr(L, name).restype = _st
@@ -262,3 +264,22 @@ def reg_set_timing_events(events):
         return
     arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
     _check(_lib().reg_set_timing_events(arr, 3), "reg_set_timing_events")
+
+
+def reg_mi_loss_grad_noalloc(loss: RegLossDesc, F, M, u, pad: int = REG_PAD_BORDER, sim=None, grad=None,
+                             with_grad: bool = True):
+    """MI similarity (+ gradient) through the entry point that needs no
+    workspace.  For callers that cannot allocate device memory the outputs
+    must be passed in (``sim``, ``grad``); allocating them here is only a
+    convenience for tests."""
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _need(u, (3,) + tuple(F.shape), torch.float32, "u")
+    if sim is None:
+        sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    if with_grad and grad is None:
+        grad = torch.empty_like(u)
+    _check(_lib().reg_mi_loss_grad_noalloc(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d,
+                                           int(pad), _ptr(sim), _ptr(grad if with_grad else None), _stream(F)),
+           "reg_mi_loss_grad_noalloc")
+    return (sim, grad) if with_grad else sim
