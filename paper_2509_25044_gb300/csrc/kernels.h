@@ -4,10 +4,33 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "reg_common.cuh"
 #include "step_common.cuh"
 
 namespace regk {
+
+// compile-time dispatch helpers for the launchers: the padding mode, the
+// image storage type and the moment storage type become template arguments
+template <int V>
+using IC = std::integral_constant<int, V>;
+template <typename Fn>
+inline void with_pad(int pad, Fn &&fn) {
+    if (pad == REG_PAD_ZEROS)
+        fn(IC<REG_PAD_ZEROS>{});
+    else
+        fn(IC<REG_PAD_BORDER>{});
+}
+template <typename Fn>
+inline void with_type(int dt, Fn &&fn) {  // fn receives a null pointer of the element type
+    if (dt == REG_BF16)
+        fn((__nv_bfloat16 *)nullptr);
+    else
+        fn((float *)nullptr);
+}
+template <typename P>
+using elem_t = std::remove_pointer_t<P>;
 
 // Tile-march geometry shared by every stencil / sweep kernel: a CTA owns a
 // 32 x 8 column tile in (x, y) and marches through a chunk of z-planes.
@@ -16,14 +39,21 @@ constexpr int TY = 8;
 constexpr int TILE_THREADS = TX * TY;
 constexpr int MAX_BINS = 64;
 constexpr int MAX_RADIUS = 7;  // LNCC window <= 15
+// MI histogram fixed point: one unit of kernel weight = 2^20 counts.  A CTA
+// adds at most MI_MAX_CTA_VOXELS voxels into its shared 32-bit bins, each
+// voxel at most (2/3)^2 of a unit per bin: 8192 * 0.445 * 2^20 < 2^32, so a
+// bin cannot wrap.
+constexpr float MI_FIXED_SCALE = 1048576.0f;
+constexpr int MI_MAX_CTA_VOXELS = 8192;
 
 struct MarchGrid {
     int tiles_x, tiles_y, chunks, zc;
     long long blocks() const { return (long long)tiles_x * tiles_y * chunks; }
 };
 
-// target_blocks: roughly how many CTAs to aim for; min_zc: smallest chunk
-MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc);
+// target_blocks: roughly how many CTAs to aim for; min_zc / max_zc: bounds
+// on the z-chunk (max_zc wins)
+MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc, int max_zc = 1 << 30);
 
 struct MiParams {
     float f_lo, f_scale, m_lo, m_scale;  // vhat = clamp((v - lo) * scale, 0, 1)

@@ -58,9 +58,9 @@ size_t lncc_smem_bytes(int r, int K) {
     return sizeof(float) * ((size_t)K * RH * RW + (size_t)K * RH * TX + (size_t)W * K * TILE_THREADS);
 }
 
-template <typename T, bool COEF>
+template <typename T, bool COEF, int PAD>
 __global__ void __launch_bounds__(TILE_THREADS)
-    lncc_stats_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, int pad,
+    lncc_stats_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                       LnccParams P, int zc, float *__restrict__ coef, double *__restrict__ partials,
                       unsigned *__restrict__ counter, double *__restrict__ sim_out, unsigned *err) {
     extern __shared__ float smem[];
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             if (qin && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
                 const long long p = (long long)q * g.nxy + (long long)gy * g.nx + gx;
                 f = ld_vox(F, p) - shF;
-                j = sample(M, g, gx, gy, q, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p), pad) - shJ;
+                j = sample<T, PAD>(M, g, gx, gy, q, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p)) - shJ;
             }
             s5[e] = f;
             s5[plane + e] = j;
@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(TILE_THREADS)
     }
 }
 
-template <typename T, typename MT, bool STEP>
+template <typename T, typename MT, bool STEP, int PAD>
 __global__ void __launch_bounds__(TILE_THREADS)
     lncc_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
-                       int pad, LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
+                       LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
                        float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                        double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
                        unsigned *err) {
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 for (int c = 0; c < 3; ++c) nxt[c] = __ldg(u + c * g.n + p + g.nxy);
             }
             float sx, sy, sz;
-            const float jv = sample_grad(M, g, x, y, zo, cur[0], cur[1], cur[2], pad, sx, sy, sz);
+            const float jv = sample_grad<T, PAD>(M, g, x, y, zo, cur[0], cur[1], cur[2], sx, sy, sz);
             const float fv = ld_vox(F, p);
             const float gj = fmaf(fv, Sa[2], fmaf(2.0f * jv, Sa[1], Sa[0]));
             const float gs[3] = {gj * sx, gj * sy, gj * sz};
@@ -278,63 +278,39 @@ __global__ void __launch_bounds__(TILE_THREADS)
 
 MarchGrid lncc_grid(const Dims &g, int r) { return march_grid(g, 6LL * num_sms() * 3, 4 * r > 16 ? 4 * r : 16); }
 
-template <typename T>
-static cudaError_t stats_dispatch(bool with_coef, dim3 grid, size_t smem, cudaStream_t s, const void *F,
-                                  const void *M, const float *u, const Dims &g, int pad, const LnccParams &P,
-                                  int zc, float *coef, double *partials, unsigned *counter, double *sim_out) {
-    cudaError_t e;
-    if (with_coef) {
-        e = cudaFuncSetAttribute(lncc_stats_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        lncc_stats_kernel<T, true><<<grid, dim3(TX, TY), smem, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc,
-                                                                    coef, partials, counter, sim_out, error_word());
-    } else {
-        e = cudaFuncSetAttribute(lncc_stats_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        lncc_stats_kernel<T, false><<<grid, dim3(TX, TY), smem, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc,
-                                                                     coef, partials, counter, sim_out, error_word());
-    }
-    return cudaGetLastError();
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_lncc_stats(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                               const LnccParams &P, float *coef, double *partials, unsigned *counter,
                               double *sim_out, cudaStream_t s) {
     const MarchGrid G = lncc_grid(g, P.r);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 5);
-    if (dt == REG_BF16)
-        return stats_dispatch<__nv_bfloat16>(coef != nullptr, grid, smem, s, F, M, u, g, pad, P, G.zc, coef,
-                                             partials, counter, sim_out);
-    return stats_dispatch<float>(coef != nullptr, grid, smem, s, F, M, u, g, pad, P, G.zc, coef, partials, counter,
-                                 sim_out);
-}
-
-template <typename T, typename MT, bool STEP>
-static cudaError_t sweep2_launch(dim3 grid, size_t smem, cudaStream_t s, const void *F, const void *M,
-                                 const float *u, const Dims &g, int pad, const LnccParams &P, int zc,
-                                 const float *coef, float *grad_out, float *u_out, void *m, void *v,
-                                 const StepParams &S, double *partials, unsigned *counter, double *r_out) {
-    cudaError_t e = cudaFuncSetAttribute(lncc_sweep2_kernel<T, MT, STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    unsigned *err = error_word();
+    cudaError_t e = cudaSuccess;
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            if (coef) {
+                e = allow_smem(lncc_stats_kernel<T, true, PD>, smem);
+                if (e == cudaSuccess)
+                    lncc_stats_kernel<T, true, PD><<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, G.zc,
+                                                                             coef, partials, counter, sim_out, err);
+            } else {
+                e = allow_smem(lncc_stats_kernel<T, false, PD>, smem);
+                if (e == cudaSuccess)
+                    lncc_stats_kernel<T, false, PD><<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P,
+                                                                              G.zc, coef, partials, counter, sim_out,
+                                                                              err);
+            }
+        });
+    });
     if (e != cudaSuccess) return e;
-    lncc_sweep2_kernel<T, MT, STEP><<<grid, dim3(TX, TY), smem, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc,
-                                                                     coef, grad_out, u_out, (MT *)m, (MT *)v, S,
-                                                                     partials, counter, r_out, error_word());
     return cudaGetLastError();
-}
-
-template <typename T, typename MT>
-static cudaError_t sweep2_step(bool step, dim3 grid, size_t smem, cudaStream_t s, const void *F, const void *M,
-                               const float *u, const Dims &g, int pad, const LnccParams &P, int zc,
-                               const float *coef, float *grad_out, float *u_out, void *m, void *v,
-                               const StepParams &S, double *partials, unsigned *counter, double *r_out) {
-    if (step)
-        return sweep2_launch<T, MT, true>(grid, smem, s, F, M, u, g, pad, P, zc, coef, grad_out, u_out, m, v, S,
-                                          partials, counter, r_out);
-    return sweep2_launch<T, MT, false>(grid, smem, s, F, M, u, g, pad, P, zc, coef, grad_out, u_out, m, v, S,
-                                       partials, counter, r_out);
 }
 
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
@@ -342,21 +318,34 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                                float *u_out, void *m, void *v, int mdt, const StepParams &S,
                                double *partials, unsigned *counter, double *r_out, cudaStream_t s) {
     const MarchGrid G = lncc_grid(g, P.r);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 3);
-    const bool mb = step && mdt == REG_BF16;
-    if (dt == REG_BF16) {
-        if (mb)
-            return sweep2_step<__nv_bfloat16, __nv_bfloat16>(step, grid, smem, s, F, M, u, g, pad, P, G.zc, coef,
-                                                             grad_out, u_out, m, v, S, partials, counter, r_out);
-        return sweep2_step<__nv_bfloat16, float>(step, grid, smem, s, F, M, u, g, pad, P, G.zc, coef, grad_out,
-                                                 u_out, m, v, S, partials, counter, r_out);
-    }
-    if (mb)
-        return sweep2_step<float, __nv_bfloat16>(step, grid, smem, s, F, M, u, g, pad, P, G.zc, coef, grad_out,
-                                                 u_out, m, v, S, partials, counter, r_out);
-    return sweep2_step<float, float>(step, grid, smem, s, F, M, u, g, pad, P, G.zc, coef, grad_out, u_out, m, v, S,
-                                     partials, counter, r_out);
+    unsigned *err = error_word();
+    cudaError_t e = cudaSuccess;
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            if (!step) {
+                e = allow_smem(lncc_sweep2_kernel<T, float, false, PD>, smem);
+                if (e == cudaSuccess)
+                    lncc_sweep2_kernel<T, float, false, PD><<<grid, block, smem, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (float *)m, (float *)v, S,
+                        partials, counter, r_out, err);
+                return;
+            }
+            with_type(mdt, [&](auto mp) {
+                using MT = elem_t<decltype(mp)>;
+                e = allow_smem(lncc_sweep2_kernel<T, MT, true, PD>, smem);
+                if (e == cudaSuccess)
+                    lncc_sweep2_kernel<T, MT, true, PD><<<grid, block, smem, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
+                        partials, counter, r_out, err);
+            });
+        });
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 }  // namespace regk

@@ -4,12 +4,13 @@
 //   sweep 1 (mi_hist_kernel): warp M on chip, map F and the warped value to
 //     bin coordinates, add the 4 x 4 cubic B-spline outer product of each
 //     voxel into a per-CTA joint histogram in shared memory.  Entries are
-//     unsigned 64-bit fixed point (2^-32 per unit weight), so the sums are
-//     exact integers and the histogram does not depend on the order of the
-//     atomics (deterministic).  Each CTA then adds its non-zero bins to the
-//     global histogram (integer atomics, order-free).  No N x B Parzen block
-//     is ever materialised (the memory the paper removes).
-//   finalise (mi_finalize_kernel): p = hist / (2^32 N) in FP64, marginals
+//     unsigned fixed point (2^-20 per unit weight: 32-bit per CTA, 64-bit
+//     global), so the sums are exact integers and the histogram does not
+//     depend on the order of the atomics (deterministic).  Each CTA then adds
+//     its non-zero bins to the global histogram (integer atomics, order-
+//     free).  No N x B Parzen block is ever materialised (the memory the
+//     paper removes).
+//   finalise (mi_finalize_kernel): p = hist / (2^20 N) in FP64, marginals
 //     as row / column sums, MI = sum p log(p / (pI pJ)), and the FP32 table
 //     G'[m][n] = -(B-3) m_scale / N * log(p / (pI pJ)) of the adjoint.
 //   sweep 2 (mi_sweep2_kernel): warp again with slope, the adjoint
@@ -52,15 +53,35 @@ __device__ __forceinline__ float to_bin(float v, float lo, float scale, int B) {
     return fmaf(t, (float)(B - 3), 1.0f);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS) mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M,
-                                                               const float *__restrict__ u, Dims g, int pad,
-                                                               MiParams P, int zc,
-                                                               unsigned long long *__restrict__ hist) {
-    __shared__ unsigned long long sh[MAX_BINS * MAX_BINS];
+// Shared histogram of one CTA: HIST_COPIES private copies (lane % copies
+// picks one), each padded by one word so that the same bin of different
+// copies falls in different banks.  Lanes of a warp usually see the same
+// bins (neighbouring voxels), so the copies cut same-address serialisation.
+constexpr int HIST_WORDS = 8 * (32 * 32 + 1);  // >= copies * (B*B + 1) for every B <= 64
+__host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 8 : 2; }
+
+__device__ __forceinline__ void flush16(unsigned *shc, int K, int B, const unsigned acc[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        if (acc[e]) atomicAdd(shc + K + (e >> 2) * B + (e & 3), acc[e]);
+}
+
+// Each thread marches its (x, y) column through the z-chunk.  While its
+// voxels stay in the same 4 x 4 bin block K (most consecutive voxels do on
+// smooth or piecewise-constant images), the thread only adds its fixed-point
+// weights into registers; the 16 sums go to shared memory when the block
+// changes.  Bins are 32-bit fixed point (MI_FIXED_SCALE); the per-CTA voxel
+// cap keeps them from wrapping; each CTA adds its bins (summed over the
+// copies) to the global 64-bit histogram.
+template <typename T, int PAD>
+__global__ void __launch_bounds__(TILE_THREADS, 4) mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M,
+                                                                  const float *__restrict__ u, Dims g, MiParams P,
+                                                                  int zc, unsigned long long *__restrict__ hist) {
+    __shared__ unsigned sh[HIST_WORDS];
     const int B = P.bins, BB = B * B;
+    const int copies = hist_copies(B), pitch = BB + 1;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < BB; i += TILE_THREADS) sh[i] = 0ull;
+    for (int i = tid; i < copies * pitch; i += TILE_THREADS) sh[i] = 0u;
     __syncthreads();
 
     const int x = blockIdx.x * TX + threadIdx.x;
@@ -68,26 +89,38 @@ __global__ void __launch_bounds__(TILE_THREADS) mi_hist_kernel(const T *__restri
     const int z0 = blockIdx.z * zc;
     const int z1 = min(g.nz, z0 + zc);
     if (x < g.nx && y < g.ny) {
+        unsigned *shc = sh + (threadIdx.x % copies) * pitch;
+        const long long col = (long long)y * g.nx + x;
+        int K = -1;
+        unsigned acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0u;
         for (int z = z0; z < z1; ++z) {
-            const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+            const long long p = (long long)z * g.nxy + col;
             const float fv = ld_vox(F, p);
-            const float jv = sample(M, g, x, y, z, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p), pad);
+            const float jv =
+                sample<T, PAD>(M, g, x, y, z, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p));
             float wf[4], wj[4];
             const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
             const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
+            const int key = iF * B + iJ;
+            if (key != K) {
+                if (K >= 0) flush16(shc, K, B, acc);
+                K = key;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const unsigned long long q = __float2ull_rn(wf[a] * wj[b] * 4294967296.0f);
-                    if (q) atomicAdd(&sh[(iF + a) * B + iJ + b], q);
-                }
+                for (int e = 0; e < 16; ++e) acc[e] = 0u;
             }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a * 4 + b] += __float2uint_rn(wf[a] * wj[b] * MI_FIXED_SCALE);
         }
+        if (K >= 0) flush16(shc, K, B, acc);
     }
     __syncthreads();
     for (int i = tid; i < BB; i += TILE_THREADS) {
-        const unsigned long long v = sh[i];
+        unsigned long long v = 0;
+        for (int c = 0; c < copies; ++c) v += sh[c * pitch + i];
         if (v) atomicAdd(hist + i, v);
     }
 }
@@ -131,9 +164,9 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
     }
 }
 
-template <typename T, typename MT, bool STEP>
-__global__ void __launch_bounds__(TILE_THREADS)
-    mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, int pad,
+template <typename T, typename MT, bool STEP, int PAD>
+__global__ void __launch_bounds__(TILE_THREADS, 3)
+    mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                      MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                      double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
@@ -150,29 +183,53 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const int z0 = blockIdx.z * zc;
     const int z1 = min(g.nz, z0 + zc);
     float rpart = 0.0f;
-    if (x < g.nx && y < g.ny) {
-        const long long col = (long long)y * g.nx + x;
+    const bool act = x < g.nx;
+    if (y < g.ny) {  // warp-uniform: every lane of the row runs the loop (x-neighbours by shuffle)
+        const int lane = threadIdx.x;
+        // lanes past the x edge shadow the last column (loads stay in bounds,
+        // nothing is stored for them)
+        const int xe = act ? x : g.nx - 1;
+        const long long col = (long long)y * g.nx + xe;
+        const bool hxm = act && x > 0, hxp = act && x + 1 < g.nx;
+        // registers roll one plane ahead: u at z-1 / z / z+1, and F, m, v of
+        // the next plane are requested before the current plane is computed
         float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
+        float fcur, mcur[3] = {0.f, 0.f, 0.f}, vcur[3] = {0.f, 0.f, 0.f};
         {
             const long long p = (long long)z0 * g.nxy + col;
 #pragma unroll
             for (int c = 0; c < 3; ++c) cur[c] = __ldg(u + c * g.n + p);
-            if (STEP && z0 > 0) {
+            fcur = ld_vox(F, p);
+            if (STEP) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) prv[c] = __ldg(u + c * g.n + p - g.nxy);
+                for (int c = 0; c < 3; ++c) {
+                    mcur[c] = ld_moment(m, c * g.n + p);
+                    vcur[c] = ld_moment(v, c * g.n + p);
+                    if (z0 > 0) prv[c] = __ldg(u + c * g.n + p - g.nxy);
+                }
             }
         }
         for (int z = z0; z < z1; ++z) {
             const long long p = (long long)z * g.nxy + col;
+            float fnxt = 0.0f, mnxt[3] = {0.f, 0.f, 0.f}, vnxt[3] = {0.f, 0.f, 0.f};
             if (z + 1 < g.nz) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) nxt[c] = __ldg(u + c * g.n + p + g.nxy);
             }
-            const float fv = ld_vox(F, p);
+            if (z + 1 < z1) {
+                fnxt = ld_vox(F, p + g.nxy);
+                if (STEP) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        mnxt[c] = ld_moment(m, c * g.n + p + g.nxy);
+                        vnxt[c] = ld_moment(v, c * g.n + p + g.nxy);
+                    }
+                }
+            }
             float sx, sy, sz;
-            const float jv = sample_grad(M, g, x, y, z, cur[0], cur[1], cur[2], pad, sx, sy, sz);
+            const float jv = sample_grad<T, PAD>(M, g, xe, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
             float wf[4], dj[4];
-            const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
+            const int iF = bspline_weights(to_bin(fcur, P.f_lo, P.f_scale, B), B, wf) - 1;
             const float tj = (jv - P.m_lo) * P.m_scale;
             const int iJ = bspline_dweights(to_bin(jv, P.m_lo, P.m_scale, B), B, dj) - 1;
             float gj = 0.0f;
@@ -183,24 +240,38 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 gj = fmaf(wf[a], t, gj);
             }
             if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
-            float gs[3] = {gj * sx, gj * sy, gj * sz};
+            const float gs[3] = {gj * sx, gj * sy, gj * sz};
             if (STEP) {
-                float gR[3];
-                diffusion_at(u, g, x, y, z, p, cur, prv, nxt, gR, rpart);
+                float xm[3], xp[3], gR[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
-                    if (grad_out) grad_out[c * g.n + p] = gt;
-                    u_out[c * g.n + p] = adam_elem(cur[c], gt, m, v, c * g.n + p, S);
+                    const float dn = __shfl_down_sync(0xffffffffu, cur[c], 1);
+                    const float up = __shfl_up_sync(0xffffffffu, cur[c], 1);
+                    xp[c] = (lane == TX - 1 && hxp) ? __ldg(u + c * g.n + p + 1) : dn;
+                    xm[c] = (lane == 0 && hxm) ? __ldg(u + c * g.n + p - 1) : up;
                 }
-            } else {
+                float rp = 0.0f;
+                diffusion_xn(u, g, y, z, p, hxm, hxp, cur, prv, nxt, xm, xp, gR, rp);
+                if (act) {
+                    rpart += rp;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                        if (grad_out) grad_out[c * g.n + p] = gt;
+                        u_out[c * g.n + p] = adam_update(cur[c], gt, mcur[c], vcur[c], m, v, c * g.n + p, S);
+                    }
+                }
+            } else if (act) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) grad_out[c * g.n + p] = gs[c];
             }
+            fcur = fnxt;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 prv[c] = cur[c];
                 cur[c] = nxt[c];
+                mcur[c] = mnxt[c];
+                vcur[c] = vnxt[c];
             }
         }
     }
@@ -224,42 +295,31 @@ __global__ void __launch_bounds__(TILE_THREADS)
     }
 }
 
-MarchGrid mi_hist_grid(const Dims &g) { return march_grid(g, 2LL * num_sms() * 4, 1); }
+MarchGrid mi_hist_grid(const Dims &g) {
+    return march_grid(g, 2LL * num_sms() * 4, 1, MI_MAX_CTA_VOXELS / TILE_THREADS);
+}
 MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                            const MiParams &P, unsigned long long *hist, cudaStream_t s) {
     const MarchGrid G = mi_hist_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
-    if (dt == REG_BF16)
-        mi_hist_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)F, (const __nv_bfloat16 *)M,
-                                                              u, g, pad, P, G.zc, hist);
-    else
-        mi_hist_kernel<float><<<grid, block, 0, s>>>((const float *)F, (const float *)M, u, g, pad, P, G.zc, hist);
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            mi_hist_kernel<T, decltype(pd)::value>
+                <<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc, hist);
+        });
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
                                double *sim_out, cudaStream_t s) {
-    const double inv_total = 1.0 / (4294967296.0 * (double)N);
+    const double inv_total = 1.0 / ((double)MI_FIXED_SCALE * (double)N);
     const double gscale = -(double)(P.bins - 3) * (double)P.m_scale / (double)N;
     mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, inv_total, gscale, Gtab, sim_out, error_word());
     return cudaGetLastError();
-}
-
-template <typename T, typename MT>
-static void mi_sweep2_dispatch(bool step, dim3 grid, dim3 block, cudaStream_t s, const void *F, const void *M,
-                               const float *u, const Dims &g, int pad, const MiParams &P, int zc,
-                               const float *Gtab, float *grad_out, float *u_out, void *m, void *v,
-                               const StepParams &S, double *partials, unsigned *counter, double *r_out) {
-    if (step)
-        mi_sweep2_kernel<T, MT, true><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc, Gtab,
-                                                             grad_out, u_out, (MT *)m, (MT *)v, S, partials,
-                                                             counter, r_out, error_word());
-    else
-        mi_sweep2_kernel<T, MT, false><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, pad, P, zc, Gtab,
-                                                              grad_out, u_out, (MT *)m, (MT *)v, S, partials,
-                                                              counter, r_out, error_word());
 }
 
 cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
@@ -268,22 +328,25 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                              unsigned *counter, double *r_out, cudaStream_t s) {
     const MarchGrid G = mi_sweep_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
-    const bool mb = step && mdt == REG_BF16;
-    if (dt == REG_BF16) {
-        if (mb)
-            mi_sweep2_dispatch<__nv_bfloat16, __nv_bfloat16>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab,
-                                                             grad_out, u_out, m, v, S, partials, counter, r_out);
-        else
-            mi_sweep2_dispatch<__nv_bfloat16, float>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out,
-                                                     u_out, m, v, S, partials, counter, r_out);
-    } else {
-        if (mb)
-            mi_sweep2_dispatch<float, __nv_bfloat16>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out,
-                                                     u_out, m, v, S, partials, counter, r_out);
-        else
-            mi_sweep2_dispatch<float, float>(step, grid, block, s, F, M, u, g, pad, P, G.zc, Gtab, grad_out, u_out,
-                                             m, v, S, partials, counter, r_out);
-    }
+    unsigned *err = error_word();
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            if (!step) {
+                mi_sweep2_kernel<T, float, false, PD><<<grid, block, 0, s>>>(
+                    (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m, (float *)v, S,
+                    partials, counter, r_out, err);
+                return;
+            }
+            with_type(mdt, [&](auto mp) {
+                using MT = elem_t<decltype(mp)>;
+                mi_sweep2_kernel<T, MT, true, PD><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc,
+                                                                        Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
+                                                                        partials, counter, r_out, err);
+            });
+        });
+    });
     return cudaGetLastError();
 }
 

@@ -47,42 +47,31 @@ __device__ __forceinline__ float ld_vox(const __nv_bfloat16 *p, long long i) {
 //   ZEROS : corners outside the volume read as 0.
 // ---------------------------------------------------------------------------
 struct Axis {
-    int i0;       // lower corner index (may be out of range in ZEROS mode)
+    int i0, i1;   // corner indices (may be out of range in ZEROS mode)
     float a;      // fraction in [0,1]
     float slope;  // 1 or 0 (clamped axis)
     bool v0, v1;  // corner validity (ZEROS)
 };
 
-__device__ __forceinline__ Axis axis_setup(int p, float uu, int n, int pad) {
+template <int PAD>
+__device__ __forceinline__ Axis axis_setup(int p, float uu, int n) {
     Axis ax;
     // non-finite or absurd displacements are clamped; any |u| > 2^20 voxels
     // is outside every supported volume, so border / zero semantics hold.
-    if (!(uu == uu)) uu = 0.0f;
-    uu = fminf(fmaxf(uu, -1048576.0f), 1048576.0f);
+    uu = (uu == uu) ? fminf(fmaxf(uu, -1048576.0f), 1048576.0f) : 0.0f;
     const float fl = floorf(uu);
-    float a = uu - fl;
+    const float a = uu - fl;
     const int f = p + (int)fl;
-    if (pad == REG_PAD_BORDER) {
+    if (PAD == REG_PAD_BORDER) {
+        const bool lowc = f < 0, highc = f > n - 2;
+        ax.slope = (n > 1 && !lowc && (!highc || (f == n - 1 && a == 0.0f))) ? 1.0f : 0.0f;
+        ax.i0 = max(lowc ? 0 : (highc ? n - 2 : f), 0);
+        ax.i1 = min(ax.i0 + 1, n - 1);
+        ax.a = (n == 1 || lowc) ? 0.0f : (highc ? 1.0f : a);
         ax.v0 = ax.v1 = true;
-        if (n == 1) {
-            ax.i0 = 0;
-            ax.a = 0.0f;
-            ax.slope = 0.0f;
-        } else if (f < 0) {
-            ax.i0 = 0;
-            ax.a = 0.0f;
-            ax.slope = 0.0f;
-        } else if (f > n - 2) {
-            ax.slope = (f == n - 1 && a == 0.0f) ? 1.0f : 0.0f;
-            ax.i0 = n - 2;
-            ax.a = 1.0f;
-        } else {
-            ax.i0 = f;
-            ax.a = a;
-            ax.slope = 1.0f;
-        }
     } else {
         ax.i0 = f;
+        ax.i1 = f + 1;
         ax.a = a;
         ax.slope = 1.0f;
         ax.v0 = (unsigned)f < (unsigned)n;
@@ -91,52 +80,64 @@ __device__ __forceinline__ Axis axis_setup(int p, float uu, int n, int pad) {
     return ax;
 }
 
-template <typename T>
-__device__ __forceinline__ float corner(const T *M, const Dims &g, const Axis &X, const Axis &Y, const Axis &Z,
-                                        int bx, int by, int bz) {
-    const bool ok = (bx ? X.v1 : X.v0) && (by ? Y.v1 : Y.v0) && (bz ? Z.v1 : Z.v0);
-    if (!ok) return 0.0f;
-    // BORDER mode with n == 1 uses i0 = 0, i0+1 = 1 with weight 0: clamp index
-    const int ix = min(X.i0 + bx, g.nx - 1);
-    const int iy = min(Y.i0 + by, g.ny - 1);
-    const int iz = min(Z.i0 + bz, g.nz - 1);
-    return ld_vox(M, ((long long)iz * g.ny + iy) * g.nx + ix);
+// the 8 corner values c[bz*4 + by*2 + bx] (0 outside the volume in ZEROS mode)
+template <typename T, int PAD>
+__device__ __forceinline__ void gather8(const T *M, const Dims &g, const Axis &X, const Axis &Y, const Axis &Z,
+                                        float c[8]) {
+    const long long r00 = ((long long)Z.i0 * g.ny + Y.i0) * g.nx, r01 = ((long long)Z.i0 * g.ny + Y.i1) * g.nx;
+    const long long r10 = ((long long)Z.i1 * g.ny + Y.i0) * g.nx, r11 = ((long long)Z.i1 * g.ny + Y.i1) * g.nx;
+    if (PAD == REG_PAD_BORDER) {
+        c[0] = ld_vox(M, r00 + X.i0);
+        c[1] = ld_vox(M, r00 + X.i1);
+        c[2] = ld_vox(M, r01 + X.i0);
+        c[3] = ld_vox(M, r01 + X.i1);
+        c[4] = ld_vox(M, r10 + X.i0);
+        c[5] = ld_vox(M, r10 + X.i1);
+        c[6] = ld_vox(M, r11 + X.i0);
+        c[7] = ld_vox(M, r11 + X.i1);
+    } else {
+        const bool y0z0 = Y.v0 && Z.v0, y1z0 = Y.v1 && Z.v0, y0z1 = Y.v0 && Z.v1, y1z1 = Y.v1 && Z.v1;
+        c[0] = (X.v0 && y0z0) ? ld_vox(M, r00 + X.i0) : 0.0f;
+        c[1] = (X.v1 && y0z0) ? ld_vox(M, r00 + X.i1) : 0.0f;
+        c[2] = (X.v0 && y1z0) ? ld_vox(M, r01 + X.i0) : 0.0f;
+        c[3] = (X.v1 && y1z0) ? ld_vox(M, r01 + X.i1) : 0.0f;
+        c[4] = (X.v0 && y0z1) ? ld_vox(M, r10 + X.i0) : 0.0f;
+        c[5] = (X.v1 && y0z1) ? ld_vox(M, r10 + X.i1) : 0.0f;
+        c[6] = (X.v0 && y1z1) ? ld_vox(M, r11 + X.i0) : 0.0f;
+        c[7] = (X.v1 && y1z1) ? ld_vox(M, r11 + X.i1) : 0.0f;
+    }
 }
 
 // (1-a) lo + a hi, exact at a = 0 and a = 1 (so u = 0 reproduces M bit for bit)
 __device__ __forceinline__ float lerp1(float a, float lo, float hi) { return fmaf(a, hi, (1.0f - a) * lo); }
 
 // value only
-template <typename T>
+template <typename T, int PAD>
 __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
-                                        float uz, int pad) {
-    const Axis X = axis_setup(x, ux, g.nx, pad);
-    const Axis Y = axis_setup(y, uy, g.ny, pad);
-    const Axis Z = axis_setup(z, uz, g.nz, pad);
-    const float c000 = corner(M, g, X, Y, Z, 0, 0, 0), c100 = corner(M, g, X, Y, Z, 1, 0, 0);
-    const float c010 = corner(M, g, X, Y, Z, 0, 1, 0), c110 = corner(M, g, X, Y, Z, 1, 1, 0);
-    const float c001 = corner(M, g, X, Y, Z, 0, 0, 1), c101 = corner(M, g, X, Y, Z, 1, 0, 1);
-    const float c011 = corner(M, g, X, Y, Z, 0, 1, 1), c111 = corner(M, g, X, Y, Z, 1, 1, 1);
-    const float e00 = lerp1(X.a, c000, c100), e10 = lerp1(X.a, c010, c110);
-    const float e01 = lerp1(X.a, c001, c101), e11 = lerp1(X.a, c011, c111);
+                                        float uz) {
+    const Axis X = axis_setup<PAD>(x, ux, g.nx);
+    const Axis Y = axis_setup<PAD>(y, uy, g.ny);
+    const Axis Z = axis_setup<PAD>(z, uz, g.nz);
+    float c[8];
+    gather8<T, PAD>(M, g, X, Y, Z, c);
+    const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
+    const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);
     const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
     return lerp1(Z.a, f0, f1);
 }
 
 // value and slope dJ/dphi
-template <typename T>
+template <typename T, int PAD>
 __device__ __forceinline__ float sample_grad(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
-                                             float uz, int pad, float &gx, float &gy, float &gz) {
-    const Axis X = axis_setup(x, ux, g.nx, pad);
-    const Axis Y = axis_setup(y, uy, g.ny, pad);
-    const Axis Z = axis_setup(z, uz, g.nz, pad);
-    const float c000 = corner(M, g, X, Y, Z, 0, 0, 0), c100 = corner(M, g, X, Y, Z, 1, 0, 0);
-    const float c010 = corner(M, g, X, Y, Z, 0, 1, 0), c110 = corner(M, g, X, Y, Z, 1, 1, 0);
-    const float c001 = corner(M, g, X, Y, Z, 0, 0, 1), c101 = corner(M, g, X, Y, Z, 1, 0, 1);
-    const float c011 = corner(M, g, X, Y, Z, 0, 1, 1), c111 = corner(M, g, X, Y, Z, 1, 1, 1);
-    const float d00 = c100 - c000, d10 = c110 - c010, d01 = c101 - c001, d11 = c111 - c011;
-    const float e00 = lerp1(X.a, c000, c100), e10 = lerp1(X.a, c010, c110);
-    const float e01 = lerp1(X.a, c001, c101), e11 = lerp1(X.a, c011, c111);
+                                             float uz, float &gx, float &gy, float &gz) {
+    const Axis X = axis_setup<PAD>(x, ux, g.nx);
+    const Axis Y = axis_setup<PAD>(y, uy, g.ny);
+    const Axis Z = axis_setup<PAD>(z, uz, g.nz);
+    float c[8];
+    gather8<T, PAD>(M, g, X, Y, Z, c);
+    const float d00 = c[1] - c[0], d10 = c[3] - c[2], d01 = c[5] - c[4], d11 = c[7] - c[6];
+    const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
+    const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);
     const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
     const float dy0 = e10 - e00, dy1 = e11 - e01;
     const float dx0 = fmaf(Y.a, d10 - d00, d00), dx1 = fmaf(Y.a, d11 - d01, d01);

@@ -31,7 +31,7 @@ int num_sms() {
     return cached;
 }
 
-MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc) {
+MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc, int max_zc) {
     MarchGrid G;
     G.tiles_x = (g.nx + TX - 1) / TX;
     G.tiles_y = (g.ny + TY - 1) / TY;
@@ -39,6 +39,8 @@ MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc) {
     long long chunks = (target_blocks + tiles - 1) / tiles;
     const long long max_chunks = (g.nz + min_zc - 1) / min_zc;
     if (chunks > max_chunks) chunks = max_chunks;
+    const long long min_chunks = (g.nz + max_zc - 1) / max_zc;
+    if (chunks < min_chunks) chunks = min_chunks;
     if (chunks < 1) chunks = 1;
     G.zc = (int)((g.nz + chunks - 1) / chunks);
     G.chunks = (g.nz + G.zc - 1) / G.zc;

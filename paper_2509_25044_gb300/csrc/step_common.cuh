@@ -33,6 +33,19 @@ __device__ __forceinline__ float adam_elem(float u, float g, MT *m, MT *v, long 
     return u - S.lr_bc1 * (mn / denom);
 }
 
+// Same update with the old moments already loaded (m0, v0).
+template <typename MT>
+__device__ __forceinline__ float adam_update(float u, float g, float m0, float v0, MT *m, MT *v, long long i,
+                                             const StepParams &S) {
+    const float gs = S.gscale * g;
+    const float mn = fmaf(S.b1, m0, (1.0f - S.b1) * gs);
+    const float vn = fmaf(S.b2, v0, (1.0f - S.b2) * gs * gs);
+    st_moment(m, i, mn);
+    st_moment(v, i, vn);
+    const float denom = fmaf(sqrtf(vn), S.rsqrt_bc2, S.eps);
+    return u - S.lr_bc1 * (mn / denom);
+}
+
 // Diffusion regulariser at voxel (x,y,z) for all three channels.
 //   grad:  gR_c = (2/N) sum_d [ (u_c(p) - u_c(p+e_d)) [p+e_d inside]
 //                             + (u_c(p) - u_c(p-e_d)) [p-e_d inside] ]
@@ -57,6 +70,42 @@ __device__ __forceinline__ void diffusion_at(const float *__restrict__ u, const 
             rpart = fmaf(d, d, rpart);
         }
         if (hxm) acc += c0 - __ldg(uc + p - 1);
+        if (hyp) {
+            const float d = __ldg(uc + p + g.nx) - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hym) acc += c0 - __ldg(uc + p - g.nx);
+        if (hzp) {
+            const float d = nxt[c] - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hzm) acc += c0 - prv[c];
+        gR[c] = acc;
+    }
+}
+
+// The same stencil with the x-neighbours supplied by the caller (a warp
+// holds a row of x, so they come from lane shuffles); hxm / hxp say whether
+// x-1 / x+1 lie inside the volume.
+__device__ __forceinline__ void diffusion_xn(const float *__restrict__ u, const Dims &g, int y, int z, long long p,
+                                             bool hxm, bool hxp, const float cur[3], const float prv[3],
+                                             const float nxt[3], const float xm[3], const float xp[3], float gR[3],
+                                             float &rpart) {
+    const bool hym = y > 0, hyp = y + 1 < g.ny;
+    const bool hzm = z > 0, hzp = z + 1 < g.nz;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float *uc = u + (long long)c * g.n;
+        const float c0 = cur[c];
+        float acc = 0.0f;
+        if (hxp) {
+            const float d = xp[c] - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hxm) acc += c0 - xm[c];
         if (hyp) {
             const float d = __ldg(uc + p + g.nx) - c0;
             acc -= d;

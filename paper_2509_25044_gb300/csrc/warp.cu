@@ -8,9 +8,9 @@
 
 namespace regk {
 
-template <typename T, bool SLOPE>
+template <typename T, bool SLOPE, int PAD>
 __global__ void __launch_bounds__(TILE_THREADS) warp_kernel(const T *__restrict__ M, const float *__restrict__ u,
-                                                            Dims g, int pad, int zc, float *__restrict__ J,
+                                                            Dims g, int zc, float *__restrict__ J,
                                                             float *__restrict__ dJ) {
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
@@ -21,33 +21,30 @@ __global__ void __launch_bounds__(TILE_THREADS) warp_kernel(const T *__restrict_
         const float ux = __ldg(u + p), uy = __ldg(u + g.n + p), uz = __ldg(u + 2 * g.n + p);
         if (SLOPE) {
             float sx, sy, sz;
-            J[p] = sample_grad(M, g, x, y, z, ux, uy, uz, pad, sx, sy, sz);
+            J[p] = sample_grad<T, PAD>(M, g, x, y, z, ux, uy, uz, sx, sy, sz);
             dJ[p] = sx;
             dJ[g.n + p] = sy;
             dJ[2 * g.n + p] = sz;
         } else {
-            J[p] = sample(M, g, x, y, z, ux, uy, uz, pad);
+            J[p] = sample<T, PAD>(M, g, x, y, z, ux, uy, uz);
         }
     }
-}
-
-template <typename T>
-static void warp_dispatch(dim3 grid, cudaStream_t s, const void *M, const float *u, const Dims &g, int pad, int zc,
-                          float *J, float *dJ) {
-    if (dJ)
-        warp_kernel<T, true><<<grid, dim3(TX, TY), 0, s>>>((const T *)M, u, g, pad, zc, J, dJ);
-    else
-        warp_kernel<T, false><<<grid, dim3(TX, TY), 0, s>>>((const T *)M, u, g, pad, zc, J, dJ);
 }
 
 cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, int pad, float *J, float *dJ,
                         cudaStream_t s) {
     const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);
-    if (dt == REG_BF16)
-        warp_dispatch<__nv_bfloat16>(grid, s, M, u, g, pad, G.zc, J, dJ);
-    else
-        warp_dispatch<float>(grid, s, M, u, g, pad, G.zc, J, dJ);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            if (dJ)
+                warp_kernel<T, true, PD><<<grid, block, 0, s>>>((const T *)M, u, g, G.zc, J, dJ);
+            else
+                warp_kernel<T, false, PD><<<grid, block, 0, s>>>((const T *)M, u, g, G.zc, J, dJ);
+        });
+    });
     return cudaGetLastError();
 }
 
