@@ -31,6 +31,15 @@ inline void with_type(int dt, Fn &&fn) {  // fn receives a null pointer of the e
 }
 template <typename P>
 using elem_t = std::remove_pointer_t<P>;
+// voxel index type: 32-bit offsets within a channel when the volume has
+// fewer than 2^31 voxels (cheaper address arithmetic), 64-bit otherwise
+template <typename Fn>
+inline void with_index(const Dims &g, Fn &&fn) {
+    if (g.n < (1LL << 31))
+        fn((int *)nullptr);
+    else
+        fn((long long *)nullptr);
+}
 
 // Tile-march geometry shared by every stencil / sweep kernel: a CTA owns a
 // 32 x 8 column tile in (x, y) and marches through a chunk of z-planes.

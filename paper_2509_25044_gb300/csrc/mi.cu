@@ -73,7 +73,7 @@ __device__ __forceinline__ void flush16(unsigned *shc, int K, int B, const unsig
 // changes.  Bins are 32-bit fixed point (MI_FIXED_SCALE); the per-CTA voxel
 // cap keeps them from wrapping; each CTA adds its bins (summed over the
 // copies) to the global 64-bit histogram.
-template <typename T, int PAD>
+template <typename T, int PAD, typename I>
 __global__ void __launch_bounds__(TILE_THREADS, 4) mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M,
                                                                   const float *__restrict__ u, Dims g, MiParams P,
                                                                   int zc, unsigned long long *__restrict__ hist) {
@@ -90,16 +90,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) mi_hist_kernel(const T *__res
     const int z1 = min(g.nz, z0 + zc);
     if (x < g.nx && y < g.ny) {
         unsigned *shc = sh + (threadIdx.x % copies) * pitch;
-        const long long col = (long long)y * g.nx + x;
+        const float *u0 = u, *u1 = u + g.n, *u2 = u + 2 * g.n;
+        const I nxy = (I)g.nxy;
+        I p = (I)z0 * nxy + (I)y * g.nx + x;
         int K = -1;
         unsigned acc[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) acc[e] = 0u;
-        for (int z = z0; z < z1; ++z) {
-            const long long p = (long long)z * g.nxy + col;
+        for (int z = z0; z < z1; ++z, p += nxy) {
             const float fv = ld_vox(F, p);
-            const float jv =
-                sample<T, PAD>(M, g, x, y, z, __ldg(u + p), __ldg(u + g.n + p), __ldg(u + 2 * g.n + p));
+            const float jv = sample<T, PAD, I>(M, g, x, y, z, __ldg(u0 + p), __ldg(u1 + p), __ldg(u2 + p));
             float wf[4], wj[4];
             const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
             const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
     }
 }
 
-template <typename T, typename MT, bool STEP, int PAD>
+template <typename T, typename MT, bool STEP, int PAD, typename I>
 __global__ void __launch_bounds__(TILE_THREADS, 3)
     mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                      MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
@@ -183,51 +183,47 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
     const int z0 = blockIdx.z * zc;
     const int z1 = min(g.nz, z0 + zc);
     float rpart = 0.0f;
-    const bool act = x < g.nx;
-    if (y < g.ny) {  // warp-uniform: every lane of the row runs the loop (x-neighbours by shuffle)
-        const int lane = threadIdx.x;
-        // lanes past the x edge shadow the last column (loads stay in bounds,
-        // nothing is stored for them)
-        const int xe = act ? x : g.nx - 1;
-        const long long col = (long long)y * g.nx + xe;
-        const bool hxm = act && x > 0, hxp = act && x + 1 < g.nx;
+    if (x < g.nx && y < g.ny) {
+        // per-channel base pointers; voxel offsets within a channel are of type I
+        const float *uc[3] = {u, u + g.n, u + 2 * g.n};
+        MT *mc[3] = {m, m + g.n, m + 2 * g.n};
+        MT *vc[3] = {v, v + g.n, v + 2 * g.n};
+        const I nxy = (I)g.nxy, nx = (I)g.nx;
+        I p = (I)z0 * nxy + (I)y * nx + x;
+        const bool hxm = x > 0, hxp = x + 1 < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
         // registers roll one plane ahead: u at z-1 / z / z+1, and F, m, v of
         // the next plane are requested before the current plane is computed
         float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
         float fcur, mcur[3] = {0.f, 0.f, 0.f}, vcur[3] = {0.f, 0.f, 0.f};
-        {
-            const long long p = (long long)z0 * g.nxy + col;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) cur[c] = __ldg(u + c * g.n + p);
-            fcur = ld_vox(F, p);
-            if (STEP) {
+        for (int c = 0; c < 3; ++c) cur[c] = __ldg(uc[c] + p);
+        fcur = ld_vox(F, p);
+        if (STEP) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    mcur[c] = ld_moment(m, c * g.n + p);
-                    vcur[c] = ld_moment(v, c * g.n + p);
-                    if (z0 > 0) prv[c] = __ldg(u + c * g.n + p - g.nxy);
-                }
+            for (int c = 0; c < 3; ++c) {
+                mcur[c] = ld_moment(mc[c], p);
+                vcur[c] = ld_moment(vc[c], p);
+                if (z0 > 0) prv[c] = __ldg(uc[c] + p - nxy);
             }
         }
-        for (int z = z0; z < z1; ++z) {
-            const long long p = (long long)z * g.nxy + col;
+        for (int z = z0; z < z1; ++z, p += nxy) {
             float fnxt = 0.0f, mnxt[3] = {0.f, 0.f, 0.f}, vnxt[3] = {0.f, 0.f, 0.f};
             if (z + 1 < g.nz) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(u + c * g.n + p + g.nxy);
+                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
             }
             if (z + 1 < z1) {
-                fnxt = ld_vox(F, p + g.nxy);
+                fnxt = ld_vox(F, p + nxy);
                 if (STEP) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        mnxt[c] = ld_moment(m, c * g.n + p + g.nxy);
-                        vnxt[c] = ld_moment(v, c * g.n + p + g.nxy);
+                        mnxt[c] = ld_moment(mc[c], p + nxy);
+                        vnxt[c] = ld_moment(vc[c], p + nxy);
                     }
                 }
             }
             float sx, sy, sz;
-            const float jv = sample_grad<T, PAD>(M, g, xe, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
+            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
             float wf[4], dj[4];
             const int iF = bspline_weights(to_bin(fcur, P.f_lo, P.f_scale, B), B, wf) - 1;
             const float tj = (jv - P.m_lo) * P.m_scale;
@@ -242,28 +238,17 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
             if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
             const float gs[3] = {gj * sx, gj * sy, gj * sz};
             if (STEP) {
-                float xm[3], xp[3], gR[3];
+                float gR[3];
+                diffusion_ptr<I>(uc, p, nx, hxm, hxp, hym, hyp, z > 0, z + 1 < g.nz, cur, prv, nxt, gR, rpart);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float dn = __shfl_down_sync(0xffffffffu, cur[c], 1);
-                    const float up = __shfl_up_sync(0xffffffffu, cur[c], 1);
-                    xp[c] = (lane == TX - 1 && hxp) ? __ldg(u + c * g.n + p + 1) : dn;
-                    xm[c] = (lane == 0 && hxm) ? __ldg(u + c * g.n + p - 1) : up;
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    if (grad_out) (grad_out + c * g.n)[p] = gt;
+                    (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
                 }
-                float rp = 0.0f;
-                diffusion_xn(u, g, y, z, p, hxm, hxp, cur, prv, nxt, xm, xp, gR, rp);
-                if (act) {
-                    rpart += rp;
+            } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
-                        if (grad_out) grad_out[c * g.n + p] = gt;
-                        u_out[c * g.n + p] = adam_update(cur[c], gt, mcur[c], vcur[c], m, v, c * g.n + p, S);
-                    }
-                }
-            } else if (act) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) grad_out[c * g.n + p] = gs[c];
+                for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
             }
             fcur = fnxt;
 #pragma unroll
@@ -307,8 +292,11 @@ cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u,
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
-            mi_hist_kernel<T, decltype(pd)::value>
-                <<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc, hist);
+            with_index(g, [&](auto ip) {
+                using I = elem_t<decltype(ip)>;
+                mi_hist_kernel<T, decltype(pd)::value, I>
+                    <<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc, hist);
+            });
         });
     });
     return cudaGetLastError();
@@ -333,17 +321,20 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
-            if (!step) {
-                mi_sweep2_kernel<T, float, false, PD><<<grid, block, 0, s>>>(
-                    (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m, (float *)v, S,
-                    partials, counter, r_out, err);
-                return;
-            }
-            with_type(mdt, [&](auto mp) {
-                using MT = elem_t<decltype(mp)>;
-                mi_sweep2_kernel<T, MT, true, PD><<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc,
-                                                                        Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
-                                                                        partials, counter, r_out, err);
+            with_index(g, [&](auto ip) {
+                using I = elem_t<decltype(ip)>;
+                if (!step) {
+                    mi_sweep2_kernel<T, float, false, PD, I><<<grid, block, 0, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m, (float *)v, S,
+                        partials, counter, r_out, err);
+                    return;
+                }
+                with_type(mdt, [&](auto mp) {
+                    using MT = elem_t<decltype(mp)>;
+                    mi_sweep2_kernel<T, MT, true, PD, I><<<grid, block, 0, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
+                        partials, counter, r_out, err);
+                });
             });
         });
     });

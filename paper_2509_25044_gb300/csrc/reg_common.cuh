@@ -33,8 +33,12 @@ inline Dims make_dims(reg_dims d) {
 // ---------------------------------------------------------------------------
 // voxel loads (read-only path)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float ld_vox(const float *p, long long i) { return __ldg(p + i); }
-__device__ __forceinline__ float ld_vox(const __nv_bfloat16 *p, long long i) {
+template <typename I>
+__device__ __forceinline__ float ld_vox(const float *p, I i) {
+    return __ldg(p + i);
+}
+template <typename I>
+__device__ __forceinline__ float ld_vox(const __nv_bfloat16 *p, I i) {
     return __bfloat162float(__ldg(p + i));
 }
 
@@ -81,11 +85,13 @@ __device__ __forceinline__ Axis axis_setup(int p, float uu, int n) {
 }
 
 // the 8 corner values c[bz*4 + by*2 + bx] (0 outside the volume in ZEROS mode)
-template <typename T, int PAD>
+// I is the voxel index type: int when the volume has fewer than 2^31 voxels
+// (cheaper address arithmetic), long long otherwise.
+template <typename T, int PAD, typename I = long long>
 __device__ __forceinline__ void gather8(const T *M, const Dims &g, const Axis &X, const Axis &Y, const Axis &Z,
                                         float c[8]) {
-    const long long r00 = ((long long)Z.i0 * g.ny + Y.i0) * g.nx, r01 = ((long long)Z.i0 * g.ny + Y.i1) * g.nx;
-    const long long r10 = ((long long)Z.i1 * g.ny + Y.i0) * g.nx, r11 = ((long long)Z.i1 * g.ny + Y.i1) * g.nx;
+    const I r00 = ((I)Z.i0 * g.ny + Y.i0) * g.nx, r01 = ((I)Z.i0 * g.ny + Y.i1) * g.nx;
+    const I r10 = ((I)Z.i1 * g.ny + Y.i0) * g.nx, r11 = ((I)Z.i1 * g.ny + Y.i1) * g.nx;
     if (PAD == REG_PAD_BORDER) {
         c[0] = ld_vox(M, r00 + X.i0);
         c[1] = ld_vox(M, r00 + X.i1);
@@ -112,14 +118,14 @@ __device__ __forceinline__ void gather8(const T *M, const Dims &g, const Axis &X
 __device__ __forceinline__ float lerp1(float a, float lo, float hi) { return fmaf(a, hi, (1.0f - a) * lo); }
 
 // value only
-template <typename T, int PAD>
+template <typename T, int PAD, typename I = long long>
 __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
                                         float uz) {
     const Axis X = axis_setup<PAD>(x, ux, g.nx);
     const Axis Y = axis_setup<PAD>(y, uy, g.ny);
     const Axis Z = axis_setup<PAD>(z, uz, g.nz);
     float c[8];
-    gather8<T, PAD>(M, g, X, Y, Z, c);
+    gather8<T, PAD, I>(M, g, X, Y, Z, c);
     const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
     const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);
     const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
@@ -127,14 +133,14 @@ __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y,
 }
 
 // value and slope dJ/dphi
-template <typename T, int PAD>
+template <typename T, int PAD, typename I = long long>
 __device__ __forceinline__ float sample_grad(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
                                              float uz, float &gx, float &gy, float &gz) {
     const Axis X = axis_setup<PAD>(x, ux, g.nx);
     const Axis Y = axis_setup<PAD>(y, uy, g.ny);
     const Axis Z = axis_setup<PAD>(z, uz, g.nz);
     float c[8];
-    gather8<T, PAD>(M, g, X, Y, Z, c);
+    gather8<T, PAD, I>(M, g, X, Y, Z, c);
     const float d00 = c[1] - c[0], d10 = c[3] - c[2], d01 = c[5] - c[4], d11 = c[7] - c[6];
     const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
     const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);

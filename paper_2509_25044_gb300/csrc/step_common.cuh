@@ -15,10 +15,22 @@ struct StepParams {
     float b1, b2, eps, gscale;
 };
 
-__device__ __forceinline__ float ld_moment(const float *p, long long i) { return p[i]; }
-__device__ __forceinline__ float ld_moment(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
-__device__ __forceinline__ void st_moment(float *p, long long i, float v) { p[i] = v; }
-__device__ __forceinline__ void st_moment(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
+template <typename I>
+__device__ __forceinline__ float ld_moment(const float *p, I i) {
+    return p[i];
+}
+template <typename I>
+__device__ __forceinline__ float ld_moment(const __nv_bfloat16 *p, I i) {
+    return __bfloat162float(p[i]);
+}
+template <typename I>
+__device__ __forceinline__ void st_moment(float *p, I i, float v) {
+    p[i] = v;
+}
+template <typename I>
+__device__ __forceinline__ void st_moment(__nv_bfloat16 *p, I i, float v) {
+    p[i] = __float2bfloat16_rn(v);
+}
 
 // Adam on one element (torch.optim.Adam with bias correction; the update
 // uses the new moments in FP32, the stored moments are rounded to MT).
@@ -84,6 +96,54 @@ __device__ __forceinline__ void diffusion_at(const float *__restrict__ u, const 
         if (hzm) acc += c0 - prv[c];
         gR[c] = acc;
     }
+}
+
+// The same stencil on per-channel base pointers with a voxel index of type I
+// (int for volumes below 2^31 voxels); the h* flags say which neighbours lie
+// inside the volume.
+template <typename I>
+__device__ __forceinline__ void diffusion_ptr(const float *const uc[3], I p, I nx, bool hxm, bool hxp, bool hym,
+                                              bool hyp, bool hzm, bool hzp, const float cur[3], const float prv[3],
+                                              const float nxt[3], float gR[3], float &rpart) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float c0 = cur[c];
+        float acc = 0.0f;
+        if (hxp) {
+            const float d = __ldg(uc[c] + p + 1) - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hxm) acc += c0 - __ldg(uc[c] + p - 1);
+        if (hyp) {
+            const float d = __ldg(uc[c] + p + nx) - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hym) acc += c0 - __ldg(uc[c] + p - nx);
+        if (hzp) {
+            const float d = nxt[c] - c0;
+            acc -= d;
+            rpart = fmaf(d, d, rpart);
+        }
+        if (hzm) acc += c0 - prv[c];
+        gR[c] = acc;
+    }
+}
+
+// Adam on one element with the old moments already loaded; the new moments
+// are stored to m[i], v[i]; returns the updated displacement.  The quotient
+// uses the fast reciprocal division (a few ulp, far inside the parity bar).
+template <typename MT, typename I>
+__device__ __forceinline__ float adam_fast(float u, float g, float m0, float v0, MT *m, MT *v, I i,
+                                           const StepParams &S) {
+    const float gs = S.gscale * g;
+    const float mn = fmaf(S.b1, m0, (1.0f - S.b1) * gs);
+    const float vn = fmaf(S.b2, v0, (1.0f - S.b2) * gs * gs);
+    st_moment(m, i, mn);
+    st_moment(v, i, vn);
+    const float denom = fmaf(sqrtf(vn), S.rsqrt_bc2, S.eps);
+    return fmaf(-S.lr_bc1, __fdividef(mn, denom), u);
 }
 
 // The same stencil with the x-neighbours supplied by the caller (a warp
