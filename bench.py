@@ -237,7 +237,7 @@ def run_ours(args):
     cfg = synth.CONFIGS[args.config]
     kind = cfg["kind"]
     bf16 = cfg["dtype"] == "bf16"
-    d = synth.make(args.config, device=dev, seed=cfg["seed"] + 1000 * rank)
+    d = synth.make(args.config, device=dev, seed=cfg["seed"] + 1000 * rank, n=args.n)
     F = d["F"].to(torch.bfloat16 if bf16 else torch.float32).contiguous()
     M = d["M"].to(torch.bfloat16 if bf16 else torch.float32).contiguous()
     shape = tuple(F.shape)
@@ -370,6 +370,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--config", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -74,7 +74,8 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
 
 size_t workspace_bytes(const Dims &g, const reg_loss_desc *L) {
     size_t bytes = align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L));
-    if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 3 * (size_t)g.n);
+    // LNCC: three coefficient fields and the warped image
+    if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 4 * (size_t)g.n);
     return bytes;
 }
 
@@ -84,7 +85,8 @@ struct Ws {
     float *gtab;
     double *scratch;
     double *partials;
-    float *coef;
+    float *coef;   // LNCC: [3][N] adjoint coefficients
+    float *warped; // LNCC: [N] warped moving image
 };
 
 Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
@@ -96,6 +98,7 @@ Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
     w.scratch = (double *)(b + WS_SCRATCH);
     w.partials = (double *)(b + WS_PARTIALS);
     w.coef = (float *)(b + align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L)));
+    w.warped = w.coef + 3 * (size_t)g.n;
     return w;
 }
 
@@ -173,7 +176,8 @@ reg_status run_sweep1(const reg_loss_desc *L, const void *F, const void *M, int 
     REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
     if (L->kind == REG_LOSS_LNCC) {
         LnccParams P{L->window / 2, L->eps};
-        REG_CUDA(launch_lncc_stats(F, M, img_dt, u, g, pad, P, need_grad ? w.coef : nullptr, w.partials,
+        REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s));
+        REG_CUDA(launch_lncc_stats(F, w.warped, img_dt, g, P, need_grad ? w.coef : nullptr, w.partials,
                                    w.counters + 0, sim_out, s));
     } else {
         const MiParams P = mi_params(L);

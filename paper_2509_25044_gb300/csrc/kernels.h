@@ -93,11 +93,10 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                              void *m, void *v, int mdt, const StepParams &S, double *partials,
                              unsigned *counter, double *r_out, cudaStream_t s);
 
-// First LNCC sweep: window statistics -> similarity (+ optional adjoint
-// coefficient fields, [3][N] floats).
-cudaError_t launch_lncc_stats(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
-                              const LnccParams &P, float *coef, double *partials, unsigned *counter,
-                              double *sim_out, cudaStream_t s);
+// First LNCC sweep: window statistics of F and the warped image J (already
+// in HBM, FP32) -> similarity (+ optional adjoint coefficient fields, [3][N]).
+cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims &g, const LnccParams &P, float *coef,
+                              double *partials, unsigned *counter, double *sim_out, cudaStream_t s);
 // Second LNCC sweep: box sums of the coefficient fields -> adjoint (+ optional
 // diffusion + Adam).
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,

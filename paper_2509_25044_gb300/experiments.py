@@ -1,0 +1,124 @@
+"""Time-to-solution experiments on the synthetic workloads.
+
+    python -m paper_2509_25044_gb300.experiments ttl --config c2 [--iters 300]
+
+`ttl` (time to loss): runs the plain FP32 registration (FP32 images and Adam
+moments) and the BF16 storage form (BF16 images and moments, FP32 arithmetic)
+of the same pair for the same number of iterations.  The target comes from
+the FP32 run's objective C + lambda R on the FP32 images: its final value L*
+and its start value L0.  A run reaches the target when its iterate, evaluated
+on the FP32 images, has made 99 % of the FP32 run's decrease, i.e.
+L <= L* + 0.01 (L0 - L*) (the objective itself can barely move -- 1 - S near
+1 on noisy windows -- so 1 % of L* would say nothing).  Each run's time to
+solution is its number of iterations to the target times its measured
+time per iteration (CUDA events).  The BF16 run is repeated
+deterministically to evaluate its iterates on the FP32 images every few
+iterations outside the timed pass.  Both final fields are checked for folding
+(det(I + grad u) > 0 everywhere).  Prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import capi, synth
+from .register import RegConfig, Registration
+
+
+def _cfg(c: dict, d: dict, moments: str, lam_scale: float = 1.0, adam_eps: float = 1e-8) -> RegConfig:
+    lam = c["lam"] * lam_scale
+    if c["kind"] == "lncc":
+        return RegConfig(loss="lncc", window=c["window"], eps=1e-5, lam=lam, lr=c["lr"], moments=moments,
+                         adam_eps=adam_eps)
+    return RegConfig(loss="mi", bins=c["bins"], f_range=d["f_range"], m_range=d["m_range"], lam=lam, lr=c["lr"],
+                     moments=moments, adam_eps=adam_eps)
+
+
+def _first_within(values, target, tol):
+    idx = np.nonzero(np.asarray(values) <= target + tol)[0]
+    return int(idx[0]) if idx.size else None
+
+
+def time_to_loss(config: str, iters: int | None = None, eval_every: int = 10, n: int | None = None,
+                 rel_tol: float = 0.01, lam_scale: float = 1.0, adam_eps: float = 1e-8) -> dict:
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    d = synth.make(config, device=dev, n=n)
+    c = d["config"]
+    iters = iters or c["iters"]
+    F32, M32 = d["F"].contiguous(), d["M"].contiguous()
+    del d["u_true"]
+
+    # plain FP32 run: its own per-iteration objective is already on FP32 images
+    r32 = Registration(F32, M32, _cfg(c, d, "f32", lam_scale, adam_eps))
+    res32 = r32.run(iters)
+    final32 = r32.objective()
+    fold32 = r32.fold_check()
+    L_star = final32["objective"]
+    L0 = float(res32.objective[0])
+    tol = rel_tol * max(L0 - L_star, 0.0)
+    trace32 = np.append(res32.objective[1:], final32["objective"])  # objective after each step
+    k32 = _first_within(trace32, L_star, tol)
+
+    # BF16 storage form: timed pass, then a deterministic replay evaluated on FP32 images
+    Fb, Mb = F32.to(torch.bfloat16).contiguous(), M32.to(torch.bfloat16).contiguous()
+    cfg_b = _cfg(c, d, "bf16", lam_scale, adam_eps)
+    if cfg_b.loss == "mi":  # ranges of the stored BF16 values
+        cfg_b.f_range = (float(Fb.min()), float(Fb.max()))
+        cfg_b.m_range = (float(Mb.min()), float(Mb.max()))
+    rb = Registration(Fb, Mb, cfg_b)
+    resb = rb.run(iters)
+    foldb = rb.fold_check()
+    rb2 = Registration(Fb, Mb, cfg_b)
+    checkpoints, evals = [], []
+    done = 0
+    while done < iters:
+        step = min(eval_every, iters - done)
+        rb2.run(step)
+        done += step
+        checkpoints.append(done)
+        evals.append(rb2.objective(F=F32, M=M32)["objective"])
+    same = bool(torch.equal(rb2.current, rb.current))
+    kb_idx = _first_within(evals, L_star, tol)
+    kb = checkpoints[kb_idx] if kb_idx is not None else None
+
+    out = {
+        "experiment": "time_to_loss", "config": config, "n": F32.shape[0], "iters": iters,
+        "lam": c["lam"] * lam_scale, "lr": c["lr"], "adam_eps": adam_eps,
+        "target": {"objective_fp32_start": L0, "objective_fp32_final": L_star,
+                   "rule": f"L <= L* + {rel_tol} (L0 - L*)"},
+        "fp32": {"ms_per_iter": res32.ms_per_iter, "iters_to_target": (k32 + 1) if k32 is not None else None,
+                 "time_to_target_ms": (k32 + 1) * res32.ms_per_iter if k32 is not None else None,
+                 "final": final32, "fold": fold32},
+        "bf16": {"ms_per_iter": resb.ms_per_iter, "iters_to_target_upper": kb,
+                 "time_to_target_ms": kb * resb.ms_per_iter if kb is not None else None,
+                 "final_on_fp32_images": evals[-1], "final_rel_to_fp32_final": (evals[-1] - L_star) / abs(L_star),
+                 "final_progress_vs_fp32": (L0 - evals[-1]) / max(L0 - L_star, 1e-300),
+                 "fold": foldb, "replay_bitwise_identical": same, "eval_every": eval_every},
+    }
+    if out["fp32"]["time_to_target_ms"] and out["bf16"]["time_to_target_ms"]:
+        out["speedup_bf16_vs_fp32"] = out["fp32"]["time_to_target_ms"] / out["bf16"]["time_to_target_ms"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("ttl")
+    t.add_argument("--config", default="c2")
+    t.add_argument("--iters", type=int, default=None)
+    t.add_argument("--n", type=int, default=None)
+    t.add_argument("--eval-every", type=int, default=10)
+    t.add_argument("--lam-scale", type=float, default=1.0)
+    t.add_argument("--adam-eps", type=float, default=1e-8)
+    args = ap.parse_args()
+    if args.cmd == "ttl":
+        print(json.dumps(time_to_loss(args.config, args.iters, args.eval_every, args.n, lam_scale=args.lam_scale,
+                                      adam_eps=args.adam_eps)))
+
+
+if __name__ == "__main__":
+    main()

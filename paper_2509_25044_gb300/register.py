@@ -1,0 +1,123 @@
+"""Registration driver: runs the fused iteration (reg_iterate) for a pair.
+
+Everything here is orchestration: buffers are torch tensors on the device, each
+iteration is one C-ABI call (two sweeps of sm_103a kernels), the objective of
+every iteration is written by the kernels into a device array and read once at
+the end, so the loop never synchronises with the host.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+@dataclass
+class RegConfig:
+    loss: str = "lncc"          # "lncc" or "mi"
+    window: int = 7             # LNCC window side
+    eps: float = 1e-5           # LNCC epsilon
+    bins: int = 32              # MI bins
+    f_range: tuple | None = None
+    m_range: tuple | None = None
+    lam: float = 0.1            # diffusion weight
+    lr: float = 0.1             # Adam step size (voxels)
+    beta1: float = 0.9
+    beta2: float = 0.999
+    adam_eps: float = 1e-8
+    moments: str = "f32"        # "f32" or "bf16"
+    pad: int = capi.REG_PAD_BORDER
+
+    def loss_desc(self, F):
+        if self.loss == "lncc":
+            return capi.lncc_desc(self.window, self.eps)
+        fr = self.f_range if self.f_range is not None else (float(F.min()), float(F.max()))
+        mr = self.m_range if self.m_range is not None else (0.0, 1.0)
+        return capi.mi_desc(fr, mr, self.bins)
+
+
+@dataclass
+class RegResult:
+    u: torch.Tensor
+    sim: np.ndarray           # similarity per iteration (at the iterate before the step)
+    R: np.ndarray             # R(u) per iteration
+    objective: np.ndarray     # C + lam R per iteration
+    ms_per_iter: float
+    extra: dict = field(default_factory=dict)
+
+
+class Registration:
+    """Holds the device state of one registration (u ping-pong, Adam moments,
+    workspace) so that runs can be continued and timed without reallocation."""
+
+    def __init__(self, F: torch.Tensor, M: torch.Tensor, cfg: RegConfig, u0: torch.Tensor | None = None):
+        if F.device.type != "cuda":
+            raise ValueError("F and M must be CUDA tensors")
+        self.F, self.M, self.cfg = F.contiguous(), M.contiguous(), cfg
+        self.shape = tuple(F.shape)
+        self.N = F.numel()
+        dev = F.device
+        self.loss = cfg.loss_desc(F)
+        mt = torch.bfloat16 if cfg.moments == "bf16" else torch.float32
+        self.u = [torch.zeros((3,) + self.shape, device=dev), torch.zeros((3,) + self.shape, device=dev)]
+        if u0 is not None:
+            self.u[0].copy_(u0)
+        self.m = torch.zeros((3,) + self.shape, dtype=mt, device=dev)
+        self.v = torch.zeros((3,) + self.shape, dtype=mt, device=dev)
+        self.ws = capi.workspace(self.loss, self.F)
+        self.adam = capi.adam_desc(cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps,
+                                   capi.REG_BF16 if cfg.moments == "bf16" else capi.REG_F32, float(self.N))
+        self.t = 0
+
+    @property
+    def current(self) -> torch.Tensor:
+        return self.u[self.t % 2]
+
+    def run(self, iters: int) -> RegResult:
+        hist = torch.zeros((iters, 2), dtype=torch.float64, device=self.F.device)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for k in range(iters):
+            a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
+            self.t += 1
+            capi.reg_iterate(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t,
+                             self.ws, pad=self.cfg.pad, obj=hist[k])
+        end.record()
+        torch.cuda.synchronize()
+        h = hist.cpu().numpy()
+        sim, R = h[:, 0], h[:, 1]
+        loss = 1.0 - sim if self.cfg.loss == "lncc" else -sim
+        return RegResult(u=self.current, sim=sim, R=R, objective=loss + self.cfg.lam * R,
+                         ms_per_iter=start.elapsed_time(end) / max(iters, 1))
+
+    def objective(self, u: torch.Tensor | None = None, F=None, M=None) -> dict:
+        """Similarity, R and objective at u (default: the current iterate),
+        optionally on other images (for example the FP32 pair of a BF16 run)."""
+        u = self.current if u is None else u
+        F = self.F if F is None else F
+        M = self.M if M is None else M
+        ws = self.ws if F.dtype == self.F.dtype else capi.workspace(self.loss, F)
+        sim = capi.reg_loss(self.loss, F, M, u, ws, pad=self.cfg.pad)
+        R = capi.reg_regularize(u, 0.0, ws)
+        s, r = float(sim.item()), float(R.item())
+        c = 1.0 - s if self.cfg.loss == "lncc" else -s
+        return dict(sim=s, R=r, objective=c + self.cfg.lam * r)
+
+    def fold_check(self, u: torch.Tensor | None = None) -> dict:
+        u = self.current if u is None else u
+        mn, nf = capi.reg_jacdet_min(u)
+        return dict(min_det=float(mn.item()), n_fold=int(nf.item()))
+
+
+def register(F, M, cfg: RegConfig, iters: int, u0=None) -> RegResult:
+    """Run `iters` fused iterations from u0 (zero by default)."""
+    reg = Registration(F, M, cfg, u0)
+    t0 = time.perf_counter()
+    res = reg.run(iters)
+    res.extra.update(reg.fold_check())
+    res.extra["wall_s"] = time.perf_counter() - t0
+    return res
