@@ -202,6 +202,13 @@ REG_API reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const voi
  * time each sweep inside a long run without synchronising. */
 REG_API reg_status reg_set_timing_events(void *const *events, int n);
 
+/* Test hook for the tensor-core engine: C[M x N] (FP32, row-major) =
+ * A B^T with BF16 A and B, computed by the tcgen05 mainloop used by the
+ * convolutions.  a_mn_major == 0: A is [M][K] (K contiguous), 1: [K][M];
+ * likewise B with N.  M % 128 == 0, N in {16, 32, 48, 64}, K % 64 == 0. */
+REG_API reg_status reg_debug_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int a_mn_major,
+                                       int b_mn_major, void *stream);
+
 /* Test hook for failure detection: a one-thread kernel polls *flag (device
  * unsigned) until it equals `expect` or `timeout_ns` nanoseconds of device
  * time pass; on expiry it latches REG_ERR_TIMEOUT in the device error word

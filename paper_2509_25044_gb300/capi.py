@@ -28,7 +28,8 @@ STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR
 # every C entry point declared in include/reg.h
 EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
-           "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc")
+           "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
+           "reg_debug_gemm_bf16")
 
 
 class RegError(RuntimeError):
@@ -82,6 +83,8 @@ def _lib():
         L.reg_get_device_error.argtypes = [_vp]
         L.reg_debug_wait_flag.argtypes = [_vp, ctypes.c_uint, ctypes.c_ulonglong, _vp]
         L.reg_set_timing_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        L.reg_debug_gemm_bf16.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _vp]
         L.reg_mi_loss_grad_noalloc.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                                ctypes.c_int, _vp, _vp, _vp]
         for name in EXPORTS:
@@ -283,3 +286,12 @@ def reg_mi_loss_grad_noalloc(loss: RegLossDesc, F, M, u, pad: int = REG_PAD_BORD
                                            int(pad), _ptr(sim), _ptr(grad if with_grad else None), _stream(F)),
            "reg_mi_loss_grad_noalloc")
     return (sim, grad) if with_grad else sim
+
+
+def reg_debug_gemm_bf16(A, B, M: int, N: int, K: int, a_mn_major: bool = False, b_mn_major: bool = False, C=None):
+    """C = A B^T on the tensor cores (test hook); A, B bf16 in the stated layouts."""
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(_lib().reg_debug_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(bool(a_mn_major)),
+                                      int(bool(b_mn_major)), _stream(A)), "reg_debug_gemm_bf16")
+    return C

@@ -113,6 +113,10 @@ cudaError_t launch_jacdet(const float *u, const Dims &g, float *min_out, unsigne
 cudaError_t launch_wait_flag(const unsigned *flag, unsigned expect, unsigned long long timeout_ns,
                              cudaStream_t s);
 
+// tensor-core GEMM test hook (C = A B^T, BF16 in, FP32 out)
+cudaError_t launch_gemm_test(const void *A, const void *B, float *C, int M, int N, int K, int a_mn, int b_mn,
+                             cudaStream_t s);
+
 int num_sms();
 // device address of the device error word on the current device
 unsigned *error_word();
