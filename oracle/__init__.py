@@ -67,6 +67,13 @@ def _load():
         lib.or_adam.restype = None
         lib.or_jacdet.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         lib.or_jacdet.restype = None
+        ci = ctypes.c_int
+        lib.or_conv3d.argtypes = [_dp, ci, _dp, _dp, ci, ci, ci, ci, _dp]
+        lib.or_conv3d.restype = None
+        lib.or_conv3d_dgrad.argtypes = [_dp, ci, _dp, ci, ci, ci, ci, _dp]
+        lib.or_conv3d_dgrad.restype = None
+        lib.or_conv3d_wgrad.argtypes = [_dp, ci, _dp, ci, ci, ci, ci, _dp]
+        lib.or_conv3d_wgrad.restype = None
         _lib = lib
     return _lib
 
@@ -202,6 +209,38 @@ def jacdet(u):
     d = np.empty(u.shape[1:], dtype=np.float64)
     _load().or_jacdet(_ptr(u), nx, ny, nz, _ptr(d))
     return d
+
+
+def conv3d(x, w, bias=None):
+    """x: [nz, ny, nx, Cin] channels-last; w: [Cout, 27, Cin]; returns [nz, ny, nx, Cout]."""
+    x = _f64(x)
+    w = _f64(w)
+    nz, ny, nx, cin = x.shape
+    cout = w.shape[0]
+    out = np.empty((nz, ny, nx, cout))
+    b = _f64(bias) if bias is not None else None
+    _load().or_conv3d(_ptr(x), cin, _ptr(w), _ptr(b), cout, nx, ny, nz, _ptr(out))
+    return out
+
+
+def conv3d_dgrad(dout, w):
+    dout = _f64(dout)
+    w = _f64(w)
+    nz, ny, nx, cout = dout.shape
+    cin = w.shape[2]
+    din = np.empty((nz, ny, nx, cin))
+    _load().or_conv3d_dgrad(_ptr(dout), cout, _ptr(w), cin, nx, ny, nz, _ptr(din))
+    return din
+
+
+def conv3d_wgrad(x, dout):
+    x = _f64(x)
+    dout = _f64(dout)
+    nz, ny, nx, cin = x.shape
+    cout = dout.shape[3]
+    dw = np.empty((cout, 27, cin))
+    _load().or_conv3d_wgrad(_ptr(x), cin, _ptr(dout), cout, nx, ny, nz, _ptr(dw))
+    return dw
 
 
 # --------------------------------------------------------------------------

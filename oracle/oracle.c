@@ -596,3 +596,76 @@ void or_lncc_grad_points(const double *F, const double *J, int nx, int ny, int n
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* 3-D convolution of the learned initialiser (3x3x3 taps, zero padding 1,  */
+/* stride 1), channels-last: in[v][Cin], w[Cout][27][Cin] with tap          */
+/* t = (kz*3 + ky)*3 + kx for offset (kx-1, ky-1, kz-1), out[v][Cout].       */
+/* The plain definition: out[v][o] = bias[o] + sum_t sum_c w[o][t][c]        */
+/* in[v + off(t)][c], and its two adjoints.                                  */
+/* ------------------------------------------------------------------------ */
+static int tap_neighbour(int x, int y, int z, int t, int nx, int ny, int nz, long *q)
+{
+    const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+    if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) return 0;
+    *q = lin(xx, yy, zz, nx, ny);
+    return 1;
+}
+
+void or_conv3d(const double *in, int Cin, const double *w, const double *bias, int Cout, int nx, int ny, int nz,
+               double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const long v = lin(x, y, z, nx, ny);
+                for (int o = 0; o < Cout; ++o) {
+                    double acc = bias ? bias[o] : 0.0;
+                    for (int t = 0; t < 27; ++t) {
+                        long q;
+                        if (!tap_neighbour(x, y, z, t, nx, ny, nz, &q)) continue;
+                        for (int c = 0; c < Cin; ++c) acc += w[((long)o * 27 + t) * Cin + c] * in[q * Cin + c];
+                    }
+                    out[v * Cout + o] = acc;
+                }
+            }
+}
+
+/* din[q][c] = sum over (v, t) with v + off(t) = q of sum_o w[o][t][c] dout[v][o] */
+void or_conv3d_dgrad(const double *dout, int Cout, const double *w, int Cin, int nx, int ny, int nz, double *din)
+{
+    const long N = (long)nx * ny * nz;
+    memset(din, 0, sizeof(double) * (size_t)N * Cin);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const long v = lin(x, y, z, nx, ny);
+                for (int t = 0; t < 27; ++t) {
+                    long q;
+                    if (!tap_neighbour(x, y, z, t, nx, ny, nz, &q)) continue;
+                    for (int o = 0; o < Cout; ++o)
+                        for (int c = 0; c < Cin; ++c)
+                            din[q * Cin + c] += w[((long)o * 27 + t) * Cin + c] * dout[v * Cout + o];
+                }
+            }
+}
+
+/* dw[o][t][c] = sum_v dout[v][o] in[v + off(t)][c] */
+void or_conv3d_wgrad(const double *in, int Cin, const double *dout, int Cout, int nx, int ny, int nz, double *dw)
+{
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < Cout; ++o)
+        for (int t = 0; t < 27; ++t)
+            for (int c = 0; c < Cin; ++c) {
+                double acc = 0.0;
+                for (int z = 0; z < nz; ++z)
+                    for (int y = 0; y < ny; ++y)
+                        for (int x = 0; x < nx; ++x) {
+                            long q;
+                            if (!tap_neighbour(x, y, z, t, nx, ny, nz, &q)) continue;
+                            acc += dout[lin(x, y, z, nx, ny) * Cout + o] * in[q * Cin + c];
+                        }
+                dw[((long)o * 27 + t) * Cin + c] = acc;
+            }
+}
