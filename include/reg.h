@@ -202,10 +202,102 @@ REG_API reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const voi
  * time each sweep inside a long run without synchronising. */
 REG_API reg_status reg_set_timing_events(void *const *events, int n);
 
+/* ------------------------------------------------------------------------
+ * Learned initialiser: operators of a small 3-D U-Net that predicts a
+ * half-resolution initial displacement from a downsampled (F, M) pair.  The
+ * paper has no learned initialiser of its own (it trains other networks
+ * with its fused losses, Sec. 4); the network is specified alongside the
+ * method as an extension.  The convolutions are the only tensor-core work:
+ * BF16 implicit GEMMs on tcgen05 with FP32 accumulation in tensor memory.
+ *
+ * Layouts: activations are channels-last BF16 [nz][ny][nx][C] with C % 8 == 0
+ * (8 channels = one 16-byte load); volumes here have fewer than 2^31
+ * voxels.  Weights are packed BF16 [rows][Kpad], k = tap * Cin + cin,
+ * tap = (kz * 3 + ky) * 3 + kx for the offset (kx-1, ky-1, kz-1), Kpad =
+ * reg_nn_conv_kpad(Cin), rows = Cout rounded up to 16 (extra rows and K
+ * padding zero).  3 x 3 x 3 taps, zero padding 1, stride 1.  Displacement
+ * fields are SoA FP32 [3][nz][ny][nx] in voxel units of their own grid.
+ * All entry points validate on the host, enqueue on `stream`, allocate
+ * nothing; scratch buffers are the caller's.
+ * ------------------------------------------------------------------------ */
+
+/* Kpad (the packed K length, a multiple of 64) for Cin input channels. */
+REG_API size_t reg_nn_conv_kpad(int Cin);
+
+/* out = epilogue(conv(in, W)): epilogue 0 = LeakyReLU(acc + bias, slope) ->
+ * BF16 channels-last (Cout % 8 == 0); 1 = acc -> BF16 (no bias); 2 = acc +
+ * bias -> FP32 SoA [Cout][N voxels] (any Cout <= 64).  Cin in [8, 128]. */
+REG_API reg_status reg_nn_conv3d_fwd(const void *in, int Cin, const void *W, const float *bias, int Cout, reg_dims d,
+                                     int epilogue, float slope, void *out, void *stream);
+
+/* Data gradient: din (BF16 channels-last, Cin) = conv^T(dpre (Cout), W): the
+ * weights are flipped and transposed into Wd_scratch
+ * (reg_nn_dgrad_scratch_bytes), then the forward kernel runs on them. */
+REG_API size_t reg_nn_dgrad_scratch_bytes(int Cin, int Cout);
+REG_API reg_status reg_nn_conv3d_dgrad(const void *dpre, int Cout, const void *W, int Cin, reg_dims d,
+                                       void *Wd_scratch, void *din, void *stream);
+
+/* Weight gradient: dW (FP32, packed [Cout][Kpad]) = sum over voxels of
+ * in_col (x) dpre, split over voxel ranges into scratch
+ * (reg_nn_wgrad_scratch_bytes) and reduced in a fixed order (deterministic).
+ * Cout in {16, 32, 48, 64} (pad a smaller Cout with zero channels). */
+REG_API size_t reg_nn_wgrad_scratch_bytes(reg_dims d, int Cin, int Cout);
+REG_API reg_status reg_nn_conv3d_wgrad(const void *in, int Cin, const void *dpre, int Cout, reg_dims d,
+                                       void *scratch, size_t scratch_bytes, float *dW, void *stream);
+
+/* Network input: average-pool F and M (img_dt, dims d) by `factor`, map each
+ * to (v - lo) / (hi - lo), write channels-last BF16 with 8 channels (F, M,
+ * six zeros) at d / factor. */
+REG_API reg_status reg_nn_pack_pair(const void *F, const void *M, int img_dt, reg_dims d, int factor, float f_lo,
+                                    float f_hi, float m_lo, float m_hi, void *out, void *stream);
+
+/* dpre = dout * (out > 0 ? 1 : slope) over n BF16 elements (LeakyReLU backward
+ * from its output, which has the sign of its input). */
+REG_API reg_status reg_nn_leaky_bwd(const void *out, const void *dout, long long n, float slope, void *dpre,
+                                    void *stream);
+
+/* dbias[c] = sum over V voxels of dpre[v][c] (fixed-order FP64 partials). */
+REG_API size_t reg_nn_bias_grad_scratch_bytes(int C);
+REG_API reg_status reg_nn_bias_grad(const void *dpre, long long V, int C, void *scratch, float *dbias, void *stream);
+
+/* 2x average pooling of a channels-last BF16 volume of dims d_in (even), or
+ * its backward (in = gradient at d_in / 2, out = gradient at d_in). */
+REG_API reg_status reg_nn_avgpool2(const void *in, int C, reg_dims d_in, void *out, int backward, void *stream);
+
+/* 2x trilinear upsampling (voxel-centre aligned, border clamped) of a
+ * channels-last BF16 volume of dims d_coarse, or its backward (a gather). */
+REG_API reg_status reg_nn_upsample2(const void *in, int C, reg_dims d_coarse, void *out, int backward, void *stream);
+
+/* Channel concat / slice over V voxels: put writes src (Csrc channels) into
+ * channels [c0, c0 + Csrc) of dst (Cdst channels); take copies channels
+ * [c0, c0 + Cdst) of src into dst; accumulate != 0 adds instead of copying. */
+REG_API reg_status reg_nn_put_channels(const void *src, int Csrc, long long V, void *dst, int Cdst, int c0,
+                                       int accumulate, void *stream);
+REG_API reg_status reg_nn_take_channels(const void *src, int Csrc, int c0, long long V, void *dst, int Cdst,
+                                        int accumulate, void *stream);
+
+/* Training loss: loss (device double) = mean of (pred - target)^2 over the 3
+ * SoA channels of V voxels; dpred = its gradient as channels-last BF16 with
+ * Cpad channels (channels >= 3 zero). */
+REG_API size_t reg_nn_mse_scratch_bytes(void);
+REG_API reg_status reg_nn_mse(const float *pred, const float *target, long long V, int Cpad, void *dpred,
+                              void *scratch, double *loss, void *stream);
+
+/* Displacement resampling: 2x average pooling rescaled to the coarse voxel
+ * size (u / 2), and trilinear upsampling by an integer factor rescaled to the
+ * fine voxel size (u * factor). */
+REG_API reg_status reg_nn_field_down2(const float *u, reg_dims d_fine, float *out, void *stream);
+REG_API reg_status reg_nn_field_upsample(const float *u, reg_dims d_coarse, int factor, float *out, void *stream);
+
+/* Adam on FP32 master weights (n elements, grad_scale applied), optionally
+ * writing the BF16 copy used by the convolutions. */
+REG_API reg_status reg_nn_adam(float *w, float *m, float *v, const float *g, long long n, const reg_adam_desc *adam,
+                               int t, void *w_bf16, void *stream);
+
 /* Test hook for the tensor-core engine: C[M x N] (FP32, row-major) =
  * A B^T with BF16 A and B, computed by the tcgen05 mainloop used by the
  * convolutions.  a_mn_major == 0: A is [M][K] (K contiguous), 1: [K][M];
- * likewise B with N.  M % 128 == 0, N in {16, 32, 48, 64}, K % 64 == 0. */
+ * likewise B with N.  M % 128 == 0, N % 16 == 0 and N <= 128, K % 64 == 0. */
 REG_API reg_status reg_debug_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int a_mn_major,
                                        int b_mn_major, void *stream);
 

@@ -295,3 +295,62 @@ def reg_debug_gemm_bf16(A, B, M: int, N: int, K: int, a_mn_major: bool = False, 
     _check(_lib().reg_debug_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(bool(a_mn_major)),
                                       int(bool(b_mn_major)), _stream(A)), "reg_debug_gemm_bf16")
     return C
+
+
+# ---------------------------------------------------------------------------
+# learned-initialiser operators (reg_nn_*): argument marshalling only
+# ---------------------------------------------------------------------------
+_SZ = ctypes.c_size_t
+_NN = {
+    "reg_nn_conv_kpad": ([ctypes.c_int], _SZ),
+    "reg_nn_conv3d_fwd": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, RegDims, ctypes.c_int, ctypes.c_float, _vp, _vp],
+                          _st),
+    "reg_nn_dgrad_scratch_bytes": ([ctypes.c_int, ctypes.c_int], _SZ),
+    "reg_nn_conv3d_dgrad": ([_vp, ctypes.c_int, _vp, ctypes.c_int, RegDims, _vp, _vp, _vp], _st),
+    "reg_nn_wgrad_scratch_bytes": ([RegDims, ctypes.c_int, ctypes.c_int], _SZ),
+    "reg_nn_conv3d_wgrad": ([_vp, ctypes.c_int, _vp, ctypes.c_int, RegDims, _vp, _SZ, _vp, _vp], _st),
+    "reg_nn_pack_pair": ([_vp, _vp, ctypes.c_int, RegDims, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, ctypes.c_float, _vp, _vp], _st),
+    "reg_nn_leaky_bwd": ([_vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp], _st),
+    "reg_nn_bias_grad_scratch_bytes": ([ctypes.c_int], _SZ),
+    "reg_nn_bias_grad": ([_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp], _st),
+    "reg_nn_avgpool2": ([_vp, ctypes.c_int, RegDims, _vp, ctypes.c_int, _vp], _st),
+    "reg_nn_upsample2": ([_vp, ctypes.c_int, RegDims, _vp, ctypes.c_int, _vp], _st),
+    "reg_nn_put_channels": ([_vp, ctypes.c_int, ctypes.c_longlong, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+                            _st),
+    "reg_nn_take_channels": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, ctypes.c_int, ctypes.c_int,
+                              _vp], _st),
+    "reg_nn_mse_scratch_bytes": ([], _SZ),
+    "reg_nn_mse": ([_vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp], _st),
+    "reg_nn_field_down2": ([_vp, RegDims, _vp, _vp], _st),
+    "reg_nn_field_upsample": ([_vp, RegDims, ctypes.c_int, _vp, _vp], _st),
+    "reg_nn_adam": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.POINTER(RegAdamDesc), ctypes.c_int, _vp, _vp],
+                    _st),
+}
+EXPORTS = EXPORTS + tuple(_NN)
+_nn_ready = False
+
+
+def nn():
+    """The library with the reg_nn_* signatures declared."""
+    global _nn_ready
+    L = _lib()
+    if not _nn_ready:
+        for name, (args, res) in _NN.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _nn_ready = True
+    return L
+
+
+def nn_check(status, where):
+    _check(status, where)
+
+
+def ptr(t):
+    return _ptr(t)
+
+
+def stream_of(t=None):
+    return _stream(t)

@@ -331,7 +331,7 @@ reg_status reg_debug_gemm_bf16(const void *A, const void *B, float *C, int M, in
     REG_TRY(check_ptr(A));
     REG_TRY(check_ptr(B));
     REG_TRY(check_ptr(C));
-    if (M <= 0 || M % 128 || N < 16 || N > 64 || N % 16 || K <= 0 || K % 64) return REG_ERR_SHAPE;
+    if (M <= 0 || M % 128 || N < 16 || N > 128 || N % 16 || K <= 0 || K % 64) return REG_ERR_SHAPE;
     if ((a_mn_major & ~1) || (b_mn_major & ~1)) return REG_ERR_INVALID_ARG;
     return cuda_status(launch_gemm_test(A, B, C, M, N, K, a_mn_major, b_mn_major, (cudaStream_t)stream));
 }

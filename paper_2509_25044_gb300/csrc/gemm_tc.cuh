@@ -14,9 +14,9 @@ constexpr int GEMM_THREADS = 128;  // 4 warps: one TMEM lane (tile row) per thre
 constexpr int GEMM_M = 128;
 constexpr int GEMM_KC = 64;        // K elements per staged chunk (4 MMAs of K = 16)
 constexpr int GEMM_KG = GEMM_KC / 8;
-constexpr int GEMM_MAXN = 64;
+constexpr int GEMM_MAXN = 128;
 constexpr int GEMM_A_BYTES = GEMM_M * GEMM_KC * 2;        // 16 KiB
-constexpr int GEMM_B_BYTES = GEMM_MAXN * GEMM_KC * 2;     // 8 KiB
+constexpr int GEMM_B_BYTES = GEMM_MAXN * GEMM_KC * 2;     // 16 KiB
 constexpr int GEMM_STAGE_BYTES = GEMM_A_BYTES + GEMM_B_BYTES;
 
 struct GemmShared {

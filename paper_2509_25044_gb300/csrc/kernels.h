@@ -122,3 +122,35 @@ int num_sms();
 unsigned *error_word();
 
 }  // namespace regk
+
+// ---- learned initialiser (unet.cu, unet_ops.cu) -------------------------------
+namespace regk {
+size_t gemm_smem_bytes();
+cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, const float *bias, int Cout, int N,
+                            const Dims &d, int epi, float slope, void *out, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const void *in, int Cin, const void *dpre, int Cout, const Dims &d, float *part,
+                              float *dW, int Kpad, cudaStream_t s);
+size_t wgrad_part_bytes(const Dims &d, int Cin, int Cout);
+cudaError_t launch_repack_dgrad(const void *W, int Cout, int Cin, int Kpad, void *Wd, int Nd, int Kpad_d,
+                                cudaStream_t s);
+cudaError_t launch_pack_pair(const void *F, const void *M, int dt, const Dims &gin, int factor, float f_lo,
+                             float f_scale, float m_lo, float m_scale, void *out, cudaStream_t s);
+cudaError_t launch_leaky_bwd(const void *out, const void *dout, long long n, float slope, void *dpre, cudaStream_t s);
+int bias_grad_blocks();
+cudaError_t launch_bias_grad(const void *dpre, long long V, int C, double *part, float *dbias, cudaStream_t s);
+cudaError_t launch_avgpool2(const void *in, int C, const Dims &gi, void *out, cudaStream_t s);
+cudaError_t launch_avgpool2_bwd(const void *dout, int C, const Dims &gi, void *din, cudaStream_t s);
+cudaError_t launch_upsample2(const void *in, int C, const Dims &gc, void *out, cudaStream_t s);
+cudaError_t launch_upsample2_bwd(const void *dout, int C, const Dims &gc, void *din, cudaStream_t s);
+cudaError_t launch_put_channels(const void *src, int Csrc, long long V, void *dst, int Cdst, int c0, int acc,
+                                cudaStream_t s);
+cudaError_t launch_take_channels(const void *src, int Csrc, int c0, long long V, void *dst, int Cdst, int acc,
+                                 cudaStream_t s);
+int mse_blocks();
+cudaError_t launch_mse(const float *pred, const float *tgt, long long V, int Cpad, void *dpred, double *part,
+                       double *loss, cudaStream_t s);
+cudaError_t launch_field_down2(const float *u, const Dims &gf, float *out, cudaStream_t s);
+cudaError_t launch_field_up(const float *u, const Dims &gc, int factor, float *out, cudaStream_t s);
+cudaError_t launch_adam_weights(float *w, float *m, float *v, const float *g, long long n, const StepParams &S,
+                                void *w_bf16, cudaStream_t s);
+}  // namespace regk

@@ -114,10 +114,121 @@ def main():
     t.add_argument("--eval-every", type=int, default=10)
     t.add_argument("--lam-scale", type=float, default=1.0)
     t.add_argument("--adam-eps", type=float, default=1e-8)
+    li = sub.add_parser("learned-init")
+    li.add_argument("--pairs", type=int, default=2000)
+    li.add_argument("--epochs", type=int, default=4)
+    li.add_argument("--lr", type=float, default=3e-4)
+    li.add_argument("--eval-config", default="c2")
+    li.add_argument("--eval-n", type=int, default=None)
+    li.add_argument("--save", default=None)
     args = ap.parse_args()
+    if args.cmd == "learned-init":
+        tr, net = train_init(args.pairs, args.epochs, lr=args.lr, out_path=args.save)
+        print(json.dumps(tr), flush=True)
+        print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n)), flush=True)
+        return
     if args.cmd == "ttl":
         print(json.dumps(time_to_loss(args.config, args.iters, args.eval_every, args.n, lam_scale=args.lam_scale,
                                       adam_eps=args.adam_eps)))
+
+
+# ---------------------------------------------------------------------------
+# learned initialiser: training and evaluation
+# ---------------------------------------------------------------------------
+def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 3e-4, seed0: int = 10_000,
+               out_path: str | None = None, log_every: int = 200) -> dict:
+    """Train the U-Net on n_pairs seeded pairs made with the library's warp
+    (targets: the known fields pooled to n/2).  Pairs are generated once and
+    kept on the device (packed inputs + targets)."""
+    import time
+    from .unet import UNet, training_pair
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    net = UNet(n_in=n, seed=0, device=dev)
+    L = net.L
+    t0 = time.perf_counter()
+    xs, ts = [], []
+    for i in range(n_pairs):
+        p = training_pair(n, seed0 + i, dev)
+        net.pack(p["F"], p["M"], 1, (float(p["F"].min()), float(p["F"].max())),
+                 (float(p["M"].min()), float(p["M"].max())))
+        xs.append(net.a["x0"].clone())
+        t = torch.empty((3, (n // 2) ** 3), device=dev)
+        capi.nn_check(L.reg_nn_field_down2(capi.ptr(p["v"]), capi.RegDims(n, n, n), capi.ptr(t), capi.stream_of(t)),
+                      "field_down2")
+        ts.append(t)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    hist = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    order_rng = np.random.default_rng(seed0)
+    for ep in range(epochs):
+        order = order_rng.permutation(n_pairs)
+        tot = torch.zeros((), dtype=torch.float64, device=dev)
+        for j, i in enumerate(order):
+            net.a["x0"].copy_(xs[i])
+            net.forward()
+            tot += net.loss_and_backward(ts[i])[0]
+            net.step(lr)
+        hist.append(float(tot.item()) / n_pairs)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    # baseline: predicting zero
+    zero = float(np.mean([float((t ** 2).mean().item()) for t in ts[:200]]))
+    out = {"experiment": "train_init", "n_pairs": n_pairs, "epochs": epochs, "n": n, "lr": lr,
+           "pair_generation_s": gen_s, "train_ms": train_ms, "ms_per_pair_step": train_ms / (epochs * n_pairs),
+           "loss_per_epoch": hist, "zero_prediction_loss": zero, "device_error": capi.reg_get_device_error()}
+    if out_path:
+        state = {k: (P.w.cpu(), P.b.cpu()) for k, P in net.p.items()}
+        torch.save({"state": state, "meta": out}, out_path)
+    return out, net
+
+
+def eval_init(net, config: str = "c2", iters: int | None = None, lam_scale: float = 10.0, n: int | None = None,
+              rel_tol: float = 0.01) -> dict:
+    """Registration of a held-out pair from zero and from the network's
+    initial field: iterations (and time) for the learned-init run to reach
+    the zero-init run's final objective within 1 % of the zero-init run's
+    total decrease; fold checks of both."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = synth.make(config, device=dev, n=n)
+    c = d["config"]
+    iters = iters or c["iters"]
+    F, M = d["F"].contiguous(), d["M"].contiguous()
+    cfg = _cfg(c, d, "f32", lam_scale)
+    r0 = Registration(F, M, cfg)
+    res0 = r0.run(iters)
+    fin0 = r0.objective()
+    L0, Lstar = float(res0.objective[0]), fin0["objective"]
+    tol = rel_tol * max(L0 - Lstar, 0.0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    u0 = net.predict_init(F, M, (float(F.min()), float(F.max())), (float(M.min()), float(M.max())))
+    ev1.record()
+    torch.cuda.synchronize()
+    init_ms = ev0.elapsed_time(ev1)
+    r1 = Registration(F, M, cfg, u0=u0)
+    res1 = r1.run(iters)
+    fin1 = r1.objective()
+    tr0 = np.append(res0.objective[1:], Lstar)
+    tr1 = np.append(res1.objective[1:], fin1["objective"])
+    k0 = _first_within(tr0, Lstar, tol)
+    k1 = _first_within(tr1, Lstar, tol)
+    err = lambda u: float(((u + d["u_true"]).norm() / d["u_true"].norm()).item())
+    out = {"experiment": "eval_init", "config": config, "n": F.shape[0], "iters": iters, "lam": cfg.lam,
+           "zero_init": {"objective_start": L0, "objective_final": Lstar, "iters_to_target": None if k0 is None else k0 + 1,
+                         "ms_per_iter": res0.ms_per_iter, "fold": r0.fold_check(), "rel_err_vs_inverse_true": err(r0.current)},
+           "learned_init": {"objective_start": float(res1.objective[0]), "objective_final": fin1["objective"],
+                            "iters_to_target": None if k1 is None else k1 + 1, "ms_per_iter": res1.ms_per_iter,
+                            "init_ms": init_ms, "fold": r1.fold_check(), "rel_err_vs_inverse_true": err(r1.current),
+                            "init_rel_err_vs_inverse_true": err(u0)}}
+    if k0 is not None and k1 is not None:
+        t0 = (k0 + 1) * res0.ms_per_iter
+        t1 = init_ms + (k1 + 1) * res1.ms_per_iter
+        out["time_to_target_ms"] = {"zero_init": t0, "learned_init": t1, "speedup": t0 / t1}
+    return out
 
 
 if __name__ == "__main__":

@@ -17,7 +17,7 @@ def capi():
 
 
 @pytest.mark.parametrize("a_mn,b_mn", [(0, 0), (1, 1), (0, 1), (1, 0)])
-@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (256, 32, 192), (128, 64, 128), (384, 48, 64)])
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (256, 32, 192), (128, 64, 128), (384, 48, 64), (128, 128, 256)])
 def test_gemm_matches_matmul(capi, a_mn, b_mn, M, N, K):
     g = torch.Generator(device=DEV).manual_seed(M * 7 + N * 3 + K + 11 * a_mn + 5 * b_mn)
     A = torch.randn((M, K), generator=g, device=DEV).to(torch.bfloat16)

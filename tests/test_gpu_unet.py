@@ -1,0 +1,169 @@
+"""Learned initialiser on the GPU: the tcgen05 implicit-GEMM convolutions
+against the FP64 oracle (forward, data and weight gradients), the whole
+U-Net forward/backward against an FP64 re-implementation with the same
+weights (torch functional ops on CPU), and a short training run."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2509_25044_gb300 import build, capi
+    build.build()
+    capi.load()
+    return capi
+
+
+def _pack_w(w, rows, kpad):
+    """[Cout][27][Cin] float -> packed [rows][kpad] (bf16 values)."""
+    cout, _, cin = w.shape
+    out = np.zeros((rows, kpad), dtype=np.float32)
+    out[:cout, :27 * cin] = w.reshape(cout, 27 * cin)
+    return torch.from_numpy(out).to(DEV).to(torch.bfloat16)
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("shape,cin,cout", [((9, 10, 11), 8, 16), ((6, 7, 8), 32, 64), ((5, 6, 4), 96, 32)])
+def test_conv_forward_matches_oracle(capi, shape, cin, cout):
+    L = capi.nn()
+    rng = np.random.default_rng(cin + cout)
+    x = _bf(rng.standard_normal(shape + (cin,)))
+    w = _bf(rng.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin)).float().numpy()
+    b = rng.standard_normal(cout).astype(np.float32)
+    kpad = int(L.reg_nn_conv_kpad(cin))
+    rows = (cout + 15) // 16 * 16
+    W = _pack_w(w, rows, kpad)
+    bias = torch.zeros(rows, device=DEV)
+    bias[:cout] = torch.from_numpy(b)
+    xd = x.to(DEV).contiguous()
+    V = int(np.prod(shape))
+    d = capi.RegDims(shape[2], shape[1], shape[0])
+    out32 = torch.empty((cout, V), device=DEV)
+    capi.nn_check(L.reg_nn_conv3d_fwd(capi.ptr(xd), cin, capi.ptr(W), capi.ptr(bias), cout, d, 2, 0.2,
+                                      capi.ptr(out32), capi.stream_of(xd)), "fwd f32")
+    outb = torch.empty((V, cout), dtype=torch.bfloat16, device=DEV)
+    capi.nn_check(L.reg_nn_conv3d_fwd(capi.ptr(xd), cin, capi.ptr(W), capi.ptr(bias), cout, d, 0, 0.2,
+                                      capi.ptr(outb), capi.stream_of(xd)), "fwd leaky")
+    torch.cuda.synchronize()
+    ref = O.conv3d(x.float().numpy(), w, b).reshape(V, cout)
+    got = out32.cpu().numpy().T
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    leaky = np.where(ref > 0, ref, 0.2 * ref)
+    assert np.abs(outb.float().cpu().numpy() - leaky).max() <= 2 ** -7 * np.abs(leaky).max()
+    assert capi.reg_get_device_error() == 0
+
+
+@pytest.mark.parametrize("shape,cin,cout", [((9, 10, 11), 16, 16), ((6, 8, 7), 96, 32), ((4, 5, 6), 128, 64)])
+def test_conv_gradients_match_oracle(capi, shape, cin, cout):
+    L = capi.nn()
+    rng = np.random.default_rng(3 * cin + cout)
+    x = _bf(rng.standard_normal(shape + (cin,)))
+    w = _bf(rng.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin)).float().numpy()
+    g = _bf(rng.standard_normal(shape + (cout,)))
+    kpad = int(L.reg_nn_conv_kpad(cin))
+    W = _pack_w(w, (cout + 15) // 16 * 16, kpad)
+    d = capi.RegDims(shape[2], shape[1], shape[0])
+    V = int(np.prod(shape))
+    xd, gd = x.to(DEV).contiguous(), g.to(DEV).contiguous()
+    wd = torch.empty(int(L.reg_nn_dgrad_scratch_bytes(cin, cout)), dtype=torch.uint8, device=DEV)
+    din = torch.empty((V, cin), dtype=torch.bfloat16, device=DEV)
+    capi.nn_check(L.reg_nn_conv3d_dgrad(capi.ptr(gd), cout, capi.ptr(W), cin, d, capi.ptr(wd), capi.ptr(din),
+                                        capi.stream_of(gd)), "dgrad")
+    ws = torch.empty(int(L.reg_nn_wgrad_scratch_bytes(d, cin, cout)), dtype=torch.uint8, device=DEV)
+    dW = torch.empty((cout, kpad), dtype=torch.float32, device=DEV)
+    capi.nn_check(L.reg_nn_conv3d_wgrad(capi.ptr(xd), cin, capi.ptr(gd), cout, d, capi.ptr(ws), ws.numel(),
+                                        capi.ptr(dW), capi.stream_of(gd)), "wgrad")
+    torch.cuda.synchronize()
+    ref_din = O.conv3d_dgrad(g.float().numpy(), w).reshape(V, cin)
+    assert np.abs(din.float().cpu().numpy() - ref_din).max() <= 2 ** -7 * np.abs(ref_din).max()
+    ref_dw = O.conv3d_wgrad(x.float().numpy(), g.float().numpy()).reshape(cout, 27 * cin)
+    got = dW.cpu().numpy()
+    assert np.abs(got[:, :27 * cin] - ref_dw).max() <= 1e-4 * np.abs(ref_dw).max()
+    assert not got[:, 27 * cin:].any()
+
+
+def _torch_unet(net, x0, target):
+    """FP64 CPU re-implementation with the network's BF16 weights."""
+    import torch.nn.functional as Fn
+    from paper_2509_25044_gb300.unet import LAYERS, SLOPE
+    ws, bs = {}, {}
+    for name, cin, cout, _ in LAYERS:
+        P = net.p[name]
+        w = P.wb.double().cpu()[:cout, :27 * cin].reshape(cout, 3, 3, 3, cin).permute(0, 4, 1, 2, 3)
+        ws[name] = w.clone().requires_grad_(True)
+        bs[name] = P.b.double().cpu()[:cout].clone().requires_grad_(True)
+
+    def conv(name, t, act=True):
+        y = Fn.conv3d(t, ws[name], bs[name], padding=1)
+        return Fn.leaky_relu(y, SLOPE) if act else y
+
+    up = lambda t: Fn.interpolate(t, scale_factor=2, mode="trilinear", align_corners=False)
+    e0 = conv("c0b", conv("c0a", x0))
+    e1 = conv("c1b", conv("c1a", Fn.avg_pool3d(e0, 2)))
+    e2 = conv("c2b", conv("c2a", Fn.avg_pool3d(e1, 2)))
+    b3 = conv("c3b", conv("c3a", Fn.avg_pool3d(e2, 2)))
+    d2 = conv("d2b", conv("d2a", torch.cat([up(b3), e2], 1)))
+    d1 = conv("d1b", conv("d1a", torch.cat([up(d2), e1], 1)))
+    u = conv("head", d1, act=False)
+    loss = ((u - target) ** 2).mean()
+    loss.backward()
+    return u, loss, ws, bs
+
+
+def test_unet_forward_backward_match_fp64_reference(capi):
+    from paper_2509_25044_gb300.unet import LAYERS, UNet, training_pair
+    n = 32
+    net = UNet(n_in=n, seed=3, device=DEV)
+    pair = training_pair(n, 5, DEV)
+    net.pack(pair["F"], pair["M"], 1, (float(pair["F"].min()), float(pair["F"].max())),
+             (float(pair["M"].min()), float(pair["M"].max())))
+    u = net.forward().clone()
+    target = torch.randn((3, (n // 2) ** 3), device=DEV) * 0.1
+    loss = net.loss_and_backward(target)
+    torch.cuda.synchronize()
+    x0 = net.a["x0"].double().cpu().reshape(n, n, n, 8).permute(3, 0, 1, 2)[None]
+    tgt = target.double().cpu().reshape(3, n // 2, n // 2, n // 2)[None]
+    ur, lr_, ws, bs = _torch_unet(net, x0, tgt)
+    ur = ur[0].reshape(3, -1).detach()
+    rel = lambda a, b: float((a - b).norm() / b.norm())
+    assert rel(u.double().cpu(), ur) < 3e-2
+    assert abs(loss.item() - lr_.item()) < 3e-2 * lr_.item()
+    for name, cin, cout, _ in LAYERS:
+        P = net.p[name]
+        gw = P.gw.double().cpu()[:cout, :27 * cin].reshape(cout, 3, 3, 3, cin).permute(0, 4, 1, 2, 3)
+        assert rel(gw, ws[name].grad) < 8e-2, name
+        assert rel(P.gb.double().cpu()[:cout], bs[name].grad) < 8e-2, name
+    assert capi.reg_get_device_error() == 0
+
+
+def test_unet_training_reduces_loss(capi):
+    from paper_2509_25044_gb300.unet import UNet, training_pair
+    n = 32
+    net = UNet(n_in=n, seed=1, device=DEV)
+    pairs = [training_pair(n, 100 + i, DEV) for i in range(4)]
+    tgts = []
+    for p in pairs:
+        t = torch.empty((3, (n // 2) ** 3), device=DEV)
+        capi.nn_check(net.L.reg_nn_field_down2(capi.ptr(p["v"]), capi.RegDims(n, n, n), capi.ptr(t),
+                                               capi.stream_of(t)), "down2")
+        tgts.append(t)
+    losses = []
+    for epoch in range(30):
+        tot = 0.0
+        for p, t in zip(pairs, tgts):
+            net.pack(p["F"], p["M"], 1, (float(p["F"].min()), float(p["F"].max())),
+                     (float(p["M"].min()), float(p["M"].max())))
+            net.forward()
+            tot += net.loss_and_backward(t).item()
+            net.step(5e-4)
+        losses.append(tot / len(pairs))
+    assert losses[-1] < 0.85 * losses[0], losses
