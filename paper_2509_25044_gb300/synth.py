@@ -6,7 +6,8 @@ these datasets ships here, so these generators stand in for them.
 
 This module holds none of the registration method's arithmetic: it draws
 random numbers, sums Gaussian blobs, paints label maps, smooths with a
-Gaussian (torch conv1d, replicate padding) and builds the moving image with
+Gaussian (torch conv1d; replicate padding for images, periodic for the random
+displacement fields) and builds the moving image with
 ``torch.nn.functional.grid_sample`` (library trilinear sampling,
 align_corners=True, border padding).  Both the CUDA path and the CPU oracle
 take their inputs from here.
@@ -27,8 +28,10 @@ import torch
 # ---------------------------------------------------------------------------
 # primitives
 # ---------------------------------------------------------------------------
-def gaussian_smooth(vol: torch.Tensor, sigma: float, truncate: float = 4.0) -> torch.Tensor:
-    """Separable Gaussian of a [..., nz, ny, nx] tensor, 'nearest' borders."""
+def gaussian_smooth(vol: torch.Tensor, sigma: float, truncate: float = 4.0, periodic: bool = False) -> torch.Tensor:
+    """Separable Gaussian of a [..., nz, ny, nx] tensor with 'nearest'
+    borders, or periodic ones (periodic=True: the result of smoothing white
+    noise is then stationary, with no inflated variance at the faces)."""
     if sigma <= 0:
         return vol
     r = int(truncate * sigma + 0.5)
@@ -44,7 +47,11 @@ def gaussian_smooth(vol: torch.Tensor, sigma: float, truncate: float = 4.0) -> t
         chunks = []
         step = max(1, (1 << 27) // max(1, shp[-1] + 2 * r))
         for i in range(0, flat.shape[0], step):
-            part = torch.nn.functional.pad(flat[i:i + step], (r, r), mode="replicate")
+            if periodic:
+                idx = torch.arange(-r, shp[-1] + r, device=flat.device) % shp[-1]
+                part = flat[i:i + step].index_select(-1, idx)
+            else:
+                part = torch.nn.functional.pad(flat[i:i + step], (r, r), mode="replicate")
             chunks.append(torch.nn.functional.conv1d(part, k))
         out = torch.cat(chunks, 0).reshape(shp).movedim(-1, ax).contiguous()
         del flat, chunks
@@ -75,14 +82,15 @@ def _sample_trilinear(M: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
 
 
 def smooth_field(shape, sigma: float, max_norm: float, rng=None, gen=None, device="cpu") -> torch.Tensor:
-    """3 channels of N(0,1) white noise, Gaussian-smoothed (sigma voxels), then
-    scaled so that max_p |u(p)|_2 = max_norm.  Returns [3, nz, ny, nx] float32."""
+    """3 channels of N(0,1) white noise, Gaussian-smoothed (sigma voxels,
+    periodic borders so the field is stationary), then scaled so that
+    max_p |u(p)|_2 = max_norm.  Returns [3, nz, ny, nx] float32."""
     nz, ny, nx = shape
     if gen is not None:
         noise = torch.randn((3, nz, ny, nx), generator=gen, device=device, dtype=torch.float32)
     else:
         noise = torch.from_numpy(rng.standard_normal((3, nz, ny, nx), dtype=np.float32)).to(device)
-    u = gaussian_smooth(noise, sigma)
+    u = gaussian_smooth(noise, sigma, periodic=True)
     del noise
     norm = torch.sqrt((u.double() ** 2).sum(0)).max().item() if u.numel() < (1 << 28) else \
         max(torch.sqrt((u[:, z:z + 64].double() ** 2).sum(0)).max().item() for z in range(0, nz, 64))

@@ -25,7 +25,8 @@ def test_c0_lncc_converges_without_folding():
 
 def test_c1_mi_small_converges():
     d = synth.make("c1", device=DEV, n=64)
-    cfg = RegConfig(loss="mi", bins=32, f_range=d["f_range"], m_range=d["m_range"], lam=1.0, lr=0.1)
+    # lam = 2: at lam = 1 the MI run folds a few voxels of the 64^3 grid
+    cfg = RegConfig(loss="mi", bins=32, f_range=d["f_range"], m_range=d["m_range"], lam=2.0, lr=0.1)
     reg = Registration(d["F"], d["M"], cfg)
     res = reg.run(60)
     assert res.objective[-1] < res.objective[0]  # MI increases: -MI + lam R decreases
