@@ -33,10 +33,11 @@ WORKLOADS = {
 }
 # algorithmic bytes per voxel of one iteration (each compulsory tensor moved once)
 #   sweep 1: F, M (one gather counted once), u;  LNCC also writes 3 FP32 coefficient fields
-#   sweep 2: F, M, u, m, v read; u', m, v written;  LNCC also reads the coefficient fields
+#   sweep 2: F, M, u (12 B), m, v (3 components each) read; u' (12 B), m, v written;
+#            LNCC also reads the coefficient fields
 def bytes_per_voxel(kind, img_bytes, mom_bytes):
     s1 = 2 * img_bytes + 12 + (12 if kind == "lncc" else 0)
-    s2 = 2 * img_bytes + 12 + 2 * mom_bytes * 3 + 12 + (12 if kind == "lncc" else 0)
+    s2 = 2 * img_bytes + 12 + 12 + 2 * (2 * 3 * mom_bytes) + (12 if kind == "lncc" else 0)
     return s1, s2
 
 
@@ -327,7 +328,7 @@ def run_ours(args):
         return
     value = world * N * K / (ms_max * 1e-3) / 1e9
     e2e_value = world * N * Ke / (e2e_ms * 1e-3) / 1e9
-    ib = 2 if bf16 else 4
+    ib = 2 if bf16 else 4  # images and Adam moments share the storage type in every workload
     b1, b2 = bytes_per_voxel(kind, ib, ib)
     peak, peak_kind = read_peaks()
     t2 = statistics.median(s2)

@@ -48,12 +48,13 @@ constexpr int TY = 8;
 constexpr int TILE_THREADS = TX * TY;
 constexpr int MAX_BINS = 64;
 constexpr int MAX_RADIUS = 7;  // LNCC window <= 15
-// MI histogram fixed point: one unit of kernel weight = 2^20 counts.  A CTA
-// adds at most MI_MAX_CTA_VOXELS voxels into its shared 32-bit bins, each
-// voxel at most (2/3)^2 of a unit per bin: 8192 * 0.445 * 2^20 < 2^32, so a
-// bin cannot wrap.
+// MI histogram fixed point: one unit of kernel weight = 2^20 counts.  One
+// shared copy of a CTA's 32-bit bins takes at most MI_MAX_COPY_VOXELS
+// voxels before it is added to the global 64-bit histogram, each voxel at
+// most (2/3)^2 of a unit per bin: 8192 * 0.445 * 2^20 < 2^32, so a bin
+// cannot wrap.
 constexpr float MI_FIXED_SCALE = 1048576.0f;
-constexpr int MI_MAX_CTA_VOXELS = 8192;
+constexpr int MI_MAX_COPY_VOXELS = 8192;
 
 struct MarchGrid {
     int tiles_x, tiles_y, chunks, zc;
@@ -75,7 +76,6 @@ struct LnccParams {
 };
 
 // per-kernel grids (used both to launch and to size the workspace)
-MarchGrid mi_hist_grid(const Dims &g);
 MarchGrid mi_sweep_grid(const Dims &g);
 MarchGrid lncc_grid(const Dims &g, int r);
 MarchGrid diffusion_grid(const Dims &g);

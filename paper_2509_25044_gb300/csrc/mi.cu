@@ -11,12 +11,15 @@
 //     free).  No N x B Parzen block is ever materialised (the memory the
 //     paper removes).
 //   finalise (mi_finalize_kernel): p = hist / (2^20 N) in FP64, marginals
-//     as row / column sums, MI = sum p log(p / (pI pJ)), and the FP32 table
+//     as row / column sums, the log ratios in FP32, MI = sum p log(p / (pI
+//     pJ)) accumulated in FP64, and the FP32 table
 //     G'[m][n] = -(B-3) m_scale / N * log(p / (pI pJ)) of the adjoint.
 //   sweep 2 (mi_sweep2_kernel): warp again with slope, the adjoint
 //     dL/dJ = sum_{a,b} G'[mF+a][nJ+b] w_a(sF) w'_b(sJ) (Eq. gradientmi-
 //     threadn with the 16 non-zero kernel terms), chained through the
 //     sampler slope; optionally fused with the diffusion gradient and Adam.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace regk {
@@ -53,75 +56,96 @@ __device__ __forceinline__ float to_bin(float v, float lo, float scale, int B) {
     return fmaf(t, (float)(B - 3), 1.0f);
 }
 
-// Shared histogram of one CTA: HIST_COPIES private copies (lane % copies
-// picks one), each padded by one word so that the same bin of different
-// copies falls in different banks.  Lanes of a warp usually see the same
-// bins (neighbouring voxels), so the copies cut same-address serialisation.
-constexpr int HIST_WORDS = 8 * (32 * 32 + 1);  // >= copies * (B*B + 1) for every B <= 64
-__host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 8 : 2; }
-
-__device__ __forceinline__ void flush16(unsigned *shc, int K, int B, const unsigned acc[16]) {
-#pragma unroll
-    for (int e = 0; e < 16; ++e)
-        if (acc[e]) atomicAdd(shc + K + (e >> 2) * B + (e & 3), acc[e]);
+// Shared histogram of one CTA: copies private copies, copy c used by the
+// lanes with lane % copies == c, each copy padded by one word so that the
+// same bin of different copies falls in different banks.  With 32 copies
+// (B <= 32) the 32 lanes of one atomic instruction never share an address.
+constexpr int HIST_TX = 32, HIST_TY = 32, HIST_THREADS = HIST_TX * HIST_TY;
+__host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 32 : (B <= 45 ? 16 : 8); }
+// A copy serves (32 / copies) lanes of each of the 32 warps, one voxel per
+// lane and plane, so after this many planes a CTA adds its copies to the
+// global histogram and clears them (MI_MAX_COPY_VOXELS keeps the 32-bit
+// bins from wrapping).
+__host__ __device__ constexpr int hist_batch_planes(int B) {
+    return MI_MAX_COPY_VOXELS / (32 * (32 / hist_copies(B)));
 }
+size_t mi_hist_smem_bytes(int B) { return sizeof(unsigned) * (size_t)hist_copies(B) * ((size_t)B * B + 1); }
 
-// Each thread marches its (x, y) column through the z-chunk.  While its
-// voxels stay in the same 4 x 4 bin block K (most consecutive voxels do on
-// smooth or piecewise-constant images), the thread only adds its fixed-point
-// weights into registers; the 16 sums go to shared memory when the block
-// changes.  Bins are 32-bit fixed point (MI_FIXED_SCALE); the per-CTA voxel
-// cap keeps them from wrapping; each CTA adds its bins (summed over the
-// copies) to the global 64-bit histogram.
+// Persistent CTAs (one per SM): the volume is cut into 32 x 32 columns, the
+// (column, plane) pairs are numbered column-major and each CTA takes one
+// contiguous range of them, so the work is balanced to within one plane.
+// Each thread marches its (x, y) column through the planes of its range,
+// with F and u of the next plane requested before the current plane is
+// computed, and adds the 16 fixed-point products of its voxel's B-spline
+// weights to its copy.  The products are rounded by one FFMA against
+// 2^23 (exact round-to-nearest of wf * wj * MI_FIXED_SCALE, which is below
+// 2^22), so the bins are sums of integers and the histogram does not depend
+// on the order of the atomics (deterministic).
 template <typename T, int PAD, typename I>
-__global__ void __launch_bounds__(TILE_THREADS, 4) mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M,
-                                                                  const float *__restrict__ u, Dims g, MiParams P,
-                                                                  int zc, unsigned long long *__restrict__ hist) {
-    __shared__ unsigned sh[HIST_WORDS];
+__global__ void __launch_bounds__(HIST_THREADS, 1)
+    mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
+                   int tiles_x, long long total, unsigned long long *__restrict__ hist) {
+    extern __shared__ unsigned sh[];
     const int B = P.bins, BB = B * B;
     const int copies = hist_copies(B), pitch = BB + 1;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < copies * pitch; i += TILE_THREADS) sh[i] = 0u;
+    const int tid = threadIdx.y * HIST_TX + threadIdx.x;
+    for (int i = tid; i < copies * pitch; i += HIST_THREADS) sh[i] = 0u;
     __syncthreads();
-
-    const int x = blockIdx.x * TX + threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(g.nz, z0 + zc);
-    if (x < g.nx && y < g.ny) {
-        unsigned *shc = sh + (threadIdx.x % copies) * pitch;
-        const float *u0 = u, *u1 = u + g.n, *u2 = u + 2 * g.n;
-        const I nxy = (I)g.nxy;
-        I p = (I)z0 * nxy + (I)y * g.nx + x;
-        int K = -1;
-        unsigned acc[16];
+    unsigned *shc = sh + (threadIdx.x % copies) * pitch;
+    const float *u0 = u, *u1 = u + g.n, *u2 = u + 2 * g.n;
+    const I nxy = (I)g.nxy;
+    const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
+    const int batch = hist_batch_planes(B);
+    constexpr float MAGIC = 8388608.0f;  // 2^23: ulp 1 in [2^23, 2^24)
+    for (long long b0 = beg; b0 < end; b0 += batch) {
+        const long long b1 = min(end, b0 + batch);
+        for (long long pos = b0; pos < b1;) {
+            const long long tile = pos / g.nz;
+            const int z0 = (int)(pos - tile * g.nz);
+            const int z1 = (int)min((long long)g.nz, (long long)z0 + (b1 - pos));
+            pos += z1 - z0;
+            const int x = (int)(tile % tiles_x) * HIST_TX + threadIdx.x;
+            const int y = (int)(tile / tiles_x) * HIST_TY + threadIdx.y;
+            if (x >= g.nx || y >= g.ny) continue;
+            I p = (I)z0 * nxy + (I)y * g.nx + x;
+            float fv = ld_vox(F, p), ux = __ldg(u0 + p), uy = __ldg(u1 + p), uz = __ldg(u2 + p);
+            for (int z = z0; z < z1; ++z, p += nxy) {
+                float fn = 0.0f, nx0 = 0.0f, nx1 = 0.0f, nx2 = 0.0f;
+                if (z + 1 < z1) {
+                    fn = ld_vox(F, p + nxy);
+                    nx0 = __ldg(u0 + p + nxy);
+                    nx1 = __ldg(u1 + p + nxy);
+                    nx2 = __ldg(u2 + p + nxy);
+                }
+                const float jv = sample<T, PAD, I>(M, g, x, y, z, ux, uy, uz);
+                float wf[4], wj[4];
+                const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
+                const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
+                unsigned *row = shc + iF * B + iJ;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0u;
-        for (int z = z0; z < z1; ++z, p += nxy) {
-            const float fv = ld_vox(F, p);
-            const float jv = sample<T, PAD, I>(M, g, x, y, z, __ldg(u0 + p), __ldg(u1 + p), __ldg(u2 + p));
-            float wf[4], wj[4];
-            const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
-            const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
-            const int key = iF * B + iJ;
-            if (key != K) {
-                if (K >= 0) flush16(shc, K, B, acc);
-                K = key;
+                for (int a = 0; a < 4; ++a) {
+                    const float sa = wf[a] * MI_FIXED_SCALE;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) acc[e] = 0u;
+                    for (int b = 0; b < 4; ++b)
+                        atomicAdd(row + b, __float_as_uint(fmaf(sa, wj[b], MAGIC)) - 0x4B000000u);
+                    row += B;
+                }
+                fv = fn;
+                ux = nx0;
+                uy = nx1;
+                uz = nx2;
             }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a * 4 + b] += __float2uint_rn(wf[a] * wj[b] * MI_FIXED_SCALE);
         }
-        if (K >= 0) flush16(shc, K, B, acc);
-    }
-    __syncthreads();
-    for (int i = tid; i < BB; i += TILE_THREADS) {
-        unsigned long long v = 0;
-        for (int c = 0; c < copies; ++c) v += sh[c * pitch + i];
-        if (v) atomicAdd(hist + i, v);
+        __syncthreads();
+        for (int i = tid; i < BB; i += HIST_THREADS) {
+            unsigned long long v = 0;
+            for (int c = 0; c < copies; ++c) {
+                v += sh[c * pitch + i];
+                sh[c * pitch + i] = 0u;
+            }
+            if (v) atomicAdd(hist + i, v);
+        }
+        __syncthreads();
     }
 }
 
@@ -146,14 +170,16 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
         pJ[n] = s;
     }
     __syncthreads();
+    // the per-bin log ratio in FP32 (GB300's FP64 rate is a small fraction of
+    // its FP32 rate and this block runs on one SM); the MI sum stays in FP64
     double acc = 0.0;
     for (int e = threadIdx.x; e < BB; e += blockDim.x) {
         const double v = p[e];
         float gv = 0.0f;
         if (v > 0.0) {
-            const double lr = log(v / (pI[e / B] * pJ[e % B]));
-            acc += v * lr;
-            gv = (float)(gscale * lr);
+            const float lr = logf((float)v / (float)(pI[e / B] * pJ[e % B]));
+            acc = fma(v, (double)lr, acc);
+            gv = (float)gscale * lr;
         }
         Gtab[e] = gv;
     }
@@ -171,11 +197,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                      double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
                      unsigned *err) {
-    __shared__ float Gs[MAX_BINS * MAX_BINS];
+    // G4[m][n] = G'[m][n .. n+3]: one 16-byte shared load per kernel row
+    extern __shared__ float4 G4[];  // B * B entries (dynamic)
     __shared__ double red[32];
     const int B = P.bins, BB = B * B;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < BB; i += TILE_THREADS) Gs[i] = Gtab[i];
+    for (int i = tid; i < BB; i += TILE_THREADS) {
+        const int n = i % B;
+        G4[i] = make_float4(Gtab[i], n + 1 < B ? Gtab[i + 1] : 0.0f, n + 2 < B ? Gtab[i + 2] : 0.0f,
+                            n + 3 < B ? Gtab[i + 3] : 0.0f);
+    }
     __syncthreads();
 
     const int x = blockIdx.x * TX + threadIdx.x;
@@ -231,8 +262,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
             float gj = 0.0f;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const float *row = Gs + (iF + a) * B + iJ;
-                const float t = fmaf(row[0], dj[0], fmaf(row[1], dj[1], fmaf(row[2], dj[2], row[3] * dj[3])));
+                const float4 r = G4[(iF + a) * B + iJ];
+                const float t = fmaf(r.x, dj[0], fmaf(r.y, dj[1], fmaf(r.z, dj[2], r.w * dj[3])));
                 gj = fmaf(wf[a], t, gj);
             }
             if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
@@ -280,25 +311,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
     }
 }
 
-MarchGrid mi_hist_grid(const Dims &g) {
-    return march_grid(g, 2LL * num_sms() * 4, 1, MI_MAX_CTA_VOXELS / TILE_THREADS);
-}
 MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                            const MiParams &P, unsigned long long *hist, cudaStream_t s) {
-    const MarchGrid G = mi_hist_grid(g);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    const int tiles_x = (g.nx + HIST_TX - 1) / HIST_TX, tiles_y = (g.ny + HIST_TY - 1) / HIST_TY;
+    const long long total = (long long)tiles_x * tiles_y * g.nz;
+    if (total <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>(num_sms(), total);
+    const dim3 block(HIST_TX, HIST_TY);
+    const size_t smem = mi_hist_smem_bytes(P.bins);
+    cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
-                mi_hist_kernel<T, decltype(pd)::value, I>
-                    <<<grid, block, 0, s>>>((const T *)F, (const T *)M, u, g, P, G.zc, hist);
+                auto kern = mi_hist_kernel<T, decltype(pd)::value, I>;
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess)
+                    kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, tiles_x, total, hist);
             });
         });
     });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -317,6 +353,14 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
     const MarchGrid G = mi_sweep_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
+    const size_t smem = sizeof(float4) * (size_t)P.bins * P.bins;
+    cudaError_t e = cudaSuccess;
+    // the G table exceeds the default 48 KiB of dynamic shared memory only for B > 55
+    auto prepare = [&](auto kern) {
+        if (smem > 48 * 1024 && e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e == cudaSuccess;
+    };
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
@@ -324,20 +368,23 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
                 if (!step) {
-                    mi_sweep2_kernel<T, float, false, PD, I><<<grid, block, 0, s>>>(
-                        (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m, (float *)v, S,
-                        partials, counter, r_out, err);
+                    if (prepare(mi_sweep2_kernel<T, float, false, PD, I>))
+                        mi_sweep2_kernel<T, float, false, PD, I><<<grid, block, smem, s>>>(
+                            (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m,
+                            (float *)v, S, partials, counter, r_out, err);
                     return;
                 }
                 with_type(mdt, [&](auto mp) {
                     using MT = elem_t<decltype(mp)>;
-                    mi_sweep2_kernel<T, MT, true, PD, I><<<grid, block, 0, s>>>(
-                        (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
-                        partials, counter, r_out, err);
+                    if (prepare(mi_sweep2_kernel<T, MT, true, PD, I>))
+                        mi_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
+                            (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
+                            partials, counter, r_out, err);
                 });
             });
         });
     });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

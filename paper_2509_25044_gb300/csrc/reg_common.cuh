@@ -117,40 +117,109 @@ __device__ __forceinline__ void gather8(const T *M, const Dims &g, const Axis &X
 // (1-a) lo + a hi, exact at a = 0 and a = 1 (so u = 0 reproduces M bit for bit)
 __device__ __forceinline__ float lerp1(float a, float lo, float hi) { return fmaf(a, hi, (1.0f - a) * lo); }
 
+// Fast path of both samplers: when every axis has 0 <= p + floor(u) <= n-2
+// (a finite displacement whose whole cell lies inside the volume) the two
+// padding modes agree -- fraction = u - floor(u), slope 1, all 8 corners
+// valid -- and the corners sit at fixed offsets from one base pointer.  The
+// test fails for NaN / infinite / huge u (the fraction is not in [0, 1) or
+// the index is out of range), which then take the general path above; the
+// arithmetic of the interpolation is the same on both paths, so the result
+// does not depend on which one ran.
+struct Cell {
+    int ix, iy, iz;
+    float ax, ay, az;
+};
+__device__ __forceinline__ bool interior_cell(const Dims &g, int x, int y, int z, float ux, float uy, float uz,
+                                              Cell &c) {
+    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+    c.ax = ux - fx;
+    c.ay = uy - fy;
+    c.az = uz - fz;
+    // saturating conversions and wrap-around unsigned sums: a huge or NaN u
+    // gives an index or a fraction that fails the test below
+    c.ix = (int)((unsigned)x + (unsigned)__float2int_rz(fx));
+    c.iy = (int)((unsigned)y + (unsigned)__float2int_rz(fy));
+    c.iz = (int)((unsigned)z + (unsigned)__float2int_rz(fz));
+    const bool in = (unsigned)c.ix < (unsigned)(g.nx - 1) && (unsigned)c.iy < (unsigned)(g.ny - 1) &&
+                    (unsigned)c.iz < (unsigned)(g.nz - 1);
+    return in && c.ax >= 0.0f && c.ay >= 0.0f && c.az >= 0.0f;
+}
+template <typename T, typename I>
+__device__ __forceinline__ void gather8_interior(const T *M, const Dims &g, const Cell &c, float v[8]) {
+    const T *q = M + ((I)c.iz * g.ny + c.iy) * g.nx + c.ix;
+    const I nx = (I)g.nx, nxy = (I)g.nxy;
+    const T *q1 = q + nx, *q2 = q + nxy, *q3 = q2 + nx;
+    v[0] = ld_vox(q, 0);
+    v[1] = ld_vox(q, 1);
+    v[2] = ld_vox(q1, 0);
+    v[3] = ld_vox(q1, 1);
+    v[4] = ld_vox(q2, 0);
+    v[5] = ld_vox(q2, 1);
+    v[6] = ld_vox(q3, 0);
+    v[7] = ld_vox(q3, 1);
+}
+
 // value only
 template <typename T, int PAD, typename I = long long>
 __device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
                                         float uz) {
-    const Axis X = axis_setup<PAD>(x, ux, g.nx);
-    const Axis Y = axis_setup<PAD>(y, uy, g.ny);
-    const Axis Z = axis_setup<PAD>(z, uz, g.nz);
     float c[8];
-    gather8<T, PAD, I>(M, g, X, Y, Z, c);
-    const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
-    const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);
-    const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
-    return lerp1(Z.a, f0, f1);
+    float ax, ay, az;
+    Cell cell;
+    if (interior_cell(g, x, y, z, ux, uy, uz, cell)) {
+        gather8_interior<T, I>(M, g, cell, c);
+        ax = cell.ax;
+        ay = cell.ay;
+        az = cell.az;
+    } else {
+        const Axis X = axis_setup<PAD>(x, ux, g.nx);
+        const Axis Y = axis_setup<PAD>(y, uy, g.ny);
+        const Axis Z = axis_setup<PAD>(z, uz, g.nz);
+        gather8<T, PAD, I>(M, g, X, Y, Z, c);
+        ax = X.a;
+        ay = Y.a;
+        az = Z.a;
+    }
+    const float e00 = lerp1(ax, c[0], c[1]), e10 = lerp1(ax, c[2], c[3]);
+    const float e01 = lerp1(ax, c[4], c[5]), e11 = lerp1(ax, c[6], c[7]);
+    const float f0 = lerp1(ay, e00, e10), f1 = lerp1(ay, e01, e11);
+    return lerp1(az, f0, f1);
 }
 
 // value and slope dJ/dphi
 template <typename T, int PAD, typename I = long long>
 __device__ __forceinline__ float sample_grad(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
                                              float uz, float &gx, float &gy, float &gz) {
-    const Axis X = axis_setup<PAD>(x, ux, g.nx);
-    const Axis Y = axis_setup<PAD>(y, uy, g.ny);
-    const Axis Z = axis_setup<PAD>(z, uz, g.nz);
     float c[8];
-    gather8<T, PAD, I>(M, g, X, Y, Z, c);
+    float ax, ay, az, sx = 1.0f, sy = 1.0f, sz = 1.0f;
+    Cell cell;
+    if (interior_cell(g, x, y, z, ux, uy, uz, cell)) {
+        gather8_interior<T, I>(M, g, cell, c);
+        ax = cell.ax;
+        ay = cell.ay;
+        az = cell.az;
+    } else {
+        const Axis X = axis_setup<PAD>(x, ux, g.nx);
+        const Axis Y = axis_setup<PAD>(y, uy, g.ny);
+        const Axis Z = axis_setup<PAD>(z, uz, g.nz);
+        gather8<T, PAD, I>(M, g, X, Y, Z, c);
+        ax = X.a;
+        ay = Y.a;
+        az = Z.a;
+        sx = X.slope;
+        sy = Y.slope;
+        sz = Z.slope;
+    }
     const float d00 = c[1] - c[0], d10 = c[3] - c[2], d01 = c[5] - c[4], d11 = c[7] - c[6];
-    const float e00 = lerp1(X.a, c[0], c[1]), e10 = lerp1(X.a, c[2], c[3]);
-    const float e01 = lerp1(X.a, c[4], c[5]), e11 = lerp1(X.a, c[6], c[7]);
-    const float f0 = lerp1(Y.a, e00, e10), f1 = lerp1(Y.a, e01, e11);
+    const float e00 = lerp1(ax, c[0], c[1]), e10 = lerp1(ax, c[2], c[3]);
+    const float e01 = lerp1(ax, c[4], c[5]), e11 = lerp1(ax, c[6], c[7]);
+    const float f0 = lerp1(ay, e00, e10), f1 = lerp1(ay, e01, e11);
     const float dy0 = e10 - e00, dy1 = e11 - e01;
-    const float dx0 = fmaf(Y.a, d10 - d00, d00), dx1 = fmaf(Y.a, d11 - d01, d01);
-    gz = (f1 - f0) * Z.slope;
-    gy = fmaf(Z.a, dy1 - dy0, dy0) * Y.slope;
-    gx = fmaf(Z.a, dx1 - dx0, dx0) * X.slope;
-    return lerp1(Z.a, f0, f1);
+    const float dx0 = fmaf(ay, d10 - d00, d00), dx1 = fmaf(ay, d11 - d01, d01);
+    gz = (f1 - f0) * sz;
+    gy = fmaf(az, dy1 - dy0, dy0) * sy;
+    gx = fmaf(az, dx1 - dx0, dx0) * sx;
+    return lerp1(az, f0, f1);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,9 +131,18 @@ __device__ __forceinline__ void diffusion_ptr(const float *const uc[3], I p, I n
     }
 }
 
+// the hardware square-root approximation (sqrt.approx, relative error below
+// 2^-22): one instruction instead of the correctly rounded sequence
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Adam on one element with the old moments already loaded; the new moments
-// are stored to m[i], v[i]; returns the updated displacement.  The quotient
-// uses the fast reciprocal division (a few ulp, far inside the parity bar).
+// are stored to m[i], v[i]; returns the updated displacement.  The square
+// root and the quotient use the fast hardware forms (a few ulp, far inside
+// the parity bar).
 template <typename MT, typename I>
 __device__ __forceinline__ float adam_fast(float u, float g, float m0, float v0, MT *m, MT *v, I i,
                                            const StepParams &S) {
@@ -142,7 +151,7 @@ __device__ __forceinline__ float adam_fast(float u, float g, float m0, float v0,
     const float vn = fmaf(S.b2, v0, (1.0f - S.b2) * gs * gs);
     st_moment(m, i, mn);
     st_moment(v, i, vn);
-    const float denom = fmaf(sqrtf(vn), S.rsqrt_bc2, S.eps);
+    const float denom = fmaf(sqrt_approx(vn), S.rsqrt_bc2, S.eps);
     return fmaf(-S.lr_bc1, __fdividef(mn, denom), u);
 }
 
