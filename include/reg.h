@@ -224,15 +224,28 @@ REG_API reg_status reg_set_timing_events(void *const *events, int n);
 /* Kpad (the packed K length, a multiple of 64) for Cin input channels. */
 REG_API size_t reg_nn_conv_kpad(int Cin);
 
+/* Scratch for the TMA-fed forward convolution: the weights re-tiled into the
+ * tensor cores' shared-memory layout (0 when Cin % 16 != 0: that shape has
+ * only the gather kernel). */
+REG_API size_t reg_nn_conv_scratch_bytes(int Cin, int Cout);
+
 /* out = epilogue(conv(in, W)): epilogue 0 = LeakyReLU(acc + bias, slope) ->
  * BF16 channels-last (Cout % 8 == 0); 1 = acc -> BF16 (no bias); 2 = acc +
- * bias -> FP32 SoA [Cout][N voxels] (any Cout <= 64).  Cin in [8, 128]. */
+ * bias -> FP32 SoA [Cout][N voxels] (any Cout <= 64).  Cin in [8, 128].
+ * With scratch (>= reg_nn_conv_scratch_bytes bytes, 16-byte aligned,
+ * else REG_ERR_WORKSPACE / REG_ERR_ALIGN) and Cin % 16 == 0, nx <= 254 the
+ * input brick of each output tile is loaded by TMA and every tap is one
+ * shifted tensor-core operand; otherwise (scratch NULL) each CTA gathers
+ * its im2col tile from global memory.  Both give the same sums up to FP32
+ * accumulation order. */
 REG_API reg_status reg_nn_conv3d_fwd(const void *in, int Cin, const void *W, const float *bias, int Cout, reg_dims d,
-                                     int epilogue, float slope, void *out, void *stream);
+                                     int epilogue, float slope, void *scratch, size_t scratch_bytes, void *out,
+                                     void *stream);
 
 /* Data gradient: din (BF16 channels-last, Cin) = conv^T(dpre (Cout), W): the
  * weights are flipped and transposed into Wd_scratch
- * (reg_nn_dgrad_scratch_bytes), then the forward kernel runs on them. */
+ * (reg_nn_dgrad_scratch_bytes, which also holds their re-tiled copy), then
+ * the forward kernel runs on them (the TMA-fed one when Cout % 16 == 0). */
 REG_API size_t reg_nn_dgrad_scratch_bytes(int Cin, int Cout);
 REG_API reg_status reg_nn_conv3d_dgrad(const void *dpre, int Cout, const void *W, int Cin, reg_dims d,
                                        void *Wd_scratch, void *din, void *stream);

@@ -303,7 +303,9 @@ def reg_debug_gemm_bf16(A, B, M: int, N: int, K: int, a_mn_major: bool = False, 
 _SZ = ctypes.c_size_t
 _NN = {
     "reg_nn_conv_kpad": ([ctypes.c_int], _SZ),
-    "reg_nn_conv3d_fwd": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, RegDims, ctypes.c_int, ctypes.c_float, _vp, _vp],
+    "reg_nn_conv_scratch_bytes": ([ctypes.c_int, ctypes.c_int], _SZ),
+    "reg_nn_conv3d_fwd": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, RegDims, ctypes.c_int, ctypes.c_float, _vp,
+                           ctypes.c_size_t, _vp, _vp],
                           _st),
     "reg_nn_dgrad_scratch_bytes": ([ctypes.c_int, ctypes.c_int], _SZ),
     "reg_nn_conv3d_dgrad": ([_vp, ctypes.c_int, _vp, ctypes.c_int, RegDims, _vp, _vp, _vp], _st),

@@ -14,6 +14,11 @@ reg_status st(cudaError_t e) { return e == cudaSuccess ? REG_OK : REG_ERR_CUDA; 
 bool dims_ok(reg_dims d) { return d.nx >= 1 && d.ny >= 1 && d.nz >= 1 && (long long)d.nx * d.ny * d.nz < (1LL << 31); }
 bool even(reg_dims d) { return d.nx % 2 == 0 && d.ny % 2 == 0 && d.nz % 2 == 0; }
 int kpad_of(int K) { return (K + 63) / 64 * 64; }
+// flipped / transposed data-gradient weights, rounded up to 256 bytes (the
+// re-tiled copy for the TMA-fed kernel follows them in the scratch)
+size_t dgrad_wd_bytes(int Cin, int Cout) {
+    return (sizeof(uint16_t) * (size_t)((Cin + 15) / 16 * 16) * kpad_of(27 * Cout) + 255) / 256 * 256;
+}
 
 }  // namespace
 
@@ -21,17 +26,30 @@ extern "C" {
 
 size_t reg_nn_conv_kpad(int Cin) { return (size_t)kpad_of(27 * Cin); }
 
+size_t reg_nn_conv_scratch_bytes(int Cin, int Cout) {
+    if (Cin < 8 || Cout < 1) return 0;
+    return conv_view_weight_bytes(Cin, (Cout + 15) / 16 * 16);
+}
+
 reg_status reg_nn_conv3d_fwd(const void *in, int Cin, const void *W, const float *bias, int Cout, reg_dims d,
-                             int epilogue, float slope, void *out, void *stream) {
+                             int epilogue, float slope, void *scratch, size_t scratch_bytes, void *out, void *stream) {
     if (!dims_ok(d)) return REG_ERR_SHAPE;
     if (Cin < 8 || Cin % 8 || Cin > 128 || Cout < 1 || Cout > 64) return REG_ERR_SHAPE;
     if (epilogue < 0 || epilogue > 2) return REG_ERR_INVALID_ARG;
     if (epilogue != 2 && Cout % 8) return REG_ERR_SHAPE;
     if (!al16(in) || !al16(W) || !al16(out)) return in && W && out ? REG_ERR_ALIGN : REG_ERR_INVALID_ARG;
     if (epilogue != 1 && !bias) return REG_ERR_INVALID_ARG;
-    const int N = (Cout + 15) / 16 * 16;
-    return st(launch_conv_fwd(in, Cin, W, kpad_of(27 * Cin), bias, Cout, N, make_dims(d), epilogue, slope, out,
-                              (cudaStream_t)stream));
+    if (scratch && !al16(scratch)) return REG_ERR_ALIGN;
+    const int N = (Cout + 15) / 16 * 16, Kpad = kpad_of(27 * Cin);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = conv_view_weight_bytes(Cin, N);
+    if (scratch && need) {
+        if (scratch_bytes < need) return REG_ERR_WORKSPACE;
+        const cudaError_t e = launch_conv_view(in, Cin, W, N, Kpad, bias, Cout, N, make_dims(d), epilogue, slope,
+                                               scratch, out, s);
+        if (e != cudaErrorNotSupported) return st(e);
+    }
+    return st(launch_conv_fwd(in, Cin, W, Kpad, bias, Cout, N, make_dims(d), epilogue, slope, out, s));
 }
 
 reg_status reg_nn_conv3d_dgrad(const void *dpre, int Cout, const void *W, int Cin, reg_dims d, void *Wd_scratch,
@@ -43,11 +61,18 @@ reg_status reg_nn_conv3d_dgrad(const void *dpre, int Cout, const void *W, int Ci
     const cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_repack_dgrad(W, Cout, Cin, Kpad, Wd_scratch, Nd, Kpad_d, s);
     if (e != cudaSuccess) return REG_ERR_CUDA;
+    if (conv_view_weight_bytes(Cout, Nd)) {
+        void *tiles = (unsigned char *)Wd_scratch + dgrad_wd_bytes(Cin, Cout);
+        e = launch_conv_view(dpre, Cout, Wd_scratch, Nd, Kpad_d, nullptr, Cin, Nd, make_dims(d), 1, 0.0f, tiles,
+                             din, s);
+        if (e != cudaErrorNotSupported) return st(e);
+    }
     return st(launch_conv_fwd(dpre, Cout, Wd_scratch, Kpad_d, nullptr, Cin, Nd, make_dims(d), 1, 0.0f, din, s));
 }
 
 size_t reg_nn_dgrad_scratch_bytes(int Cin, int Cout) {
-    return sizeof(uint16_t) * (size_t)((Cin + 15) / 16 * 16) * kpad_of(27 * Cout);
+    if (Cin < 8 || Cout < 8) return 0;
+    return dgrad_wd_bytes(Cin, Cout) + conv_view_weight_bytes(Cout, (Cin + 15) / 16 * 16);
 }
 
 size_t reg_nn_wgrad_scratch_bytes(reg_dims d, int Cin, int Cout) {

@@ -126,6 +126,14 @@ unsigned *error_word();
 // ---- learned initialiser (unet.cu, unet_ops.cu) -------------------------------
 namespace regk {
 size_t gemm_smem_bytes();
+// convolution epilogues: LeakyReLU(acc + bias) -> BF16, acc -> BF16, acc + bias -> FP32 SoA
+enum ConvEpi { EPI_BIAS_LEAKY_BF16 = 0, EPI_PLAIN_BF16 = 1, EPI_BIAS_F32_SOA = 2 };
+// TMA-fed convolution (Cin % 16 == 0, nx <= 254): weights re-tiled into
+// Wt_scratch (conv_view_weight_bytes); cudaErrorNotSupported if the shape
+// has no such path
+size_t conv_view_weight_bytes(int Cin, int N);
+cudaError_t launch_conv_view(const void *in, int Cin, const void *W, int rows, int Kpad, const float *bias, int Cout,
+                             int N, const Dims &d, int epi, float slope, void *Wt_scratch, void *out, cudaStream_t s);
 cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, const float *bias, int Cout, int N,
                             const Dims &d, int epi, float slope, void *out, cudaStream_t s);
 cudaError_t launch_conv_wgrad(const void *in, int Cin, const void *dpre, int Cout, const Dims &d, float *part,

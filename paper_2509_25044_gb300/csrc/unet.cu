@@ -114,7 +114,6 @@ __device__ __forceinline__ uint4 tap_load(const __nv_bfloat16 *__restrict__ act,
     return __ldg(reinterpret_cast<const uint4 *>(act + v * C + c0));
 }
 
-enum ConvEpi { EPI_BIAS_LEAKY_BF16 = 0, EPI_PLAIN_BF16 = 1, EPI_BIAS_F32_SOA = 2 };
 
 // forward conv (also the data gradient, with transposed / flipped weights):
 // out[v][n] = epi( sum_k in_col[v][k] W[n][k] ), one CTA per 128 voxels

@@ -115,6 +115,8 @@ class UNet:
         g["dpred"] = torch.empty((self.V[1], 16), dtype=BF, device=self.dev)
         g["up"] = torch.empty((self.V[2], 64), dtype=BF, device=self.dev)  # upsample-backward outputs
         self.g = g
+        cs = max(int(self.L.reg_nn_conv_scratch_bytes(cin, cout)) for _, cin, cout, _ in LAYERS)
+        self.cs = torch.empty(max(cs, 16), dtype=torch.uint8, device=self.dev)
         wd = max(int(self.L.reg_nn_dgrad_scratch_bytes(cin, cout)) for _, cin, cout, _ in LAYERS)
         self.wd = torch.empty(wd, dtype=torch.uint8, device=self.dev)
         wg = max(int(self.L.reg_nn_wgrad_scratch_bytes(_dims(self.n[lv]), cin, (cout + 15) // 16 * 16))
@@ -131,7 +133,8 @@ class UNet:
     def _conv(self, name, src, dst, level, epi=0):
         P = self.p[name]
         capi.nn_check(self.L.reg_nn_conv3d_fwd(capi.ptr(src), P.cin, capi.ptr(P.wb), capi.ptr(P.b), P.cout,
-                                               _dims(self.n[level]), epi, SLOPE, capi.ptr(dst), self._s()),
+                                               _dims(self.n[level]), epi, SLOPE, capi.ptr(self.cs), self.cs.numel(),
+                                               capi.ptr(dst), self._s()),
                       f"conv {name}")
 
     def _pool(self, src, C, level, dst, backward=0):
