@@ -259,8 +259,8 @@ REG_API reg_status reg_nn_conv3d_wgrad(const void *in, int Cin, const void *dpre
                                        void *scratch, size_t scratch_bytes, float *dW, void *stream);
 
 /* Network input: average-pool F and M (img_dt, dims d) by `factor`, map each
- * to (v - lo) / (hi - lo), write channels-last BF16 with 8 channels (F, M,
- * six zeros) at d / factor. */
+ * to (v - lo) / (hi - lo), write channels-last BF16 with 16 channels (F, M,
+ * 14 zeros) at d / factor. */
 REG_API reg_status reg_nn_pack_pair(const void *F, const void *M, int img_dt, reg_dims d, int factor, float f_lo,
                                     float f_hi, float m_lo, float m_hi, void *out, void *stream);
 

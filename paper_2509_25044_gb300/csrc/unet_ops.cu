@@ -62,7 +62,9 @@ __global__ void pack_pair_kernel(const T *__restrict__ F, const T *__restrict__ 
     t[1] = __float2bfloat16_rn((sm * inv - m_lo) * m_scale);
 #pragma unroll
     for (int i = 2; i < 8; ++i) t[i] = __float2bfloat16_rn(0.0f);
-    *reinterpret_cast<uint4 *>(out + v * 8) = *reinterpret_cast<const uint4 *>(t);
+    // 16 channels (F, M, 14 zeros): the input convolution then takes the TMA-fed path
+    *reinterpret_cast<uint4 *>(out + v * 16) = *reinterpret_cast<const uint4 *>(t);
+    *reinterpret_cast<uint4 *>(out + v * 16 + 8) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 cudaError_t launch_pack_pair(const void *F, const void *M, int dt, const Dims &gin, int factor, float f_lo,

@@ -117,7 +117,7 @@ def main():
     li = sub.add_parser("learned-init")
     li.add_argument("--pairs", type=int, default=2000)
     li.add_argument("--epochs", type=int, default=4)
-    li.add_argument("--lr", type=float, default=3e-4)
+    li.add_argument("--lr", type=float, default=2e-4)
     li.add_argument("--eval-config", default="c2")
     li.add_argument("--eval-n", type=int, default=None)
     li.add_argument("--save", default=None)
@@ -135,7 +135,7 @@ def main():
 # ---------------------------------------------------------------------------
 # learned initialiser: training and evaluation
 # ---------------------------------------------------------------------------
-def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 3e-4, seed0: int = 10_000,
+def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 2e-4, seed0: int = 10_000,
                out_path: str | None = None, log_every: int = 200) -> dict:
     """Train the U-Net on n_pairs seeded pairs made with the library's warp
     (targets: the known fields pooled to n/2).  Pairs are generated once and
@@ -150,9 +150,9 @@ def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 3
     xs, ts = [], []
     for i in range(n_pairs):
         p = training_pair(n, seed0 + i, dev)
-        net.pack(p["F"], p["M"], 1, (float(p["F"].min()), float(p["F"].max())),
-                 (float(p["M"].min()), float(p["M"].max())))
-        xs.append(net.a["x0"].clone())
+        # images kept as BF16 (the network sees them in BF16 anyway); packed per step
+        xs.append((p["F"].to(torch.bfloat16), p["M"].to(torch.bfloat16),
+                   (float(p["F"].min()), float(p["F"].max())), (float(p["M"].min()), float(p["M"].max()))))
         t = torch.empty((3, (n // 2) ** 3), device=dev)
         capi.nn_check(L.reg_nn_field_down2(capi.ptr(p["v"]), capi.RegDims(n, n, n), capi.ptr(t), capi.stream_of(t)),
                       "field_down2")
@@ -167,7 +167,8 @@ def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 3
         order = order_rng.permutation(n_pairs)
         tot = torch.zeros((), dtype=torch.float64, device=dev)
         for j, i in enumerate(order):
-            net.a["x0"].copy_(xs[i])
+            Fb, Mb, fr, mr = xs[i]
+            net.pack(Fb, Mb, 1, fr, mr)
             net.forward()
             tot += net.loss_and_backward(ts[i])[0]
             net.step(lr)

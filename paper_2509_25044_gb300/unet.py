@@ -4,7 +4,7 @@ to a half-resolution initial displacement for the registration.
 Network (channels 16-32-64-64, two 3x3x3 convolutions per level, LeakyReLU
 0.2, 2x average pooling down, 2x trilinear upsampling + channel concat up):
 
-    128^3 x 8 (F, M, zeros) --c0a,c0b--> e0 16 --pool--> 64^3
+    128^3 x 16 (F, M, zeros) --c0a,c0b--> e0 16 --pool--> 64^3
       --c1a,c1b--> e1 32 --pool--> 32^3 --c2a,c2b--> e2 64 --pool--> 16^3
       --c3a,c3b--> b3 64 --up--> 32^3 [64 | e2 64] --d2a,d2b--> d2 64
       --up--> 64^3 [64 | e1 32] --d1a,d1b--> d1 32 --head--> u 3 @ 64^3
@@ -30,7 +30,7 @@ BF = torch.bfloat16
 
 # (name, Cin, Cout, grid level)  level 0 = 128^3 ... 3 = 16^3
 LAYERS = [
-    ("c0a", 8, 16, 0), ("c0b", 16, 16, 0),
+    ("c0a", 16, 16, 0), ("c0b", 16, 16, 0),
     ("c1a", 16, 32, 1), ("c1b", 32, 32, 1),
     ("c2a", 32, 64, 2), ("c2b", 64, 64, 2),
     ("c3a", 64, 64, 3), ("c3b", 64, 64, 3),
@@ -73,10 +73,10 @@ class UNet:
             kpad = int(self.L.reg_nn_conv_kpad(cin))
             rows = (cout + 15) // 16 * 16
             w = np.zeros((rows, kpad), dtype=np.float32)
-            std = math.sqrt(2.0 / (1.0 + SLOPE ** 2) / (27 * cin))
+            real_cin = 2 if name == "c0a" else cin  # the input has 2 real channels (F, M)
+            std = math.sqrt(2.0 / (1.0 + SLOPE ** 2) / (27 * real_cin))
             if name == "head":
                 std *= 0.1  # start near the zero displacement
-            real_cin = 2 if name == "c0a" else cin
             blk = rng.standard_normal((cout, 27, real_cin)).astype(np.float32) * std
             wv = w[:cout, :27 * cin].reshape(cout, 27, cin)
             wv[:, :, :real_cin] = blk
@@ -93,7 +93,7 @@ class UNet:
 
     def _alloc(self):
         a = {}
-        a["x0"] = self._act(0, 8)
+        a["x0"] = self._act(0, 16)
         a["c0a"], a["e0"] = self._act(0, 16), self._act(0, 16)
         a["p0"] = self._act(1, 16)
         a["c1a"], a["e1"] = self._act(1, 32), self._act(1, 32)

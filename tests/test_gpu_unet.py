@@ -144,7 +144,7 @@ def test_unet_forward_backward_match_fp64_reference(capi):
     target = torch.randn((3, (n // 2) ** 3), device=DEV) * 0.1
     loss = net.loss_and_backward(target)
     torch.cuda.synchronize()
-    x0 = net.a["x0"].double().cpu().reshape(n, n, n, 8).permute(3, 0, 1, 2)[None]
+    x0 = net.a["x0"].double().cpu().reshape(n, n, n, 16).permute(3, 0, 1, 2)[None]
     tgt = target.double().cpu().reshape(3, n // 2, n // 2, n // 2)[None]
     ur, lr_, ws, bs = _torch_unet(net, x0, tgt)
     ur = ur[0].reshape(3, -1).detach()
@@ -171,15 +171,16 @@ def test_unet_training_reduces_loss(capi):
                                                capi.stream_of(t)), "down2")
         tgts.append(t)
     losses = []
-    for epoch in range(60):
+    for epoch in range(80):
         tot = 0.0
         for p, t in zip(pairs, tgts):
             net.pack(p["F"], p["M"], 1, (float(p["F"].min()), float(p["F"].max())),
                      (float(p["M"].min()), float(p["M"].max())))
             net.forward()
             tot += net.loss_and_backward(t).item()
-            net.step(5e-4)
+            net.step(2e-4)
         losses.append(tot / len(pairs))
-    # memorising 4 pairs: the loss falls steadily (about 2 % per 10 epochs)
-    assert losses[-1] < 0.9 * losses[0], losses
-    assert np.mean(losses[-5:]) < np.mean(losses[:5]), losses
+    # memorising 4 pairs (Adam at 2e-4 is stable here; 1e-3 diverges): the
+    # loss falls by an order of magnitude within 80 epochs
+    assert losses[-1] < 0.3 * losses[0], [round(v, 4) for v in losses]
+    assert np.mean(losses[-5:]) < 0.3 * np.mean(losses[:5]), [round(v, 4) for v in losses]
