@@ -362,7 +362,71 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.config)
+    if not args.no_unet:
+        out["tensor_core"] = unet_tensor_core(dev, read_bf16_peak())
     print(json.dumps(out), flush=True)
+
+
+def read_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    return 1900.0, "fallback 1.9 PFLOP/s"
+
+
+def unet_tensor_core(dev, peak):
+    """The learned initialiser's forward pass at a 128^3 input (the only
+    tensor-core work): 13 tcgen05 convolutions plus pooling / upsampling.
+    Timed with CUDA events after the registration run (outside its timed
+    region); FLOPs are the convolutions' algorithmic 2 * 27 * Cin * Cout per
+    output voxel with the real channel counts (2 input channels, 3 output)."""
+    import torch
+    from paper_2509_25044_gb300 import capi
+    from paper_2509_25044_gb300.unet import LAYERS, UNet
+    n = 128
+    net = UNet(n_in=n, seed=0, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    F = torch.rand((n, n, n), generator=g, device=dev)
+    M = torch.rand((n, n, n), generator=g, device=dev)
+    net.pack(F, M, 1, (0.0, 1.0), (0.0, 1.0))
+    real = {"c0a": (2, 16), "head": (32, 3)}
+    flops = sum(2.0 * 27 * real.get(nm, (ci, co))[0] * real.get(nm, (ci, co))[1] * net.V[lv]
+                for nm, ci, co, lv in LAYERS)
+    for _ in range(3):
+        net.forward()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        net.forward()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # the largest convolution alone (d1a: 96 -> 32 channels at 64^3)
+    nm, ci, co, lv = [l for l in LAYERS if l[0] == "d1a"][0]
+    src = torch.zeros((net.V[lv], ci), dtype=torch.bfloat16, device=dev)
+    dst = torch.empty((net.V[lv], co), dtype=torch.bfloat16, device=dev)
+    for _ in range(3):
+        net._conv(nm, src, dst, lv)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        net._conv(nm, src, dst, lv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_k = e0.elapsed_time(e1) / reps
+    fl_k = 2.0 * 27 * ci * co * net.V[lv]
+    tf_k = fl_k / (ms_k * 1e-3) / 1e12
+    return {"workload": "U-Net initialiser forward, 128^3 x 2-channel input, BF16 x BF16 -> FP32 (tcgen05)",
+            "ms_forward": ms, "tflops_forward": flops / (ms * 1e-3) / 1e12, "gflop_forward": flops / 1e9,
+            "kernel": "conv_view_kernel (d1a, 96 -> 32 channels, 64^3)", "kernel_ms": ms_k,
+            "roofline": {"bound": "tensor", "achieved": tf_k, "peak": peak[0], "unit": "TFLOP/s",
+                         "frac": tf_k / peak[0], "peak_source": peak[1]},
+            "device_error": capi.reg_get_device_error()}
 
 
 def main():
@@ -374,6 +438,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-unet", action="store_true", help="skip the tensor-core (U-Net) measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
