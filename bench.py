@@ -129,7 +129,8 @@ def setup_dist(n_gpus):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
     return rank, world, local
 
 
@@ -356,7 +357,7 @@ def run_ours(args):
                       "iteration_GBps": (b1 + b2) * N / (ms_max / K * 1e-3) / 1e9},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * ib, "d2h_bytes_per_step": 16,
                 "note": "per step: pinned host F, M -> device, one iteration, objective -> host"},
-        "gpu_launches": (3 if kind == "mi" else 2) * K,
+        "gpu_launches": 3 * K,  # MI: histogram, finalize, sweep 2; LNCC: warp, window statistics, sweep 2
         "clocks": clk,
         "objective_last": objv, "device_error": err, "wall_s": wall,
     }
