@@ -51,9 +51,57 @@ struct LnccSmem {
 
 size_t lncc_smem_bytes(int r, int K) { return LnccSmem(r, K).bytes(); }
 
-// x box sums of every staged row (sliding over 8-wide segments)
+// x box sums of every staged row (sliding over 8-wide segments).  A job is
+// (quantity k, staged row yy, segment seg); thread tid owns jobs tid,
+// tid + TILE_THREADS, ...  Their offsets depend only on tid, so they are
+// computed once per CTA (XJobs) instead of once per plane.
+constexpr int MAX_XJOBS = 3;  // K * RH * (TX / SEGW) <= 5 * (8 + 2 * 7) * 4 = 440 < 3 * 256
+struct XJobs {
+    int n;
+    int in[MAX_XJOBS], out[MAX_XJOBS];
+};
 template <int K>
-__device__ __forceinline__ void xpass(const float *__restrict__ st, float *__restrict__ hx, const LnccSmem &L, int r,
+__device__ __forceinline__ XJobs make_xjobs(const LnccSmem &L, int tid) {
+    constexpr int SEGS = TX / SEGW;
+    XJobs J;
+    J.n = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_XJOBS; ++i) {
+        const int job = tid + i * TILE_THREADS;
+        J.in[i] = J.out[i] = 0;
+        if (job < K * L.RH * SEGS) {
+            const int seg = job % SEGS;
+            const int rest = job / SEGS;
+            const int yy = rest % L.RH;
+            const int k = rest / L.RH;
+            J.in[i] = (k * L.RH + yy) * L.RWP + seg * SEGW;
+            J.out[i] = (k * L.RH + yy) * L.HXP + seg * SEGW;
+            J.n = i + 1;
+        }
+    }
+    return J;
+}
+__device__ __forceinline__ void xpass(const float *__restrict__ st, float *__restrict__ hx, const XJobs &J, int r) {
+#pragma unroll
+    for (int i = 0; i < MAX_XJOBS; ++i) {
+        if (i >= J.n) break;
+        const float *row = st + J.in[i];
+        float *out = hx + J.out[i];
+        float acc = 0.0f;
+        for (int d = 0; d <= 2 * r; ++d) acc += row[d];
+        out[0] = acc;
+#pragma unroll
+        for (int t = 1; t < SEGW; ++t) {
+            acc += row[t + 2 * r] - row[t - 1];
+            out[t] = acc;
+        }
+    }
+}
+
+// x box sums of every staged row (sliding over 8-wide segments), job
+// indices derived per plane (the register-lean form used by sweep 2)
+template <int K>
+__device__ __forceinline__ void xpass_lean(const float *__restrict__ st, float *__restrict__ hx, const LnccSmem &L, int r,
                                       int tid) {
     constexpr int SEGS = TX / SEGW;
     for (int job = tid; job < K * L.RH * SEGS; job += TILE_THREADS) {
@@ -94,8 +142,44 @@ __device__ __forceinline__ void ypass(const float *__restrict__ hx, float *__res
     }
 }
 
-template <typename T, bool COEF, typename I>
-__global__ void __launch_bounds__(TILE_THREADS)
+// Staging of one input plane (tile + r halo) without per-element index
+// arithmetic: thread (tx, ty) covers staged columns tx, tx + 32 (RW <= 46)
+// and rows ty, ty + 8 [, ty + 16] (NY = 2 for r <= 4, 3 up to r = 7).  The
+// slot (j, i) sits at shared offset sbase + 8 j RWP + 32 i and global
+// in-plane offset gbase + 8 j nx + 32 i; bit 2 (j * 2 + i) of `smask` says it
+// is inside the staged tile, of `gmask` that it is also inside the volume.
+// The loads of plane q + 1 are issued before plane q is box-summed.
+constexpr int STAGE_NX = 2;
+template <typename I>
+struct Stage {
+    int sbase;
+    I gbase;
+    unsigned smask, gmask;
+};
+template <int NY, typename I>
+__device__ __forceinline__ Stage<I> make_stage(const LnccSmem &L, int r, int x0, int y0, const Dims &g) {
+    Stage<I> S;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    S.sbase = ty * L.RWP + tx;
+    S.gbase = (I)(y0 - r + ty) * g.nx + (x0 - r + tx);
+    S.smask = S.gmask = 0u;
+#pragma unroll
+    for (int j = 0; j < NY; ++j)
+#pragma unroll
+        for (int i = 0; i < STAGE_NX; ++i) {
+            const int xx = tx + TX * i, yy = ty + TY * j;
+            const int gx = x0 - r + xx, gy = y0 - r + yy;
+            const unsigned bit = 1u << (j * STAGE_NX + i);
+            if (xx < L.RW && yy < L.RH) {
+                S.smask |= bit;
+                if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) S.gmask |= bit;
+            }
+        }
+    return S;
+}
+
+template <typename T, bool COEF, typename I, int NY>
+__global__ void __launch_bounds__(TILE_THREADS, 3)
     lncc_stats_kernel(const T *__restrict__ F, const float *__restrict__ J, Dims g, LnccParams P, int zc,
                       float *__restrict__ coef, double *__restrict__ partials, unsigned *__restrict__ counter,
                       double *__restrict__ sim_out, unsigned *err) {
@@ -124,32 +208,49 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const float shF = shift[0], shJ = shift[1];
     const float cxy = active ? (float)(win_count(x, r, g.nx) * win_count(y, r, g.ny)) : 1.0f;
     const float inv_n = 1.0f / (float)g.n;
-    const int plane = L.RH * L.RW;
     const int kst = L.RH * L.RWP;
+    const XJobs xj = make_xjobs<5>(L, tid);
+    const Stage<I> sg = make_stage<NY, I>(L, r, x0, y0, g);
+    const I rowstep = (I)TY * g.nx;
+    float pf[NY][STAGE_NX], pj[NY][STAGE_NX];
+    auto fetch = [&](int q) {
+        const bool qin = q >= 0 && q < g.nz;
+        const I qoff = (I)q * nxy + sg.gbase;
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+            for (int i = 0; i < STAGE_NX; ++i) {
+                float f = 0.0f, jv = 0.0f;
+                if (qin && (sg.gmask >> (j * STAGE_NX + i) & 1u)) {
+                    const I p = qoff + (I)j * rowstep + TX * i;
+                    f = ld_vox(F, p) - shF;
+                    jv = __ldg(J + p) - shJ;
+                }
+                pf[j][i] = f;
+                pj[j][i] = jv;
+            }
+    };
+    fetch(z0 - r);
     float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float nsum = 0.0f;
     int slot = 0;
     for (int q = z0 - r; q < z1 + r; ++q) {
-        const bool qin = q >= 0 && q < g.nz;
-        const I qoff = (I)q * nxy;
-        for (int e = tid; e < plane; e += TILE_THREADS) {
-            const int yy = e / L.RW, xx = e - yy * L.RW;
-            const int gx = x0 - r + xx, gy = y0 - r + yy;
-            float f = 0.0f, j = 0.0f;
-            if (qin && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
-                const I p = qoff + (I)gy * g.nx + gx;
-                f = ld_vox(F, p) - shF;
-                j = __ldg(J + p) - shJ;
-            }
-            const int o = yy * L.RWP + xx;
-            st[o] = f;
-            st[kst + o] = j;
-            st[2 * kst + o] = f * f;
-            st[3 * kst + o] = j * j;
-            st[4 * kst + o] = f * j;
-        }
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+            for (int i = 0; i < STAGE_NX; ++i)
+                if (sg.smask >> (j * STAGE_NX + i) & 1u) {
+                    const int o = sg.sbase + j * TY * L.RWP + TX * i;
+                    const float f = pf[j][i], jv = pj[j][i];
+                    st[o] = f;
+                    st[kst + o] = jv;
+                    st[2 * kst + o] = f * f;
+                    st[3 * kst + o] = jv * jv;
+                    st[4 * kst + o] = f * jv;
+                }
+        if (q + 1 < z1 + r) fetch(q + 1);  // in flight during the box sums of plane q
         __syncthreads();
-        xpass<5>(st, hx, L, r, tid);
+        xpass(st, hx, xj, r);
         float old[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) old[k] = ring[(slot * 5 + k) * TILE_THREADS + tid];
@@ -263,7 +364,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             st[2 * kst + o] = a2;
         }
         __syncthreads();
-        xpass<3>(st, hx, L, r, tid);
+        xpass_lean<3>(st, hx, L, r, tid);
         float old[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) old[k] = ring[(slot * 3 + k) * TILE_THREADS + tid];
@@ -330,6 +431,15 @@ MarchGrid lncc_grid(const Dims &g, int r) {
     return march_grid(g, 4LL * num_sms() * 3, 8 * r > 32 ? 8 * r : 32);
 }
 
+// staged rows per thread: TY + 2r <= 16 rows fit in 2 passes of 8
+template <typename Fn>
+inline void with_stage_rows(int r, Fn &&fn) {
+    if (TY + 2 * r <= 2 * TY)
+        fn(IC<2>{});
+    else
+        fn(IC<3>{});
+}
+
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -346,17 +456,20 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
         using T = elem_t<decltype(tp)>;
         with_index(g, [&](auto ip) {
             using I = elem_t<decltype(ip)>;
-            if (coef) {
-                e = allow_smem(lncc_stats_kernel<T, true, I>, smem);
-                if (e == cudaSuccess)
-                    lncc_stats_kernel<T, true, I><<<grid, block, smem, s>>>((const T *)F, J, g, P, G.zc, coef,
-                                                                            partials, counter, sim_out, err);
-            } else {
-                e = allow_smem(lncc_stats_kernel<T, false, I>, smem);
-                if (e == cudaSuccess)
-                    lncc_stats_kernel<T, false, I><<<grid, block, smem, s>>>((const T *)F, J, g, P, G.zc, coef,
-                                                                             partials, counter, sim_out, err);
-            }
+            with_stage_rows(P.r, [&](auto ny) {
+                constexpr int NY = decltype(ny)::value;
+                if (coef) {
+                    e = allow_smem(lncc_stats_kernel<T, true, I, NY>, smem);
+                    if (e == cudaSuccess)
+                        lncc_stats_kernel<T, true, I, NY><<<grid, block, smem, s>>>(
+                            (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
+                } else {
+                    e = allow_smem(lncc_stats_kernel<T, false, I, NY>, smem);
+                    if (e == cudaSuccess)
+                        lncc_stats_kernel<T, false, I, NY><<<grid, block, smem, s>>>(
+                            (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
+                }
+            });
         });
     });
     if (e != cudaSuccess) return e;
@@ -391,8 +504,8 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                     e = allow_smem(lncc_sweep2_kernel<T, MT, true, PD, I>, smem);
                     if (e == cudaSuccess)
                         lncc_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
-                            (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
-                            partials, counter, r_out, err);
+                            (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m,
+                            (MT *)v, S, partials, counter, r_out, err);
                 });
             });
         });
