@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
 }
 
 template <typename T, typename MT, bool STEP, int PAD, typename I>
-__global__ void __launch_bounds__(TILE_THREADS, 3)
+__global__ void __launch_bounds__(TILE_THREADS, 4)
     mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                      MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,

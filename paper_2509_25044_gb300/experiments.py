@@ -104,6 +104,55 @@ def time_to_loss(config: str, iters: int | None = None, eval_every: int = 10, n:
     return out
 
 
+def eval_init_pairs(net, n_pairs: int = 8, n: int = 128, seed0: int = 90_000, iters: int = 200, window: int = 7,
+                    lam: float = 1.0, lr: float = 0.1, rel_tol: float = 0.01) -> dict:
+    """Held-out pairs of the training distribution (seeds never used in
+    training), registered with LNCC from zero and from the network's field:
+    iterations (and time, inference included) for the learned-init run to
+    reach the zero-init run's target (reading: L <= L* + rel_tol (L0 - L*),
+    L0 and L* the zero-init run's first and final objectives), final
+    objectives, fold checks and the error to the known field."""
+    from .unet import training_pair
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    for i in range(n_pairs):
+        p = training_pair(n, seed0 + i, dev)
+        F, M, v = p["F"].contiguous(), p["M"].contiguous(), p["v"]
+        cfg = RegConfig(loss="lncc", window=window, eps=1e-5, lam=lam, lr=lr)
+        r0 = Registration(F, M, cfg)
+        res0 = r0.run(iters)
+        fin0 = r0.objective()
+        L0, Lstar = float(res0.objective[0]), fin0["objective"]
+        tol = rel_tol * max(L0 - Lstar, 0.0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        u0 = net.predict_init(F, M, (float(F.min()), float(F.max())), (float(M.min()), float(M.max())))
+        ev1.record()
+        torch.cuda.synchronize()
+        init_ms = ev0.elapsed_time(ev1)
+        r1 = Registration(F, M, cfg, u0=u0)
+        res1 = r1.run(iters)
+        fin1 = r1.objective()
+        k0 = _first_within(np.append(res0.objective[1:], Lstar), Lstar, tol)
+        k1 = _first_within(np.append(res1.objective[1:], fin1["objective"]), Lstar, tol)
+        err = lambda u: float(((u - v).norm() / v.norm()).item())
+        row = {"seed": seed0 + i, "max_disp": float(v.norm(dim=0).max().item()),
+               "zero": {"L0": L0, "L_final": Lstar, "iters_to_target": None if k0 is None else k0 + 1,
+                        "fold": r0.fold_check()["n_fold"], "rel_err": err(r0.current)},
+               "learned": {"L0": float(res1.objective[0]), "L_final": fin1["objective"],
+                           "iters_to_target": None if k1 is None else k1 + 1, "init_ms": init_ms,
+                           "fold": r1.fold_check()["n_fold"], "rel_err": err(r1.current), "init_rel_err": err(u0)},
+               "ms_per_iter": res0.ms_per_iter}
+        if k0 is not None and k1 is not None:
+            row["time_to_target_ms"] = {"zero": (k0 + 1) * res0.ms_per_iter,
+                                        "learned": init_ms + (k1 + 1) * res1.ms_per_iter}
+            row["speedup"] = row["time_to_target_ms"]["zero"] / row["time_to_target_ms"]["learned"]
+        rows.append(row)
+    sp = [r["speedup"] for r in rows if "speedup" in r]
+    return {"experiment": "eval_init_pairs", "n": n, "pairs": n_pairs, "iters": iters, "window": window, "lam": lam,
+            "lr": lr, "median_speedup": float(np.median(sp)) if sp else None, "reached": len(sp), "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -121,11 +170,14 @@ def main():
     li.add_argument("--eval-config", default="c2")
     li.add_argument("--eval-n", type=int, default=None)
     li.add_argument("--save", default=None)
+    li.add_argument("--eval-pairs", type=int, default=8)
     args = ap.parse_args()
     if args.cmd == "learned-init":
         tr, net = train_init(args.pairs, args.epochs, lr=args.lr, out_path=args.save)
         print(json.dumps(tr), flush=True)
-        print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n)), flush=True)
+        print(json.dumps(eval_init_pairs(net, n_pairs=args.eval_pairs)), flush=True)
+        if args.eval_config != "none":
+            print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n)), flush=True)
         return
     if args.cmd == "ttl":
         print(json.dumps(time_to_loss(args.config, args.iters, args.eval_every, args.n, lam_scale=args.lam_scale,
