@@ -251,9 +251,12 @@ REG_API reg_status reg_nn_conv3d_dgrad(const void *dpre, int Cout, const void *W
                                        void *Wd_scratch, void *din, void *stream);
 
 /* Weight gradient: dW (FP32, packed [Cout][Kpad]) = sum over voxels of
- * in_col (x) dpre, split over voxel ranges into scratch
- * (reg_nn_wgrad_scratch_bytes) and reduced in a fixed order (deterministic).
- * Cout in {16, 32, 48, 64} (pad a smaller Cout with zero channels). */
+ * in_col (x) dpre, as per-CTA partial sums in scratch
+ * (reg_nn_wgrad_scratch_bytes) reduced in a fixed order (deterministic).
+ * Cout in {16, 32, 48, 64} (pad a smaller Cout with zero channels).  With
+ * Cin % 16 == 0 and nx <= 254, persistent CTAs stream TMA-loaded input
+ * bricks and dpre rows through the tensor cores with the 27 per-tap sums in
+ * tensor memory; otherwise each CTA gathers im2col tiles. */
 REG_API size_t reg_nn_wgrad_scratch_bytes(reg_dims d, int Cin, int Cout);
 REG_API reg_status reg_nn_conv3d_wgrad(const void *in, int Cin, const void *dpre, int Cout, reg_dims d,
                                        void *scratch, size_t scratch_bytes, float *dW, void *stream);

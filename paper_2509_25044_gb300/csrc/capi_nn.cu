@@ -77,7 +77,9 @@ size_t reg_nn_dgrad_scratch_bytes(int Cin, int Cout) {
 
 size_t reg_nn_wgrad_scratch_bytes(reg_dims d, int Cin, int Cout) {
     if (!dims_ok(d)) return 0;
-    return wgrad_part_bytes(make_dims(d), Cin, Cout);
+    const Dims g = make_dims(d);
+    const size_t a = wgrad_part_bytes(g, Cin, Cout), b = conv_wgrad_view_bytes(g, Cin, Cout);
+    return a > b ? a : b;
 }
 
 reg_status reg_nn_conv3d_wgrad(const void *in, int Cin, const void *dpre, int Cout, reg_dims d, void *scratch,
@@ -85,8 +87,15 @@ reg_status reg_nn_conv3d_wgrad(const void *in, int Cin, const void *dpre, int Co
     if (!dims_ok(d)) return REG_ERR_SHAPE;
     if (Cin < 8 || Cin % 8 || Cin > 128 || Cout < 16 || Cout % 16 || Cout > 64) return REG_ERR_SHAPE;
     if (!al16(in) || !al16(dpre) || !al16(scratch) || !al16(dW)) return REG_ERR_ALIGN;
-    if (scratch_bytes < wgrad_part_bytes(make_dims(d), Cin, Cout)) return REG_ERR_WORKSPACE;
-    return st(launch_conv_wgrad(in, Cin, dpre, Cout, make_dims(d), (float *)scratch, dW, kpad_of(27 * Cin),
+    const Dims g = make_dims(d);
+    const size_t need_view = conv_wgrad_view_bytes(g, Cin, Cout);
+    if (need_view && scratch_bytes >= need_view) {
+        const cudaError_t e = launch_conv_wgrad_view(in, Cin, dpre, Cout, g, (float *)scratch, dW, kpad_of(27 * Cin),
+                                                     (cudaStream_t)stream);
+        if (e != cudaErrorNotSupported) return st(e);
+    }
+    if (scratch_bytes < wgrad_part_bytes(g, Cin, Cout)) return REG_ERR_WORKSPACE;
+    return st(launch_conv_wgrad(in, Cin, dpre, Cout, g, (float *)scratch, dW, kpad_of(27 * Cin),
                                 (cudaStream_t)stream));
 }
 

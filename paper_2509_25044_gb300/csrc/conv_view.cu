@@ -150,16 +150,17 @@ __global__ void __launch_bounds__(VIEW_THREADS, 1)
                 break;
             }
             umma::fence_after_sync();
+            // descriptors move by whole 16-byte units: add to the start field
+            const uint64_t a_base = umma::sdesc(vaddr + (uint32_t)(G.q0 * 16), (uint32_t)G.VGB, 128u);
+            const uint64_t b_base = umma::sdesc(waddr, (uint32_t)(G.Nb / 8) * 128u, 128u);
 #pragma unroll 1
             for (int t = 0; t < 27; ++t) {
-                const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-                const int off = dz * plane + dy * G.P + dx;
-                const uint64_t bd = umma::sdesc(waddr + (uint32_t)(t * 32 * G.Nb), (uint32_t)(G.Nb / 8) * 128u, 128u);
-                const uint32_t a0 = vaddr + (uint32_t)((G.q0 + off) * 16);
-                for (int j = 0; j < G.MT; ++j) {
-                    const uint64_t ad = umma::sdesc(a0 + (uint32_t)(j * 128 * 16), (uint32_t)G.VGB, 128u);
-                    umma::mma_bf16(tmem + (uint32_t)(j * G.Nb), ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
-                }
+                const int off = (t / 9 - 1) * plane + ((t / 3) % 3 - 1) * G.P + (t % 3 - 1);
+                const uint64_t bd = b_base + (uint64_t)(2 * t * G.Nb);  // t * 32 Nb bytes
+                const uint64_t ad0 = a_base + (uint64_t)(int64_t)off;
+                const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
+                for (int j = 0; j < G.MT; ++j)
+                    umma::mma_bf16(tmem + (uint32_t)(j * G.Nb), ad0 + (uint64_t)(128 * j), bd, idesc, acc);
             }
             umma::commit(&bars[1]);
         }
@@ -292,6 +293,220 @@ bool choose_geom(const Dims &d, int Cin, int Cout, int N, float slope, ViewGeom 
     return false;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores:
+//   dW[co][tap][ci] = sum over voxels p of dpre[p][co] * in[p + off(tap)][ci]
+// The voxels are the GEMM's K dimension.  Persistent CTAs (one per SM) each
+// take a contiguous range of tiles (one plane, Ty rows, the whole x extent)
+// and keep the 27 per-tap accumulators D_tap[co][16 ci] in TMEM (27 x 16 of
+// the 512 columns) while they stream their tiles through a 2-stage TMA ring:
+//   A = dpre^T, MN-major: the tile's rows of dpre (x from -1 to nx, so the two
+//       halo columns are zero), one shared region per 8-channel group; M is
+//       128, the regions of channel groups >= Cout / 8 stay zero;
+//   B = the input brick of the tile (3 planes x Ty+2 rows x nx+2 columns,
+//       zero outside the volume) for one 16-channel chunk, MN-major, shifted
+//       by the tap's offset exactly as in the forward kernel.
+// After its tiles a CTA writes its 27 x 16 partial sums per output channel
+// for the chunk; the partials are summed over CTAs in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int WG_BOFF = 8;  // zeroed positions in front of each brick region (the tap -1 reads)
+
+struct WgGeom {
+    int nx, ny, nz, Cin, Cout, nchunks;
+    int Ty, P, By;        // tile rows, row pitch (nx + 2), brick rows (Ty + 2)
+    int tiles_y, ntiles;  // ntiles = nz * tiles_y
+    int ksteps;           // ceil(Ty P / 16)
+    int cgo;              // real 8-channel groups of dpre (Cout / 8)
+    int VGX, VGD;         // bytes per brick region / dpre region (multiples of 128)
+    uint32_t tx_bytes;    // bytes landing per tile
+};
+
+__host__ __device__ inline size_t wg_stage_bytes(const WgGeom &G) { return 2 * (size_t)G.VGX + 16 * (size_t)G.VGD; }
+__host__ __device__ inline size_t wg_smem_bytes(const WgGeom &G) { return 2 * wg_stage_bytes(G) + 128 + 1024; }
+
+bool choose_wg(const Dims &d, int Cin, int Cout, WgGeom &G) {
+    if (Cin % VIEW_CK || Cin < VIEW_CK || Cout % 8 || Cout < 8 || Cout > 128 || d.nx + 2 > 256) return false;
+    G.nx = d.nx;
+    G.ny = d.ny;
+    G.nz = d.nz;
+    G.Cin = Cin;
+    G.Cout = Cout;
+    G.nchunks = Cin / VIEW_CK;
+    G.cgo = Cout / 8;
+    G.P = d.nx + 2;
+    double best = -1.0;
+    WgGeom bestG = G;
+    for (int Ty = 1; Ty <= d.ny && Ty + 2 <= 256; ++Ty) {
+        WgGeom g = G;
+        g.Ty = Ty;
+        g.By = Ty + 2;
+        g.ksteps = (Ty * g.P + 15) / 16;
+        const int brick = 3 * g.By * g.P;
+        g.VGX = ((WG_BOFF + brick + 32) * 16 + 127) / 128 * 128;  // reads end within 16 positions of the brick
+        g.VGD = ((16 * g.ksteps + 16) * 16 + 127) / 128 * 128;
+        if (wg_smem_bytes(g) > 220 * 1024) break;
+        g.tiles_y = (d.ny + Ty - 1) / Ty;
+        const double useful = (double)d.nx * d.ny / (double)(g.tiles_y * 16 * g.ksteps);
+        const double reload = 3.0 * g.By / Ty;
+        const double score = useful - 0.02 * reload;
+        if (score > best) {
+            best = score;
+            bestG = g;
+        }
+    }
+    if (best < 0.0) return false;
+    G = bestG;
+    G.ntiles = G.tiles_y * d.nz;
+    // too few tiles to occupy the SMs (a 16^3 level): the gather kernel's
+    // voxel split is faster there
+    if (G.ntiles < num_sms() / 2) return false;
+    G.tx_bytes = (uint32_t)(2 * 3 * G.By * G.P * 16 + G.cgo * G.Ty * G.P * 16);
+    return true;
+}
+
+__global__ void __launch_bounds__(VIEW_THREADS, 1)
+    conv_wgrad_view_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dmap,
+                           WgGeom G, float *__restrict__ part, unsigned *err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (umma::smem_addr(smem_raw) & 1023u)) & 1023u);
+    const size_t stage_bytes = wg_stage_bytes(G);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * stage_bytes);  // [0,1] loads, [2,3] MMAs
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 4);
+    int *flag = reinterpret_cast<int *>(tmem_holder + 1);
+    const int tid = threadIdx.x;
+
+    // zero both stages once: the dpre regions of absent channel groups, the
+    // slack behind every region and the front guard of the bricks are never
+    // written by the copies and must read as 0
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(sm);
+        const size_t n16 = 2 * stage_bytes / 16;
+        for (size_t i = tid; i < n16; i += VIEW_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) umma::mbar_init(&bars[i], 1);
+        *flag = 0;
+    }
+    if (tid < 32) umma::tmem_alloc(tmem_holder, 512u);
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    const long long t_beg = (long long)G.ntiles * blockIdx.x / gridDim.x;
+    const long long t_end = (long long)G.ntiles * (blockIdx.x + 1) / gridDim.x;
+    const int per_chunk = (int)(t_end - t_beg);
+    const int total = per_chunk * G.nchunks;
+    const uint32_t idesc = umma::idesc_bf16(128, 16, 1, 1);
+    const int plane = G.By * G.P;
+    const int q0 = WG_BOFF + (G.By + 1) * G.P;
+    // brick offset of each tap in positions (= 16-byte descriptor units)
+    int toff[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) toff[t] = (t / 9 - 1) * plane + ((t / 3) % 3 - 1) * G.P + (t % 3 - 1);
+
+    auto stage_ptr = [&](int st) { return sm + (size_t)st * stage_bytes; };
+    auto issue_load = [&](int it) {
+        const int st = it & 1;
+        const int chunk = it / per_chunk;
+        const long long tile = t_beg + it % per_chunk;
+        const int z = (int)(tile / G.tiles_y), y0 = (int)(tile % G.tiles_y) * G.Ty;
+        unsigned char *xs = stage_ptr(st);
+        unsigned char *ds = xs + 2 * (size_t)G.VGX;
+        tma::expect_tx(&bars[st], G.tx_bytes);
+        for (int g = 0; g < 2; ++g)
+            tma::load_4d(xs + (size_t)g * G.VGX + WG_BOFF * 16, &xmap, chunk * VIEW_CK + 8 * g, -1, y0 - 1, z - 1,
+                         &bars[st]);
+        for (int g = 0; g < G.cgo; ++g) tma::load_4d(ds + (size_t)g * G.VGD, &dmap, 8 * g, -1, y0, z, &bars[st]);
+    };
+
+    bool ok = true;
+    int it = 0;
+    if (tid == 0 && total > 0) issue_load(0);
+    for (int chunk = 0; chunk < G.nchunks; ++chunk) {
+        if (tid == 0) {
+            for (int i = 0; i < per_chunk && ok; ++i, ++it) {
+                if (it + 1 < total) {
+                    // the stage of iteration it + 1 was last read by iteration it - 1
+                    if (it >= 1 && !umma::mbar_wait(&bars[2 + ((it + 1) & 1)], ((it - 1) >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    issue_load(it + 1);
+                }
+                if (!umma::mbar_wait(&bars[it & 1], (it >> 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t xa = umma::smem_addr(stage_ptr(it & 1));
+                const uint32_t da = xa + 2 * (uint32_t)G.VGX;
+                // descriptors move by whole 16-byte units: add to the start field
+                const uint64_t ad0 = umma::sdesc(da, 128u, (uint32_t)G.VGD);
+                const uint64_t bd0 = umma::sdesc(xa + (uint32_t)(q0 * 16), 128u, (uint32_t)G.VGX);
+                for (int ks = 0; ks < G.ksteps; ++ks) {
+                    const uint64_t ad = ad0 + (uint64_t)(16 * ks);
+                    const uint64_t bk = bd0 + (uint64_t)(16 * ks);
+                    const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+                    for (int t = 0; t < 27; ++t)
+                        umma::mma_bf16(tmem + (uint32_t)(t * 16), ad, bk + (uint64_t)(int64_t)toff[t], idesc, acc);
+                }
+                umma::commit(&bars[2 + (it & 1)]);
+            }
+            if (!ok) *flag = 1;
+        }
+        __syncthreads();
+        if (*flag) break;
+        // the chunk's last MMAs complete, then every warp reads its 32 TMEM lanes
+        // (only thread 0 advances `it`; every thread derives the last iteration)
+        const int last = (chunk + 1) * per_chunk - 1;
+        if (per_chunk > 0 && !umma::mbar_wait(&bars[2 + (last & 1)], (last >> 1) & 1)) {
+            if (tid == 0) *flag = 1;
+        }
+        umma::fence_after_sync();
+        __syncthreads();
+        if (*flag) break;
+        const int warp = tid >> 5, row = tid;
+        const int K = 27 * G.Cin;
+        float *dst = part + ((size_t)blockIdx.x * G.Cout + row) * K + chunk * VIEW_CK;
+        for (int t = 0; t < 27; ++t) {
+            float acc[16];
+            umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * 16), acc);
+            if (row < G.Cout) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) dst[(size_t)t * G.Cin + j] = per_chunk > 0 ? acc[j] : 0.0f;
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+    }
+    if (*flag) {
+        if (tid == 0) {
+            latch_error(err, REG_ERR_TIMEOUT);
+            // bounded waits for whatever may still be in flight
+            if (it >= 1) umma::mbar_wait(&bars[2 + ((it - 1) & 1)], ((it - 1) >> 1) & 1);
+            umma::mbar_wait(&bars[it & 1], (it >> 1) & 1);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) umma::tmem_dealloc(tmem, 512u);
+}
+
+// dW[co][k] (FP32, [Cout][Kpad]) = sum over CTAs (fixed order) of part[cta][co][k]
+__global__ void wg_reduce_kernel(const float *__restrict__ part, int nparts, int Cout, int K, int Kpad,
+                                 float *__restrict__ dW) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Cout * Kpad) return;
+    const int co = idx / Kpad, k = idx % Kpad;
+    float acc = 0.0f;
+    if (k < K)
+        for (int c = 0; c < nparts; ++c) acc += part[((size_t)c * Cout + co) * K + k];
+    dW[idx] = acc;
+}
+
 }  // namespace
 
 size_t conv_view_weight_bytes(int Cin, int N) {
@@ -331,6 +546,37 @@ cudaError_t launch_conv_view(const void *in, int Cin, const void *W, int rows, i
         default: run(conv_view_kernel<EPI_BIAS_F32_SOA>); break;
     }
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+size_t conv_wgrad_view_bytes(const Dims &d, int Cin, int Cout) {
+    WgGeom G;
+    if (!choose_wg(d, Cin, Cout, G)) return 0;
+    const int grid = (int)std::min<long long>(num_sms(), G.ntiles);
+    return sizeof(float) * (size_t)grid * Cout * 27 * Cin;
+}
+
+cudaError_t launch_conv_wgrad_view(const void *in, int Cin, const void *dpre, int Cout, const Dims &d, float *part,
+                                   float *dW, int Kpad, cudaStream_t s) {
+    WgGeom G;
+    if (!choose_wg(d, Cin, Cout, G)) return cudaErrorNotSupported;
+    CUtensorMap xmap, dmap;
+    const uint64_t xdims[4] = {(uint64_t)Cin, (uint64_t)d.nx, (uint64_t)d.ny, (uint64_t)d.nz};
+    const uint32_t xbox[4] = {8u, (uint32_t)G.P, (uint32_t)G.By, 3u};
+    const uint64_t ddims[4] = {(uint64_t)Cout, (uint64_t)d.nx, (uint64_t)d.ny, (uint64_t)d.nz};
+    const uint32_t dbox[4] = {8u, (uint32_t)G.P, (uint32_t)G.Ty, 1u};
+    if (!tma::make_map_bf16_4d(&xmap, in, xdims, xbox) || !tma::make_map_bf16_4d(&dmap, dpre, ddims, dbox))
+        return cudaErrorNotSupported;
+    const int grid = (int)std::min<long long>(num_sms(), G.ntiles);
+    const size_t smem = wg_smem_bytes(G);
+    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_view_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    conv_wgrad_view_kernel<<<grid, VIEW_THREADS, smem, s>>>(xmap, dmap, G, part, error_word());
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int K = 27 * Cin, total = Cout * Kpad;
+    wg_reduce_kernel<<<(total + 255) / 256, 256, 0, s>>>(part, grid, Cout, K, Kpad, dW);
     return cudaGetLastError();
 }
 

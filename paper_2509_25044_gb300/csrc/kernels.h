@@ -132,6 +132,11 @@ enum ConvEpi { EPI_BIAS_LEAKY_BF16 = 0, EPI_PLAIN_BF16 = 1, EPI_BIAS_F32_SOA = 2
 // Wt_scratch (conv_view_weight_bytes); cudaErrorNotSupported if the shape
 // has no such path
 size_t conv_view_weight_bytes(int Cin, int N);
+// TMA-fed weight gradient (Cin % 16 == 0, Cout % 8 == 0, Cout <= 128, nx <= 254): per-CTA
+// partials in `part` (conv_wgrad_view_bytes, 0 if the shape has no such path)
+size_t conv_wgrad_view_bytes(const Dims &d, int Cin, int Cout);
+cudaError_t launch_conv_wgrad_view(const void *in, int Cin, const void *dpre, int Cout, const Dims &d, float *part,
+                                   float *dW, int Kpad, cudaStream_t s);
 cudaError_t launch_conv_view(const void *in, int Cin, const void *W, int rows, int Kpad, const float *bias, int Cout,
                              int N, const Dims &d, int epi, float slope, void *Wt_scratch, void *out, cudaStream_t s);
 cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, const float *bias, int Cout, int N,

@@ -20,7 +20,7 @@ from . import capi
 class RegConfig:
     loss: str = "lncc"          # "lncc" or "mi"
     window: int = 7             # LNCC window side
-    eps: float = 1e-5           # LNCC epsilon
+    eps: float = 1e-9           # LNCC epsilon, added to B C (count-normalised moments)
     bins: int = 32              # MI bins
     f_range: tuple | None = None
     m_range: tuple | None = None

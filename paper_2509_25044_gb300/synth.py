@@ -182,28 +182,25 @@ def _paint(labels: torch.Tensor, table: np.ndarray, noise_std: float, smooth_sig
 # ---------------------------------------------------------------------------
 def mono_pair(n: int, seed: int, blob_sigma=(2.0, 8.0), field_sigma=4.0, max_disp=3.0, n_blobs=40,
               device="cpu", gpu_rng: bool = False):
-    """Mono-modal pair: the blob image B (sum of Gaussian blobs) and a smooth
-    field u_true (white noise smoothed at field_sigma, scaled to
-    max |u| = max_disp); F = B + N(0, 0.02^2) and M = B o (id + u_true) plus
-    its own N(0, 0.02^2).  The noise is acquisition noise, drawn once per
-    image: warping F's noise along with the blobs would make the noise itself
-    a matching target that the twice-interpolated copy cannot meet, and the
-    LNCC optimum would no longer sit at the true field."""
+    """Mono-modal pair as the workload states it: F = B + N(0, 0.02^2), the
+    blob image B (sum of Gaussian blobs) with its noise, and M = F o (id +
+    u_true) for a smooth field u_true (white noise smoothed at field_sigma,
+    scaled to max |u| = max_disp).  The noise is part of the imaged texture
+    and moves with it, so LNCC windows on the flat parts of the blobs still
+    carry a matching signal."""
     shape = (n, n, n)
     rng = None if gpu_rng else np.random.default_rng(seed)
     gen = None
     if gpu_rng:
         gen = torch.Generator(device=device)
         gen.manual_seed(seed)
-    Bimg = blobs(shape, n_blobs, blob_sigma, noise_std=0.0, rng=rng, gen=gen, device=device)
+    F = blobs(shape, n_blobs, blob_sigma, noise_std=0.0, rng=rng, gen=gen, device=device)
     u_true = smooth_field(shape, field_sigma, max_disp, rng=rng, gen=gen, device=device)
-    M = _sample_trilinear(Bimg, u_true)
-    F = Bimg
-    for img in (F, M):
-        if gen is not None:
-            img.add_(torch.randn(shape, generator=gen, device=device, dtype=torch.float32), alpha=0.02)
-        else:
-            img.add_(torch.from_numpy(rng.standard_normal(shape, dtype=np.float32)).to(device), alpha=0.02)
+    if gen is not None:
+        F.add_(torch.randn(shape, generator=gen, device=device, dtype=torch.float32), alpha=0.02)
+    else:
+        F.add_(torch.from_numpy(rng.standard_normal(shape, dtype=np.float32)).to(device), alpha=0.02)
+    M = _sample_trilinear(F, u_true)
     return dict(F=F, M=M, u_true=u_true, seed=seed, rng="philox" if gpu_rng else "pcg64")
 
 
@@ -237,27 +234,6 @@ def multimodal_pair(n: int, seed: int, field_sigma=6.0, max_disp=5.0, n_labels=6
     m_range = (float(M.min()), float(M.max()))
     return dict(F=F, M=M, u_true=u_true, f_range=f_range, m_range=m_range, seed=seed,
                 rng="philox" if gpu_rng else "pcg64")
-
-
-def init_training_pair(n: int, seed: int, device="cpu"):
-    """Learned-initialiser training pair at n^3: a blob image B as in the
-    mono-modal recipe (blob sigma scaled to the grid), a random smooth field
-    v_true (sigma ~ U[4,12], max |v| ~ U(0,10]), M = B + noise and
-    F = B o (id + v_true) + noise, so that v_true is the displacement the
-    registration of M onto F should recover."""
-    rng = np.random.default_rng(seed)
-    s = n / 64.0
-    Bimg = blobs((n, n, n), 40, (2.0 * s, 8.0 * s), noise_std=0.0, rng=rng, device=device)
-    sigma = rng.uniform(4.0, 12.0)
-    mx = rng.uniform(0.0, 10.0)
-    if mx == 0.0:
-        mx = 10.0
-    v_true = smooth_field((n, n, n), sigma, mx, rng=rng, device=device)
-    F = _sample_trilinear(Bimg, v_true)
-    M = Bimg
-    for img in (F, M):
-        img.add_(torch.from_numpy(rng.standard_normal((n, n, n), dtype=np.float32)).to(device), alpha=0.02)
-    return dict(F=F, M=M, v_true=v_true, seed=seed)
 
 
 CONFIGS = {

@@ -275,9 +275,12 @@ class UNet:
 
 def training_pair(n: int, seed: int, device) -> dict:
     """One training pair at n^3 made with the library's own warp: a blob
-    image B, a random smooth field v_true (sigma ~ U[4,12], max |v| ~ U(0,10]),
-    M = B + noise, F = (B o (id + v_true)) + noise.  Random numbers come from
-    torch's Philox generator on the device, seeded with `seed`."""
+    image B (sigma scaled to the grid) with N(0, 0.02^2) noise as M, a random
+    smooth field v_true (sigma ~ U[4,12], max |v| ~ U(0,10]) and F = M o (id +
+    v_true), so that v_true is the displacement the registration of M onto F
+    recovers (the noise is part of the texture and moves with it, as in the
+    mono-modal workloads).  Random numbers come from torch's Philox generator
+    on the device, seeded with `seed`."""
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     s = n / 64.0
@@ -286,8 +289,6 @@ def training_pair(n: int, seed: int, device) -> dict:
     sigma = 4.0 + 8.0 * float(u01[0])
     mx = 10.0 * (1.0 - float(u01[1]))  # in (0, 10]
     v = synth.smooth_field((n, n, n), sigma, mx, gen=gen, device=device)
-    F = capi.reg_warp(B, v)
-    M = B.clone()
-    for img in (F, M):
-        img.add_(torch.randn((n, n, n), generator=gen, device=device, dtype=torch.float32), alpha=0.02)
+    M = B.add_(torch.randn((n, n, n), generator=gen, device=device, dtype=torch.float32), alpha=0.02)
+    F = capi.reg_warp(M, v)
     return dict(F=F, M=M, v=v)
