@@ -176,13 +176,15 @@ def main():
     li.add_argument("--eval-n", type=int, default=None)
     li.add_argument("--save", default=None)
     li.add_argument("--eval-pairs", type=int, default=8)
+    li.add_argument("--eval-lam", type=float, default=2.0, help="regulariser weight of the evaluation runs")
     args = ap.parse_args()
     if args.cmd == "learned-init":
         tr, net = train_init(args.pairs, args.epochs, lr=args.lr, out_path=args.save)
         print(json.dumps(tr), flush=True)
-        print(json.dumps(eval_init_pairs(net, n_pairs=args.eval_pairs)), flush=True)
+        print(json.dumps(eval_init_pairs(net, n_pairs=args.eval_pairs, lam=args.eval_lam)), flush=True)
         if args.eval_config != "none":
-            print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n)), flush=True)
+            print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=args.eval_lam / 0.1)),
+                  flush=True)
         return
     if args.cmd == "ttl":
         print(json.dumps(time_to_loss(args.config, args.iters, args.eval_every, args.n, lam_scale=args.lam_scale,

@@ -75,8 +75,12 @@ def test_conv_forward_matches_oracle(capi, shape, cin, cout, tma):
     assert capi.reg_get_device_error() == 0
 
 
+# small volumes take the gather weight-gradient kernel; volumes with at
+# least 76 tiles (here 77-80 planes) the persistent TMA-fed tensor-core one
+# (one chunk, six chunks, 8 output channel groups)
 @pytest.mark.parametrize("shape,cin,cout", [((9, 10, 11), 16, 16), ((6, 8, 7), 96, 32), ((4, 5, 6), 128, 64),
-                                            ((5, 9, 12), 8, 16)])
+                                            ((5, 9, 12), 8, 16), ((80, 5, 24), 16, 16), ((78, 3, 10), 96, 32),
+                                            ((77, 3, 8), 128, 64)])
 def test_conv_gradients_match_oracle(capi, shape, cin, cout):
     L = capi.nn()
     rng = np.random.default_rng(3 * cin + cout)
