@@ -47,6 +47,8 @@ def _load():
         lib.or_lncc_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, _dp]
         lib.or_lncc_grad.restype = ctypes.c_double
+        lib.or_lncc_grad_ants.argtypes = lib.or_lncc_grad.argtypes
+        lib.or_lncc_grad_ants.restype = ctypes.c_double
         lib.or_lncc_grad_points.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.POINTER(ctypes.c_long), ctypes.c_int, _dp, _dp]
         lib.or_lncc_grad_points.restype = None
@@ -125,6 +127,17 @@ def lncc_grad(F, J, win: int, eps: float):
     nx, ny, nz = _dims(F)
     g = np.empty_like(F)
     S = _load().or_lncc_grad(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps), _ptr(g))
+    return S, g
+
+
+def lncc_grad_ants(F, J, win: int, eps: float):
+    """(S, approximate dL/dJ) with the convolution of the gamma family skipped
+    (the ANTs gradient approximation, App. fused LNCC)."""
+    F = _f64(F)
+    J = _f64(J)
+    nx, ny, nz = _dims(F)
+    g = np.empty_like(F)
+    S = _load().or_lncc_grad_ants(_ptr(F), _ptr(J), nx, ny, nz, int(win), float(eps), _ptr(g))
     return S, g
 
 
@@ -251,6 +264,7 @@ class LossSpec:
     kind: int = LOSS_LNCC
     window: int = 7
     eps: float = 1e-5
+    lncc_grad: int = 0  # 0: exact adjoint, 1: ANTs approximation
     bins: int = 32
     f_range: tuple = (0.0, 1.0)
     m_range: tuple = (0.0, 1.0)
@@ -262,7 +276,7 @@ def similarity_and_grad(F, M, u, spec: LossSpec, pad: int = PAD_BORDER, need_gra
     if spec.kind == LOSS_LNCC:
         if not need_grad:
             return lncc(F, J, spec.window, spec.eps), None
-        S, gJ = lncc_grad(F, J, spec.window, spec.eps)
+        S, gJ = (lncc_grad_ants if spec.lncc_grad == 1 else lncc_grad)(F, J, spec.window, spec.eps)
         return S, gJ[None] * dJ
     Fh, _ = normalize(F, *spec.f_range)
     Jh, dJh = normalize(J, *spec.m_range)

@@ -259,6 +259,44 @@ double or_lncc_grad(const double *F, const double *J, int nx, int ny, int nz, in
 }
 
 /* ------------------------------------------------------------------------ */
+/* The ANTs gradient approximation of the LNCC loss (App. fused LNCC,        */
+/* paragraph "ANTs gradient approximation"): the convolution of the gamma   */
+/* family with the window weights is skipped, i.e. every voxel k keeps only */
+/* the term of its own window.  The exact gradient averages                 */
+/*   gamma_i (F_k - muF_i) ... over the c_k windows i that contain k with   */
+/* weights 1/c_i; the approximation replaces that average by the term of    */
+/* i = k:                                                                    */
+/*   gJ_k = c_k [ alpha_k (F_k - muF_k) + beta_k (J_k - muJ_k) ]             */
+/* with alpha, beta as in or_lncc_grad (they carry dL/dn = -1/N and 1/c_k).  */
+/* Equivalently gJ_k = -(c_k / N) d n_k / d J_k, the derivative of the       */
+/* voxel's own window NCC with respect to its centre value.                 */
+/* Returns S as or_lncc does.                                                */
+/* ------------------------------------------------------------------------ */
+double or_lncc_grad_ants(const double *F, const double *J, int nx, int ny, int nz, int win, double eps,
+                         double *gJ)
+{
+    const long N = (long)nx * ny * nz;
+    double *wq = (double *)malloc(sizeof(double) * 6 * (size_t)N);
+    const double S = or_lncc(F, J, nx, ny, nz, win, eps, NULL, wq);
+    const double *muF = wq, *muJ = wq + N, *A = wq + 2 * N, *B = wq + 3 * N, *C = wq + 4 * N,
+                 *cnt = wq + 5 * N;
+    const double dLdn = -1.0 / (double)N;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < N; ++k) {
+        const double D = B[k] * C[k] + eps;
+        double g = 0.0;
+        if (D > 0.0) {
+            const double alpha = dLdn * (2.0 * A[k] / D) / cnt[k];
+            const double beta = dLdn * (-A[k] * A[k] * B[k] / (D * D)) * 2.0 / cnt[k];
+            g = cnt[k] * (alpha * (F[k] - muF[k]) + beta * (J[k] - muJ[k]));
+        }
+        gJ[k] = g;
+    }
+    free(wq);
+    return S;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Cubic B-spline Parzen kernel and its derivative (Sec. 2.2, Eq. mi, with   */
 /* the 3rd-order B-spline choice of kappa).                                  */
 /* ------------------------------------------------------------------------ */

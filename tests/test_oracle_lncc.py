@@ -127,3 +127,52 @@ def test_pointwise_gradient_equals_full_field(rng):
     gp, npnt = O.lncc_grad_points(F, J, 5, 1e-4, pts)
     np.testing.assert_allclose(gp, g.ravel()[pts], rtol=1e-12, atol=1e-18)
     np.testing.assert_allclose(npnt, n.ravel()[pts], rtol=1e-12)
+
+
+# ---- the ANTs gradient approximation (App. fused LNCC) ----------------------
+def _count(k, shape, r):
+    """in-volume size of the window of side 2r+1 at linear index k"""
+    nz, ny, nx = shape
+    z, rem = divmod(k, ny * nx)
+    y, x = divmod(rem, nx)
+    c = 1
+    for v, n in ((x, nx), (y, ny), (z, nz)):
+        c *= min(v + r, n - 1) - max(v - r, 0) + 1
+    return c
+
+
+@pytest.mark.parametrize("win,eps", [(3, 1e-5), (5, 1e-9)])
+def test_ants_gradient_is_the_own_window_derivative(rng, win, eps):
+    """gJ_k = -(c_k / N) d n_k / d J_k: central differences of the voxel's own
+    window NCC (corner, face, interior voxels)."""
+    shape = (7, 8, 9)
+    F = rng.random(shape)
+    J = 0.6 * F + 0.4 * rng.random(shape)
+    _, g = O.lncc_grad_ants(F, J, win, eps)
+    N = F.size
+    h = 1e-5
+    for k in (0, N - 1, 4 * 72 + 3 * 9 + 4, 2 * 72 + 0 * 9 + 5, 5 * 72 + 7 * 9 + 8):
+        Jp, Jm = J.copy(), J.copy()
+        Jp.flat[k] += h
+        Jm.flat[k] -= h
+        dn = (O.lncc(F, Jp, win, eps, per_voxel=True)[1].flat[k] -
+              O.lncc(F, Jm, win, eps, per_voxel=True)[1].flat[k]) / (2 * h)
+        expect = -_count(k, shape, win // 2) / N * dn
+        assert abs(g.flat[k] - expect) <= 1e-6 * max(abs(expect), 1e-12), (k, g.flat[k], expect)
+
+
+def test_ants_gradient_approximates_the_exact_adjoint():
+    """On smooth images the local approximation points along the exact
+    gradient (cosine > 0.8 for 5^3 and 7^3 windows) and transforms like it
+    under J -> a J + b (the gradient of a scale-free similarity scales 1/a)."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(1)
+    F = gaussian_filter(rng.standard_normal((16, 16, 16)), 2.0)
+    J = gaussian_filter(rng.standard_normal((16, 16, 16)), 2.0) * 0.3 + 0.8 * np.roll(F, 1, axis=2)
+    for win in (5, 7):
+        _, ge = O.lncc_grad(F, J, win, 0.0)
+        _, ga = O.lncc_grad_ants(F, J, win, 0.0)
+        cos = float((ge * ga).sum() / np.linalg.norm(ge) / np.linalg.norm(ga))
+        assert cos > 0.8, (win, cos)
+        _, ga2 = O.lncc_grad_ants(F, 3.0 * J - 2.0, win, 0.0)
+        np.testing.assert_allclose(3.0 * ga2, ga, rtol=1e-7, atol=1e-12 * np.abs(ga).max())
