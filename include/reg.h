@@ -80,13 +80,21 @@ typedef enum reg_loss_kind { REG_LOSS_LNCC = 0, REG_LOSS_MI = 1 } reg_loss_kind;
  *     Intensities are mapped to [0,1] by (v - lo) / (hi - lo) and clamped;
  *     the kernel of bin m sits at s = m with s = v (bins - 3) + 1.
  *     Similarity = MI (natural log); loss C = -MI.
- *     Requires f_hi > f_lo and m_hi > m_lo (the fixed / moving ranges). */
+ *     Requires f_hi > f_lo and m_hi > m_lo (the fixed / moving ranges).
+ *   lncc_grad (LNCC gradients only): REG_LNCC_GRAD_EXACT (0) is the exact
+ *     adjoint (the coefficient fields box-summed a second time);
+ *     REG_LNCC_GRAD_ANTS (1) is the ANTs approximation of App. fused LNCC,
+ *     which skips that second convolution: dL/dJ_k = c_k (a_J + 2 J_k a_JJ +
+ *     F_k a_FJ)_k with the coefficients of voxel k's own window (c_k its
+ *     in-volume size).  The similarity value is the same in both modes. */
+typedef enum reg_lncc_grad { REG_LNCC_GRAD_EXACT = 0, REG_LNCC_GRAD_ANTS = 1 } reg_lncc_grad;
 typedef struct reg_loss_desc {
     int kind;   /* reg_loss_kind */
     int window; /* LNCC */
     float eps;  /* LNCC */
     int bins;   /* MI */
     float f_lo, f_hi, m_lo, m_hi; /* MI intensity ranges */
+    int lncc_grad; /* reg_lncc_grad */
 } reg_loss_desc;
 
 /* Adam (the optimiser state m1, m2 of Sec. 3.1), torch.optim.Adam semantics

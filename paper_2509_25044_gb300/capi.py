@@ -45,7 +45,7 @@ class RegDims(ctypes.Structure):
 class RegLossDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("window", ctypes.c_int), ("eps", ctypes.c_float), ("bins", ctypes.c_int),
                 ("f_lo", ctypes.c_float), ("f_hi", ctypes.c_float), ("m_lo", ctypes.c_float),
-                ("m_hi", ctypes.c_float)]
+                ("m_hi", ctypes.c_float), ("lncc_grad", ctypes.c_int)]
 
 
 class RegAdamDesc(ctypes.Structure):
@@ -139,8 +139,13 @@ def _need(t, shape, dtype, name):
         raise TypeError(f"{name} dtype {t.dtype} != {dtype}")
 
 
-def lncc_desc(window: int = 7, eps: float = 1e-5) -> RegLossDesc:
-    return RegLossDesc(REG_LOSS_LNCC, int(window), float(eps), 0, 0.0, 1.0, 0.0, 1.0)
+REG_LNCC_GRAD_EXACT, REG_LNCC_GRAD_ANTS = 0, 1
+
+
+def lncc_desc(window: int = 7, eps: float = 1e-5, ants: bool = False) -> RegLossDesc:
+    """ants=True: the ANTs gradient approximation (no second box sum)."""
+    return RegLossDesc(REG_LOSS_LNCC, int(window), float(eps), 0, 0.0, 1.0, 0.0, 1.0,
+                       REG_LNCC_GRAD_ANTS if ants else REG_LNCC_GRAD_EXACT)
 
 
 def mi_desc(f_range, m_range, bins: int = 32) -> RegLossDesc:

@@ -38,6 +38,7 @@ reg_status check_loss(const reg_loss_desc *L) {
     if (L->kind == REG_LOSS_LNCC) {
         if (L->window < 3 || L->window > 2 * MAX_RADIUS + 1 || (L->window & 1) == 0) return REG_ERR_SHAPE;
         if (!(L->eps >= 0.0f) || !isfinite(L->eps)) return REG_ERR_INVALID_ARG;
+        if (L->lncc_grad != REG_LNCC_GRAD_EXACT && L->lncc_grad != REG_LNCC_GRAD_ANTS) return REG_ERR_INVALID_ARG;
         return REG_OK;
     }
     if (L->kind == REG_LOSS_MI) {
@@ -175,7 +176,7 @@ reg_status run_sweep1(const reg_loss_desc *L, const void *F, const void *M, int 
                       const Dims &g, int pad, const Ws &w, double *sim_out, bool need_grad, cudaStream_t s) {
     REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
     if (L->kind == REG_LOSS_LNCC) {
-        LnccParams P{L->window / 2, L->eps};
+        LnccParams P{L->window / 2, L->eps, L->lncc_grad == REG_LNCC_GRAD_ANTS};
         REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s));
         REG_CUDA(launch_lncc_stats(F, w.warped, img_dt, g, P, need_grad ? w.coef : nullptr, w.partials,
                                    w.counters + 0, sim_out, s));
@@ -250,7 +251,7 @@ reg_status reg_loss_grad(const reg_loss_desc *loss, const void *F, const void *M
     REG_TRY(run_sweep1(loss, F, M, img_dt, u, g, pad, w, sim_out, true, s));
     StepParams S{};
     if (loss->kind == REG_LOSS_LNCC) {
-        LnccParams P{loss->window / 2, loss->eps};
+        LnccParams P{loss->window / 2, loss->eps, loss->lncc_grad == REG_LNCC_GRAD_ANTS};
         REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u, g, pad, P, w.coef, grad_u, false, nullptr, nullptr, nullptr,
                                     REG_F32, S, w.partials, w.counters + 1, w.scratch, s));
     } else {
@@ -314,7 +315,7 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
     REG_CUDA(mark(1, s));
     const StepParams S = step_params(adam, t, lambda, g);
     if (loss->kind == REG_LOSS_LNCC) {
-        LnccParams P{loss->window / 2, loss->eps};
+        LnccParams P{loss->window / 2, loss->eps, loss->lncc_grad == REG_LNCC_GRAD_ANTS};
         REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u_in, g, pad, P, w.coef, grad_out, true, u_out, m, v,
                                     adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s));
     } else {

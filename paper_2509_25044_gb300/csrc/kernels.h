@@ -73,11 +73,13 @@ struct MiParams {
 struct LnccParams {
     int r;      // window radius, window = 2r + 1
     float eps;  // added to B C
+    int ants;   // 1: gradient with the ANTs approximation (no second box sum)
 };
 
 // per-kernel grids (used both to launch and to size the workspace)
 MarchGrid mi_sweep_grid(const Dims &g);
 MarchGrid lncc_grid(const Dims &g, int r);
+MarchGrid lncc_ants_grid(const Dims &g);
 MarchGrid diffusion_grid(const Dims &g);
 
 cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, int pad, float *J, float *dJ,

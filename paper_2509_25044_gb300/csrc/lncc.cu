@@ -426,10 +426,123 @@ __global__ void __launch_bounds__(TILE_THREADS)
     }
 }
 
+// Sweep 2 with the ANTs gradient approximation (App. fused LNCC): no second
+// box sum, each voxel uses the coefficients of its own window,
+//   dL/dJ_k = c_k (a_J + 2 J_k a_JJ + F_k a_FJ)_k,
+// so the sweep streams the coefficient fields like the MI sweep streams its
+// inputs (plane-ahead prefetch of u, F, the coefficients and the moments).
+template <typename T, typename MT, bool STEP, int PAD, typename I>
+__global__ void __launch_bounds__(TILE_THREADS, 4)
+    lncc_sweep2_ants_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
+                            LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
+                            float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
+                            double *__restrict__ partials, unsigned *__restrict__ counter,
+                            double *__restrict__ r_out, unsigned *err) {
+    __shared__ double red[32];
+    const int r = P.r;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(g.nz, z0 + zc);
+    float rpart = 0.0f;
+    if (x < g.nx && y < g.ny) {
+        const float *uc[3] = {u, u + g.n, u + 2 * g.n};
+        const float *cf[3] = {coef, coef + g.n, coef + 2 * g.n};
+        MT *mc[3] = {m, m + g.n, m + 2 * g.n};
+        MT *vc[3] = {v, v + g.n, v + 2 * g.n};
+        const I nxy = (I)g.nxy, nx = (I)g.nx;
+        I p = (I)z0 * nxy + (I)y * nx + x;
+        const bool hxm = x > 0, hxp = x + 1 < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
+        const float cxy = (float)(win_count(x, r, g.nx) * win_count(y, r, g.ny));
+        float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
+        float fcur, acur[3], mcur[3] = {0.f, 0.f, 0.f}, vcur[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cur[c] = __ldg(uc[c] + p);
+            acur[c] = __ldg(cf[c] + p);
+        }
+        fcur = ld_vox(F, p);
+        if (STEP) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                mcur[c] = ld_moment(mc[c], p);
+                vcur[c] = ld_moment(vc[c], p);
+                if (z0 > 0) prv[c] = __ldg(uc[c] + p - nxy);
+            }
+        }
+        for (int z = z0; z < z1; ++z, p += nxy) {
+            float fnxt = 0.0f, anxt[3] = {0.f, 0.f, 0.f}, mnxt[3] = {0.f, 0.f, 0.f}, vnxt[3] = {0.f, 0.f, 0.f};
+            if (z + 1 < g.nz) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
+            }
+            if (z + 1 < z1) {
+                fnxt = ld_vox(F, p + nxy);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) anxt[c] = __ldg(cf[c] + p + nxy);
+                if (STEP) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        mnxt[c] = ld_moment(mc[c], p + nxy);
+                        vnxt[c] = ld_moment(vc[c], p + nxy);
+                    }
+                }
+            }
+            float sx, sy, sz;
+            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
+            const float ck = cxy * (float)win_count(z, r, g.nz);
+            const float gj = ck * fmaf(fcur, acur[2], fmaf(2.0f * jv, acur[1], acur[0]));
+            const float gs[3] = {gj * sx, gj * sy, gj * sz};
+            if (STEP) {
+                float gR[3];
+                diffusion_ptr<I>(uc, p, nx, hxm, hxp, hym, hyp, z > 0, z + 1 < g.nz, cur, prv, nxt, gR, rpart);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    if (grad_out) (grad_out + c * g.n)[p] = gt;
+                    (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
+            }
+            fcur = fnxt;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+                acur[c] = anxt[c];
+                mcur[c] = mnxt[c];
+                vcur[c] = vnxt[c];
+            }
+        }
+    }
+    if (STEP) {
+        const double bs = block_sum((double)rpart, red);
+        const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (tid == 0) partials[bid] = bs;
+        if (arrive_last(counter)) {
+            const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+            double acc = 0.0;
+            for (long long i = tid; i < nb; i += TILE_THREADS) acc += __ldcg(partials + i);
+            const double tot = block_sum(acc, red);
+            if (tid == 0) {
+                const double R = tot / (double)g.n;
+                if (!isfinite(R)) latch_error(err, REG_ERR_NONFINITE);
+                r_out[0] = R;
+                *counter = 0u;
+            }
+        }
+    }
+}
+
 // longer z-chunks amortise the 2r warm-up planes of every chunk
 MarchGrid lncc_grid(const Dims &g, int r) {
     return march_grid(g, 4LL * num_sms() * 3, 8 * r > 32 ? 8 * r : 32);
 }
+// the streaming (ANTs) sweep has no warm-up planes: the MI sweep's grid
+MarchGrid lncc_ants_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
 
 // staged rows per thread: TY + 2r <= 16 rows fit in 2 passes of 8
 template <typename Fn>
@@ -476,10 +589,44 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
     return cudaGetLastError();
 }
 
+static cudaError_t launch_lncc_sweep2_ants(const void *F, const void *M, int dt, const float *u, const Dims &g,
+                                           int pad, const LnccParams &P, const float *coef, float *grad_out,
+                                           bool step, float *u_out, void *m, void *v, int mdt, const StepParams &S,
+                                           double *partials, unsigned *counter, double *r_out, cudaStream_t s) {
+    const MarchGrid G = lncc_ants_grid(g);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    unsigned *err = error_word();
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            with_index(g, [&](auto ip) {
+                using I = elem_t<decltype(ip)>;
+                if (!step) {
+                    lncc_sweep2_ants_kernel<T, float, false, PD, I><<<grid, block, 0, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (float *)m, (float *)v, S,
+                        partials, counter, r_out, err);
+                    return;
+                }
+                with_type(mdt, [&](auto mp) {
+                    using MT = elem_t<decltype(mp)>;
+                    lncc_sweep2_ants_kernel<T, MT, true, PD, I><<<grid, block, 0, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
+                        partials, counter, r_out, err);
+                });
+            });
+        });
+    });
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                                const LnccParams &P, const float *coef, float *grad_out, bool step,
                                float *u_out, void *m, void *v, int mdt, const StepParams &S,
                                double *partials, unsigned *counter, double *r_out, cudaStream_t s) {
+    if (P.ants)
+        return launch_lncc_sweep2_ants(F, M, dt, u, g, pad, P, coef, grad_out, step, u_out, m, v, mdt, S, partials,
+                                       counter, r_out, s);
     const MarchGrid G = lncc_grid(g, P.r);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 3);

@@ -109,6 +109,41 @@ def time_to_loss(config: str, iters: int | None = None, eval_every: int = 1, n: 
     return out
 
 
+def ants_vs_exact(config: str, iters: int | None = None, n: int | None = None, lam_scale: float = 20.0,
+                  rel_tol: float = 0.01) -> dict:
+    """The ANTs gradient approximation against the exact adjoint (both FP32
+    storage): time for the approximate run to reach the exact run's target
+    L <= L* + rel_tol (L0 - L*); the objective itself is the same function in
+    both runs, only the gradient differs.  Fold checks of both."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    d = synth.make(config, device=dev, n=n)
+    c = d["config"]
+    iters = iters or c["iters"]
+    F, M = d["F"].contiguous(), d["M"].contiguous()
+    out = {"experiment": "ants_vs_exact", "config": config, "n": F.shape[0], "iters": iters,
+           "lam": c["lam"] * lam_scale}
+    runs = {}
+    for ants in (False, True):
+        cfg = _cfg(c, d, "f32", lam_scale)
+        cfg.ants = ants
+        r = Registration(F, M, cfg)
+        res = r.run(iters)
+        fin = r.objective()
+        runs[ants] = (res, fin, r.fold_check())
+    res0, fin0, fold0 = runs[False]
+    L0, Lstar = float(res0.objective[0]), fin0["objective"]
+    tol = rel_tol * max(L0 - Lstar, 0.0)
+    for ants, (res, fin, fold) in runs.items():
+        k = _first_within(np.append(res.objective[1:], fin["objective"]), Lstar, tol)
+        out["ants" if ants else "exact"] = {"ms_per_iter": res.ms_per_iter, "iters_to_target": None if k is None else k + 1,
+                                            "time_to_target_ms": None if k is None else (k + 1) * res.ms_per_iter,
+                                            "final": fin, "fold": fold}
+    if out["exact"]["time_to_target_ms"] and out["ants"]["time_to_target_ms"]:
+        out["speedup_ants_vs_exact"] = out["exact"]["time_to_target_ms"] / out["ants"]["time_to_target_ms"]
+    return out
+
+
 def eval_init_pairs(net, n_pairs: int = 8, n: int = 128, seed0: int = 90_000, iters: int = 200, window: int = 7,
                     lam: float = 1.0, lr: float = 0.1, rel_tol: float = 0.01) -> dict:
     """Held-out pairs of the training distribution (seeds never used in
@@ -168,6 +203,11 @@ def main():
     t.add_argument("--eval-every", type=int, default=1)
     t.add_argument("--lam-scale", type=float, default=1.0)
     t.add_argument("--adam-eps", type=float, default=1e-8)
+    an = sub.add_parser("ants")
+    an.add_argument("--config", default="c2")
+    an.add_argument("--iters", type=int, default=None)
+    an.add_argument("--n", type=int, default=None)
+    an.add_argument("--lam-scale", type=float, default=20.0)
     li = sub.add_parser("learned-init")
     li.add_argument("--pairs", type=int, default=2000)
     li.add_argument("--epochs", type=int, default=4)
@@ -185,6 +225,9 @@ def main():
         if args.eval_config != "none":
             print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=args.eval_lam / 0.1)),
                   flush=True)
+        return
+    if args.cmd == "ants":
+        print(json.dumps(ants_vs_exact(args.config, args.iters, args.n, args.lam_scale)))
         return
     if args.cmd == "ttl":
         print(json.dumps(time_to_loss(args.config, args.iters, args.eval_every, args.n, lam_scale=args.lam_scale,

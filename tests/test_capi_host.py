@@ -92,6 +92,11 @@ def test_loss_and_iterate_validation(capi):
     # workspace too small
     assert L.reg_loss(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need - 1,
                       vp(FAKE), None) == 5
+    # unknown LNCC gradient mode (neither the exact adjoint nor the ANTs approximation)
+    bad_mode = capi.lncc_desc(7, 1e-5)
+    bad_mode.lncc_grad = 2
+    assert L.reg_loss(ctypes.byref(bad_mode), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need,
+                      vp(FAKE), None) == 1
     # bad eps
     bad = capi.lncc_desc(7, -1.0)
     assert L.reg_loss(ctypes.byref(bad), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need,

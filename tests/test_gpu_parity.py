@@ -76,6 +76,29 @@ def test_lncc_matches_oracle(capi, shape, window, pad):
     assert rel_l2(to64(g), gr) <= GRAD_RTOL
 
 
+# the ANTs gradient approximation (App. fused LNCC): the same similarity, the
+# gradient without the second box sum; ragged volumes, borders, both pads
+@pytest.mark.parametrize("shape,window", [((16, 16, 16), 7), ((21, 35, 40), 5), ((12, 13, 14), 15),
+                                          ((1, 9, 40), 3)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_lncc_ants_gradient_matches_oracle(capi, shape, window, pad):
+    F, M = mono_images(shape, 9)
+    u = field(shape, 3.0, 2.5, 10)
+    loss = capi.lncc_desc(window, 1e-4, ants=True)
+    ws = capi.workspace(loss, F.to(DEV))
+    Fd, Md, ud = F.to(DEV), M.to(DEV), u.to(DEV)
+    sim, g = capi.reg_loss_grad(loss, Fd, Md, ud, ws, pad=pad)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=window, eps=1e-4, lncc_grad=1)
+    Sr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec, pad)
+    assert_rel(sim.item(), Sr, LOSS_RTOL, "S")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL
+    # the exact adjoint differs: the flag is honoured
+    spec0 = O.LossSpec(kind=O.LOSS_LNCC, window=window, eps=1e-4)
+    _, g0 = O.similarity_and_grad(to64(F), to64(M), to64(u), spec0, pad)
+    assert rel_l2(to64(g), g0) > 10 * GRAD_RTOL
+
+
 def test_lncc_bf16_storage(capi):
     shape = (32, 40, 48)
     F, M = mono_images(shape, 11)
@@ -208,10 +231,11 @@ def test_jacdet_matches_oracle(capi):
 # fused iteration
 # ---------------------------------------------------------------------------
 def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
-    if kind == "lncc":
+    if kind in ("lncc", "lncc_ants"):
         F, M = mono_images(shape, seed)
-        loss = capi.lncc_desc(7, 1e-4)
-        spec = O.LossSpec(kind=O.LOSS_LNCC, window=7, eps=1e-4)
+        ants = kind == "lncc_ants"
+        loss = capi.lncc_desc(7, 1e-4, ants=ants)
+        spec = O.LossSpec(kind=O.LOSS_LNCC, window=7, eps=1e-4, lncc_grad=int(ants))
     else:
         F, M = multimodal_images(shape, seed)
         fr = (float(F.min()), float(F.max()))
@@ -237,7 +261,7 @@ def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
                 dtype=dtype)
 
 
-@pytest.mark.parametrize("kind", ["lncc", "mi"])
+@pytest.mark.parametrize("kind", ["lncc", "mi", "lncc_ants"])
 @pytest.mark.parametrize("shape", [(24, 20, 35), (48, 48, 48)])
 def test_iterate_matches_oracle(capi, kind, shape):
     c = _iterate_case(capi, kind, shape, t=3)
