@@ -47,6 +47,11 @@ def _load():
         lib.or_lncc_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, _dp]
         lib.or_lncc_grad.restype = ctypes.c_double
+        cf = ctypes.c_float
+        lib.or_mi_hard.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, cf, cf, cf, cf, _dp]
+        lib.or_mi_hard.restype = ctypes.c_double
+        lib.or_mi_hard_grad.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_int, cf, cf, cf, cf, _dp]
+        lib.or_mi_hard_grad.restype = ctypes.c_double
         lib.or_lncc_grad_ants.argtypes = lib.or_lncc_grad.argtypes
         lib.or_lncc_grad_ants.restype = ctypes.c_double
         lib.or_lncc_grad_points.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -182,6 +187,36 @@ def mi_grad(Fh, Jh, bins: int):
     return v, g.reshape(shape)
 
 
+def _range32(rng):
+    """(lo, scale) as the library forms them: float lo, hi; scale = float(1 / (hi - lo))."""
+    lo, hi = float(np.float32(rng[0])), float(np.float32(rng[1]))
+    return lo, float(np.float32(1.0 / (hi - lo)))
+
+
+def mi_hard(F, J, bins: int, f_range, m_range, with_hist: bool = False):
+    """Hard-binned (approximate) MI of raw intensities F, J (App. fused MI)."""
+    F = _f64(F).ravel()
+    J = _f64(J).ravel()
+    p = np.empty((bins, bins), dtype=np.float64) if with_hist else None
+    (fl, fs), (ml, ms) = _range32(f_range), _range32(m_range)
+    v = _load().or_mi_hard(_ptr(F), _ptr(J), F.size, int(bins), fl, fs, ml, ms, _ptr(p))
+    return (v, p) if with_hist else v
+
+
+def mi_hard_grad(F, J, bins: int, f_range, m_range):
+    """(approximate MI, dL/dJh) for L = -MI: the Parzen adjoint with the
+    hard-binned PMF's table."""
+    shape = np.shape(J)
+    Fr = _f64(F).ravel()
+    Jr = _f64(J).ravel()
+    Fh, _ = normalize(Fr, *f_range)
+    Jh, _ = normalize(Jr, *m_range)
+    g = np.empty_like(Jr)
+    (fl, fs), (ml, ms) = _range32(f_range), _range32(m_range)
+    v = _load().or_mi_hard_grad(_ptr(Fr), _ptr(Jr), _ptr(Fh), _ptr(Jh), Fr.size, int(bins), fl, fs, ml, ms, _ptr(g))
+    return v, g.reshape(shape)
+
+
 def normalize(v, lo: float, hi: float):
     """Map intensities to [0,1]: vh = clamp((v-lo)/(hi-lo), 0, 1), and dvh/dv."""
     v = _f64(v)
@@ -268,6 +303,7 @@ class LossSpec:
     bins: int = 32
     f_range: tuple = (0.0, 1.0)
     m_range: tuple = (0.0, 1.0)
+    mi_estimator: int = 0  # 0: Parzen, 1: hard-binned approximation
 
 
 def similarity_and_grad(F, M, u, spec: LossSpec, pad: int = PAD_BORDER, need_grad: bool = True):
@@ -280,6 +316,11 @@ def similarity_and_grad(F, M, u, spec: LossSpec, pad: int = PAD_BORDER, need_gra
         return S, gJ[None] * dJ
     Fh, _ = normalize(F, *spec.f_range)
     Jh, dJh = normalize(J, *spec.m_range)
+    if spec.mi_estimator == 1:
+        if not need_grad:
+            return mi_hard(F, J, spec.bins, spec.f_range, spec.m_range), None
+        v, gJh = mi_hard_grad(F, J, spec.bins, spec.f_range, spec.m_range)
+        return v, (gJh * dJh)[None] * dJ
     if not need_grad:
         return mi(Fh, Jh, spec.bins), None
     v, gJh = mi_grad(Fh, Jh, spec.bins)

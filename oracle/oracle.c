@@ -390,11 +390,12 @@ double or_mi(const double *Fh, const double *Jh, long N, int B, double *p_out)
 /*   dL/dJh_k = -(1/N) (B-3) sum_{m,n} G[m][n] kappa(sF_k - m) kappa'(sJ_k - n). */
 /* Returns MI.                                                               */
 /* ------------------------------------------------------------------------ */
-double or_mi_grad(const double *Fh, const double *Jh, long N, int B, double *gJh)
+/* The Parzen adjoint of MI for a given joint PMF p (B*B): marginals,        */
+/* G = log(p / (pI pJ)), then gJh_k = -(B-3)/N sum_mn G[m][n] kappa(sF_k-m)   */
+/* kappa'(sJ_k-n)  (Eq. gradientmi-threadn).                                  */
+static void mi_adjoint(const double *Fh, const double *Jh, long N, int B, const double *p, double *gJh)
 {
     const int BB = B * B;
-    double *p = (double *)malloc(sizeof(double) * (size_t)BB);
-    const double mi = or_mi(Fh, Jh, N, B, p);
     double pI[256], pJ[256];
     for (int m = 0; m < B; ++m) {
         pI[m] = 0.0;
@@ -426,6 +427,97 @@ double or_mi_grad(const double *Fh, const double *Jh, long N, int B, double *gJh
         gJh[k] = scale * g;
     }
     free(G);
+}
+
+double or_mi_grad(const double *Fh, const double *Jh, long N, int B, double *gJh)
+{
+    double *p = (double *)malloc(sizeof(double) * (size_t)B * B);
+    const double mi = or_mi(Fh, Jh, N, B, p);
+    mi_adjoint(Fh, Jh, N, B, p, gJh);
+    free(p);
+    return mi;
+}
+
+static double mi_of_pmf(const double *p, int B)
+{
+    double pI[256], pJ[256];
+    for (int m = 0; m < B; ++m) {
+        pI[m] = 0.0;
+        pJ[m] = 0.0;
+    }
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            pI[m] += p[m * B + n];
+            pJ[n] += p[m * B + n];
+        }
+    double mi = 0.0;
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            const double v = p[m * B + n];
+            if (v > 0.0) mi += v * log(v / (pI[m] * pJ[n]));
+        }
+    return mi;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The approximate (hard-binned) MI estimator of App. fused MI ("An          */
+/* approximate histogram estimator"): each sample adds 1 to the bin nearest  */
+/* to it, and the count histogram, divided by N, is convolved with the       */
+/* kernel kappa; the PMF is exact for samples on bin centres.  With the bin  */
+/* layout of or_mi (kernel of bin m centred at s = m), the nearest bin of s  */
+/* is floor(s + 1/2) and the convolution weights are kappa(a) kappa(b) for   */
+/* a, b in {-1, 0, 1} (kappa(+-2) = 0): 1/6, 2/3, 1/6.                        */
+/* The bin decision is taken in FP32, as the GPU takes it:                   */
+/*   t = clamp((v - lo) * scale, 0, 1), s = fma(t, B - 3, 1), m* = floor(s + 1/2). */
+/* F, J are raw intensities; p_out (optional, B*B).                          */
+/* ------------------------------------------------------------------------ */
+static int hard_bin(double v, float lo, float scale, int B)
+{
+    float t = ((float)v - lo) * scale;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    const float sb = fmaf(t, (float)(B - 3), 1.0f);
+    int m = (int)floorf(sb + 0.5f);
+    if (m < 1) m = 1;
+    if (m > B - 2) m = B - 2;
+    return m;
+}
+
+double or_mi_hard(const double *F, const double *J, long N, int B, float f_lo, float f_scale, float m_lo,
+                  float m_scale, double *p_out)
+{
+    const int BB = B * B;
+    double *cnt = (double *)calloc((size_t)BB, sizeof(double));
+    for (long k = 0; k < N; ++k) cnt[hard_bin(F[k], f_lo, f_scale, B) * B + hard_bin(J[k], m_lo, m_scale, B)] += 1.0;
+    const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    double *p = (double *)malloc(sizeof(double) * (size_t)BB);
+    for (int m = 0; m < B; ++m)
+        for (int n = 0; n < B; ++n) {
+            double acc = 0.0;
+            for (int a = -1; a <= 1; ++a)
+                for (int b = -1; b <= 1; ++b) {
+                    const int mm = m - a, nn = n - b;
+                    if (mm < 0 || mm >= B || nn < 0 || nn >= B) continue;
+                    acc += w[a + 1] * w[b + 1] * cnt[mm * B + nn];
+                }
+            p[m * B + n] = acc / (double)N;
+        }
+    const double mi = mi_of_pmf(p, B);
+    if (p_out) memcpy(p_out, p, sizeof(double) * (size_t)BB);
+    free(p);
+    free(cnt);
+    return mi;
+}
+
+/* Gradient paired with the hard-binned forward (the paper gives only the   */
+/* forward): the Parzen adjoint (Eq. gradientmi-threadn) evaluated with the */
+/* approximate PMF's table G.  Fh, Jh are the intensities mapped to [0,1]    */
+/* in FP64 for the kernel derivative at each sample's own position.         */
+double or_mi_hard_grad(const double *F, const double *J, const double *Fh, const double *Jh, long N, int B,
+                       float f_lo, float f_scale, float m_lo, float m_scale, double *gJh)
+{
+    double *p = (double *)malloc(sizeof(double) * (size_t)B * B);
+    const double mi = or_mi_hard(F, J, N, B, f_lo, f_scale, m_lo, m_scale, p);
+    mi_adjoint(Fh, Jh, N, B, p, gJh);
     free(p);
     return mi;
 }

@@ -135,3 +135,48 @@ def test_full_chain_gradient_wrt_u_matches_central_differences(rng):
         # that entries near zero are judged on the FD rounding noise scale
         errs.append(abs(g[k] - fd) / (abs(fd) + 0.1 * rms))
     assert max(errs) < 1e-6, errs
+
+
+# ---- the hard-binned (approximate) estimator of App. fused MI -----------------
+def _snap(v, rng_, B):
+    """intensity of the bin centre nearest to v (the estimator's own rule,
+    taken in FP32 as the library takes it)"""
+    lo, hi = np.float32(rng_[0]), np.float32(rng_[1])
+    scale = np.float32(1.0 / (float(hi) - float(lo)))
+    t = np.clip((v.astype(np.float32) - lo) * scale, np.float32(0), np.float32(1))
+    s = (t.astype(np.float64) * (B - 3) + 1.0).astype(np.float32)
+    m = np.clip(np.floor(s + np.float32(0.5)), 1, B - 2).astype(np.float64)
+    return float(lo) + (m - 1.0) / (B - 3) * (float(hi) - float(lo))
+
+
+@pytest.mark.parametrize("B", [8, 32])
+def test_hard_binned_equals_parzen_on_bin_centres(rng, B):
+    """The estimator is exact for samples on bin centres (App. fused MI): the
+    hard-binned MI of (F, J) is the Parzen MI of the snapped intensities, and
+    its PMF sums to 1."""
+    F = rng.random((9, 10, 11)) * 3.0 - 1.0
+    J = 0.5 * F + rng.random((9, 10, 11))
+    # ranges representable in FP32, so the snapped centres sit exactly on s = m
+    fr, jr = (-1.0, 2.0), (float(np.float32(J.min() - 0.01)), float(np.float32(J.max() + 0.01)))
+    v, p = O.mi_hard(F, J, B, fr, jr, with_hist=True)
+    assert abs(p.sum() - 1.0) < 1e-12
+    Fs, Js = _snap(F, fr, B), _snap(J, jr, B)
+    ref = O.mi(O.normalize(Fs, *fr)[0], O.normalize(Js, *jr)[0], B)
+    assert abs(v - ref) <= 1e-12 * max(1.0, abs(ref))
+    # the paired gradient is the Parzen adjoint with the approximate table:
+    # on snapped samples it equals the Parzen gradient
+    _, gh = O.mi_hard_grad(Fs, Js, B, fr, jr)
+    _, gp = O.mi_grad(O.normalize(Fs, *fr)[0], O.normalize(Js, *jr)[0], B)
+    np.testing.assert_allclose(gh.ravel(), gp.ravel(), rtol=1e-9, atol=1e-12 * np.abs(gp).max())
+
+
+def test_hard_binned_symmetry_and_constant(rng):
+    F = rng.random((8, 8, 8))
+    J = np.sqrt(F) + 0.1 * rng.random((8, 8, 8))
+    a = O.mi_hard(F, J, 16, (0.0, 1.0), (0.0, 1.2))
+    b = O.mi_hard(J, F, 16, (0.0, 1.2), (0.0, 1.0))
+    assert abs(a - b) < 1e-12
+    assert abs(O.mi_hard(F, np.full_like(F, 0.3), 16, (0.0, 1.0), (0.0, 1.0))) < 1e-12
+    # an approximation of the Parzen value on continuous intensities
+    ref = O.mi(F, np.clip(J / 1.2, 0, 1), 16)
+    assert abs(a - ref) < 0.1 * ref
