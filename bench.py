@@ -248,7 +248,7 @@ def run_ours(args):
     if kind == "lncc":
         loss = capi.lncc_desc(cfg["window"], 1e-9, ants=args.lncc_grad == "ants")
     else:
-        loss = capi.mi_desc(d["f_range"], d["m_range"], cfg["bins"])
+        loss = capi.mi_desc(d["f_range"], d["m_range"], cfg["bins"], hard=args.mi_estimator == "hard")
     mdt = capi.REG_BF16 if bf16 else capi.REG_F32
     mtype = torch.bfloat16 if bf16 else torch.float32
     u = [torch.zeros((3,) + shape, device=dev), torch.zeros((3,) + shape, device=dev)]
@@ -347,7 +347,8 @@ def run_ours(args):
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16+f32" if bf16 else "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config] + (", ANTs gradient approximation"
-                                                         if kind == "lncc" and args.lncc_grad == "ants" else ""),
+                                                         if kind == "lncc" and args.lncc_grad == "ants" else "")
+                   + (", hard-binned histogram" if kind == "mi" and args.mi_estimator == "hard" else ""),
                    "name": args.config, "n": shape[0],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2 (working set {(b1 + b2) * N / 1e9:.2f} GB/iteration > 129 MB)"},
@@ -446,6 +447,8 @@ def main():
     ap.add_argument("--no-unet", action="store_true", help="skip the tensor-core (U-Net) measurement")
     ap.add_argument("--lncc-grad", default="exact", choices=["exact", "ants"],
                     help="LNCC gradient: exact adjoint or the ANTs approximation (no second box sum)")
+    ap.add_argument("--mi-estimator", default="parzen", choices=["parzen", "hard"],
+                    help="MI histogram: cubic B-spline Parzen estimate or the hard-binned approximation")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -86,15 +86,24 @@ typedef enum reg_loss_kind { REG_LOSS_LNCC = 0, REG_LOSS_MI = 1 } reg_loss_kind;
  *     REG_LNCC_GRAD_ANTS (1) is the ANTs approximation of App. fused LNCC,
  *     which skips that second convolution: dL/dJ_k = c_k (a_J + 2 J_k a_JJ +
  *     F_k a_FJ)_k with the coefficients of voxel k's own window (c_k its
- *     in-volume size).  The similarity value is the same in both modes. */
+ *     in-volume size).  The similarity value is the same in both modes.
+ *   mi_estimator (MI only): REG_MI_PARZEN (0) is the Parzen estimate above;
+ *     REG_MI_HARD (1) is the approximate histogram estimator of App. fused MI:
+ *     each sample adds 1 to its nearest bin (m = floor(s + 1/2) of its bin
+ *     coordinate s, taken in FP32), and the count histogram / N is convolved
+ *     with kappa(a) kappa(b), a, b in {-1, 0, 1} (1/6, 2/3, 1/6) -- exact for
+ *     samples on bin centres.  Its gradient is the Parzen adjoint evaluated
+ *     with the approximate PMF's table. */
 typedef enum reg_lncc_grad { REG_LNCC_GRAD_EXACT = 0, REG_LNCC_GRAD_ANTS = 1 } reg_lncc_grad;
+typedef enum reg_mi_estimator { REG_MI_PARZEN = 0, REG_MI_HARD = 1 } reg_mi_estimator;
 typedef struct reg_loss_desc {
     int kind;   /* reg_loss_kind */
     int window; /* LNCC */
     float eps;  /* LNCC */
     int bins;   /* MI */
     float f_lo, f_hi, m_lo, m_hi; /* MI intensity ranges */
-    int lncc_grad; /* reg_lncc_grad */
+    int lncc_grad;    /* reg_lncc_grad */
+    int mi_estimator; /* reg_mi_estimator */
 } reg_loss_desc;
 
 /* Adam (the optimiser state m1, m2 of Sec. 3.1), torch.optim.Adam semantics

@@ -45,7 +45,7 @@ class RegDims(ctypes.Structure):
 class RegLossDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("window", ctypes.c_int), ("eps", ctypes.c_float), ("bins", ctypes.c_int),
                 ("f_lo", ctypes.c_float), ("f_hi", ctypes.c_float), ("m_lo", ctypes.c_float),
-                ("m_hi", ctypes.c_float), ("lncc_grad", ctypes.c_int)]
+                ("m_hi", ctypes.c_float), ("lncc_grad", ctypes.c_int), ("mi_estimator", ctypes.c_int)]
 
 
 class RegAdamDesc(ctypes.Structure):
@@ -148,9 +148,13 @@ def lncc_desc(window: int = 7, eps: float = 1e-5, ants: bool = False) -> RegLoss
                        REG_LNCC_GRAD_ANTS if ants else REG_LNCC_GRAD_EXACT)
 
 
-def mi_desc(f_range, m_range, bins: int = 32) -> RegLossDesc:
+REG_MI_PARZEN, REG_MI_HARD = 0, 1
+
+
+def mi_desc(f_range, m_range, bins: int = 32, hard: bool = False) -> RegLossDesc:
+    """hard=True: the hard-binned approximate histogram estimator."""
     return RegLossDesc(REG_LOSS_MI, 0, 0.0, int(bins), float(f_range[0]), float(f_range[1]), float(m_range[0]),
-                       float(m_range[1]))
+                       float(m_range[1]), 0, REG_MI_HARD if hard else REG_MI_PARZEN)
 
 
 def adam_desc(lr: float, beta1=0.9, beta2=0.999, eps=1e-8, moment_dtype=REG_F32, grad_scale=1.0) -> RegAdamDesc:

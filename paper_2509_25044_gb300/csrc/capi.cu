@@ -46,6 +46,7 @@ reg_status check_loss(const reg_loss_desc *L) {
         if (!isfinite(L->f_lo) || !isfinite(L->f_hi) || !isfinite(L->m_lo) || !isfinite(L->m_hi))
             return REG_ERR_INVALID_ARG;
         if (!(L->f_hi > L->f_lo) || !(L->m_hi > L->m_lo)) return REG_ERR_INVALID_ARG;
+        if (L->mi_estimator != REG_MI_PARZEN && L->mi_estimator != REG_MI_HARD) return REG_ERR_INVALID_ARG;
         return REG_OK;
     }
     return REG_ERR_INVALID_ARG;
@@ -110,6 +111,7 @@ MiParams mi_params(const reg_loss_desc *L) {
     P.m_lo = L->m_lo;
     P.m_scale = (float)(1.0 / ((double)L->m_hi - (double)L->m_lo));
     P.bins = L->bins;
+    P.hard = L->mi_estimator == REG_MI_HARD;
     return P;
 }
 

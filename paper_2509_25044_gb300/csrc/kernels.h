@@ -68,6 +68,7 @@ MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc, int max
 struct MiParams {
     float f_lo, f_scale, m_lo, m_scale;  // vhat = clamp((v - lo) * scale, 0, 1)
     int bins;
+    int hard;  // 1: hard-binned counts, convolved with the kernel in the finalisation
 };
 
 struct LnccParams {

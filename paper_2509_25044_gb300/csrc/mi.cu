@@ -81,7 +81,10 @@ size_t mi_hist_smem_bytes(int B) { return sizeof(unsigned) * (size_t)hist_copies
 // 2^23 (exact round-to-nearest of wf * wj * MI_FIXED_SCALE, which is below
 // 2^22), so the bins are sums of integers and the histogram does not depend
 // on the order of the atomics (deterministic).
-template <typename T, int PAD, typename I>
+// nearest bin of bin coordinate s (the hard-binned estimator's rule)
+__device__ __forceinline__ int nearest_bin(float s, int B) { return min(max((int)floorf(s + 0.5f), 1), B - 2); }
+
+template <typename T, int PAD, typename I, bool HARD>
 __global__ void __launch_bounds__(HIST_THREADS, 1)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
                    int tiles_x, long long total, unsigned long long *__restrict__ hist) {
@@ -118,17 +121,25 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
                     nx2 = __ldg(u2 + p + nxy);
                 }
                 const float jv = sample<T, PAD, I>(M, g, x, y, z, ux, uy, uz);
-                float wf[4], wj[4];
-                const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
-                const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
-                unsigned *row = shc + iF * B + iJ;
+                if (HARD) {
+                    // one count at the nearest bins; the kernel is applied to
+                    // the B x B counts in the finalisation
+                    const int mF = nearest_bin(to_bin(fv, P.f_lo, P.f_scale, B), B);
+                    const int mJ = nearest_bin(to_bin(jv, P.m_lo, P.m_scale, B), B);
+                    atomicAdd(shc + mF * B + mJ, 1u);
+                } else {
+                    float wf[4], wj[4];
+                    const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
+                    const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
+                    unsigned *row = shc + iF * B + iJ;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float sa = wf[a] * MI_FIXED_SCALE;
+                    for (int a = 0; a < 4; ++a) {
+                        const float sa = wf[a] * MI_FIXED_SCALE;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        atomicAdd(row + b, __float_as_uint(fmaf(sa, wj[b], MAGIC)) - 0x4B000000u);
-                    row += B;
+                        for (int b = 0; b < 4; ++b)
+                            atomicAdd(row + b, __float_as_uint(fmaf(sa, wj[b], MAGIC)) - 0x4B000000u);
+                        row += B;
+                    }
                 }
                 fv = fn;
                 ux = nx0;
@@ -150,14 +161,30 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
 }
 
 __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long long *__restrict__ hist, int B,
-                                                           double inv_total, double gscale,
+                                                           int hard, double inv_total, double gscale,
                                                            float *__restrict__ Gtab, double *__restrict__ sim_out,
                                                            unsigned *err) {
     __shared__ double p[MAX_BINS * MAX_BINS];
     __shared__ double pI[MAX_BINS], pJ[MAX_BINS];
     __shared__ double red[32];
     const int BB = B * B;
-    for (int e = threadIdx.x; e < BB; e += blockDim.x) p[e] = (double)hist[e] * inv_total;
+    if (!hard) {
+        for (int e = threadIdx.x; e < BB; e += blockDim.x) p[e] = (double)hist[e] * inv_total;
+    } else {
+        // counts at the nearest bins convolved with kappa(a) kappa(b), a, b in {-1, 0, 1}
+        const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+        for (int e = threadIdx.x; e < BB; e += blockDim.x) {
+            const int m = e / B, n = e % B;
+            double acc = 0.0;
+            for (int a = -1; a <= 1; ++a)
+                for (int b = -1; b <= 1; ++b) {
+                    const int mm = m - a, nn = n - b;
+                    if (mm < 0 || mm >= B || nn < 0 || nn >= B) continue;
+                    acc += w[a + 1] * w[b + 1] * (double)hist[mm * B + nn];
+                }
+            p[e] = acc * inv_total;
+        }
+    }
     __syncthreads();
     if (threadIdx.x < B) {
         double s = 0.0;
@@ -327,10 +354,15 @@ cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u,
         with_pad(pad, [&](auto pd) {
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
-                auto kern = mi_hist_kernel<T, decltype(pd)::value, I>;
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e == cudaSuccess)
-                    kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, tiles_x, total, hist);
+                auto run = [&](auto kern) {
+                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e == cudaSuccess)
+                        kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, tiles_x, total, hist);
+                };
+                if (P.hard)
+                    run(mi_hist_kernel<T, decltype(pd)::value, I, true>);
+                else
+                    run(mi_hist_kernel<T, decltype(pd)::value, I, false>);
             });
         });
     });
@@ -340,9 +372,10 @@ cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u,
 
 cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
                                double *sim_out, cudaStream_t s) {
-    const double inv_total = 1.0 / ((double)MI_FIXED_SCALE * (double)N);
+    // Parzen bins hold fixed-point weight (MI_FIXED_SCALE per unit); hard bins hold counts
+    const double inv_total = 1.0 / ((P.hard ? 1.0 : (double)MI_FIXED_SCALE) * (double)N);
     const double gscale = -(double)(P.bins - 3) * (double)P.m_scale / (double)N;
-    mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, inv_total, gscale, Gtab, sim_out, error_word());
+    mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, P.hard, inv_total, gscale, Gtab, sim_out, error_word());
     return cudaGetLastError();
 }
 

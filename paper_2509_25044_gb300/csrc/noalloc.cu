@@ -65,6 +65,7 @@ extern "C" reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const 
     if (!isfinite(loss->f_lo) || !isfinite(loss->f_hi) || !isfinite(loss->m_lo) || !isfinite(loss->m_hi) ||
         !(loss->f_hi > loss->f_lo) || !(loss->m_hi > loss->m_lo))
         return REG_ERR_INVALID_ARG;
+    if (loss->mi_estimator != REG_MI_PARZEN && loss->mi_estimator != REG_MI_HARD) return REG_ERR_INVALID_ARG;
     if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > (1 << 20) || d.ny > (1 << 19) || d.nz > (1 << 16) ||
         (long long)d.nx * d.ny * d.nz > (1LL << 36))
         return REG_ERR_SHAPE;
@@ -86,6 +87,7 @@ extern "C" reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const 
     P.m_lo = loss->m_lo;
     P.m_scale = (float)(1.0 / ((double)loss->m_hi - (double)loss->m_lo));
     P.bins = loss->bins;
+    P.hard = loss->mi_estimator == REG_MI_HARD;
     const Dims g = make_dims(d);
     const cudaStream_t s = (cudaStream_t)stream;
     // the histogram is accumulated with atomics and must start at zero on

@@ -22,6 +22,7 @@ class RegConfig:
     window: int = 7             # LNCC window side
     eps: float = 1e-9           # LNCC epsilon, added to B C (count-normalised moments)
     ants: bool = False          # LNCC gradient with the ANTs approximation (no second box sum)
+    mi_hard: bool = False       # MI with the hard-binned approximate histogram estimator
     bins: int = 32              # MI bins
     f_range: tuple | None = None
     m_range: tuple | None = None
@@ -38,7 +39,7 @@ class RegConfig:
             return capi.lncc_desc(self.window, self.eps, ants=self.ants)
         fr = self.f_range if self.f_range is not None else (float(F.min()), float(F.max()))
         mr = self.m_range if self.m_range is not None else (0.0, 1.0)
-        return capi.mi_desc(fr, mr, self.bins)
+        return capi.mi_desc(fr, mr, self.bins, hard=self.mi_hard)
 
 
 @dataclass

@@ -97,6 +97,11 @@ def test_loss_and_iterate_validation(capi):
     bad_mode.lncc_grad = 2
     assert L.reg_loss(ctypes.byref(bad_mode), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need,
                       vp(FAKE), None) == 1
+    # unknown MI estimator
+    bad_est = capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32)
+    bad_est.mi_estimator = 5
+    assert L.reg_loss(ctypes.byref(bad_est), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), 1 << 30,
+                      vp(FAKE), None) == 1
     # bad eps
     bad = capi.lncc_desc(7, -1.0)
     assert L.reg_loss(ctypes.byref(bad), vp(FAKE), vp(FAKE), 0, vp(FAKE), dims(), 0, vp(FAKE), need,

@@ -146,6 +146,33 @@ def test_mi_matches_oracle(capi, shape, bins, pad):
     assert rel_l2(to64(g), gr) <= GRAD_RTOL
 
 
+# the hard-binned approximate estimator (App. fused MI): nearest-bin counts
+# convolved with the kernel in the finalisation, the Parzen adjoint with
+# the approximate table
+@pytest.mark.parametrize("shape,bins", [((16, 16, 16), 32), ((33, 29, 40), 32), ((24, 26, 28), 8),
+                                        ((1, 7, 50), 16)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_mi_hard_binned_matches_oracle(capi, shape, bins, pad):
+    F, M = multimodal_images(shape, 13)
+    u = field(shape, 3.0, 2.0, 14)
+    fr = (float(F.min()), float(F.max()))
+    mr = (float(M.min()), float(M.max()))
+    loss = capi.mi_desc(fr, mr, bins, hard=True)
+    ws = capi.workspace(loss, F.to(DEV))
+    Fd, Md, ud = F.to(DEV), M.to(DEV), u.to(DEV)
+    sim1 = capi.reg_loss(loss, Fd, Md, ud, ws, pad=pad)
+    sim, g = capi.reg_loss_grad(loss, Fd, Md, ud, ws, pad=pad)
+    torch.cuda.synchronize()
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=bins, f_range=fr, m_range=mr, mi_estimator=1)
+    Sr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec, pad)
+    assert_rel(sim1.item(), Sr, LOSS_RTOL, "MI (reg_loss)")
+    assert_rel(sim.item(), Sr, LOSS_RTOL, "MI (reg_loss_grad)")
+    assert rel_l2(to64(g), gr) <= GRAD_RTOL
+    # a different estimate from the Parzen one: the flag is honoured
+    spec0 = O.LossSpec(kind=O.LOSS_MI, bins=bins, f_range=fr, m_range=mr)
+    assert abs(O.similarity_and_grad(to64(F), to64(M), to64(u), spec0, pad, need_grad=False)[0] - Sr) > 1e-4 * Sr
+
+
 def test_mi_bf16_storage(capi):
     shape = (40, 36, 44)
     F, M = multimodal_images(shape, 31)
@@ -240,8 +267,9 @@ def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
         F, M = multimodal_images(shape, seed)
         fr = (float(F.min()), float(F.max()))
         mr = (float(M.min()), float(M.max()))
-        loss = capi.mi_desc(fr, mr, 32)
-        spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=fr, m_range=mr)
+        hard = kind == "mi_hard"
+        loss = capi.mi_desc(fr, mr, 32, hard=hard)
+        spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=fr, m_range=mr, mi_estimator=int(hard))
     u = field(shape, 3.0, 2.0, seed + 1)
     N = int(np.prod(shape))
     gen = torch.Generator().manual_seed(seed)
@@ -261,7 +289,7 @@ def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
                 dtype=dtype)
 
 
-@pytest.mark.parametrize("kind", ["lncc", "mi", "lncc_ants"])
+@pytest.mark.parametrize("kind", ["lncc", "mi", "lncc_ants", "mi_hard"])
 @pytest.mark.parametrize("shape", [(24, 20, 35), (48, 48, 48)])
 def test_iterate_matches_oracle(capi, kind, shape):
     c = _iterate_case(capi, kind, shape, t=3)
