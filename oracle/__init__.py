@@ -52,6 +52,9 @@ def _load():
         lib.or_mi_hard.restype = ctypes.c_double
         lib.or_mi_hard_grad.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_int, cf, cf, cf, cf, _dp]
         lib.or_mi_hard_grad.restype = ctypes.c_double
+        lib.or_gaussian_smooth.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, _dp]
+        lib.or_gaussian_smooth.restype = None
         lib.or_lncc_grad_ants.argtypes = lib.or_lncc_grad.argtypes
         lib.or_lncc_grad_ants.restype = ctypes.c_double
         lib.or_lncc_grad_points.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -223,6 +226,17 @@ def normalize(v, lo: float, hi: float):
     t = (v - lo) / (hi - lo)
     d = np.where((t >= 0.0) & (t <= 1.0), 1.0 / (hi - lo), 0.0)
     return np.clip(t, 0.0, 1.0), d
+
+
+def gaussian_smooth(u, sigma: float):
+    """Separable Gaussian (radius floor(4 sigma + 1/2), nearest borders) of
+    every channel of u [C][nz][ny][nx] (or of one volume [nz][ny][nx])."""
+    u = _f64(u)
+    v = u[None] if u.ndim == 3 else u
+    out = np.empty_like(v)
+    nx, ny, nz = _dims(v[0])
+    _load().or_gaussian_smooth(_ptr(np.ascontiguousarray(v)), nx, ny, nz, v.shape[0], float(sigma), _ptr(out))
+    return out[0] if u.ndim == 3 else out
 
 
 def diffusion(u, with_grad: bool = True):

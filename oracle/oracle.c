@@ -523,6 +523,56 @@ double or_mi_hard_grad(const double *F, const double *J, const double *Fh, const
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gaussian smoothing of a field (the sigma_grad / sigma_warp smoothing      */
+/* regularisation the paper runs with, FireANTs style): each of nch SoA      */
+/* channels [nch][nz][ny][nx] is convolved separably along x, y, z with       */
+/* w_k = exp(-k^2 / (2 sigma^2)) / sum, |k| <= floor(4 sigma + 1/2), borders  */
+/* repeating the edge voxel.  out may not alias in.                          */
+/* ------------------------------------------------------------------------ */
+void or_gaussian_smooth(const double *in, int nx, int ny, int nz, int nch, double sigma, double *out)
+{
+    const long N = (long)nx * ny * nz;
+    const int r = (int)(4.0 * sigma + 0.5);
+    double *w = (double *)malloc(sizeof(double) * (size_t)(2 * r + 1));
+    double sum = 0.0;
+    for (int k = -r; k <= r; ++k) {
+        w[k + r] = exp(-0.5 * (double)k * (double)k / (sigma * sigma));
+        sum += w[k + r];
+    }
+    for (int k = 0; k <= 2 * r; ++k) w[k] /= sum;
+    double *a = (double *)malloc(sizeof(double) * (size_t)N);
+    double *b = (double *)malloc(sizeof(double) * (size_t)N);
+    const int n[3] = {nx, ny, nz};
+    for (int c = 0; c < nch; ++c) {
+        memcpy(a, in + (long)c * N, sizeof(double) * (size_t)N);
+        for (int axis = 0; axis < 3; ++axis) {
+#pragma omp parallel for schedule(static)
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        int q[3] = {x, y, z};
+                        const int q0 = q[axis];
+                        double acc = 0.0;
+                        for (int k = -r; k <= r; ++k) {
+                            int qq = q0 + k;
+                            qq = qq < 0 ? 0 : (qq > n[axis] - 1 ? n[axis] - 1 : qq);
+                            q[axis] = qq;
+                            acc += w[k + r] * a[lin(q[0], q[1], q[2], nx, ny)];
+                        }
+                        b[lin(x, y, z, nx, ny)] = acc;
+                    }
+            double *t = a;
+            a = b;
+            b = t;
+        }
+        memcpy(out + (long)c * N, a, sizeof(double) * (size_t)N);
+    }
+    free(a);
+    free(b);
+    free(w);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Diffusion regulariser (Sec. 1 lists the Sobolev norm of the gradient as  */
 /* a common R; this is its first-order, squared form):                       */
 /*   R(u) = (1/N) sum_c sum_d sum_{p : p+e_d inside} (u_c(p+e_d) - u_c(p))^2  */

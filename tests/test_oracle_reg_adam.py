@@ -114,3 +114,26 @@ def test_jacdet_detects_folding():
     x = np.arange(8, dtype=np.float64)
     u[0] = -2.0 * x  # phi_x = -x : orientation reversed
     assert (O.jacdet(u) < 0).all()
+
+
+# ---- Gaussian smoothing of gradient / warp (the sigma_grad / sigma_warp
+# regularisation the paper runs with) ------------------------------------------
+@pytest.mark.parametrize("sigma", [0.5, 1.0, 2.3])
+def test_gaussian_smooth_equals_scipy(rng, sigma):
+    """A library special case: scipy.ndimage.gaussian_filter with mode
+    'nearest' and truncate 4 (the same radius floor(4 sigma + 1/2))."""
+    from scipy.ndimage import gaussian_filter
+    u = rng.standard_normal((3, 7, 11, 13))
+    s = O.gaussian_smooth(u, sigma)
+    for c in range(3):
+        ref = gaussian_filter(u[c], sigma, mode="nearest", truncate=4.0)
+        np.testing.assert_allclose(s[c], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_gaussian_smooth_preserves_constants_and_mass(rng):
+    u = np.full((2, 5, 6, 7), 3.25)
+    np.testing.assert_allclose(O.gaussian_smooth(u, 1.5), u, rtol=1e-14)
+    # a linear ramp is preserved away from the borders (symmetric kernel)
+    x = np.broadcast_to(np.arange(40, dtype=np.float64), (3, 3, 40)).copy()
+    s = O.gaussian_smooth(x, 1.0)
+    np.testing.assert_allclose(s[:, :, 8:32], x[:, :, 8:32], rtol=0, atol=1e-12)
