@@ -117,6 +117,16 @@ typedef struct reg_adam_desc {
     float grad_scale;
 } reg_adam_desc;
 
+/* Gaussian smoothing of a field (the sigma_grad / sigma_warp smoothing
+ * regularisation the paper runs its registrations with, FireANTs style:
+ * the gradient is smoothed before the optimiser step, the warp after it).
+ * u, tmp, out: SoA FP32 [3][nz][ny][nx] device buffers, 16-byte aligned,
+ * pairwise distinct (tmp is scratch).  Each channel is convolved separably
+ * along x, y, z with w_k = exp(-k^2 / (2 sigma^2)) / sum over |k| <=
+ * floor(4 sigma + 1/2), borders repeating the edge voxel.
+ * 0 < sigma <= 7.9, else REG_ERR_INVALID_ARG. */
+REG_API reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 REG_API int reg_version(void);
 

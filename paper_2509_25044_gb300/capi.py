@@ -29,7 +29,7 @@ STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR
 EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
-           "reg_debug_gemm_bf16")
+           "reg_debug_gemm_bf16", "reg_smooth_field")
 
 
 class RegError(RuntimeError):
@@ -87,6 +87,7 @@ def _lib():
                                           ctypes.c_int, _vp]
         L.reg_mi_loss_grad_noalloc.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                                ctypes.c_int, _vp, _vp, _vp]
+        L.reg_smooth_field.argtypes = [_vp, RegDims, ctypes.c_float, _vp, _vp, _vp]
         for name in EXPORTS:
             if name not in ("reg_version", "reg_status_string"):
                 getattr(L, name).restype = _st
@@ -227,6 +228,17 @@ def reg_regularize(u, lam: float, ws, r=None, grad=None):
     _check(_lib().reg_regularize(_ptr(u), d, float(lam), _ptr(ws), ws.numel(), _ptr(r), _ptr(grad), _stream(u)),
            "reg_regularize")
     return r
+
+
+def reg_smooth_field(u, sigma: float, out=None, tmp=None):
+    """Gaussian smoothing of a [3][nz][ny][nx] FP32 field (out != u)."""
+    d = dims_of(u[0])
+    if out is None:
+        out = torch.empty_like(u)
+    if tmp is None:
+        tmp = torch.empty_like(u)
+    _check(_lib().reg_smooth_field(_ptr(u), d, float(sigma), _ptr(tmp), _ptr(out), _stream(u)), "reg_smooth_field")
+    return out
 
 
 def reg_step(u_in, u_out, m, v, grad, adam: RegAdamDesc, t: int):

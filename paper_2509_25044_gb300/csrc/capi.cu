@@ -329,6 +329,16 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
     return REG_OK;
 }
 
+reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_ptr(u));
+    REG_TRY(check_ptr(tmp));
+    REG_TRY(check_ptr(out));
+    if (!(sigma > 0.0f) || !(sigma <= 7.9f)) return REG_ERR_INVALID_ARG;
+    if (u == tmp || u == out || tmp == out) return REG_ERR_INVALID_ARG;
+    return cuda_status(launch_smooth_field(u, make_dims(d), sigma, tmp, out, (cudaStream_t)stream));
+}
+
 reg_status reg_debug_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int a_mn_major,
                                int b_mn_major, void *stream) {
     REG_TRY(check_ptr(A));

@@ -65,6 +65,14 @@ struct MarchGrid {
 // on the z-chunk (max_zc wins)
 MarchGrid march_grid(const Dims &g, long long target_blocks, int min_zc, int max_zc = 1 << 30);
 
+// Gaussian smoothing weights: radius r = floor(4 sigma + 1/2) <= SMOOTH_MAX_R
+constexpr int SMOOTH_MAX_R = 32;
+struct SmoothWeights {
+    int r;
+    float w[2 * SMOOTH_MAX_R + 1];
+};
+cudaError_t launch_smooth_field(const float *u, const Dims &g, float sigma, float *tmp, float *out, cudaStream_t s);
+
 struct MiParams {
     float f_lo, f_scale, m_lo, m_scale;  // vhat = clamp((v - lo) * scale, 0, 1)
     int bins;

@@ -32,6 +32,8 @@ class RegConfig:
     beta2: float = 0.999
     adam_eps: float = 1e-8
     moments: str = "f32"        # "f32" or "bf16"
+    sigma_grad: float = 0.0     # > 0: Gaussian smoothing of the gradient before each Adam step
+    sigma_warp: float = 0.0     # > 0: Gaussian smoothing of the field after each step
     pad: int = capi.REG_PAD_BORDER
 
     def loss_desc(self, F):
@@ -74,6 +76,13 @@ class Registration:
         self.adam = capi.adam_desc(cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps,
                                    capi.REG_BF16 if cfg.moments == "bf16" else capi.REG_F32, float(self.N))
         self.t = 0
+        self.smoothing = cfg.sigma_grad > 0.0 or cfg.sigma_warp > 0.0
+        if self.smoothing:
+            self.g = torch.empty_like(self.u[0])
+            self.tmp = torch.empty_like(self.u[0])
+            self.tmp2 = torch.empty_like(self.u[0])
+            self.sim1 = torch.zeros(2, dtype=torch.float64, device=dev)  # 16-byte aligned outputs
+            self.r1 = torch.zeros(2, dtype=torch.float64, device=dev)
 
     @property
     def current(self) -> torch.Tensor:
@@ -86,8 +95,22 @@ class Registration:
         for k in range(iters):
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
             self.t += 1
-            capi.reg_iterate(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t,
-                             self.ws, pad=self.cfg.pad, obj=hist[k])
+            if not self.smoothing:
+                capi.reg_iterate(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t,
+                                 self.ws, pad=self.cfg.pad, obj=hist[k])
+                continue
+            # smoothing regularisation: gradient -> smooth(sigma_grad) -> Adam -> smooth(sigma_warp)
+            capi.reg_loss_grad(self.loss, self.F, self.M, a, self.ws, pad=self.cfg.pad, sim=self.sim1, grad=self.g)
+            capi.reg_regularize(a, self.cfg.lam, self.ws, r=self.r1, grad=self.g)
+            hist[k, 0] = self.sim1[0]
+            hist[k, 1] = self.r1[0]
+            g = self.g
+            if self.cfg.sigma_grad > 0.0:
+                g = capi.reg_smooth_field(self.g, self.cfg.sigma_grad, out=self.tmp2, tmp=self.tmp)
+            capi.reg_step(a, b, self.m, self.v, g, self.adam, self.t)
+            if self.cfg.sigma_warp > 0.0:
+                capi.reg_smooth_field(b, self.cfg.sigma_warp, out=self.tmp2, tmp=self.tmp)
+                b.copy_(self.tmp2)
         end.record()
         torch.cuda.synchronize()
         h = hist.cpu().numpy()

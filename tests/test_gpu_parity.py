@@ -335,3 +335,34 @@ def test_bounded_wait_times_out_and_context_survives(capi):
     capi.reg_debug_wait_flag(flag, 1, 2_000_000)
     assert capi.reg_get_device_error() == 0
     assert torch.ones(3, device=DEV).sum().item() == 3.0
+
+
+# ---------------------------------------------------------------------------
+# Gaussian smoothing of fields (sigma_grad / sigma_warp regularisation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,sigma", [((9, 10, 37), 1.0), ((1, 5, 6), 0.5), ((40, 33, 20), 2.3), ((3, 70, 4), 7.9)])
+def test_smooth_field_matches_oracle(capi, shape, sigma):
+    u = field(shape, 2.0, 3.0, 5) + torch.randn((3,) + shape, generator=torch.Generator().manual_seed(5))
+    out = capi.reg_smooth_field(u.to(DEV), sigma)
+    torch.cuda.synchronize()
+    ref = O.gaussian_smooth(to64(u), sigma)
+    np.testing.assert_allclose(to64(out), ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+def test_smoothing_regularised_registration(capi):
+    """The driver's smoothing path (gradient -> smooth -> Adam -> smooth, no
+    diffusion term) decreases the objective and regularises the field: far
+    fewer folded voxels than the same run without smoothing."""
+    from paper_2509_25044_gb300 import synth
+    from paper_2509_25044_gb300.register import RegConfig, Registration
+    d = synth.make("c0", device=DEV)
+    folds = {}
+    for sg, sw in ((0.0, 0.0), (1.0, 1.0)):
+        cfg = RegConfig(loss="lncc", window=7, eps=1e-9, lam=0.0, lr=0.1, sigma_grad=sg, sigma_warp=sw)
+        r = Registration(d["F"], d["M"], cfg)
+        res = r.run(50)
+        assert np.all(np.isfinite(res.objective))
+        assert res.objective[-1] < res.objective[0]
+        folds[sg] = r.fold_check()["n_fold"]
+    assert folds[1.0] * 10 <= max(folds[0.0], 1), folds
+    assert capi.reg_get_device_error() == 0
