@@ -158,6 +158,27 @@ def approx_vs_exact(config: str, variant: str = "ants", iters: int | None = None
     return out
 
 
+def regularisers(config: str = "c0", iters: int = 50, n: int | None = None) -> dict:
+    """The diffusion penalty against the Gaussian smoothing regularisation
+    (sigma_grad before each Adam step, sigma_warp after it) on one
+    mono-modal workload: final objective, error to the inverse of the true
+    field, folds and time per iteration."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    d = synth.make(config, device=dev, n=n)
+    c = d["config"]
+    rows = []
+    for sg, sw, lam in ((0.0, 0.0, 0.0), (0.0, 0.0, 2.0), (1.0, 0.5, 0.0), (1.0, 1.0, 0.0), (2.0, 1.0, 0.0)):
+        cfg = RegConfig(loss="lncc", window=c["window"], eps=LNCC_EPS, lam=lam, lr=c["lr"], sigma_grad=sg,
+                        sigma_warp=sw)
+        r = Registration(d["F"], d["M"], cfg)
+        res = r.run(iters)
+        err = float(((r.current + d["u_true"]).norm() / d["u_true"].norm()).item())
+        rows.append({"sigma_grad": sg, "sigma_warp": sw, "lam": lam, "similarity_loss_final": float(1.0 - res.sim[-1]),
+                     "rel_err_vs_inverse_true": err, "fold": r.fold_check()["n_fold"], "ms_per_iter": res.ms_per_iter})
+    return {"experiment": "regularisers", "config": config, "iters": iters, "rows": rows}
+
+
 def eval_init_pairs(net, n_pairs: int = 8, n: int = 128, seed0: int = 90_000, iters: int = 200, window: int = 7,
                     lam: float = 1.0, lr: float = 0.1, rel_tol: float = 0.01) -> dict:
     """Held-out pairs of the training distribution (seeds never used in
@@ -217,6 +238,10 @@ def main():
     t.add_argument("--eval-every", type=int, default=1)
     t.add_argument("--lam-scale", type=float, default=1.0)
     t.add_argument("--adam-eps", type=float, default=1e-8)
+    rg = sub.add_parser("regularisers")
+    rg.add_argument("--config", default="c0")
+    rg.add_argument("--iters", type=int, default=50)
+    rg.add_argument("--n", type=int, default=None)
     an = sub.add_parser("approx")
     an.add_argument("--variant", default="ants", choices=["ants", "mi_hard"])
     an.add_argument("--config", default="c2")
@@ -240,6 +265,9 @@ def main():
         if args.eval_config != "none":
             print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=args.eval_lam / 0.1)),
                   flush=True)
+        return
+    if args.cmd == "regularisers":
+        print(json.dumps(regularisers(args.config, args.iters, args.n)))
         return
     if args.cmd == "approx":
         print(json.dumps(approx_vs_exact(args.config, args.variant, args.iters, args.n, args.lam_scale)))
