@@ -52,6 +52,8 @@ def _load():
         lib.or_mi_hard.restype = ctypes.c_double
         lib.or_mi_hard_grad.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_int, cf, cf, cf, cf, _dp]
         lib.or_mi_hard_grad.restype = ctypes.c_double
+        lib.or_downsample2.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        lib.or_downsample2.restype = None
         lib.or_gaussian_smooth.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, _dp]
         lib.or_gaussian_smooth.restype = None
@@ -226,6 +228,15 @@ def normalize(v, lo: float, hi: float):
     t = (v - lo) / (hi - lo)
     d = np.where((t >= 0.0) & (t <= 1.0), 1.0 / (hi - lo), 0.0)
     return np.clip(t, 0.0, 1.0), d
+
+
+def downsample2(img):
+    """2x2x2 block mean of an even-sized volume [nz][ny][nx]."""
+    img = _f64(img)
+    nx, ny, nz = _dims(img)
+    out = np.empty((nz // 2, ny // 2, nx // 2))
+    _load().or_downsample2(_ptr(img), nx, ny, nz, _ptr(out))
+    return out
 
 
 def gaussian_smooth(u, sigma: float):

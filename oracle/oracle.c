@@ -573,6 +573,25 @@ void or_gaussian_smooth(const double *in, int nx, int ny, int nz, int nch, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* 2x downsampling of an image for the multi-scale schedule the paper runs   */
+/* (coarse-to-fine levels): out[z][y][x] = mean of in over the 2x2x2 block   */
+/* (2x, 2y, 2z); nx, ny, nz even.                                            */
+/* ------------------------------------------------------------------------ */
+void or_downsample2(const double *in, int nx, int ny, int nz, double *out)
+{
+    const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+    for (int z = 0; z < mz; ++z)
+        for (int y = 0; y < my; ++y)
+            for (int x = 0; x < mx; ++x) {
+                double acc = 0.0;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) acc += in[lin(2 * x + dx, 2 * y + dy, 2 * z + dz, nx, ny)];
+                out[lin(x, y, z, mx, my)] = acc / 8.0;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Diffusion regulariser (Sec. 1 lists the Sobolev norm of the gradient as  */
 /* a common R; this is its first-order, squared form):                       */
 /*   R(u) = (1/N) sum_c sum_d sum_{p : p+e_d inside} (u_c(p+e_d) - u_c(p))^2  */

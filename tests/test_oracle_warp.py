@@ -144,3 +144,12 @@ def test_slope_on_knots_uses_the_upper_cell():
     np.testing.assert_allclose(dJ[0][:, :, -1], fwd[:, :, -1], atol=1e-15)
     np.testing.assert_allclose(dJ[2][:-1], np.diff(M, axis=0), atol=1e-15)
     np.testing.assert_allclose(dJ[2][-1], M[-1] - M[-2], atol=1e-15)
+
+
+def test_downsample2_is_the_block_mean(rng):
+    """The coarse level of the multi-scale schedule: the 2x2x2 block mean,
+    the same as numpy's reshape-and-mean, and a constant stays constant."""
+    img = rng.random((6, 8, 10))
+    ref = img.reshape(3, 2, 4, 2, 5, 2).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(O.downsample2(img), ref, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(O.downsample2(np.full((4, 4, 4), 0.7)), 0.7, rtol=1e-15)
