@@ -127,6 +127,13 @@ typedef struct reg_adam_desc {
  * 0 < sigma <= 7.9, else REG_ERR_INVALID_ARG. */
 REG_API reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream);
 
+/* 2x downsampling of an image for the coarse levels of a multi-scale
+ * registration (the coarse-to-fine schedules the paper runs with):
+ * out[z][y][x] = mean of the 2x2x2 block of `in` at (2x, 2y, 2z), FP32 sums,
+ * stored in the image dtype.  nx, ny, nz even (else REG_ERR_SHAPE); out has
+ * (nx/2, ny/2, nz/2) voxels and may not alias in. */
+REG_API reg_status reg_downsample2(const void *in, int dt, reg_dims d, void *out, void *stream);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 REG_API int reg_version(void);
 
@@ -184,6 +191,21 @@ REG_API reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const v
                        float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
                        const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
                        float *grad_out, void *stream);
+
+/* `iters` fused iterations (as reg_iterate) in one call, numbered t0 + 1 ..
+ * t0 + iters, without returning to the caller between them: iteration k
+ * (0-based) reads u[k % 2] and writes u[(k + 1) % 2] with u = {u_a, u_b}, so
+ * the last iterate is in u_a when iters is even and in u_b when it is odd.
+ * obj_hist: device double[2 * iters]; entry 2k, 2k + 1 = {similarity,
+ * R} at iteration k's input.  The launches are those of `iters`
+ * reg_iterate calls on `stream` (same results bit for bit); only the host
+ * work between them is gone, which is what bounds small volumes.
+ * iters = 0 does nothing; iters < 0 or t0 < 0 is REG_ERR_INVALID_ARG; u_a
+ * and u_b must not overlap. */
+REG_API reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, float *u_a,
+                           float *u_b, void *m, void *v, reg_dims d, int pad, float lambda,
+                           const reg_adam_desc *adam, int t0, int iters, void *ws, size_t ws_bytes,
+                           double *obj_hist, void *stream);
 
 /* Fold check of phi = id + u: min over voxels of det(I + grad u) (central
  * differences, one-sided at the border) and the number of voxels with

@@ -29,7 +29,7 @@ STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR
 EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
-           "reg_debug_gemm_bf16", "reg_smooth_field")
+           "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run")
 
 
 class RegError(RuntimeError):
@@ -88,6 +88,10 @@ def _lib():
         L.reg_mi_loss_grad_noalloc.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                                ctypes.c_int, _vp, _vp, _vp]
         L.reg_smooth_field.argtypes = [_vp, RegDims, ctypes.c_float, _vp, _vp, _vp]
+        L.reg_downsample2.argtypes = [_vp, ctypes.c_int, RegDims, _vp, _vp]
+        L.reg_run.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
+                              ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, ctypes.c_int,
+                              _vp, ctypes.c_size_t, _vp, _vp]
         for name in EXPORTS:
             if name not in ("reg_version", "reg_status_string"):
                 getattr(L, name).restype = _st
@@ -241,6 +245,15 @@ def reg_smooth_field(u, sigma: float, out=None, tmp=None):
     return out
 
 
+def reg_downsample2(img):
+    """2x2x2 block mean of an even-sized FP32 / BF16 volume."""
+    nz, ny, nx = img.shape
+    out = torch.empty((nz // 2, ny // 2, nx // 2), dtype=img.dtype, device=img.device)
+    _check(_lib().reg_downsample2(_ptr(img), _img_dtype(img), dims_of(img), _ptr(out), _stream(img)),
+           "reg_downsample2")
+    return out
+
+
 def reg_step(u_in, u_out, m, v, grad, adam: RegAdamDesc, t: int):
     d = dims_of(u_in)
     _check(_lib().reg_step(_ptr(u_in), _ptr(u_out), _ptr(m), _ptr(v), _ptr(grad), d, ctypes.byref(adam), int(t),
@@ -260,6 +273,23 @@ def reg_iterate(loss: RegLossDesc, F, M, u_in, u_out, m, v, lam: float, adam: Re
                               _ptr(v), d, int(pad), float(lam), ctypes.byref(adam), int(t), _ptr(ws), ws.numel(),
                               _ptr(obj), _ptr(grad), _stream(F)), "reg_iterate")
     return obj
+
+
+def reg_run(loss: RegLossDesc, F, M, u_a, u_b, m, v, lam: float, adam: RegAdamDesc, t0: int, iters: int, ws,
+            pad: int = REG_PAD_BORDER, obj_hist=None):
+    """`iters` fused iterations t0+1..t0+iters in one native call; the last
+    iterate ends in u_a (iters even) or u_b (odd).  Returns obj_hist
+    [iters][2] = {similarity, R} per iteration."""
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _need(u_a, (3,) + tuple(F.shape), torch.float32, "u_a")
+    _need(u_b, (3,) + tuple(F.shape), torch.float32, "u_b")
+    if obj_hist is None:
+        obj_hist = torch.empty((max(iters, 1), 2), dtype=torch.float64, device=F.device)
+    _check(_lib().reg_run(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u_a), _ptr(u_b), _ptr(m), _ptr(v),
+                          d, int(pad), float(lam), ctypes.byref(adam), int(t0), int(iters), _ptr(ws), ws.numel(),
+                          _ptr(obj_hist), _stream(F)), "reg_run")
+    return obj_hist
 
 
 def reg_jacdet_min(u, out_min=None, out_nfold=None):

@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/reg.h: host-side validation, workspace
 // layout and kernel sequencing.  Every entry point validates all arguments
 // before enqueueing anything and allocates no memory.
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -329,6 +330,29 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
     return REG_OK;
 }
 
+reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, float *u_a, float *u_b,
+                   void *m, void *v, reg_dims d, int pad, float lambda, const reg_adam_desc *adam, int t0, int iters,
+                   void *ws, size_t ws_bytes, double *obj_hist, void *stream) {
+    if (iters < 0 || t0 < 0 || (long long)t0 + iters > INT_MAX) return REG_ERR_INVALID_ARG;
+    if (iters == 0) return REG_OK;
+    // validate once (the per-iteration calls repeat the same checks, which
+    // cost nothing next to a launch)
+    REG_TRY(check_common(loss, F, M, img_dt, u_a, d, pad, ws, ws_bytes));
+    REG_TRY(check_adam(adam, t0 + 1));
+    REG_TRY(check_ptr(u_b));
+    REG_TRY(check_ptr(obj_hist));
+    const bool armed = t_events_armed;
+    t_events_armed = false;  // the timing hook belongs to single reg_iterate calls
+    reg_status st = REG_OK;
+    for (int k = 0; k < iters && st == REG_OK; ++k) {
+        float *a = (k % 2) ? u_b : u_a, *b = (k % 2) ? u_a : u_b;
+        st = reg_iterate(loss, F, M, img_dt, a, b, m, v, d, pad, lambda, adam, t0 + k + 1, ws, ws_bytes,
+                         obj_hist + 2 * (size_t)k, nullptr, stream);
+    }
+    t_events_armed = armed;
+    return st;
+}
+
 reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream) {
     REG_TRY(check_dims(d));
     REG_TRY(check_ptr(u));
@@ -337,6 +361,16 @@ reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp,
     if (!(sigma > 0.0f) || !(sigma <= 7.9f)) return REG_ERR_INVALID_ARG;
     if (u == tmp || u == out || tmp == out) return REG_ERR_INVALID_ARG;
     return cuda_status(launch_smooth_field(u, make_dims(d), sigma, tmp, out, (cudaStream_t)stream));
+}
+
+reg_status reg_downsample2(const void *in, int dt, reg_dims d, void *out, void *stream) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_ptr(in));
+    REG_TRY(check_ptr(out));
+    if (dt != REG_F32 && dt != REG_BF16) return REG_ERR_DTYPE;
+    if (d.nx % 2 || d.ny % 2 || d.nz % 2) return REG_ERR_SHAPE;
+    if (in == out) return REG_ERR_INVALID_ARG;
+    return cuda_status(launch_downsample2(in, dt, make_dims(d), out, (cudaStream_t)stream));
 }
 
 reg_status reg_debug_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int a_mn_major,

@@ -72,6 +72,7 @@ struct SmoothWeights {
     float w[2 * SMOOTH_MAX_R + 1];
 };
 cudaError_t launch_smooth_field(const float *u, const Dims &g, float sigma, float *tmp, float *out, cudaStream_t s);
+cudaError_t launch_downsample2(const void *in, int dt, const Dims &gi, void *out, cudaStream_t s);
 
 struct MiParams {
     float f_lo, f_scale, m_lo, m_scale;  // vhat = clamp((v - lo) * scale, 0, 1)
@@ -87,7 +88,10 @@ struct LnccParams {
 
 // per-kernel grids (used both to launch and to size the workspace)
 MarchGrid mi_sweep_grid(const Dims &g);
-MarchGrid lncc_grid(const Dims &g, int r);
+// LNCC window-march grid for a kernel with per_sm CTAs resident per SM (the
+// default, 8 = 2048 threads / 256, bounds every kernel: workspace sizing)
+constexpr int LNCC_MAX_PER_SM = 8;
+MarchGrid lncc_grid(const Dims &g, int r, int per_sm = LNCC_MAX_PER_SM);
 MarchGrid lncc_ants_grid(const Dims &g);
 MarchGrid diffusion_grid(const Dims &g);
 

@@ -28,6 +28,8 @@
 //   fields (exact adjoint, not the ANTs shortcut), then dL/dJ, chained
 //   through the sampler slope to dL/du, optionally fused with the diffusion
 //   gradient and the Adam step.
+#include <mutex>
+
 #include "kernels.h"
 
 namespace regk {
@@ -537,9 +539,49 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     }
 }
 
-// longer z-chunks amortise the 2r warm-up planes of every chunk
-MarchGrid lncc_grid(const Dims &g, int r) {
-    return march_grid(g, 4LL * num_sms() * 3, 8 * r > 32 ? 8 * r : 32);
+// Every CTA marches zc + 2r planes (its chunk plus the window's warm-up), one
+// plane after the other.  A volume with enough tiles x long chunks (32 planes,
+// or 8r) to give every SM several CTAs keeps them: the warm-up costs at most
+// 2r / 32 of the traffic.  A smaller one would leave the GPU waiting on a few
+// long serial marches, so its z range is cut into as many chunks as one wave
+// of resident CTAs holds (chunk time shrinks with zc; a second wave would add
+// another 2r warm-up planes), down to 2 planes per chunk.
+MarchGrid lncc_grid(const Dims &g, int r, int per_sm) {
+    const long long target = 12LL * num_sms();
+    const int long_zc = 8 * r > 32 ? 8 * r : 32;
+    const long long tiles = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    const long long long_chunks = (g.nz + long_zc - 1) / long_zc;
+    if (tiles * long_chunks >= target) return march_grid(g, target, long_zc);
+    long long chunks = (long long)per_sm * num_sms() / tiles;
+    if (chunks < long_chunks) chunks = long_chunks;
+    return march_grid(g, chunks * tiles, 2);
+}
+
+// CTAs of `kernel` (TILE_THREADS threads, `smem` dynamic bytes) resident per
+// SM on the current device, cached per (kernel, smem, device)
+template <typename K>
+static int resident_per_sm(K kernel, size_t smem) {
+    struct Entry {
+        const void *fn;
+        size_t smem;
+        int dev, n;
+    };
+    static std::mutex mu;
+    static Entry cache[64];
+    static int used = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+        if (cache[i].fn == (const void *)kernel && cache[i].smem == smem && cache[i].dev == dev) return cache[i].n;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, TILE_THREADS, smem) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = 1;
+    }
+    if (n > LNCC_MAX_PER_SM) n = LNCC_MAX_PER_SM;
+    if (used < 64) cache[used++] = Entry{(const void *)kernel, smem, dev, n};
+    return n;
 }
 // the streaming (ANTs) sweep has no warm-up planes: the MI sweep's grid
 MarchGrid lncc_ants_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
@@ -558,10 +600,21 @@ static cudaError_t allow_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// opt `kernel` in to `smem` bytes and size its grid by its residency
+template <typename K>
+static cudaError_t prepare_march(K kernel, size_t smem, const Dims &g, int r, MarchGrid &G, dim3 &grid) {
+    const cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+    G = lncc_grid(g, r, resident_per_sm(kernel, smem));
+    grid = dim3(G.tiles_x, G.tiles_y, G.chunks);
+    return cudaSuccess;
+}
+
 cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims &g, const LnccParams &P, float *coef,
                               double *partials, unsigned *counter, double *sim_out, cudaStream_t s) {
-    const MarchGrid G = lncc_grid(g, P.r);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    MarchGrid G;
+    dim3 grid;
+    const dim3 block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 5);
     unsigned *err = error_word();
     cudaError_t e = cudaSuccess;
@@ -572,12 +625,12 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
             with_stage_rows(P.r, [&](auto ny) {
                 constexpr int NY = decltype(ny)::value;
                 if (coef) {
-                    e = allow_smem(lncc_stats_kernel<T, true, I, NY>, smem);
+                    e = prepare_march(lncc_stats_kernel<T, true, I, NY>, smem, g, P.r, G, grid);
                     if (e == cudaSuccess)
                         lncc_stats_kernel<T, true, I, NY><<<grid, block, smem, s>>>(
                             (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
                 } else {
-                    e = allow_smem(lncc_stats_kernel<T, false, I, NY>, smem);
+                    e = prepare_march(lncc_stats_kernel<T, false, I, NY>, smem, g, P.r, G, grid);
                     if (e == cudaSuccess)
                         lncc_stats_kernel<T, false, I, NY><<<grid, block, smem, s>>>(
                             (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
@@ -627,8 +680,9 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
     if (P.ants)
         return launch_lncc_sweep2_ants(F, M, dt, u, g, pad, P, coef, grad_out, step, u_out, m, v, mdt, S, partials,
                                        counter, r_out, s);
-    const MarchGrid G = lncc_grid(g, P.r);
-    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    MarchGrid G;
+    dim3 grid;
+    const dim3 block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 3);
     unsigned *err = error_word();
     cudaError_t e = cudaSuccess;
@@ -639,7 +693,7 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
                 if (!step) {
-                    e = allow_smem(lncc_sweep2_kernel<T, float, false, PD, I>, smem);
+                    e = prepare_march(lncc_sweep2_kernel<T, float, false, PD, I>, smem, g, P.r, G, grid);
                     if (e == cudaSuccess)
                         lncc_sweep2_kernel<T, float, false, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (float *)m,
@@ -648,7 +702,7 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                 }
                 with_type(mdt, [&](auto mp) {
                     using MT = elem_t<decltype(mp)>;
-                    e = allow_smem(lncc_sweep2_kernel<T, MT, true, PD, I>, smem);
+                    e = prepare_march(lncc_sweep2_kernel<T, MT, true, PD, I>, smem, g, P.r, G, grid);
                     if (e == cudaSuccess)
                         lncc_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m,

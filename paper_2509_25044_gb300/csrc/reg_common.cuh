@@ -42,6 +42,9 @@ __device__ __forceinline__ float ld_vox(const __nv_bfloat16 *p, I i) {
     return __bfloat162float(__ldg(p + i));
 }
 
+__device__ __forceinline__ void store_vox(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_vox(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
 // ---------------------------------------------------------------------------
 // Trilinear sampling of M at phi = p + u (voxel units), value and slope.
 // The cell index is taken from p + floor(u) and the fraction from

@@ -62,4 +62,35 @@ cudaError_t launch_smooth_field(const float *u, const Dims &g, float sigma, floa
     return cudaGetLastError();
 }
 
+// 2x2x2 block mean of an even-sized image (the coarse levels of the
+// multi-scale schedule), FP32 or BF16 in and out (the sum is FP32)
+template <typename T>
+__global__ void downsample2_kernel(const T *__restrict__ in, Dims gi, Dims go, T *__restrict__ out) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < go.n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long x = v % go.nx, y = (v / go.nx) % go.ny, z = v / go.nxy;
+        const T *b = in + (2 * z) * gi.nxy + (2 * y) * gi.nx + 2 * x;
+        float acc = 0.0f;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const T *r = b + dz * gi.nxy + dy * gi.nx;
+                acc += ld_vox(r, 0) + ld_vox(r, 1);
+            }
+        store_vox(out + v, 0.125f * acc);
+    }
+}
+
+cudaError_t launch_downsample2(const void *in, int dt, const Dims &gi, void *out, cudaStream_t s) {
+    const Dims go = make_dims(reg_dims{gi.nx / 2, gi.ny / 2, gi.nz / 2});
+    long long blocks = (go.n + 255) / 256;
+    if (blocks > 32LL * num_sms()) blocks = 32LL * num_sms();
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        downsample2_kernel<T><<<(unsigned)blocks, 256, 0, s>>>((const T *)in, gi, go, (T *)out);
+    });
+    return cudaGetLastError();
+}
+
 }  // namespace regk

@@ -179,6 +179,54 @@ def regularisers(config: str = "c0", iters: int = 50, n: int | None = None) -> d
     return {"experiment": "regularisers", "config": config, "iters": iters, "rows": rows}
 
 
+def multiscale_vs_single(n_pairs: int = 8, n: int = 128, seed0: int = 90_000, window: int = 7, lam: float = 2.0,
+                         lr: float = 0.1, iters: int = 200, scales=(4, 2, 1), ms_iters=(100, 100, 200),
+                         rel_tol: float = 0.01) -> dict:
+    """Held-out pairs of the training distribution (fields up to 10 voxels)
+    registered single-scale from zero and coarse-to-fine: time for the
+    multi-scale schedule (coarse levels included) to bring the full-resolution
+    objective to the single-scale run's target, final objectives, folds and
+    error to the known field."""
+    from .register import register_multiscale
+    from .unet import training_pair
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    cfg = RegConfig(loss="lncc", window=window, eps=LNCC_EPS, lam=lam, lr=lr)
+    rows = []
+    for i in range(n_pairs):
+        p = training_pair(n, seed0 + i, dev)
+        F, M, v = p["F"].contiguous(), p["M"].contiguous(), p["v"]
+        r0 = Registration(F, M, cfg)
+        res0 = r0.run(iters)
+        fin0 = r0.objective()
+        L0, Lstar = float(res0.objective[0]), fin0["objective"]
+        tol = rel_tol * max(L0 - Lstar, 0.0)
+        k0 = _first_within(np.append(res0.objective[1:], Lstar), Lstar, tol)
+        out = register_multiscale(F, M, cfg, scales, ms_iters)
+        last = out["levels"][-1]["result"]
+        coarse_ms = out["ms"] - last.ms_per_iter * ms_iters[-1]
+        rfin = Registration(F, M, cfg, u0=out["u"])
+        fin1 = rfin.objective()
+        k1 = _first_within(np.append(last.objective[1:], fin1["objective"]), Lstar, tol)
+        err = lambda u: float(((u - v).norm() / v.norm()).item())
+        row = {"seed": seed0 + i, "max_disp": float(v.norm(dim=0).max().item()),
+               "single": {"iters_to_target": None if k0 is None else k0 + 1, "L_final": Lstar,
+                          "ms_per_iter": res0.ms_per_iter, "fold": r0.fold_check()["n_fold"], "rel_err": err(r0.current)},
+               "multi": {"coarse_ms": coarse_ms, "full_iters_to_target": None if k1 is None else k1 + 1,
+                         "L_final": fin1["objective"], "ms_total": out["ms"], "fold": rfin.fold_check()["n_fold"],
+                         "rel_err": err(out["u"])}}
+        if k0 is not None and k1 is not None:
+            t0 = (k0 + 1) * res0.ms_per_iter
+            t1 = coarse_ms + (k1 + 1) * last.ms_per_iter
+            row["time_to_target_ms"] = {"single": t0, "multi": t1}
+            row["speedup"] = t0 / t1
+        rows.append(row)
+    sp = [r["speedup"] for r in rows if "speedup" in r]
+    return {"experiment": "multiscale_vs_single", "n": n, "pairs": n_pairs, "scales": list(scales),
+            "iters": list(ms_iters), "single_iters": iters, "lam": lam, "median_speedup": float(np.median(sp)) if sp else None,
+            "reached": len(sp), "rows": rows}
+
+
 def eval_init_pairs(net, n_pairs: int = 8, n: int = 128, seed0: int = 90_000, iters: int = 200, window: int = 7,
                     lam: float = 1.0, lr: float = 0.1, rel_tol: float = 0.01) -> dict:
     """Held-out pairs of the training distribution (seeds never used in
@@ -238,6 +286,10 @@ def main():
     t.add_argument("--eval-every", type=int, default=1)
     t.add_argument("--lam-scale", type=float, default=1.0)
     t.add_argument("--adam-eps", type=float, default=1e-8)
+    msp = sub.add_parser("multiscale")
+    msp.add_argument("--pairs", type=int, default=8)
+    msp.add_argument("--lam", type=float, default=2.0)
+    msp.add_argument("--ms-iters", default="100,100,200", help="iterations per level, coarse to fine")
     rg = sub.add_parser("regularisers")
     rg.add_argument("--config", default="c0")
     rg.add_argument("--iters", type=int, default=50)
@@ -265,6 +317,10 @@ def main():
         if args.eval_config != "none":
             print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=args.eval_lam / 0.1)),
                   flush=True)
+        return
+    if args.cmd == "multiscale":
+        its = tuple(int(x) for x in args.ms_iters.split(","))
+        print(json.dumps(multiscale_vs_single(args.pairs, lam=args.lam, ms_iters=its)))
         return
     if args.cmd == "regularisers":
         print(json.dumps(regularisers(args.config, args.iters, args.n)))

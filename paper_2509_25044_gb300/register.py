@@ -92,13 +92,15 @@ class Registration:
         hist = torch.zeros((iters, 2), dtype=torch.float64, device=self.F.device)
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record()
-        for k in range(iters):
+        if not self.smoothing and iters > 0:
+            # one native call runs all iterations (no host work between them)
+            a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
+            capi.reg_run(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t, iters,
+                         self.ws, pad=self.cfg.pad, obj_hist=hist)
+            self.t += iters
+        for k in range(iters if self.smoothing else 0):
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
             self.t += 1
-            if not self.smoothing:
-                capi.reg_iterate(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t,
-                                 self.ws, pad=self.cfg.pad, obj=hist[k])
-                continue
             # smoothing regularisation: gradient -> smooth(sigma_grad) -> Adam -> smooth(sigma_warp)
             capi.reg_loss_grad(self.loss, self.F, self.M, a, self.ws, pad=self.cfg.pad, sim=self.sim1, grad=self.g)
             capi.reg_regularize(a, self.cfg.lam, self.ws, r=self.r1, grad=self.g)
@@ -146,3 +148,46 @@ def register(F, M, cfg: RegConfig, iters: int, u0=None) -> RegResult:
     res.extra.update(reg.fold_check())
     res.extra["wall_s"] = time.perf_counter() - t0
     return res
+
+
+def register_multiscale(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 100, 100), u0=None) -> dict:
+    """Coarse-to-fine registration (the multi-scale schedules the paper runs
+    with): the level of scale s registers the images averaged down by s (2x
+    block means, reg_downsample2, repeated), starting from the previous
+    level's field upsampled trilinearly with its displacements scaled
+    (reg_nn_field_upsample); Adam restarts at every level.  Scales must be
+    decreasing powers of two ending at 1 and divide the image size.  Returns
+    the full-resolution field, every level's RegResult and the device time of
+    the whole schedule (pyramid and upsampling included)."""
+    if list(scales)[-1] != 1 or any(a <= b for a, b in zip(scales, scales[1:])):
+        raise ValueError("scales must decrease to 1")
+    if len(iters) != len(scales):
+        raise ValueError("one iteration count per scale")
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    pyr = {1: (F.contiguous(), M.contiguous())}
+    s = 1
+    while s < scales[0]:
+        f, m = pyr[s]
+        pyr[2 * s] = (capi.reg_downsample2(f), capi.reg_downsample2(m))
+        s *= 2
+    L = capi.nn()
+    u, prev, levels = u0, None, []
+    for s, it in zip(scales, iters):
+        f, m = pyr[s]
+        init = None
+        if u is not None and prev is not None:
+            factor = prev // s
+            cz, cy, cx = u.shape[1:]
+            init = torch.empty((3,) + tuple(f.shape), dtype=torch.float32, device=f.device)
+            capi.nn_check(L.reg_nn_field_upsample(capi.ptr(u), capi.RegDims(cx, cy, cz), factor, capi.ptr(init),
+                                                  capi.stream_of(init)), "field_upsample")
+        elif u is not None:
+            init = u
+        r = Registration(f, m, cfg, u0=init)
+        res = r.run(it)
+        levels.append({"scale": s, "result": res, "shape": tuple(f.shape)})
+        u, prev = r.current.clone(), s
+    end.record()
+    torch.cuda.synchronize()
+    return {"u": u, "levels": levels, "ms": start.elapsed_time(end)}

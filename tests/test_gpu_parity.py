@@ -366,3 +366,60 @@ def test_smoothing_regularised_registration(capi):
         folds[sg] = r.fold_check()["n_fold"]
     assert folds[1.0] * 10 <= max(folds[0.0], 1), folds
     assert capi.reg_get_device_error() == 0
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 10), (34, 18, 66), (2, 2, 2)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_downsample2_matches_oracle(capi, shape, dtype):
+    img = torch.rand(shape, generator=torch.Generator().manual_seed(7)) * 3.0 - 1.0
+    out = capi.reg_downsample2(_img(img, dtype))
+    torch.cuda.synchronize()
+    assert out.dtype == dtype and tuple(out.shape) == tuple(s // 2 for s in shape)
+    ref = O.downsample2(_oracle_img(img, dtype))
+    got = to64(out.float().cpu())
+    if dtype == torch.float32:  # an FP32 sum of 8 terms
+        np.testing.assert_allclose(got, ref, rtol=0, atol=4e-7 * np.abs(ref).max())
+    else:  # the FP32 mean rounded once to BF16 (8 significant bits)
+        np.testing.assert_allclose(got, ref, rtol=2.0 ** -8, atol=1e-6)
+
+
+def test_downsample2_rejects_odd_and_aliasing(capi):
+    img = torch.zeros((8, 8, 9), device=DEV)
+    with pytest.raises(RuntimeError):
+        capi.reg_downsample2(img)
+    a = torch.zeros((8, 8, 8), device=DEV)
+    st = capi._lib().reg_downsample2(capi._ptr(a), 0, capi.dims_of(a), capi._ptr(a), capi._stream(a))
+    assert st != 0
+
+
+@pytest.mark.parametrize("kind", ["lncc", "mi"])
+@pytest.mark.parametrize("iters", [1, 4, 5])
+def test_run_matches_repeated_iterate(capi, kind, iters):
+    """reg_run (all iterations in one native call) gives the iterates and
+    objective history of as many reg_iterate calls, bit for bit, and leaves
+    the last iterate in u_a / u_b by the parity of the count."""
+    shape = (12, 10, 20)
+    gen = torch.Generator().manual_seed(11)
+    F = torch.rand(shape, generator=gen).to(DEV)
+    M = torch.rand(shape, generator=gen).to(DEV)
+    loss = capi.lncc_desc(5, 1e-9) if kind == "lncc" else capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32)
+    adam = capi.adam_desc(0.05)
+    ws = capi.workspace(loss, F)
+    outs = []
+    for native in (False, True):
+        u = [torch.zeros((3,) + shape, device=DEV) for _ in range(2)]
+        u[0].copy_(0.3 * torch.randn((3,) + shape, generator=torch.Generator().manual_seed(3)))
+        m = torch.zeros((3,) + shape, device=DEV)
+        v = torch.zeros((3,) + shape, device=DEV)
+        hist = torch.zeros((iters, 2), dtype=torch.float64, device=DEV)
+        t0 = 2  # continue a run: the step numbers are t0 + 1 ..
+        if native:
+            capi.reg_run(loss, F, M, u[0], u[1], m, v, 0.5, adam, t0, iters, ws, obj_hist=hist)
+        else:
+            for k in range(iters):
+                capi.reg_iterate(loss, F, M, u[k % 2], u[(k + 1) % 2], m, v, 0.5, adam, t0 + k + 1, ws, obj=hist[k])
+        torch.cuda.synchronize()
+        outs.append((u[iters % 2].cpu(), m.cpu(), v.cpu(), hist.cpu()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    assert capi.reg_get_device_error() == 0

@@ -33,3 +33,27 @@ def test_c1_mi_small_converges():
     assert res.objective[-1] < res.objective[0]  # MI increases: -MI + lam R decreases
     assert res.sim[-1] > res.sim[0]
     assert reg.fold_check()["n_fold"] == 0
+
+
+def test_multiscale_schedule():
+    """Coarse-to-fine (scales 4, 2, 1): every level decreases its objective,
+    the returned field is full size, and its full-resolution objective is
+    below the objective at zero displacement."""
+    from paper_2509_25044_gb300.register import register_multiscale
+    d = synth.make("c0", device=DEV)
+    cfg = RegConfig(loss="lncc", window=7, eps=1e-9, lam=2.0, lr=0.1)
+    out = register_multiscale(d["F"], d["M"], cfg, scales=(4, 2, 1), iters=(30, 30, 30))
+    assert [lv["scale"] for lv in out["levels"]] == [4, 2, 1]
+    n = tuple(d["F"].shape)
+    assert [lv["shape"] for lv in out["levels"]] == [tuple(s // 4 for s in n), tuple(s // 2 for s in n), n]
+    for lv in out["levels"]:
+        obj = lv["result"].objective
+        assert np.all(np.isfinite(obj)) and obj[-1] < obj[0]
+    assert tuple(out["u"].shape) == (3,) + n
+    r = Registration(d["F"], d["M"], cfg)
+    zero = r.objective()["objective"]
+    fin = Registration(d["F"], d["M"], cfg, u0=out["u"]).objective()["objective"]
+    assert fin < zero
+    assert out["ms"] > 0
+    with pytest.raises(ValueError):
+        register_multiscale(d["F"], d["M"], cfg, scales=(2, 4, 1), iters=(1, 1, 1))
