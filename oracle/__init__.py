@@ -317,6 +317,67 @@ def conv3d_wgrad(x, dout):
 
 
 # --------------------------------------------------------------------------
+# composite affine + deformable transform (Sec. 2.1, the composite implicit
+# grid sampler; Algorithm gridsampler): phi(p) = A p + t + S u(p), A a 3x3
+# matrix acting on the voxel coordinates p = (x, y, z), t a translation in
+# voxels, S = diag(s) the scale of the displacement.  The oracle writes phi as
+# p + u_eff(p) and reuses the pinned deformable functions; the affine
+# gradients follow by the chain rule.
+# --------------------------------------------------------------------------
+def identity_grid(shape):
+    """[3, nz, ny, nx] FP64 voxel coordinates, channels (x, y, z)."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return np.stack([x, y, z])
+
+
+def composite_offset(shape, A, t, s=(1.0, 1.0, 1.0), u=None):
+    """u_eff(p) = A p + t + S u(p) - p, so that phi(p) = p + u_eff(p)."""
+    A = np.asarray(A, dtype=np.float64).reshape(3, 3)
+    t = np.asarray(t, dtype=np.float64).reshape(3)
+    s = np.asarray(s, dtype=np.float64).reshape(3)
+    X = identity_grid(shape)
+    phi = np.einsum("ij,jzyx->izyx", A, X) + t[:, None, None, None]
+    if u is not None:
+        phi = phi + s[:, None, None, None] * _f64(u)
+    return phi - X
+
+
+def warp_composite(M, A, t, s=(1.0, 1.0, 1.0), u=None, pad: int = PAD_BORDER, with_grad: bool = False):
+    """J(p) = M(A p + t + S u(p)) (Algorithm gridsampler, forward); with_grad
+    adds dJ/dphi [3, nz, ny, nx]."""
+    M = _f64(M)
+    return warp(M, composite_offset(M.shape, A, t, s, u), pad, with_grad)
+
+
+def _affine_grads(gX, s):
+    """g_u = S gX, g_A = sum_p gX(p) p^T, g_t = sum_p gX(p) for the gradient gX
+    with respect to the sampling location."""
+    X = identity_grid(gX.shape[1:])
+    s = np.asarray(s, dtype=np.float64).reshape(3)
+    g_A = np.einsum("izyx,jzyx->ij", gX, X)
+    g_t = gX.reshape(3, -1).sum(axis=1)
+    return s[:, None, None, None] * gX, g_A, g_t
+
+
+def sampler_backward_composite(M, A, t, s, u, g, pad: int = PAD_BORDER):
+    """Algorithm gridsampler, backward, without the image gradient: for an
+    upstream gradient g = dL/dJ returns (g_u, g_A, g_t)."""
+    _, dJ = warp_composite(M, A, t, s, u, pad, with_grad=True)
+    return _affine_grads(dJ * _f64(g)[None], s)
+
+
+def similarity_and_grad_composite(F, M, A, t, s=(1.0, 1.0, 1.0), u=None, spec=None, pad: int = PAD_BORDER):
+    """(similarity, dC/du, dC/dA, dC/dt) of C(F, M o phi) for the composite
+    phi; C = 1 - S (LNCC) or -MI."""
+    F = _f64(F)
+    sim, gX = similarity_and_grad(F, M, composite_offset(F.shape, A, t, s, u), spec, pad)
+    g_u, g_A, g_t = _affine_grads(gX, s)
+    return sim, g_u, g_A, g_t
+
+
+# --------------------------------------------------------------------------
 # one iteration, composed by the chain rule
 # --------------------------------------------------------------------------
 @dataclass

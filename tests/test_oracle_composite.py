@@ -1,0 +1,144 @@
+"""Pins for the oracle's composite affine + deformable transform
+phi(p) = A p + t + S u(p) (Sec. 2.1, the composite implicit grid sampler;
+Algorithm gridsampler, forward and backward).  CPU only.
+
+The forward is pinned to exact resamplings a reader can check by eye (integer
+shifts, a 90-degree rotation, a 2x decimation, a half-voxel shift); the
+backward and the loss gradients with respect to A, t and u are pinned to
+central differences of the forward."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+I3 = np.eye(3)
+
+
+def _smooth(rng, shape):
+    v = rng.standard_normal(shape)
+    return O.gaussian_smooth(v, 1.0)
+
+
+def test_identity_transform_is_plain_warp(rng):
+    M = rng.standard_normal((5, 6, 7))
+    u = 0.7 * rng.standard_normal((3,) + M.shape)
+    assert np.array_equal(O.warp_composite(M, I3, (0, 0, 0), (1, 1, 1), u), O.warp(M, u))
+    assert np.array_equal(O.warp_composite(M, I3, (0, 0, 0)), M)
+
+
+@pytest.mark.parametrize("pad", [O.PAD_BORDER, O.PAD_ZEROS])
+def test_integer_translation(rng, pad):
+    M = rng.standard_normal((6, 7, 9))
+    nz, ny, nx = M.shape
+    t = (3, -2, 1)
+    J = O.warp_composite(M, I3, t, pad=pad)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    sx, sy, sz = x + t[0], y + t[1], z + t[2]
+    val = M[np.clip(sz, 0, nz - 1), np.clip(sy, 0, ny - 1), np.clip(sx, 0, nx - 1)]
+    if pad == O.PAD_ZEROS:
+        ok = (sx >= 0) & (sx < nx) & (sy >= 0) & (sy < ny) & (sz >= 0) & (sz < nz)
+        val = np.where(ok, val, 0.0)
+    assert np.array_equal(J, val)
+
+
+def test_quarter_turn_is_a_transpose_and_flip(rng):
+    """A maps (x, y, z) to (n-1-y, x, z): J[z, y, x] = M[z, x, n-1-y].  A is
+    not symmetric, so using A^T (or reading A column-major) fails."""
+    n = 6
+    M = rng.standard_normal((4, n, n))
+    A = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    J = O.warp_composite(M, A, (n - 1, 0, 0))
+    ref = np.swapaxes(M[:, :, ::-1], 1, 2)
+    np.testing.assert_allclose(J, ref, rtol=0, atol=1e-14)
+
+
+def test_scale_two_is_decimation(rng):
+    M = rng.standard_normal((8, 10, 12))
+    J = O.warp_composite(M, 2.0 * I3, (0, 0, 0))
+    np.testing.assert_allclose(J[:4, :5, :6], M[::2, ::2, ::2], rtol=0, atol=1e-14)
+
+
+def test_half_voxel_shift_is_neighbour_mean(rng):
+    M = rng.standard_normal((3, 4, 8))
+    J = O.warp_composite(M, I3, (0.5, 0, 0))
+    np.testing.assert_allclose(J[:, :, :-1], 0.5 * (M[:, :, :-1] + M[:, :, 1:]), rtol=0, atol=1e-14)
+
+
+def test_displacement_scale_acts_per_channel(rng):
+    M = rng.standard_normal((5, 6, 7))
+    u = 0.8 * rng.standard_normal((3,) + M.shape)
+    s = (2.0, 0.5, 1.5)
+    ref = O.warp(M, np.asarray(s)[:, None, None, None] * u)
+    np.testing.assert_allclose(O.warp_composite(M, I3, (0, 0, 0), s, u), ref, rtol=0, atol=1e-14)
+
+
+def _rand_affine(rng):
+    A = I3 + 0.05 * rng.standard_normal((3, 3))
+    t = 0.6 * rng.standard_normal(3)
+    return A, t
+
+
+def test_sampler_backward_matches_differences(rng):
+    """g_A[i][j] = d/dA_ij of sum_p g(p) J(p), likewise g_t and g_u, by
+    central differences (Algorithm gridsampler, backward)."""
+    shape = (5, 6, 7)
+    M = _smooth(rng, shape)
+    u = 0.4 * rng.standard_normal((3,) + shape)
+    g = rng.standard_normal(shape)
+    A, t = _rand_affine(rng)
+    s = (1.3, 0.8, 1.1)
+    g_u, g_A, g_t = O.sampler_backward_composite(M, A, t, s, u, g)
+    L = lambda A_, t_, u_: float(np.sum(g * O.warp_composite(M, A_, t_, s, u_)))
+    h = 1e-6
+    for i in range(3):
+        for j in range(3):
+            E = np.zeros((3, 3))
+            E[i, j] = h
+            fd = (L(A + E, t, u) - L(A - E, t, u)) / (2 * h)
+            assert abs(fd - g_A[i, j]) < 1e-6 * max(1.0, abs(fd)), (i, j, fd, g_A[i, j])
+        e = np.zeros(3)
+        e[i] = h
+        fd = (L(A, t + e, u) - L(A, t - e, u)) / (2 * h)
+        assert abs(fd - g_t[i]) < 1e-6 * max(1.0, abs(fd))
+    for c, z, y, x in [(0, 2, 3, 4), (1, 0, 5, 1), (2, 4, 0, 6)]:
+        du = np.zeros_like(u)
+        du[c, z, y, x] = h
+        fd = (L(A, t, u + du) - L(A, t, u - du)) / (2 * h)
+        assert abs(fd - g_u[c, z, y, x]) < 1e-7 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("kind", ["lncc", "lncc_ants", "mi"])
+def test_loss_gradients_match_differences(rng, kind):
+    shape = (7, 6, 8)
+    F = _smooth(rng, shape)
+    F = (F - F.min()) / (F.max() - F.min())
+    A0 = I3 + np.array([[0.02, -0.03, 0.0], [0.03, 0.01, 0.0], [0.0, 0.0, -0.02]])
+    M = O.warp_composite(F, A0, (0.3, -0.2, 0.1))
+    u = 0.2 * rng.standard_normal((3,) + shape)
+    A, t = _rand_affine(rng)
+    s = (1.0, 1.0, 1.0)
+    if kind == "mi":
+        spec = O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=(0.0, 1.0), m_range=(0.0, 1.0))
+    else:
+        spec = O.LossSpec(kind=O.LOSS_LNCC, window=3, eps=1e-9, lncc_grad=1 if kind == "lncc_ants" else 0)
+    sim, g_u, g_A, g_t = O.similarity_and_grad_composite(F, M, A, t, s, u, spec)
+    sim_plain, g_plain = O.similarity_and_grad(F, M, O.composite_offset(shape, A, t, s, u), spec)
+    assert sim == sim_plain and np.array_equal(g_u, g_plain)
+    if kind == "lncc_ants":
+        return  # the approximation is not the derivative of the loss
+    sign = -1.0
+
+    def C(A_, t_):
+        return sign * O.similarity_and_grad_composite(F, M, A_, t_, s, u, spec)[0]
+
+    h = 1e-6
+    for i in range(3):
+        for j in range(3):
+            E = np.zeros((3, 3))
+            E[i, j] = h
+            fd = (C(A + E, t) - C(A - E, t)) / (2 * h)
+            assert abs(fd - g_A[i, j]) < 2e-5 * max(1e-3, np.abs(g_A).max()), (i, j, fd, g_A[i, j])
+        e = np.zeros(3)
+        e[i] = h
+        fd = (C(A, t + e) - C(A, t - e)) / (2 * h)
+        assert abs(fd - g_t[i]) < 2e-5 * max(1e-3, np.abs(g_t).max())
