@@ -192,6 +192,50 @@ REG_API reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const v
                        const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
                        float *grad_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Composite transform (Sec. 2.1, the composite implicit grid sampler;
+ * Algorithm gridsampler):
+ *     phi(p) = A p + t + S u(p),   p = (x, y, z) voxel coordinates,
+ * A row-major (A[3*i + j] takes coordinate j into output axis i), t in
+ * voxels, S = diag(s).  A = I, t = 0, s = 1 is the deformable sampler of
+ * reg_warp; a map about the volume centre c is A with t = c - A c.  No
+ * coordinate grid is materialised: the kernels form phi per voxel.  Every
+ * entry of A, t and s must be finite (else REG_ERR_INVALID_ARG); u may be
+ * NULL (u = 0, the affine part alone).
+ * ------------------------------------------------------------------------ */
+typedef struct reg_affine {
+    float A[9];
+    float t[3];
+    float s[3];
+} reg_affine;
+
+/* J = M o phi (FP32 [N]) and optionally dJ/dphi (FP32 [3][N], NULL skips it;
+ * Algorithm gridsampler, forward). */
+REG_API reg_status reg_warp_composite(const void *M, int img_dt, const float *u, reg_dims d, const reg_affine *T,
+                                      int pad, float *J, float *dJ, void *stream);
+
+/* Backward of the composite sampler (Algorithm gridsampler, backward; the
+ * gradient with respect to the moving image is not formed): for the upstream
+ * gradient g = dL/dJ (FP32 [N]),
+ *   g_u = S (dJ/dphi) g            (FP32 [3][N], overwritten; NULL skips it),
+ *   grad_affine[0..8]  = dL/dA = sum_p (dJ/dphi g)(p) p^T   (row-major),
+ *   grad_affine[9..11] = dL/dt = sum_p (dJ/dphi g)(p)
+ * (device double[12], NULL skips it), summed in a fixed order.
+ * ws: at least reg_workspace_size(NULL, d) bytes. */
+REG_API reg_status reg_warp_composite_backward(const void *M, int img_dt, const float *u, reg_dims d,
+                                               const reg_affine *T, int pad, const float *g, float *g_u,
+                                               double *grad_affine, void *ws, size_t ws_bytes, void *stream);
+
+/* Similarity of C(F, M o phi) for the composite phi (sim_out as reg_loss)
+ * and its gradients: grad_u = dC/du = S dC/dphi (FP32 [3][N], overwritten;
+ * NULL skips it) and grad_affine = dC/dA (row-major) then dC/dt (device
+ * double[12]; NULL skips it), with C = 1 - S (LNCC) or -MI.  Both NULL
+ * computes the similarity alone.  Workspace as reg_loss. */
+REG_API reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                           const float *u, reg_dims d, const reg_affine *T, int pad, void *ws,
+                                           size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
+                                           void *stream);
+
 /* `iters` fused iterations (as reg_iterate) in one call, numbered t0 + 1 ..
  * t0 + iters, without returning to the caller between them: iteration k
  * (0-based) reads u[k % 2] and writes u[(k + 1) % 2] with u = {u_a, u_b}, so

@@ -29,7 +29,8 @@ STATUS = {0: "REG_OK", 1: "REG_ERR_INVALID_ARG", 2: "REG_ERR_SHAPE", 3: "REG_ERR
 EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp", "reg_loss", "reg_loss_grad",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
-           "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run")
+           "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run", "reg_warp_composite",
+           "reg_warp_composite_backward", "reg_loss_grad_composite")
 
 
 class RegError(RuntimeError):
@@ -51,6 +52,25 @@ class RegLossDesc(ctypes.Structure):
 class RegAdamDesc(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("moment_dtype", ctypes.c_int), ("grad_scale", ctypes.c_float)]
+
+
+class RegAffine(ctypes.Structure):
+    """phi(p) = A p + t + diag(s) u(p); A row-major over (x, y, z)."""
+    _fields_ = [("A", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("s", ctypes.c_float * 3)]
+
+
+def affine_desc(A=None, t=(0.0, 0.0, 0.0), s=(1.0, 1.0, 1.0)) -> RegAffine:
+    """Descriptor of the composite transform from a 3x3 A (row-major nested
+    sequence, array or tensor; default identity), t and s."""
+    import numpy as _np
+    A = _np.eye(3) if A is None else _np.asarray(A.tolist() if hasattr(A, "tolist") else A, dtype=_np.float64)
+    T = RegAffine()
+    for i, v in enumerate(A.reshape(9)):
+        T.A[i] = float(v)
+    for i in range(3):
+        T.t[i] = float(t[i])
+        T.s[i] = float(s[i])
+    return T
 
 
 _L = None
@@ -89,6 +109,12 @@ def _lib():
                                                ctypes.c_int, _vp, _vp, _vp]
         L.reg_smooth_field.argtypes = [_vp, RegDims, ctypes.c_float, _vp, _vp, _vp]
         L.reg_downsample2.argtypes = [_vp, ctypes.c_int, RegDims, _vp, _vp]
+        _aff = ctypes.POINTER(RegAffine)
+        L.reg_warp_composite.argtypes = [_vp, ctypes.c_int, _vp, RegDims, _aff, ctypes.c_int, _vp, _vp, _vp]
+        L.reg_warp_composite_backward.argtypes = [_vp, ctypes.c_int, _vp, RegDims, _aff, ctypes.c_int, _vp, _vp, _vp,
+                                                  _vp, ctypes.c_size_t, _vp]
+        L.reg_loss_grad_composite.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
+                                              _aff, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]
         L.reg_run.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
                               ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, ctypes.c_int,
                               _vp, ctypes.c_size_t, _vp, _vp]
@@ -199,6 +225,56 @@ def reg_warp(M, u, pad: int = REG_PAD_BORDER, J=None, dJ=None, with_slope: bool 
         dJ = torch.empty_like(u)
     _check(_lib().reg_warp(_ptr(M), _img_dtype(M), _ptr(u), d, int(pad), _ptr(J), _ptr(dJ), _stream(M)), "reg_warp")
     return (J, dJ) if dJ is not None else J
+
+
+def reg_warp_composite(M, T: RegAffine, u=None, pad: int = REG_PAD_BORDER, with_slope: bool = False):
+    """J = M o (A p + t + S u) (u may be None) and optionally dJ/dphi."""
+    d = dims_of(M)
+    if u is not None:
+        _need(u, (3,) + tuple(M.shape), torch.float32, "u")
+    J = torch.empty(M.shape, dtype=torch.float32, device=M.device)
+    dJ = torch.empty((3,) + tuple(M.shape), dtype=torch.float32, device=M.device) if with_slope else None
+    _check(_lib().reg_warp_composite(_ptr(M), _img_dtype(M), _ptr(u), d, ctypes.byref(T), int(pad), _ptr(J), _ptr(dJ),
+                                     _stream(M)), "reg_warp_composite")
+    return (J, dJ) if with_slope else J
+
+
+def reg_warp_composite_backward(M, T: RegAffine, g, u=None, pad: int = REG_PAD_BORDER, ws=None, need_u: bool = True):
+    """(g_u or None, grad_affine double[12]) for the upstream gradient g = dL/dJ."""
+    d = dims_of(M)
+    _need(g, M.shape, torch.float32, "g")
+    if u is not None:
+        _need(u, (3,) + tuple(M.shape), torch.float32, "u")
+    if ws is None:
+        ws = workspace(None, M)
+    g_u = torch.empty((3,) + tuple(M.shape), dtype=torch.float32, device=M.device) if need_u else None
+    ga = torch.empty(12, dtype=torch.float64, device=M.device)
+    _check(_lib().reg_warp_composite_backward(_ptr(M), _img_dtype(M), _ptr(u), d, ctypes.byref(T), int(pad), _ptr(g),
+                                              _ptr(g_u), _ptr(ga), _ptr(ws), ws.numel(), _stream(M)),
+           "reg_warp_composite_backward")
+    return g_u, ga
+
+
+def reg_loss_grad_composite(loss: RegLossDesc, F, M, T: RegAffine, u=None, ws=None, pad: int = REG_PAD_BORDER,
+                            need_u: bool = True, need_affine: bool = True, sim=None, grad_u=None, grad_affine=None):
+    """(sim double[1], dC/du or None, dC/dA|dC/dt double[12] or None) for the composite transform."""
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    if u is not None:
+        _need(u, (3,) + tuple(F.shape), torch.float32, "u")
+    if ws is None:
+        ws = workspace(loss, F)
+    if sim is None:
+        sim = torch.empty(2, dtype=torch.float64, device=F.device)
+    if need_u and grad_u is None:
+        grad_u = torch.empty((3,) + tuple(F.shape), dtype=torch.float32, device=F.device)
+    if need_affine and grad_affine is None:
+        grad_affine = torch.empty(12, dtype=torch.float64, device=F.device)
+    _check(_lib().reg_loss_grad_composite(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d,
+                                          ctypes.byref(T), int(pad), _ptr(ws), ws.numel(), _ptr(sim),
+                                          _ptr(grad_u if need_u else None), _ptr(grad_affine if need_affine else None),
+                                          _stream(F)), "reg_loss_grad_composite")
+    return sim, (grad_u if need_u else None), (grad_affine if need_affine else None)
 
 
 def reg_loss(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None):

@@ -20,7 +20,8 @@ constexpr size_t WS_COUNTERS = WS_HIST + sizeof(unsigned long long) * MAX_BINS *
 constexpr size_t WS_ZERO_BYTES = WS_COUNTERS + 256;                  // zeroed by every call
 constexpr size_t WS_GTAB = WS_ZERO_BYTES;                            // f32[64*64]
 constexpr size_t WS_SCRATCH = WS_GTAB + sizeof(float) * MAX_BINS * MAX_BINS;  // f64[32]
-constexpr size_t WS_PARTIALS = WS_SCRATCH + 256;                     // f64[max blocks]
+constexpr size_t WS_PARTIALS = WS_SCRATCH + 256;                     // f64[12 * max blocks]
+constexpr size_t PARTIALS_PER_BLOCK = 12;  // the composite sweeps reduce dC/dA, dC/dt
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -76,7 +77,7 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
 }
 
 size_t workspace_bytes(const Dims &g, const reg_loss_desc *L) {
-    size_t bytes = align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L));
+    size_t bytes = align256(WS_PARTIALS + sizeof(double) * PARTIALS_PER_BLOCK * (size_t)max_partial_blocks(g, L));
     // LNCC: three coefficient fields and the warped image
     if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 4 * (size_t)g.n);
     return bytes;
@@ -100,7 +101,8 @@ Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
     w.gtab = (float *)(b + WS_GTAB);
     w.scratch = (double *)(b + WS_SCRATCH);
     w.partials = (double *)(b + WS_PARTIALS);
-    w.coef = (float *)(b + align256(WS_PARTIALS + sizeof(double) * (size_t)max_partial_blocks(g, L)));
+    w.coef = (float *)(b + align256(WS_PARTIALS + sizeof(double) * PARTIALS_PER_BLOCK *
+                                               (size_t)max_partial_blocks(g, L)));
     w.warped = w.coef + 3 * (size_t)g.n;
     return w;
 }
@@ -172,6 +174,26 @@ reg_status check_common(const reg_loss_desc *L, const void *F, const void *M, in
     REG_TRY(check_ptr(ws));
     if (ws_bytes < workspace_bytes(make_dims(d), L)) return REG_ERR_WORKSPACE;
     return REG_OK;
+}
+
+bool affine_ok(const reg_affine *T) {
+    if (!T) return false;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(T->A[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(T->t[i]) || !isfinite(T->s[i])) return false;
+    return true;
+}
+
+// the kernels' form: A - I (taken in double, rounded once), t, s
+AffineT to_affine(const reg_affine &T) {
+    AffineT a;
+    for (int i = 0; i < 9; ++i) a.am[i] = (float)((double)T.A[i] - (i % 4 == 0 ? 1.0 : 0.0));
+    for (int i = 0; i < 3; ++i) {
+        a.t[i] = T.t[i];
+        a.s[i] = T.s[i];
+    }
+    return a;
 }
 
 // sweep 1 of either loss: similarity into sim_out (+ LNCC coefficient fields)
@@ -351,6 +373,87 @@ reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int 
     }
     t_events_armed = armed;
     return st;
+}
+
+reg_status reg_warp_composite(const void *M, int img_dt, const float *u, reg_dims d, const reg_affine *T, int pad,
+                              float *J, float *dJ, void *stream) {
+    REG_TRY(check_dims(d));
+    if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    if (!affine_ok(T)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(M));
+    REG_TRY(check_opt_ptr(u));
+    REG_TRY(check_ptr(J));
+    REG_TRY(check_opt_ptr(dJ));
+    const AffineT A = to_affine(*T);
+    return cuda_status(launch_warp(M, img_dt, u, make_dims(d), pad, J, dJ, (cudaStream_t)stream, &A));
+}
+
+reg_status reg_warp_composite_backward(const void *M, int img_dt, const float *u, reg_dims d, const reg_affine *T,
+                                       int pad, const float *g, float *g_u, double *grad_affine, void *ws,
+                                       size_t ws_bytes, void *stream) {
+    REG_TRY(check_dims(d));
+    if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    if (!affine_ok(T)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(M));
+    REG_TRY(check_opt_ptr(u));
+    REG_TRY(check_ptr(g));
+    REG_TRY(check_opt_ptr(g_u));
+    REG_TRY(check_opt_ptr(grad_affine));
+    REG_TRY(check_ptr(ws));
+    const Dims gd = make_dims(d);
+    if (ws_bytes < workspace_bytes(gd, nullptr)) return REG_ERR_WORKSPACE;
+    const Ws w = carve(ws, gd, nullptr);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const AffineT A = to_affine(*T);
+    REG_CUDA(cudaMemsetAsync(w.counters, 0, 256, s));
+    return cuda_status(launch_composite_backward(M, img_dt, u, gd, pad, A, g, g_u, w.partials, w.counters + 2,
+                                                 grad_affine ? grad_affine : w.scratch, s));
+}
+
+reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                   const float *u, reg_dims d, const reg_affine *T, int pad, void *ws,
+                                   size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
+                                   void *stream) {
+    REG_TRY(check_dims(d));
+    REG_TRY(check_loss(loss));
+    if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    if (!affine_ok(T)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(F));
+    REG_TRY(check_ptr(M));
+    REG_TRY(check_opt_ptr(u));
+    REG_TRY(check_ptr(ws));
+    REG_TRY(check_ptr(sim_out));
+    REG_TRY(check_opt_ptr(grad_u));
+    REG_TRY(check_opt_ptr(grad_affine));
+    const Dims g = make_dims(d);
+    if (ws_bytes < workspace_bytes(g, loss)) return REG_ERR_WORKSPACE;
+    const Ws w = carve(ws, g, loss);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const AffineT A = to_affine(*T);
+    const bool need_grad = grad_u || grad_affine;
+    double *aout = grad_affine ? grad_affine : w.scratch;
+    REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
+    StepParams S{};
+    if (loss->kind == REG_LOSS_LNCC) {
+        const LnccParams P{loss->window / 2, loss->eps, loss->lncc_grad == REG_LNCC_GRAD_ANTS};
+        REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s, &A));
+        REG_CUDA(launch_lncc_stats(F, w.warped, img_dt, g, P, need_grad ? w.coef : nullptr, w.partials,
+                                   w.counters + 0, sim_out, s));
+        if (need_grad)
+            REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u, g, pad, P, w.coef, grad_u, false, nullptr, nullptr, nullptr,
+                                        REG_F32, S, w.partials, w.counters + 2, aout, s, &A));
+    } else {
+        const MiParams P = mi_params(loss);
+        REG_CUDA(launch_mi_hist(F, M, img_dt, u, g, pad, P, w.hist, s, &A));
+        REG_CUDA(launch_mi_finalize(w.hist, P, g.n, w.gtab, sim_out, s));
+        if (need_grad)
+            REG_CUDA(launch_mi_sweep2(F, M, img_dt, u, g, pad, P, w.gtab, grad_u, false, nullptr, nullptr, nullptr,
+                                      REG_F32, S, w.partials, w.counters + 2, aout, s, &A));
+    }
+    return REG_OK;
 }
 
 reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream) {

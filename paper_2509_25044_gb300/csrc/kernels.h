@@ -95,29 +95,40 @@ MarchGrid lncc_grid(const Dims &g, int r, int per_sm = LNCC_MAX_PER_SM);
 MarchGrid lncc_ants_grid(const Dims &g);
 MarchGrid diffusion_grid(const Dims &g);
 
+// aff: the composite transform phi = A p + t + S u (u may then be NULL);
+// NULL is the plain deformable warp
 cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, int pad, float *J, float *dJ,
-                        cudaStream_t s);
+                        cudaStream_t s, const AffineT *aff = nullptr);
+// Composite sampler backward: g_u = S gX (optional), out[12] = dL/dA
+// (row-major), dL/dt; partials: 12 doubles per block of mi_sweep_grid(g)
+cudaError_t launch_composite_backward(const void *M, int dt, const float *u, const Dims &g, int pad,
+                                      const AffineT &A, const float *gin, float *g_u, double *partials,
+                                      unsigned *counter, double *out, cudaStream_t s);
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
-                           const MiParams &P, unsigned long long *hist, cudaStream_t s);
+                           const MiParams &P, unsigned long long *hist, cudaStream_t s,
+                           const AffineT *aff = nullptr);
 cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
                                double *sim_out, cudaStream_t s);
-// Second MI sweep: adjoint (+ optional diffusion + Adam).
+// Second MI sweep: adjoint (+ optional diffusion + Adam).  With aff (the
+// composite transform; step must be false, u and grad_out may be NULL):
+// grad_out = S gX and r_out[12] = dC/dA, dC/dt from 12 partials per block.
 cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                              const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                              void *m, void *v, int mdt, const StepParams &S, double *partials,
-                             unsigned *counter, double *r_out, cudaStream_t s);
+                             unsigned *counter, double *r_out, cudaStream_t s, const AffineT *aff = nullptr);
 
 // First LNCC sweep: window statistics of F and the warped image J (already
 // in HBM, FP32) -> similarity (+ optional adjoint coefficient fields, [3][N]).
 cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims &g, const LnccParams &P, float *coef,
                               double *partials, unsigned *counter, double *sim_out, cudaStream_t s);
 // Second LNCC sweep: box sums of the coefficient fields -> adjoint (+ optional
-// diffusion + Adam).
+// diffusion + Adam).  aff as for launch_mi_sweep2.
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                                const LnccParams &P, const float *coef, float *grad_out, bool step,
                                float *u_out, void *m, void *v, int mdt, const StepParams &S,
-                               double *partials, unsigned *counter, double *r_out, cudaStream_t s);
+                               double *partials, unsigned *counter, double *r_out, cudaStream_t s,
+                               const AffineT *aff = nullptr);
 
 cudaError_t launch_diffusion(const float *u, const Dims &g, float lam, float *grad, double *partials,
                              unsigned *counter, double *r_out, cudaStream_t s);

@@ -305,13 +305,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
     }
 }
 
-template <typename T, typename MT, bool STEP, int PAD, typename I>
+// AFF: the composite transform (STEP false; u and grad_out may be NULL);
+// grad_out = S gX and r_out[12] = dC/dA, dC/dt.
+template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
 __global__ void __launch_bounds__(TILE_THREADS)
     lncc_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                        LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
                        float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                        double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
-                       unsigned *err) {
+                       unsigned *err, AffineT A) {
+    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     extern __shared__ float smem[];
     __shared__ double red[32];
     const int r = P.r;
@@ -333,7 +336,9 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const I col = active ? (I)y * nx + x : 0;
     const bool hxm = x > 0, hxp = x + 1 < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
     float cur[3] = {0.f, 0.f, 0.f}, prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
-    if (active) {
+    const bool has_u = !AFF || u != nullptr;  // the composite form may omit u
+    AffineAcc aacc;
+    if (active && has_u) {
         const I p = (I)z0 * nxy + col;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -379,12 +384,13 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const int zo = q - r;
         if (active && zo >= z0 && zo < z1) {
             const I p = (I)zo * nxy + col;
-            if (zo + 1 < g.nz) {
+            if (zo + 1 < g.nz && has_u) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
             }
-            float sx, sy, sz;
-            const float jv = sample_grad<T, PAD, I>(M, g, x, y, zo, cur[0], cur[1], cur[2], sx, sy, sz);
+            float sx, sy, sz, qx = cur[0], qy = cur[1], qz = cur[2];
+            if (AFF) composite_disp(A, x, y, zo, qx, qy, qz);
+            const float jv = sample_grad<T, PAD, I>(M, g, x, y, zo, qx, qy, qz, sx, sy, sz);
             const float fv = ld_vox(F, p);
             const float gj = fmaf(fv, Sa[2], fmaf(2.0f * jv, Sa[1], Sa[0]));
             const float gs[3] = {gj * sx, gj * sy, gj * sz};
@@ -398,6 +404,12 @@ __global__ void __launch_bounds__(TILE_THREADS)
                     (u_out + c * g.n)[p] =
                         adam_fast(cur[c], gt, ld_moment(mc[c], p), ld_moment(vc[c], p), mc[c], vc[c], p, S);
                 }
+            } else if (AFF) {
+                aacc.add(gs[0], gs[1], gs[2], zo);
+                if (grad_out) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = A.s[c] * gs[c];
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
@@ -409,6 +421,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
     }
+    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -433,13 +446,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
 //   dL/dJ_k = c_k (a_J + 2 J_k a_JJ + F_k a_FJ)_k,
 // so the sweep streams the coefficient fields like the MI sweep streams its
 // inputs (plane-ahead prefetch of u, F, the coefficients and the moments).
-template <typename T, typename MT, bool STEP, int PAD, typename I>
+template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
 __global__ void __launch_bounds__(TILE_THREADS, 4)
     lncc_sweep2_ants_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                             LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
                             float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                             double *__restrict__ partials, unsigned *__restrict__ counter,
-                            double *__restrict__ r_out, unsigned *err) {
+                            double *__restrict__ r_out, unsigned *err, AffineT A) {
+    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     __shared__ double red[32];
     const int r = P.r;
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -448,6 +462,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     const int z0 = blockIdx.z * zc;
     const int z1 = min(g.nz, z0 + zc);
     float rpart = 0.0f;
+    AffineAcc aacc;
+    const bool has_u = !AFF || u != nullptr;
     if (x < g.nx && y < g.ny) {
         const float *uc[3] = {u, u + g.n, u + 2 * g.n};
         const float *cf[3] = {coef, coef + g.n, coef + 2 * g.n};
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
         float fcur, acur[3], mcur[3] = {0.f, 0.f, 0.f}, vcur[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cur[c] = __ldg(uc[c] + p);
+            cur[c] = has_u ? __ldg(uc[c] + p) : 0.0f;
             acur[c] = __ldg(cf[c] + p);
         }
         fcur = ld_vox(F, p);
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
         }
         for (int z = z0; z < z1; ++z, p += nxy) {
             float fnxt = 0.0f, anxt[3] = {0.f, 0.f, 0.f}, mnxt[3] = {0.f, 0.f, 0.f}, vnxt[3] = {0.f, 0.f, 0.f};
-            if (z + 1 < g.nz) {
+            if (z + 1 < g.nz && has_u) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
             }
@@ -491,8 +507,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                     }
                 }
             }
-            float sx, sy, sz;
-            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
+            float sx, sy, sz, qx = cur[0], qy = cur[1], qz = cur[2];
+            if (AFF) composite_disp(A, x, y, z, qx, qy, qz);
+            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, qx, qy, qz, sx, sy, sz);
             const float ck = cxy * (float)win_count(z, r, g.nz);
             const float gj = ck * fmaf(fcur, acur[2], fmaf(2.0f * jv, acur[1], acur[0]));
             const float gs[3] = {gj * sx, gj * sy, gj * sz};
@@ -504,6 +521,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                     const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
                     (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
+                }
+            } else if (AFF) {
+                aacc.add(gs[0], gs[1], gs[2], z);
+                if (grad_out) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = A.s[c] * gs[c];
                 }
             } else {
 #pragma unroll
@@ -520,6 +543,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
             }
         }
     }
+    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -645,27 +669,35 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
 static cudaError_t launch_lncc_sweep2_ants(const void *F, const void *M, int dt, const float *u, const Dims &g,
                                            int pad, const LnccParams &P, const float *coef, float *grad_out,
                                            bool step, float *u_out, void *m, void *v, int mdt, const StepParams &S,
-                                           double *partials, unsigned *counter, double *r_out, cudaStream_t s) {
+                                           double *partials, unsigned *counter, double *r_out, cudaStream_t s,
+                                           const AffineT *aff) {
     const MarchGrid G = lncc_ants_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
+    const AffineT A = aff ? *aff : AffineT{};
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
+            if (aff) {  // the composite form: gradients only, 64-bit offsets
+                lncc_sweep2_ants_kernel<T, float, false, PD, long long, true><<<grid, block, 0, s>>>(
+                    (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, nullptr, nullptr, nullptr, S,
+                    partials, counter, r_out, err, A);
+                return;
+            }
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
                 if (!step) {
                     lncc_sweep2_ants_kernel<T, float, false, PD, I><<<grid, block, 0, s>>>(
                         (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (float *)m, (float *)v, S,
-                        partials, counter, r_out, err);
+                        partials, counter, r_out, err, A);
                     return;
                 }
                 with_type(mdt, [&](auto mp) {
                     using MT = elem_t<decltype(mp)>;
                     lncc_sweep2_ants_kernel<T, MT, true, PD, I><<<grid, block, 0, s>>>(
                         (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
-                        partials, counter, r_out, err);
+                        partials, counter, r_out, err, A);
                 });
             });
         });
@@ -676,10 +708,12 @@ static cudaError_t launch_lncc_sweep2_ants(const void *F, const void *M, int dt,
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                                const LnccParams &P, const float *coef, float *grad_out, bool step,
                                float *u_out, void *m, void *v, int mdt, const StepParams &S,
-                               double *partials, unsigned *counter, double *r_out, cudaStream_t s) {
+                               double *partials, unsigned *counter, double *r_out, cudaStream_t s,
+                               const AffineT *aff) {
     if (P.ants)
         return launch_lncc_sweep2_ants(F, M, dt, u, g, pad, P, coef, grad_out, step, u_out, m, v, mdt, S, partials,
-                                       counter, r_out, s);
+                                       counter, r_out, s, aff);
+    const AffineT A = aff ? *aff : AffineT{};
     MarchGrid G;
     dim3 grid;
     const dim3 block(TX, TY);
@@ -690,6 +724,14 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
+            if (aff) {  // the composite form: gradients only, 64-bit offsets
+                e = prepare_march(lncc_sweep2_kernel<T, float, false, PD, long long, true>, smem, g, P.r, G, grid);
+                if (e == cudaSuccess)
+                    lncc_sweep2_kernel<T, float, false, PD, long long, true><<<grid, block, smem, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, nullptr, nullptr, nullptr, S,
+                        partials, counter, r_out, err, A);
+                return;
+            }
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
                 if (!step) {
@@ -697,7 +739,7 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                     if (e == cudaSuccess)
                         lncc_sweep2_kernel<T, float, false, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (float *)m,
-                            (float *)v, S, partials, counter, r_out, err);
+                            (float *)v, S, partials, counter, r_out, err, A);
                     return;
                 }
                 with_type(mdt, [&](auto mp) {
@@ -706,7 +748,7 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                     if (e == cudaSuccess)
                         lncc_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m,
-                            (MT *)v, S, partials, counter, r_out, err);
+                            (MT *)v, S, partials, counter, r_out, err, A);
                 });
             });
         });

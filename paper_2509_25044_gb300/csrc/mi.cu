@@ -84,10 +84,10 @@ size_t mi_hist_smem_bytes(int B) { return sizeof(unsigned) * (size_t)hist_copies
 // nearest bin of bin coordinate s (the hard-binned estimator's rule)
 __device__ __forceinline__ int nearest_bin(float s, int B) { return min(max((int)floorf(s + 0.5f), 1), B - 2); }
 
-template <typename T, int PAD, typename I, bool HARD>
+template <typename T, int PAD, typename I, bool HARD, bool AFF>
 __global__ void __launch_bounds__(HIST_THREADS, 1)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
-                   int tiles_x, long long total, unsigned long long *__restrict__ hist) {
+                   int tiles_x, long long total, AffineT A, unsigned long long *__restrict__ hist) {
     extern __shared__ unsigned sh[];
     const int B = P.bins, BB = B * B;
     const int copies = hist_copies(B), pitch = BB + 1;
@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
     __syncthreads();
     unsigned *shc = sh + (threadIdx.x % copies) * pitch;
     const float *u0 = u, *u1 = u + g.n, *u2 = u + 2 * g.n;
+    const bool has_u = !AFF || u != nullptr;  // the composite form may omit u
     const I nxy = (I)g.nxy;
     const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
     const int batch = hist_batch_planes(B);
@@ -111,16 +112,25 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
             const int y = (int)(tile / tiles_x) * HIST_TY + threadIdx.y;
             if (x >= g.nx || y >= g.ny) continue;
             I p = (I)z0 * nxy + (I)y * g.nx + x;
-            float fv = ld_vox(F, p), ux = __ldg(u0 + p), uy = __ldg(u1 + p), uz = __ldg(u2 + p);
+            float fv = ld_vox(F, p), ux = 0.0f, uy = 0.0f, uz = 0.0f;
+            if (has_u) {
+                ux = __ldg(u0 + p);
+                uy = __ldg(u1 + p);
+                uz = __ldg(u2 + p);
+            }
             for (int z = z0; z < z1; ++z, p += nxy) {
                 float fn = 0.0f, nx0 = 0.0f, nx1 = 0.0f, nx2 = 0.0f;
                 if (z + 1 < z1) {
                     fn = ld_vox(F, p + nxy);
-                    nx0 = __ldg(u0 + p + nxy);
-                    nx1 = __ldg(u1 + p + nxy);
-                    nx2 = __ldg(u2 + p + nxy);
+                    if (has_u) {
+                        nx0 = __ldg(u0 + p + nxy);
+                        nx1 = __ldg(u1 + p + nxy);
+                        nx2 = __ldg(u2 + p + nxy);
+                    }
                 }
-                const float jv = sample<T, PAD, I>(M, g, x, y, z, ux, uy, uz);
+                float qx = ux, qy = uy, qz = uz;
+                if (AFF) composite_disp(A, x, y, z, qx, qy, qz);
+                const float jv = sample<T, PAD, I>(M, g, x, y, z, qx, qy, qz);
                 if (HARD) {
                     // one count at the nearest bins; the kernel is applied to
                     // the B x B counts in the finalisation
@@ -217,13 +227,16 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
     }
 }
 
-template <typename T, typename MT, bool STEP, int PAD, typename I>
+// AFF: the composite transform (STEP false; u and grad_out may be NULL);
+// grad_out = S gX and r_out[12] = dC/dA, dC/dt.
+template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
 __global__ void __launch_bounds__(TILE_THREADS, 4)
     mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                      MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                      double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
-                     unsigned *err) {
+                     unsigned *err, AffineT A) {
+    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     // G4[m][n] = G'[m][n .. n+3]: one 16-byte shared load per kernel row
     extern __shared__ float4 G4[];  // B * B entries (dynamic)
     __shared__ double red[32];
@@ -241,6 +254,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     const int z0 = blockIdx.z * zc;
     const int z1 = min(g.nz, z0 + zc);
     float rpart = 0.0f;
+    AffineAcc aacc;
+    const bool has_u = !AFF || u != nullptr;
     if (x < g.nx && y < g.ny) {
         // per-channel base pointers; voxel offsets within a channel are of type I
         const float *uc[3] = {u, u + g.n, u + 2 * g.n};
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
         float cur[3], prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
         float fcur, mcur[3] = {0.f, 0.f, 0.f}, vcur[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cur[c] = __ldg(uc[c] + p);
+        for (int c = 0; c < 3; ++c) cur[c] = has_u ? __ldg(uc[c] + p) : 0.0f;
         fcur = ld_vox(F, p);
         if (STEP) {
 #pragma unroll
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
         }
         for (int z = z0; z < z1; ++z, p += nxy) {
             float fnxt = 0.0f, mnxt[3] = {0.f, 0.f, 0.f}, vnxt[3] = {0.f, 0.f, 0.f};
-            if (z + 1 < g.nz) {
+            if (z + 1 < g.nz && has_u) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
             }
@@ -280,8 +295,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                     }
                 }
             }
-            float sx, sy, sz;
-            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
+            float sx, sy, sz, qx = cur[0], qy = cur[1], qz = cur[2];
+            if (AFF) composite_disp(A, x, y, z, qx, qy, qz);
+            const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, qx, qy, qz, sx, sy, sz);
             float wf[4], dj[4];
             const int iF = bspline_weights(to_bin(fcur, P.f_lo, P.f_scale, B), B, wf) - 1;
             const float tj = (jv - P.m_lo) * P.m_scale;
@@ -304,6 +320,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
                     (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
                 }
+            } else if (AFF) {
+                aacc.add(gs[0], gs[1], gs[2], z);
+                if (grad_out) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = A.s[c] * gs[c];
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
@@ -318,6 +340,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
             }
         }
     }
+    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -341,28 +364,37 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
 MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 8LL * num_sms() * 4, 1); }
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
-                           const MiParams &P, unsigned long long *hist, cudaStream_t s) {
+                           const MiParams &P, unsigned long long *hist, cudaStream_t s, const AffineT *aff) {
     const int tiles_x = (g.nx + HIST_TX - 1) / HIST_TX, tiles_y = (g.ny + HIST_TY - 1) / HIST_TY;
     const long long total = (long long)tiles_x * tiles_y * g.nz;
     if (total <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<long long>(num_sms(), total);
     const dim3 block(HIST_TX, HIST_TY);
     const size_t smem = mi_hist_smem_bytes(P.bins);
+    const AffineT A = aff ? *aff : AffineT{};
     cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            auto run = [&](auto kern) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess)
+                    kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, tiles_x, total, A, hist);
+            };
+            if (aff) {  // the composite form: 64-bit offsets only
+                if (P.hard)
+                    run(mi_hist_kernel<T, PD, long long, true, true>);
+                else
+                    run(mi_hist_kernel<T, PD, long long, false, true>);
+                return;
+            }
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
-                auto run = [&](auto kern) {
-                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                    if (e == cudaSuccess)
-                        kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, tiles_x, total, hist);
-                };
                 if (P.hard)
-                    run(mi_hist_kernel<T, decltype(pd)::value, I, true>);
+                    run(mi_hist_kernel<T, PD, I, true, false>);
                 else
-                    run(mi_hist_kernel<T, decltype(pd)::value, I, false>);
+                    run(mi_hist_kernel<T, PD, I, false, false>);
             });
         });
     });
@@ -382,8 +414,9 @@ cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P
 cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                              const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                              void *m, void *v, int mdt, const StepParams &S, double *partials,
-                             unsigned *counter, double *r_out, cudaStream_t s) {
+                             unsigned *counter, double *r_out, cudaStream_t s, const AffineT *aff) {
     const MarchGrid G = mi_sweep_grid(g);
+    const AffineT A = aff ? *aff : AffineT{};
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
     const size_t smem = sizeof(float4) * (size_t)P.bins * P.bins;
@@ -398,13 +431,20 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
+            if (aff) {  // the composite form: gradients only, 64-bit offsets
+                if (prepare(mi_sweep2_kernel<T, float, false, PD, long long, true>))
+                    mi_sweep2_kernel<T, float, false, PD, long long, true><<<grid, block, smem, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, nullptr, nullptr, nullptr, S,
+                        partials, counter, r_out, err, A);
+                return;
+            }
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
                 if (!step) {
                     if (prepare(mi_sweep2_kernel<T, float, false, PD, I>))
                         mi_sweep2_kernel<T, float, false, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (float *)m,
-                            (float *)v, S, partials, counter, r_out, err);
+                            (float *)v, S, partials, counter, r_out, err, A);
                     return;
                 }
                 with_type(mdt, [&](auto mp) {
@@ -412,7 +452,7 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                     if (prepare(mi_sweep2_kernel<T, MT, true, PD, I>))
                         mi_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
                             (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
-                            partials, counter, r_out, err);
+                            partials, counter, r_out, err, A);
                 });
             });
         });

@@ -226,6 +226,45 @@ __device__ __forceinline__ float sample_grad(const T *M, const Dims &g, int x, i
 }
 
 // ---------------------------------------------------------------------------
+// composite transform phi(p) = A p + t + S u(p) (Sec. 2.1, the composite
+// implicit grid sampler; Algorithm gridsampler).  The kernels call the
+// deformable sampler with the displacement u' = (A - I) p + t + S u, so that
+// phi = p + u' and the interior test, the padding and the interpolation are
+// those of the plain sampler.  No coordinate grid is materialised.
+// ---------------------------------------------------------------------------
+struct AffineT {
+    float am[9];  // A - I, row-major: row i is output axis i (x, y, z)
+    float t[3];   // translation, voxels
+    float s[3];   // S = diag(s)
+};
+__device__ __forceinline__ void composite_disp(const AffineT &T, int x, int y, int z, float &ux, float &uy,
+                                               float &uz) {
+    const float fx = (float)x, fy = (float)y, fz = (float)z;
+    const float ox = fmaf(T.am[0], fx, fmaf(T.am[1], fy, fmaf(T.am[2], fz, T.t[0])));
+    const float oy = fmaf(T.am[3], fx, fmaf(T.am[4], fy, fmaf(T.am[5], fz, T.t[1])));
+    const float oz = fmaf(T.am[6], fx, fmaf(T.am[7], fy, fmaf(T.am[8], fz, T.t[2])));
+    ux = fmaf(T.s[0], ux, ox);
+    uy = fmaf(T.s[1], uy, oy);
+    uz = fmaf(T.s[2], uz, oz);
+}
+
+// Per-thread sums for dC/dA = sum_p gX(p) p^T and dC/dt = sum_p gX(p), gX
+// the gradient with respect to the sampling location.  A thread marches one
+// (x, y) column, so along it only sum g and sum g z are needed.
+struct AffineAcc {
+    float G[3] = {0.f, 0.f, 0.f}, Z[3] = {0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(float gx, float gy, float gz, int z) {
+        const float fz = (float)z;
+        G[0] += gx;
+        G[1] += gy;
+        G[2] += gz;
+        Z[0] = fmaf(gx, fz, Z[0]);
+        Z[1] = fmaf(gy, fz, Z[1]);
+        Z[2] = fmaf(gz, fz, Z[2]);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -286,6 +325,44 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
     __syncthreads();
     if (last) __threadfence();
     return last;
+}
+
+// Fixed-order reduction of every thread's AffineAcc (column (x, y)) into
+// out[12] = dC/dA row-major, then dC/dt.  Every thread of the block calls it
+// (threads outside the volume with empty sums); partials holds 12 doubles
+// per block.
+__device__ __forceinline__ void affine_reduce(const AffineAcc &a, int x, int y, double *partials, unsigned *counter,
+                                              double *out, double *red, unsigned *err) {
+    double v[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        v[3 * i + 0] = (double)x * (double)a.G[i];
+        v[3 * i + 1] = (double)y * (double)a.G[i];
+        v[3 * i + 2] = (double)a.Z[i];
+        v[9 + i] = (double)a.G[i];
+    }
+    const int tid = linear_tid();
+    const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll 1
+    for (int k = 0; k < 12; ++k) {
+        const double bs = block_sum(v[k], red);
+        if (tid == 0) partials[bid * 12 + k] = bs;
+    }
+    if (arrive_last(counter)) {
+        const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+        const int nt = blockDim.x * blockDim.y * blockDim.z;
+#pragma unroll 1
+        for (int k = 0; k < 12; ++k) {
+            double acc = 0.0;
+            for (long long i = tid; i < nb; i += nt) acc += __ldcg(partials + i * 12 + k);
+            const double tot = block_sum(acc, red);
+            if (tid == 0) {
+                if (!isfinite(tot)) latch_error(err, REG_ERR_NONFINITE);
+                out[k] = tot;
+            }
+        }
+        if (tid == 0) *counter = 0u;
+    }
 }
 
 }  // namespace regk

@@ -1,24 +1,33 @@
 // warp.cu -- standalone trilinear warp J = M o (id + u) with optional slope
 // (Sec. 2.1: the deformable part of the composite implicit grid sampler;
-// Algorithm gridsampler, forward).  The identity grid is implicit in the
-// thread index, so no coordinate grid is ever materialised.  The fused loss
-// sweeps (lncc.cu, mi.cu) call the same device sampler on chip; this kernel
-// serves reg_warp and the tests.
+// Algorithm gridsampler, forward), and its composite form
+// phi(p) = A p + t + S u(p) with the backward to u, A and t.  The identity
+// grid is implicit in the thread index, so no coordinate grid is ever
+// materialised.  The fused loss sweeps (lncc.cu, mi.cu) call the same device
+// sampler on chip; these kernels serve reg_warp, the composite entry points
+// and the tests.
 #include "kernels.h"
 
 namespace regk {
 
-template <typename T, bool SLOPE, int PAD>
+template <typename T, bool SLOPE, int PAD, bool AFF>
 __global__ void __launch_bounds__(TILE_THREADS) warp_kernel(const T *__restrict__ M, const float *__restrict__ u,
-                                                            Dims g, int zc, float *__restrict__ J,
+                                                            Dims g, int zc, AffineT A, float *__restrict__ J,
                                                             float *__restrict__ dJ) {
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
+    const bool has_u = !AFF || u != nullptr;  // the composite form may omit u
     const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
     for (int z = z0; z < z1; ++z) {
         const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
-        const float ux = __ldg(u + p), uy = __ldg(u + g.n + p), uz = __ldg(u + 2 * g.n + p);
+        float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+        if (has_u) {
+            ux = __ldg(u + p);
+            uy = __ldg(u + g.n + p);
+            uz = __ldg(u + 2 * g.n + p);
+        }
+        if (AFF) composite_disp(A, x, y, z, ux, uy, uz);
         if (SLOPE) {
             float sx, sy, sz;
             J[p] = sample_grad<T, PAD>(M, g, x, y, z, ux, uy, uz, sx, sy, sz);
@@ -32,17 +41,80 @@ __global__ void __launch_bounds__(TILE_THREADS) warp_kernel(const T *__restrict_
 }
 
 cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, int pad, float *J, float *dJ,
-                        cudaStream_t s) {
+                        cudaStream_t s, const AffineT *aff) {
     const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    const AffineT A = aff ? *aff : AffineT{};
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
-            if (dJ)
-                warp_kernel<T, true, PD><<<grid, block, 0, s>>>((const T *)M, u, g, G.zc, J, dJ);
-            else
-                warp_kernel<T, false, PD><<<grid, block, 0, s>>>((const T *)M, u, g, G.zc, J, dJ);
+            auto run = [&](auto kern) { kern<<<grid, block, 0, s>>>((const T *)M, u, g, G.zc, A, J, dJ); };
+            if (aff) {
+                if (dJ)
+                    run(warp_kernel<T, true, PD, true>);
+                else
+                    run(warp_kernel<T, false, PD, true>);
+            } else if (dJ) {
+                run(warp_kernel<T, true, PD, false>);
+            } else {
+                run(warp_kernel<T, false, PD, false>);
+            }
+        });
+    });
+    return cudaGetLastError();
+}
+
+// Algorithm gridsampler, backward, without the image gradient: for the
+// upstream gradient g = dL/dJ, gX = dJ/dphi * g is the gradient with respect
+// to the sampling location; g_u = S gX (optional) and the 12 sums dL/dA,
+// dL/dt are reduced in a fixed order.
+template <typename T, int PAD>
+__global__ void __launch_bounds__(TILE_THREADS)
+    composite_backward_kernel(const T *__restrict__ M, const float *__restrict__ u, Dims g, int zc, AffineT A,
+                              const float *__restrict__ gin, float *__restrict__ g_u, double *__restrict__ partials,
+                              unsigned *__restrict__ counter, double *__restrict__ out, unsigned *err) {
+    __shared__ double red[32];
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    AffineAcc acc;
+    if (x < g.nx && y < g.ny) {
+        const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
+        for (int z = z0; z < z1; ++z) {
+            const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+            float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+            if (u) {
+                ux = __ldg(u + p);
+                uy = __ldg(u + g.n + p);
+                uz = __ldg(u + 2 * g.n + p);
+            }
+            composite_disp(A, x, y, z, ux, uy, uz);
+            float sx, sy, sz;
+            (void)sample_grad<T, PAD>(M, g, x, y, z, ux, uy, uz, sx, sy, sz);
+            const float gv = __ldg(gin + p);
+            const float gx = gv * sx, gy = gv * sy, gz = gv * sz;
+            acc.add(gx, gy, gz, z);
+            if (g_u) {
+                g_u[p] = A.s[0] * gx;
+                g_u[g.n + p] = A.s[1] * gy;
+                g_u[2 * g.n + p] = A.s[2] * gz;
+            }
+        }
+    }
+    affine_reduce(acc, x, y, partials, counter, out, red, err);
+}
+
+cudaError_t launch_composite_backward(const void *M, int dt, const float *u, const Dims &g, int pad,
+                                      const AffineT &A, const float *gin, float *g_u, double *partials,
+                                      unsigned *counter, double *out, cudaStream_t s) {
+    const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    unsigned *err = error_word();
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            composite_backward_kernel<T, decltype(pd)::value><<<grid, block, 0, s>>>(
+                (const T *)M, u, g, G.zc, A, gin, g_u, partials, counter, out, err);
         });
     });
     return cudaGetLastError();

@@ -134,6 +134,36 @@ def test_loss_and_iterate_validation(capi):
     assert L.reg_debug_wait_flag(vp(FAKE), 1, 11 * 10 ** 9, None) == 1
 
 
+def test_composite_validation(capi):
+    """Composite sampler entry points reject bad transforms, dtypes and
+    buffers before any launch."""
+    L = _lib(capi)
+    vp = ctypes.c_void_p
+    ok = capi.affine_desc()
+    nan = capi.affine_desc(A=[[1, 0, 0], [0, float("nan"), 0], [0, 0, 1]])
+    inf = capi.affine_desc(s=(1.0, float("inf"), 1.0))
+    for T, want in ((nan, 1), (inf, 1)):
+        assert L.reg_warp_composite(vp(FAKE), 0, None, dims(), ctypes.byref(T), 0, vp(FAKE), None, None) == want
+    assert L.reg_warp_composite(vp(FAKE), 0, None, dims(), None, 0, vp(FAKE), None, None) == 1
+    assert L.reg_warp_composite(vp(FAKE), 7, None, dims(), ctypes.byref(ok), 0, vp(FAKE), None, None) == 3
+    assert L.reg_warp_composite(vp(FAKE), 0, None, dims(), ctypes.byref(ok), 0, None, None, None) == 1
+    assert L.reg_warp_composite(vp(FAKE), 0, vp(FAKE + 4), dims(), ctypes.byref(ok), 0, vp(FAKE), None, None) == 4
+    # backward: workspace too small, missing upstream gradient
+    need = capi.reg_workspace_size(None, dims())
+    assert L.reg_warp_composite_backward(vp(FAKE), 0, None, dims(), ctypes.byref(ok), 0, vp(FAKE), None, None,
+                                         vp(FAKE), need - 1, None) == 5
+    assert L.reg_warp_composite_backward(vp(FAKE), 0, None, dims(), ctypes.byref(ok), 0, None, None, None,
+                                         vp(FAKE), need, None) == 1
+    lncc = capi.lncc_desc(7, 1e-5)
+    wsl = capi.reg_workspace_size(lncc, dims())
+    assert L.reg_loss_grad_composite(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, None, dims(), ctypes.byref(nan), 0,
+                                     vp(FAKE), wsl, vp(FAKE), None, None, None) == 1
+    assert L.reg_loss_grad_composite(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, None, dims(), ctypes.byref(ok), 0,
+                                     vp(FAKE), wsl - 1, vp(FAKE), None, None, None) == 5
+    assert L.reg_loss_grad_composite(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, None, dims(), ctypes.byref(ok), 0,
+                                     vp(FAKE), wsl, None, None, None, None) == 1
+
+
 def test_product_package_has_no_oracle_dependency():
     """The product path must not import, link or execute the oracle."""
     pkg = os.path.join(ROOT, "paper_2509_25044_gb300")
