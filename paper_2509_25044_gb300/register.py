@@ -58,7 +58,12 @@ class Registration:
     """Holds the device state of one registration (u ping-pong, Adam moments,
     workspace) so that runs can be continued and timed without reallocation."""
 
-    def __init__(self, F: torch.Tensor, M: torch.Tensor, cfg: RegConfig, u0: torch.Tensor | None = None):
+    def __init__(self, F: torch.Tensor, M: torch.Tensor, cfg: RegConfig, u0: torch.Tensor | None = None,
+                 affine=None):
+        """affine: an optional capi.RegAffine; the deformable field is then
+        optimised under the composite transform phi = A p + t + S u (loss
+        gradient from reg_loss_grad_composite, then the diffusion gradient and
+        Adam as separate launches)."""
         if F.device.type != "cuda":
             raise ValueError("F and M must be CUDA tensors")
         self.F, self.M, self.cfg = F.contiguous(), M.contiguous(), cfg
@@ -76,8 +81,10 @@ class Registration:
         self.adam = capi.adam_desc(cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps,
                                    capi.REG_BF16 if cfg.moments == "bf16" else capi.REG_F32, float(self.N))
         self.t = 0
+        self.affine = affine
         self.smoothing = cfg.sigma_grad > 0.0 or cfg.sigma_warp > 0.0
-        if self.smoothing:
+        self.unfused = self.smoothing or affine is not None
+        if self.unfused:
             self.g = torch.empty_like(self.u[0])
             self.tmp = torch.empty_like(self.u[0])
             self.tmp2 = torch.empty_like(self.u[0])
@@ -92,17 +99,22 @@ class Registration:
         hist = torch.zeros((iters, 2), dtype=torch.float64, device=self.F.device)
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record()
-        if not self.smoothing and iters > 0:
+        if not self.unfused and iters > 0:
             # one native call runs all iterations (no host work between them)
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
             capi.reg_run(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t, iters,
                          self.ws, pad=self.cfg.pad, obj_hist=hist)
             self.t += iters
-        for k in range(iters if self.smoothing else 0):
+        for k in range(iters if self.unfused else 0):
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
             self.t += 1
-            # smoothing regularisation: gradient -> smooth(sigma_grad) -> Adam -> smooth(sigma_warp)
-            capi.reg_loss_grad(self.loss, self.F, self.M, a, self.ws, pad=self.cfg.pad, sim=self.sim1, grad=self.g)
+            # gradient (composite or plain) -> [smooth(sigma_grad)] -> Adam -> [smooth(sigma_warp)]
+            if self.affine is not None:
+                capi.reg_loss_grad_composite(self.loss, self.F, self.M, self.affine, a, self.ws, pad=self.cfg.pad,
+                                             need_affine=False, sim=self.sim1, grad_u=self.g)
+            else:
+                capi.reg_loss_grad(self.loss, self.F, self.M, a, self.ws, pad=self.cfg.pad, sim=self.sim1,
+                                   grad=self.g)
             capi.reg_regularize(a, self.cfg.lam, self.ws, r=self.r1, grad=self.g)
             hist[k, 0] = self.sim1[0]
             hist[k, 1] = self.r1[0]
@@ -128,7 +140,11 @@ class Registration:
         F = self.F if F is None else F
         M = self.M if M is None else M
         ws = self.ws if F.dtype == self.F.dtype else capi.workspace(self.loss, F)
-        sim = capi.reg_loss(self.loss, F, M, u, ws, pad=self.cfg.pad)
+        if self.affine is not None:
+            sim = capi.reg_loss_grad_composite(self.loss, F, M, self.affine, u, ws, pad=self.cfg.pad, need_u=False,
+                                               need_affine=False)[0][:1]
+        else:
+            sim = capi.reg_loss(self.loss, F, M, u, ws, pad=self.cfg.pad)
         R = capi.reg_regularize(u, 0.0, ws)
         s, r = float(sim.item()), float(R.item())
         c = 1.0 - s if self.cfg.loss == "lncc" else -s
@@ -191,3 +207,71 @@ def register_multiscale(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 100,
     end.record()
     torch.cuda.synchronize()
     return {"u": u, "levels": levels, "ms": start.elapsed_time(end)}
+
+
+def _centre(shape):
+    nz, ny, nx = shape
+    return np.array([(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
+
+
+def affine_about_centre(A, tc, shape):
+    """(A, t) of phi(p) = A p + t for the map A (p - c) + c + tc about the
+    volume centre c (tc in voxels)."""
+    c = _centre(shape)
+    A = np.asarray(A, dtype=np.float64)
+    return A, c - A @ c + np.asarray(tc, dtype=np.float64)
+
+
+def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40), lr_A: float = 0.01,
+                    lr_t: float = 0.3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                    final_lr: float = 0.1) -> dict:
+    """Affine stage of the paper's pipeline: phi(p) = A (p - c) + c + tc about
+    the volume centre, optimised by Adam over the 12 parameters at each scale
+    of a 2x block-mean pyramid, with the similarity and dC/dA, dC/dt from the
+    composite sampler (reg_loss_grad_composite, u = 0).  tc is kept in voxels
+    of the full-resolution grid; at scale s it is tc / s.  The 12-parameter
+    bookkeeping runs on the host (one 112-byte read per iteration).  The
+    step sizes decay linearly to final_lr of their value over each level: a
+    constant Adam step leaves A jittering by about lr_A, a motion of lr_A
+    times the radius at the volume's edge.  Returns
+    A, t of the full-resolution map (phi = A p + t), tc, and the objective
+    history per level."""
+    pyr = {1: (F.contiguous(), M.contiguous())}
+    s = 1
+    while s < scales[0]:
+        f, m = pyr[s]
+        pyr[2 * s] = (capi.reg_downsample2(f), capi.reg_downsample2(m))
+        s *= 2
+    loss = cfg.loss_desc(F)
+    A = np.eye(3)
+    tc = np.zeros(3)
+    levels = []
+    for s, it in zip(scales, iters):
+        f, m = pyr[s]
+        shape = tuple(f.shape)
+        c = _centre(shape)
+        ws = capi.workspace(loss, f)
+        buf = torch.zeros(14, dtype=torch.float64, device=f.device)  # sim (2), dC/dA (9), dC/dt (3)
+        mA, vA, mt, vt = np.zeros((3, 3)), np.zeros((3, 3)), np.zeros(3), np.zeros(3)
+        hist = []
+        for k in range(it):
+            t = c - A @ c + tc / s
+            capi.reg_loss_grad_composite(loss, f, m, capi.affine_desc(A, t), None, ws, pad=cfg.pad, need_u=False,
+                                         sim=buf[0:2], grad_affine=buf[2:14])
+            h = buf.cpu().numpy()
+            sim, gA, gt = h[0], h[2:11].reshape(3, 3), h[11:14]
+            hist.append(1.0 - sim if cfg.loss == "lncc" else -sim)
+            # gradients in the centred parameters: dC/dA at fixed tc, dC/dtc
+            gA = gA - np.outer(gt, c)
+            gtc = gt / s
+            b1, b2 = 1.0 - beta1 ** (k + 1), 1.0 - beta2 ** (k + 1)
+            decay = 1.0 - (1.0 - final_lr) * k / max(it - 1, 1)
+            mA = beta1 * mA + (1 - beta1) * gA
+            vA = beta2 * vA + (1 - beta2) * gA * gA
+            mt = beta1 * mt + (1 - beta1) * gtc
+            vt = beta2 * vt + (1 - beta2) * gtc * gtc
+            A = A - decay * lr_A * (mA / b1) / (np.sqrt(vA / b2) + eps)
+            tc = tc - decay * lr_t * s * (mt / b1) / (np.sqrt(vt / b2) + eps)
+        levels.append({"scale": s, "objective": np.asarray(hist)})
+    A_full, t_full = affine_about_centre(A, tc, tuple(F.shape))
+    return {"A": A_full, "t": t_full, "tc": tc, "levels": levels}

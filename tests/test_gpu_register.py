@@ -57,3 +57,44 @@ def test_multiscale_schedule():
     assert out["ms"] > 0
     with pytest.raises(ValueError):
         register_multiscale(d["F"], d["M"], cfg, scales=(2, 4, 1), iters=(1, 1, 1))
+
+
+def test_affine_stage_recovers_known_map():
+    """Multi-modal pair related by a known affine map (rotation about two
+    axes, anisotropic scale, shift): the multi-scale MI affine stage on the
+    composite sampler recovers the map to well under a voxel."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _util import multimodal_images
+    from paper_2509_25044_gb300 import capi
+    from paper_2509_25044_gb300.register import affine_about_centre, register_affine
+    shape = (64, 64, 64)
+    F, Mbase = multimodal_images(shape, 41)
+    a, b = 0.07, 0.035
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+    A_true, t_true = affine_about_centre(Rz @ Rx @ np.diag([1.04, 0.97, 1.02]), (2.5, -1.5, 1.0), shape)
+    Ai = np.linalg.inv(A_true)
+    M = capi.reg_warp_composite(Mbase.to(DEV), capi.affine_desc(Ai, -Ai @ t_true))
+    cfg = RegConfig(loss="mi", bins=32, m_range=(float(M.min()), float(M.max())))
+    out = register_affine(F.to(DEV), M, cfg, scales=(4, 2, 1), iters=(100, 60, 40))
+    for lv in out["levels"]:
+        assert np.all(np.isfinite(lv["objective"])) and lv["objective"][-1] < lv["objective"][0]
+    from oracle import identity_grid
+    X = identity_grid(shape).reshape(3, -1)
+    err = np.linalg.norm((out["A"] - A_true) @ X + (out["t"] - t_true)[:, None], axis=0)
+    err0 = np.linalg.norm((np.eye(3) - A_true) @ X - t_true[:, None], axis=0)
+    assert err0.mean() > 2.0
+    # the map is recovered to a fraction of the initial misalignment, and the
+    # optimiser reaches the MI optimum: the objective there is no worse than
+    # at the generating map (double trilinear resampling and independent
+    # noise leave the optimum a few tenths of a voxel from that map)
+    assert err.mean() < 0.6 and err.mean() < 0.2 * err0.mean(), (err.mean(), err.max())
+    loss = cfg.loss_desc(F)
+
+    def C(A, t):
+        sim = capi.reg_loss_grad_composite(loss, F.to(DEV), M, capi.affine_desc(A, t), None, need_u=False,
+                                           need_affine=False)[0]
+        return -float(sim[0].item())
+
+    assert C(out["A"], out["t"]) <= C(A_true, t_true) + 1e-3, (C(out["A"], out["t"]), C(A_true, t_true))
