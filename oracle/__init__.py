@@ -378,6 +378,28 @@ def similarity_and_grad_composite(F, M, A, t, s=(1.0, 1.0, 1.0), u=None, spec=No
 
 
 # --------------------------------------------------------------------------
+# composition of displacement fields and scaling-and-squaring (the
+# exponential of a stationary velocity field that the paper's grid sampler
+# serves, Sec. 4 ablations): (id + w) = (id + b) o (id + a), i.e.
+# w(p) = a(p) + b(p + a(p)), each channel of b sampled with the pinned
+# trilinear warp.
+# --------------------------------------------------------------------------
+def compose_fields(a, b, pad: int = PAD_BORDER):
+    """w = a + b o (id + a) for fields [3, nz, ny, nx]."""
+    a = _f64(a)
+    b = _f64(b)
+    return a + np.stack([warp(b[c], a, pad) for c in range(3)])
+
+
+def exp_field(v, steps: int, pad: int = PAD_BORDER):
+    """Scaling and squaring: u = v / 2^steps, then steps times u <- u + u o (id + u)."""
+    u = _f64(v) / float(2 ** steps)
+    for _ in range(steps):
+        u = compose_fields(u, u, pad)
+    return u
+
+
+# --------------------------------------------------------------------------
 # one iteration, composed by the chain rule
 # --------------------------------------------------------------------------
 @dataclass

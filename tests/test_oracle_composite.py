@@ -142,3 +142,56 @@ def test_loss_gradients_match_differences(rng, kind):
         e[i] = h
         fd = (C(A, t + e) - C(A, t - e)) / (2 * h)
         assert abs(fd - g_t[i]) < 2e-5 * max(1e-3, np.abs(g_t).max())
+
+
+# --------------------------------------------------------------------------
+# field composition and scaling-and-squaring
+# --------------------------------------------------------------------------
+def test_compose_translations_add(rng):
+    shape = (5, 6, 7)
+    a = np.zeros((3,) + shape)
+    b = np.zeros((3,) + shape)
+    for c, (ta, tb) in enumerate([(0.3, 0.4), (-0.2, 0.7), (0.5, -0.1)]):
+        a[c], b[c] = ta, tb
+    np.testing.assert_allclose(O.compose_fields(a, b), a + b, rtol=0, atol=1e-15)
+
+
+def test_compose_with_linear_field_is_exact(rng):
+    """b(p) = B p is linear, so trilinear sampling is exact in the interior:
+    w(p) = a(p) + B (p + a(p))."""
+    shape = (8, 9, 10)
+    B = 0.05 * rng.standard_normal((3, 3))
+    X = O.identity_grid(shape)
+    b = np.einsum("ij,jzyx->izyx", B, X)
+    a = np.clip(0.3 * rng.standard_normal((3,) + shape), -0.9, 0.9)
+    w = O.compose_fields(a, b)
+    ref = a + np.einsum("ij,jzyx->izyx", B, X + a)
+    inner = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))  # p + a stays inside
+    np.testing.assert_allclose(w[inner], ref[inner], rtol=0, atol=1e-13)
+
+
+def test_exp_of_linear_field_is_matrix_power(rng):
+    """For v(p) = B p about the volume centre, K squarings give exactly
+    (I + B / 2^K)^(2^K) (away from the clamped border), which tends to the
+    matrix exponential expm(B)."""
+    from scipy.linalg import expm
+    shape = (24, 24, 24)
+    c = np.array([11.5, 11.5, 11.5])
+    B = np.array([[0.02, -0.08, 0.01], [0.08, 0.03, 0.0], [-0.01, 0.02, -0.04]])
+    X = O.identity_grid(shape)
+    Xc = X - c[:, None, None, None]
+    v = np.einsum("ij,jzyx->izyx", B, Xc)
+    K = 6
+    u = O.exp_field(v, K)
+    P = np.linalg.matrix_power(np.eye(3) + B / 2 ** K, 2 ** K)
+    ref = np.einsum("ij,jzyx->izyx", P - np.eye(3), Xc)
+    inner = (slice(None), slice(6, -6), slice(6, -6), slice(6, -6))
+    np.testing.assert_allclose(u[inner], ref[inner], rtol=0, atol=1e-11)
+    refE = np.einsum("ij,jzyx->izyx", expm(B) - np.eye(3), Xc)
+    assert np.abs(u[inner] - refE[inner]).max() < 2e-3
+
+
+def test_exp_of_translation_is_translation(rng):
+    v = np.zeros((3, 4, 5, 6))
+    v[0], v[1], v[2] = 1.7, -0.6, 0.25
+    np.testing.assert_allclose(O.exp_field(v, 5), v, rtol=0, atol=1e-14)
