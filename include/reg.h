@@ -236,6 +236,24 @@ REG_API reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void
                                            size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
                                            void *stream);
 
+/* Composition of displacement fields (the fused sampler applied to a
+ * 3-channel field): (id + w) = (id + b) o (id + a), i.e.
+ *     w(p) = a(p) + b(p + a(p)),
+ * all three channels of b sampled trilinearly at one location (padding
+ * `pad` as reg_warp).  a, b, w: FP32 [3][N]; w must not overlap a or b
+ * (REG_ERR_INVALID_ARG); a and b may be the same field. */
+REG_API reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pad, float *w, void *stream);
+
+/* Scaling and squaring: the exponential of a stationary velocity field v,
+ * u_0 = v / 2^steps, then `steps` times u <- u + u o (id + u) (the
+ * composition above; the first step reads v and applies the 2^-steps itself,
+ * so no scaled copy is made).  out receives u_steps; tmp is a second [3][N]
+ * buffer (ping-pong).  steps in [0, 30] (0 copies v); out, tmp and v must
+ * not overlap.  No identity or sampling grid is materialised: beyond v and
+ * out the operation holds one field (tmp). */
+REG_API reg_status reg_exp_field(const float *v, reg_dims d, int steps, int pad, float *tmp, float *out,
+                                 void *stream);
+
 /* `iters` fused iterations (as reg_iterate) in one call, numbered t0 + 1 ..
  * t0 + iters, without returning to the caller between them: iteration k
  * (0-based) reads u[k % 2] and writes u[(k + 1) % 2] with u = {u_a, u_b}, so

@@ -30,7 +30,7 @@ EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
            "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run", "reg_warp_composite",
-           "reg_warp_composite_backward", "reg_loss_grad_composite")
+           "reg_warp_composite_backward", "reg_loss_grad_composite", "reg_compose_fields", "reg_exp_field")
 
 
 class RegError(RuntimeError):
@@ -115,6 +115,8 @@ def _lib():
                                                   _vp, ctypes.c_size_t, _vp]
         L.reg_loss_grad_composite.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                               _aff, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]
+        L.reg_compose_fields.argtypes = [_vp, _vp, RegDims, ctypes.c_int, _vp, _vp]
+        L.reg_exp_field.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
         L.reg_run.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
                               ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, ctypes.c_int,
                               _vp, ctypes.c_size_t, _vp, _vp]
@@ -275,6 +277,27 @@ def reg_loss_grad_composite(loss: RegLossDesc, F, M, T: RegAffine, u=None, ws=No
                                           _ptr(grad_u if need_u else None), _ptr(grad_affine if need_affine else None),
                                           _stream(F)), "reg_loss_grad_composite")
     return sim, (grad_u if need_u else None), (grad_affine if need_affine else None)
+
+
+def reg_compose_fields(a, b, pad: int = REG_PAD_BORDER, out=None):
+    """w = a + b o (id + a) for [3][nz][ny][nx] FP32 fields."""
+    d = dims_of(a[0])
+    _need(b, tuple(a.shape), torch.float32, "b")
+    if out is None:
+        out = torch.empty_like(a)
+    _check(_lib().reg_compose_fields(_ptr(a), _ptr(b), d, int(pad), _ptr(out), _stream(a)), "reg_compose_fields")
+    return out
+
+
+def reg_exp_field(v, steps: int, pad: int = REG_PAD_BORDER, out=None, tmp=None):
+    """Scaling and squaring of the velocity field v ([3][nz][ny][nx] FP32)."""
+    d = dims_of(v[0])
+    if out is None:
+        out = torch.empty_like(v)
+    if tmp is None:
+        tmp = torch.empty_like(v)
+    _check(_lib().reg_exp_field(_ptr(v), d, int(steps), int(pad), _ptr(tmp), _ptr(out), _stream(v)), "reg_exp_field")
+    return out
 
 
 def reg_loss(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None):

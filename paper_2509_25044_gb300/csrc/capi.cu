@@ -456,6 +456,46 @@ reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, con
     return REG_OK;
 }
 
+static bool overlap3(const float *a, const float *b, long long n) {
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + sizeof(float) * 3 * (size_t)n;
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + sizeof(float) * 3 * (size_t)n;
+    return a0 < b1 && b0 < a1;
+}
+
+reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pad, float *w, void *stream) {
+    REG_TRY(check_dims(d));
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(a));
+    REG_TRY(check_ptr(b));
+    REG_TRY(check_ptr(w));
+    const Dims g = make_dims(d);
+    if (overlap3(w, a, g.n) || overlap3(w, b, g.n)) return REG_ERR_INVALID_ARG;
+    return cuda_status(launch_compose(a, b, g, pad, 1.0f, w, (cudaStream_t)stream));
+}
+
+reg_status reg_exp_field(const float *v, reg_dims d, int steps, int pad, float *tmp, float *out, void *stream) {
+    REG_TRY(check_dims(d));
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    if (steps < 0 || steps > 30) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(v));
+    REG_TRY(check_ptr(tmp));
+    REG_TRY(check_ptr(out));
+    const Dims g = make_dims(d);
+    if (overlap3(out, v, g.n) || overlap3(tmp, v, g.n) || overlap3(out, tmp, g.n)) return REG_ERR_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (steps == 0)
+        return cuda_status(cudaMemcpyAsync(out, v, sizeof(float) * 3 * (size_t)g.n, cudaMemcpyDeviceToDevice, s));
+    // the last of the ping-pong steps must land in out
+    float *dst = (steps % 2) ? out : tmp;
+    REG_CUDA(launch_compose(v, v, g, pad, (float)ldexp(1.0, -steps), dst, s));
+    for (int k = 1; k < steps; ++k) {
+        float *src = dst;
+        dst = (dst == out) ? tmp : out;
+        REG_CUDA(launch_compose(src, src, g, pad, 1.0f, dst, s));
+    }
+    return REG_OK;
+}
+
 reg_status reg_smooth_field(const float *u, reg_dims d, float sigma, float *tmp, float *out, void *stream) {
     REG_TRY(check_dims(d));
     REG_TRY(check_ptr(u));

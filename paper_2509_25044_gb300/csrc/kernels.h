@@ -99,6 +99,9 @@ MarchGrid diffusion_grid(const Dims &g);
 // NULL is the plain deformable warp
 cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, int pad, float *J, float *dJ,
                         cudaStream_t s, const AffineT *aff = nullptr);
+// Field composition w = s a + s b o (id + s a) (w must not alias a or b)
+cudaError_t launch_compose(const float *a, const float *b, const Dims &g, int pad, float scale, float *w,
+                           cudaStream_t s);
 // Composite sampler backward: g_u = S gX (optional), out[12] = dL/dA
 // (row-major), dL/dt; partials: 12 doubles per block of mi_sweep_grid(g)
 cudaError_t launch_composite_backward(const void *M, int dt, const float *u, const Dims &g, int pad,

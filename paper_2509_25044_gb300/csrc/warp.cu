@@ -120,4 +120,38 @@ cudaError_t launch_composite_backward(const void *M, int dt, const float *u, con
     return cudaGetLastError();
 }
 
+// Composition of displacement fields, (id + w) = (id + s b) o (id + s a):
+// w(p) = s a(p) + s b(p + s a(p)), the three channels of b sampled at one
+// location (the same sampler as the warp).  s folds the 2^-K of
+// scaling-and-squaring into its first step; s = 1 is the plain composition.
+template <int PAD>
+__global__ void __launch_bounds__(TILE_THREADS) compose_kernel(const float *__restrict__ a,
+                                                               const float *__restrict__ b, Dims g, int zc, float s,
+                                                               float *__restrict__ w) {
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
+    for (int z = z0; z < z1; ++z) {
+        const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+        const float ux = s * __ldg(a + p), uy = s * __ldg(a + g.n + p), uz = s * __ldg(a + 2 * g.n + p);
+        const float bx = sample<float, PAD>(b, g, x, y, z, ux, uy, uz);
+        const float by = sample<float, PAD>(b + g.n, g, x, y, z, ux, uy, uz);
+        const float bz = sample<float, PAD>(b + 2 * g.n, g, x, y, z, ux, uy, uz);
+        w[p] = fmaf(s, bx, ux);
+        w[g.n + p] = fmaf(s, by, uy);
+        w[2 * g.n + p] = fmaf(s, bz, uz);
+    }
+}
+
+cudaError_t launch_compose(const float *a, const float *b, const Dims &g, int pad, float scale, float *w,
+                           cudaStream_t s) {
+    const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    with_pad(pad, [&](auto pd) {
+        compose_kernel<decltype(pd)::value><<<grid, block, 0, s>>>(a, b, g, G.zc, scale, w);
+    });
+    return cudaGetLastError();
+}
+
 }  // namespace regk

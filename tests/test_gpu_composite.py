@@ -169,3 +169,49 @@ def test_composite_rejects_bad_affine(capi):
     T = capi.affine_desc(t=(float("nan"), 0.0, 0.0))
     with pytest.raises(RuntimeError):
         capi.reg_warp_composite(M, T)
+
+
+# ---------------------------------------------------------------------------
+# field composition and scaling-and-squaring on the fused sampler
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(16, 18, 40), (1, 9, 70), (7, 33, 5)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_compose_fields_matches_oracle(capi, shape, pad):
+    a = field(shape, 3.0, 2.0, 51)
+    b = field(shape, 2.0, 1.5, 52)
+    w = capi.reg_compose_fields(a.to(DEV), b.to(DEV), pad)
+    torch.cuda.synchronize()
+    ref = O.compose_fields(to64(a), to64(b), pad)
+    assert np.abs(to64(w) - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_compose_with_zero_is_exact(capi):
+    shape = (9, 10, 33)
+    a = field(shape, 3.0, 2.0, 54).to(DEV)
+    z = torch.zeros_like(a)
+    assert torch.equal(capi.reg_compose_fields(z, a), a)
+    assert torch.equal(capi.reg_compose_fields(a, z), a)
+    assert torch.equal(capi.reg_exp_field(z, 5), z)
+
+
+@pytest.mark.parametrize("steps", [0, 1, 4, 7])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_exp_field_matches_oracle(capi, steps, pad):
+    shape = (20, 24, 36)
+    v = field(shape, 4.0, 6.0, 53)
+    u = capi.reg_exp_field(v.to(DEV), steps, pad)
+    torch.cuda.synchronize()
+    ref = O.exp_field(to64(v), steps, pad)
+    assert np.abs(to64(u) - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert capi.reg_get_device_error() == 0
+
+
+def test_exp_field_rejects_aliasing(capi):
+    v = torch.zeros((3, 4, 4, 4), device=DEV)
+    t = torch.empty_like(v)
+    with pytest.raises(RuntimeError):
+        capi.reg_exp_field(v, 3, out=v, tmp=t)
+    with pytest.raises(RuntimeError):
+        capi.reg_exp_field(v, 31)
+    with pytest.raises(RuntimeError):
+        capi.reg_compose_fields(v, t, out=v)
