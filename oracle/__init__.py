@@ -35,9 +35,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 def _load():
     global _lib
     if _lib is None:
-        path = lib_path()
-        if not os.path.exists(path):
-            _build_lib()
+        path = _build_lib()  # compiles oracle.c when the library is missing or older than it
         lib = ctypes.CDLL(path)
         lib.or_warp.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.or_warp.restype = None
@@ -70,6 +68,10 @@ def _load():
         lib.or_mi.restype = ctypes.c_double
         lib.or_mi_grad.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, _dp]
         lib.or_mi_grad.restype = ctypes.c_double
+        lib.or_mi_of_pmf.argtypes = [_dp, ctypes.c_int]
+        lib.or_mi_of_pmf.restype = ctypes.c_double
+        lib.or_mi_adjoint_points.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_int, _dp, _dp]
+        lib.or_mi_adjoint_points.restype = None
         lib.or_diffusion.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         lib.or_diffusion.restype = ctypes.c_double
         lib.or_bf16_round.argtypes = [ctypes.c_double]
@@ -196,6 +198,24 @@ def _range32(rng):
     """(lo, scale) as the library forms them: float lo, hi; scale = float(1 / (hi - lo))."""
     lo, hi = float(np.float32(rng[0])), float(np.float32(rng[1]))
     return lo, float(np.float32(1.0 / (hi - lo)))
+
+
+def mi_of_pmf(p, bins: int) -> float:
+    """MI of a given joint PMF [bins, bins] (Eq. mi)."""
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(bins, bins))
+    return float(_load().or_mi_of_pmf(_ptr(p), int(bins)))
+
+
+def mi_adjoint_points(Fh, Jh, n_total: int, bins: int, p):
+    """dL/dJh (L = -MI) at the given voxels of a volume of n_total voxels with
+    joint PMF p (Eq. gradientmi-threadn): the per-voxel form of mi_grad for
+    sampled checks of volumes the oracle cannot histogram itself."""
+    Fh = np.ascontiguousarray(np.asarray(Fh, dtype=np.float64).ravel())
+    Jh = np.ascontiguousarray(np.asarray(Jh, dtype=np.float64).ravel())
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(bins, bins))
+    g = np.empty_like(Jh)
+    _load().or_mi_adjoint_points(_ptr(Fh), _ptr(Jh), len(Jh), int(n_total), int(bins), _ptr(p), _ptr(g))
+    return g
 
 
 def mi_hard(F, J, bins: int, f_range, m_range, with_hist: bool = False):

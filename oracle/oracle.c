@@ -393,7 +393,20 @@ double or_mi(const double *Fh, const double *Jh, long N, int B, double *p_out)
 /* The Parzen adjoint of MI for a given joint PMF p (B*B): marginals,        */
 /* G = log(p / (pI pJ)), then gJh_k = -(B-3)/N sum_mn G[m][n] kappa(sF_k-m)   */
 /* kappa'(sJ_k-n)  (Eq. gradientmi-threadn).                                  */
+static void mi_adjoint_n(const double *Fh, const double *Jh, long n, long N, int B, const double *p, double *gJh);
 static void mi_adjoint(const double *Fh, const double *Jh, long N, int B, const double *p, double *gJh)
+{
+    mi_adjoint_n(Fh, Jh, N, N, B, p, gJh);
+}
+
+/* The same adjoint at n given voxels of a volume of N voxels whose joint     */
+/* PMF is p: the per-voxel form used for sampled checks of large volumes.     */
+void or_mi_adjoint_points(const double *Fh, const double *Jh, long n, long N, int B, const double *p, double *gJh)
+{
+    mi_adjoint_n(Fh, Jh, n, N, B, p, gJh);
+}
+
+static void mi_adjoint_n(const double *Fh, const double *Jh, long n, long N, int B, const double *p, double *gJh)
 {
     const int BB = B * B;
     double pI[256], pJ[256];
@@ -414,7 +427,7 @@ static void mi_adjoint(const double *Fh, const double *Jh, long N, int B, const 
         }
     const double scale = -(double)(B - 3) / (double)N;
 #pragma omp parallel for schedule(static)
-    for (long k = 0; k < N; ++k) {
+    for (long k = 0; k < n; ++k) {
         double wF[256], dJ[256];
         const double sF = bin_coord(Fh[k], B), sJ = bin_coord(Jh[k], B);
         for (int m = 0; m < B; ++m) {
@@ -437,6 +450,10 @@ double or_mi_grad(const double *Fh, const double *Jh, long N, int B, double *gJh
     free(p);
     return mi;
 }
+
+static double mi_of_pmf(const double *p, int B);
+/* MI of a given joint PMF (B*B, row = fixed-image bin). */
+double or_mi_of_pmf(const double *p, int B) { return mi_of_pmf(p, B); }
 
 static double mi_of_pmf(const double *p, int B)
 {

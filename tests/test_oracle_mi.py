@@ -180,3 +180,18 @@ def test_hard_binned_symmetry_and_constant(rng):
     # an approximation of the Parzen value on continuous intensities
     ref = O.mi(F, np.clip(J / 1.2, 0, 1), 16)
     assert abs(a - ref) < 0.1 * ref
+
+
+def test_per_point_adjoint_and_pmf_mi_match_the_whole_volume_forms(rng):
+    """The per-voxel adjoint for a given PMF and the MI of a given PMF (used
+    for sampled checks of volumes too large for the oracle's own histogram)
+    agree with mi_grad / mi on a whole volume."""
+    N, B = 3000, 16
+    Fh = rng.uniform(0, 1, N)
+    Jh = np.clip(Fh + 0.2 * rng.standard_normal(N), 0, 1)
+    v, p = O.mi(Fh, Jh, B, with_hist=True)
+    v2, g = O.mi_grad(Fh, Jh, B)
+    assert abs(O.mi_of_pmf(p, B) - v) <= 1e-14 * abs(v)
+    idx = rng.choice(N, 50, replace=False)
+    gp = O.mi_adjoint_points(Fh[idx], Jh[idx], N, B, p)
+    np.testing.assert_allclose(gp, g[idx], rtol=1e-12, atol=0)
