@@ -287,8 +287,9 @@ REG_API reg_status reg_get_device_error(void *stream);
  * or a latency-critical loop that must never enter the allocator (cudaMalloc
  * and cudaFree can synchronise the device).  The paper has no counterpart;
  * this is a property of the library, not of the method.
- *   - Scratch: a fixed 48 KiB array inside the library (joint histogram
- *     u64[64*64] + adjoint table f32[64*64]), held by every GPU that loads
+ *   - Scratch: a fixed 112 KiB array inside the library (joint histogram
+ *     u64[64*64] + adjoint table f32[64*64] and its 4-wide rows
+ *     f32x4[64*64]), held by every GPU that loads
  *     the library until the process exits.  bins must be in [8, 64]; larger
  *     counts do not fit and return REG_ERR_SHAPE; a non-MI descriptor returns
  *     REG_ERR_UNSUPPORTED.

@@ -18,8 +18,8 @@ namespace {
 constexpr size_t WS_HIST = 0;                                        // u64[64*64]
 constexpr size_t WS_COUNTERS = WS_HIST + sizeof(unsigned long long) * MAX_BINS * MAX_BINS;  // u32[64]
 constexpr size_t WS_ZERO_BYTES = WS_COUNTERS + 256;                  // zeroed by every call
-constexpr size_t WS_GTAB = WS_ZERO_BYTES;                            // f32[64*64]
-constexpr size_t WS_SCRATCH = WS_GTAB + sizeof(float) * MAX_BINS * MAX_BINS;  // f64[32]
+constexpr size_t WS_GTAB = WS_ZERO_BYTES;                            // f32[64*64] + f32x4[64*64]
+constexpr size_t WS_SCRATCH = WS_GTAB + MI_TABLE_BYTES;               // f64[32]
 constexpr size_t WS_PARTIALS = WS_SCRATCH + 256;                     // f64[12 * max blocks]
 constexpr size_t PARTIALS_PER_BLOCK = 12;  // the composite sweeps reduce dC/dA, dC/dt
 

@@ -111,6 +111,14 @@ cudaError_t launch_composite_backward(const void *M, int dt, const float *u, con
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                            const MiParams &P, unsigned long long *hist, cudaStream_t s,
                            const AffineT *aff = nullptr);
+// The MI adjoint table region: G' (B x B floats, row = fixed-image bin),
+// then the same table as 4-wide rows, G4[m][n] = G'[m][n .. n+3] (B x B
+// float4, zero past the last bin), which the second sweep copies into shared
+// memory with 16-byte loads.
+constexpr size_t MI_TABLE_BYTES = (sizeof(float) + sizeof(float4)) * MAX_BINS * MAX_BINS;
+__host__ __device__ inline const float4 *mi_table4(const float *Gtab) {
+    return reinterpret_cast<const float4 *>(Gtab + MAX_BINS * MAX_BINS);
+}
 cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
                                double *sim_out, cudaStream_t s);
 // Second MI sweep: adjoint (+ optional diffusion + Adam).  With aff (the

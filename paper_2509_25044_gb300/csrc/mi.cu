@@ -220,10 +220,17 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
         }
         Gtab[e] = gv;
     }
-    const double mi = block_sum(acc, red);
+    const double mi = block_sum(acc, red);  // (its barriers publish the G' writes above)
     if (threadIdx.x == 0) {
         if (!isfinite(mi)) latch_error(err, REG_ERR_NONFINITE);
         sim_out[0] = mi;
+    }
+    // the 4-wide rows the second sweep loads: G4[m][n] = G'[m][n .. n+3]
+    float4 *G4 = reinterpret_cast<float4 *>(Gtab + MAX_BINS * MAX_BINS);
+    for (int e = threadIdx.x; e < BB; e += blockDim.x) {
+        const int n = e % B;
+        G4[e] = make_float4(Gtab[e], n + 1 < B ? Gtab[e + 1] : 0.0f, n + 2 < B ? Gtab[e + 2] : 0.0f,
+                            n + 3 < B ? Gtab[e + 3] : 0.0f);
     }
 }
 
@@ -242,11 +249,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     __shared__ double red[32];
     const int B = P.bins, BB = B * B;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < BB; i += TILE_THREADS) {
-        const int n = i % B;
-        G4[i] = make_float4(Gtab[i], n + 1 < B ? Gtab[i + 1] : 0.0f, n + 2 < B ? Gtab[i + 2] : 0.0f,
-                            n + 3 < B ? Gtab[i + 3] : 0.0f);
-    }
+    const float4 *T4 = mi_table4(Gtab);  // built by the finalisation
+    for (int i = tid; i < BB; i += TILE_THREADS) G4[i] = __ldg(T4 + i);
     __syncthreads();
 
     const int x = blockIdx.x * TX + threadIdx.x;

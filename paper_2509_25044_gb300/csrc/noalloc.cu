@@ -11,7 +11,7 @@
 // caller passes only its inputs and outputs.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds its 48 KiB until the process exits.  Its device address is
+// library holds its 112 KiB until the process exits.  Its device address is
 // looked up once per device (cudaGetSymbolAddress) on the first call made
 // with that device current; host code never uses the symbol itself.
 #include <mutex>
@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kNoallocMaxBins = 64;
 constexpr size_t kHistBytes = sizeof(unsigned long long) * kNoallocMaxBins * kNoallocMaxBins;  // 32 KiB
-constexpr size_t kGtabBytes = sizeof(float) * kNoallocMaxBins * kNoallocMaxBins;              // 16 KiB
+constexpr size_t kGtabBytes = MI_TABLE_BYTES;  // 80 KiB: G' and its 4-wide rows
 constexpr size_t kScratchBytes = kHistBytes + kGtabBytes;
 
 constexpr int kMaxDevices = 64;
