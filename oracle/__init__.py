@@ -39,6 +39,8 @@ def _load():
         lib = ctypes.CDLL(path)
         lib.or_warp.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.or_warp.restype = None
+        lib.or_warp_adjoint.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        lib.or_warp_adjoint.restype = None
         lib.or_lncc.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_double, _dp, _dp]
         lib.or_lncc.restype = ctypes.c_double
@@ -411,12 +413,58 @@ def compose_fields(a, b, pad: int = PAD_BORDER):
     return a + np.stack([warp(b[c], a, pad) for c in range(3)])
 
 
+def warp_adjoint(g, u, pad: int = PAD_BORDER):
+    """gM = the transpose of M -> M o (id+u) applied to g (the scatter of the
+    sampler backward): <warp(M, u), g> = <M, warp_adjoint(g, u)>."""
+    g = _f64(g)
+    u = _f64(u)
+    nx, ny, nz = _dims(g)
+    gM = np.empty_like(g)
+    _load().or_warp_adjoint(_ptr(g), _ptr(u), nx, ny, nz, int(pad), _ptr(gM))
+    return gM
+
+
+def compose_fields_backward(a, b, gw, pad: int = PAD_BORDER, scale: float = 1.0):
+    """Adjoint of w = s a + s b o (id + s a) (s = scale): returns (dL/da, dL/db)
+    for gw = dL/dw.  dL/da = s gw + s^2 (grad b)^T gw at the sample points;
+    dL/db = s times the scatter of gw."""
+    a = _f64(a)
+    b = _f64(b)
+    gw = _f64(gw)
+    sa = scale * a
+    ga = scale * gw.copy()
+    gb = np.empty_like(b)
+    for d in range(3):
+        _, dJ = warp(b[d], sa, pad, with_grad=True)
+        ga += scale * scale * gw[d][None] * dJ
+        gb[d] = scale * warp_adjoint(gw[d], sa, pad)
+    return ga, gb
+
+
 def exp_field(v, steps: int, pad: int = PAD_BORDER):
     """Scaling and squaring: u = v / 2^steps, then steps times u <- u + u o (id + u)."""
     u = _f64(v) / float(2 ** steps)
     for _ in range(steps):
         u = compose_fields(u, u, pad)
     return u
+
+
+def exp_field_backward(v, steps: int, gout, pad: int = PAD_BORDER):
+    """dL/dv for gout = dL/d exp(v): the forward steps are replayed, then each
+    squaring u <- u + u o (id + u) is differentiated with respect to its one
+    input (both adjoint terms), last step first; the 2^-steps of the first
+    step scales the result."""
+    v = _f64(v)
+    if steps == 0:
+        return _f64(gout).copy()
+    us = [v / float(2 ** steps)]
+    for _ in range(steps - 1):
+        us.append(compose_fields(us[-1], us[-1], pad))
+    g = _f64(gout)
+    for u in reversed(us):
+        ga, gb = compose_fields_backward(u, u, g, pad)
+        g = ga + gb
+    return g / float(2 ** steps)
 
 
 # --------------------------------------------------------------------------

@@ -115,6 +115,61 @@ void or_warp(const double *M, const double *u, int nx, int ny, int nz, int pad,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adjoint of the warp with respect to the moving volume (the scatter of     */
+/* Algorithm gridsampler, backward, "accumulate g_J into 8 neighbours"):      */
+/*   gM[q] = sum_p g[p] w_q(p),                                              */
+/* w_q(p) the trilinear weight of voxel q in the sample of M at p + u(p),    */
+/* with the padding of or_warp (BORDER: the point clamped first; ZEROS:      */
+/* corners outside take no weight).  Serial, so the sums have a fixed order. */
+/* ------------------------------------------------------------------------ */
+void or_warp_adjoint(const double *g, const double *u, int nx, int ny, int nz, int pad, double *gM)
+{
+    const long N = (long)nx * ny * nz;
+    const int n[3] = {nx, ny, nz};
+    for (long q = 0; q < N; ++q) gM[q] = 0.0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const long p = lin(x, y, z, nx, ny);
+                const int pc[3] = {x, y, z};
+                long i[3];
+                double a[3];
+                for (int k = 0; k < 3; ++k) {
+                    double phi = (double)pc[k] + u[(long)k * N + p];
+                    if (pad == OR_PAD_BORDER) {
+                        if (phi < 0.0) phi = 0.0;
+                        if (phi > (double)(n[k] - 1)) phi = (double)(n[k] - 1);
+                        if (n[k] == 1) {
+                            i[k] = 0;
+                            a[k] = 0.0;
+                            continue;
+                        }
+                        long f = (long)floor(phi);
+                        if (f > n[k] - 2) f = n[k] - 2;
+                        i[k] = f;
+                        a[k] = phi - (double)f;
+                    } else {
+                        long f = (long)floor(phi);
+                        i[k] = f;
+                        a[k] = phi - (double)f;
+                    }
+                }
+                for (int b = 0; b < 8; ++b) {
+                    const int bb[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+                    long c[3];
+                    double w = 1.0;
+                    int inside = 1;
+                    for (int k = 0; k < 3; ++k) {
+                        c[k] = i[k] + bb[k];
+                        w *= bb[k] ? a[k] : 1.0 - a[k];
+                        if (c[k] < 0 || c[k] > n[k] - 1) inside = 0;
+                    }
+                    if (inside && w != 0.0) gM[lin((int)c[0], (int)c[1], (int)c[2], nx, ny)] += w * g[p];
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
 /* LNCC value (App. fused LNCC, Eq. lncc-loss and Eqs. lncc-a .. lncc-c).    */
 /* The averaging filter w is a uniform box of side `win` (odd) centred at i; */
 /* at the volume border the box is truncated to the voxels inside the volume */

@@ -195,3 +195,64 @@ def test_exp_of_translation_is_translation(rng):
     v = np.zeros((3, 4, 5, 6))
     v[0], v[1], v[2] = 1.7, -0.6, 0.25
     np.testing.assert_allclose(O.exp_field(v, 5), v, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("pad", [O.PAD_BORDER, O.PAD_ZEROS])
+def test_warp_adjoint_is_the_transpose(rng, pad):
+    """<warp(M, u), g> = <M, warp_adjoint(g, u)> for every M and g (the warp is
+    linear in M), displacements reaching outside the volume included."""
+    shape = (5, 7, 6)
+    u = 1.5 * rng.standard_normal((3,) + shape)
+    for _ in range(3):
+        M = rng.standard_normal(shape)
+        g = rng.standard_normal(shape)
+        lhs = float(np.sum(O.warp(M, u, pad) * g))
+        rhs = float(np.sum(M * O.warp_adjoint(g, u, pad)))
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_warp_adjoint_of_integer_shift_is_reverse_shift(rng):
+    shape = (4, 5, 9)
+    u = np.zeros((3,) + shape)
+    u[0] = 2.0  # x + 2: interior voxels receive the value sampled from them
+    g = rng.standard_normal(shape)
+    gM = O.warp_adjoint(g, u, O.PAD_ZEROS)
+    np.testing.assert_array_equal(gM[:, :, 2:], g[:, :, :-2])
+    np.testing.assert_array_equal(gM[:, :, :2], 0.0)
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.25])
+def test_compose_backward_matches_differences(rng, scale):
+    shape = (6, 5, 7)
+    a = 0.6 * O.gaussian_smooth(rng.standard_normal((3,) + shape), 1.0) + 0.2 * rng.standard_normal((3,) + shape)
+    b = 0.8 * rng.standard_normal((3,) + shape)
+    gw = rng.standard_normal((3,) + shape)
+    ga, gb = O.compose_fields_backward(a, b, gw, scale=scale)
+
+    def L(a_, b_):
+        w = scale * a_ + np.stack([scale * O.warp(b_[c], scale * a_) for c in range(3)])
+        return float(np.sum(gw * w))
+
+    h = 1e-6
+    for c, z, y, x in [(0, 2, 3, 4), (1, 0, 1, 6), (2, 5, 4, 0), (0, 3, 0, 2)]:
+        d = np.zeros_like(a)
+        d[c, z, y, x] = h
+        fa = (L(a + d, b) - L(a - d, b)) / (2 * h)
+        fb = (L(a, b + d) - L(a, b - d)) / (2 * h)
+        assert abs(fa - ga[c, z, y, x]) <= 1e-6 * max(1.0, abs(fa)), (fa, ga[c, z, y, x])
+        assert abs(fb - gb[c, z, y, x]) <= 1e-7 * max(1.0, abs(fb)), (fb, gb[c, z, y, x])
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_exp_backward_matches_differences(rng, steps):
+    shape = (6, 6, 6)
+    v = 1.5 * O.gaussian_smooth(rng.standard_normal((3,) + shape), 1.0) + 0.05 * rng.standard_normal((3,) + shape)
+    gout = rng.standard_normal((3,) + shape)
+    gv = O.exp_field_backward(v, steps, gout)
+    L = lambda v_: float(np.sum(gout * O.exp_field(v_, steps)))
+    h = 1e-6
+    for c, z, y, x in [(0, 2, 3, 4), (1, 5, 0, 1), (2, 3, 3, 3)]:
+        d = np.zeros_like(v)
+        d[c, z, y, x] = h
+        fd = (L(v + d) - L(v - d)) / (2 * h)
+        assert abs(fd - gv[c, z, y, x]) <= 1e-6 * max(1.0, abs(fd)), (fd, gv[c, z, y, x])
