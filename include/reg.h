@@ -244,15 +244,37 @@ REG_API reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void
  * (REG_ERR_INVALID_ARG); a and b may be the same field. */
 REG_API reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pad, float *w, void *stream);
 
+/* Backward of reg_compose_fields for gw = dL/dw (FP32 [3][N]):
+ *   ga = gw + (grad b)^T gw, the slope of b taken at the sample points p + a(p);
+ *   gb = the scatter of gw onto the 8 corners of every sample with its
+ *        trilinear weights (the transpose of sampling b; Algorithm
+ *        gridsampler, backward, the moving-image gradient).
+ * ga, gb: FP32 [3][N], overwritten, overlapping neither each other nor the
+ * inputs.  When a and b are one field, pass ga == NULL: gb then receives the
+ * whole gradient (both terms).  gb is accumulated with float atomics, so its
+ * last bits can differ between runs. */
+REG_API reg_status reg_compose_fields_backward(const float *a, const float *b, const float *gw, reg_dims d, int pad,
+                                               float *ga, float *gb, void *stream);
+
 /* Scaling and squaring: the exponential of a stationary velocity field v,
  * u_0 = v / 2^steps, then `steps` times u <- u + u o (id + u) (the
  * composition above; the first step reads v and applies the 2^-steps itself,
  * so no scaled copy is made).  out receives u_steps; tmp is a second [3][N]
- * buffer (ping-pong).  steps in [0, 30] (0 copies v); out, tmp and v must
- * not overlap.  No identity or sampling grid is materialised: beyond v and
- * out the operation holds one field (tmp). */
+ * buffer (ping-pong).  saved (optional, NULL skips it): (steps - 1) x [3][N]
+ * floats receiving u_1 .. u_{steps-1} for reg_exp_field_backward (tmp is then
+ * not used).  steps in [0, 30] (0 copies v); out, tmp, saved and v must not
+ * overlap.  No identity or sampling grid is materialised. */
 REG_API reg_status reg_exp_field(const float *v, reg_dims d, int steps, int pad, float *tmp, float *out,
-                                 void *stream);
+                                 float *saved, void *stream);
+
+/* Backward of scaling and squaring: gv = dL/dv for gout = dL/d exp(v),
+ * through every squaring step (both adjoint terms of the composition), last
+ * step first.  saved: the u_1 .. u_{steps-1} written by reg_exp_field with the
+ * same v, steps and pad (may be NULL when steps <= 1); tmp: a [3][N] buffer;
+ * gv: FP32 [3][N], overwritten.  gout, tmp, gv and the inputs must not
+ * overlap.  Float atomics as in reg_compose_fields_backward. */
+REG_API reg_status reg_exp_field_backward(const float *v, reg_dims d, int steps, int pad, const float *saved,
+                                          const float *gout, float *tmp, float *gv, void *stream);
 
 /* `iters` fused iterations (as reg_iterate) in one call, numbered t0 + 1 ..
  * t0 + iters, without returning to the caller between them: iteration k

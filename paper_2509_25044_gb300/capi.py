@@ -30,7 +30,8 @@ EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp",
            "reg_regularize", "reg_step", "reg_iterate", "reg_jacdet_min", "reg_get_device_error",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
            "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run", "reg_warp_composite",
-           "reg_warp_composite_backward", "reg_loss_grad_composite", "reg_compose_fields", "reg_exp_field")
+           "reg_warp_composite_backward", "reg_loss_grad_composite", "reg_compose_fields", "reg_exp_field",
+           "reg_compose_fields_backward", "reg_exp_field_backward")
 
 
 class RegError(RuntimeError):
@@ -116,7 +117,9 @@ def _lib():
         L.reg_loss_grad_composite.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                               _aff, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]
         L.reg_compose_fields.argtypes = [_vp, _vp, RegDims, ctypes.c_int, _vp, _vp]
-        L.reg_exp_field.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.reg_exp_field.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.reg_compose_fields_backward.argtypes = [_vp, _vp, _vp, RegDims, ctypes.c_int, _vp, _vp, _vp]
+        L.reg_exp_field_backward.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
         L.reg_run.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
                               ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, ctypes.c_int,
                               _vp, ctypes.c_size_t, _vp, _vp]
@@ -289,15 +292,40 @@ def reg_compose_fields(a, b, pad: int = REG_PAD_BORDER, out=None):
     return out
 
 
-def reg_exp_field(v, steps: int, pad: int = REG_PAD_BORDER, out=None, tmp=None):
-    """Scaling and squaring of the velocity field v ([3][nz][ny][nx] FP32)."""
+def reg_exp_field(v, steps: int, pad: int = REG_PAD_BORDER, out=None, tmp=None, saved=None):
+    """Scaling and squaring of the velocity field v ([3][nz][ny][nx] FP32);
+    saved (optional, [steps - 1][3][nz][ny][nx]) keeps u_1 .. u_{steps-1}."""
     d = dims_of(v[0])
     if out is None:
         out = torch.empty_like(v)
+    if tmp is None and saved is None:
+        tmp = torch.empty_like(v)
+    _check(_lib().reg_exp_field(_ptr(v), d, int(steps), int(pad), _ptr(tmp), _ptr(out), _ptr(saved), _stream(v)),
+           "reg_exp_field")
+    return out
+
+
+def reg_compose_fields_backward(a, b, gw, pad: int = REG_PAD_BORDER, same: bool = False):
+    """(ga, gb) for gw = dL/dw of w = a + b o (id + a); same=True (a is b):
+    returns (None, the whole gradient)."""
+    d = dims_of(a[0])
+    ga = None if same else torch.empty_like(a)
+    gb = torch.empty_like(b)
+    _check(_lib().reg_compose_fields_backward(_ptr(a), _ptr(b), _ptr(gw), d, int(pad), _ptr(ga), _ptr(gb),
+                                              _stream(a)), "reg_compose_fields_backward")
+    return ga, gb
+
+
+def reg_exp_field_backward(v, steps: int, gout, saved=None, pad: int = REG_PAD_BORDER, gv=None, tmp=None):
+    """dL/dv of scaling and squaring for gout = dL/d exp(v)."""
+    d = dims_of(v[0])
+    if gv is None:
+        gv = torch.empty_like(v)
     if tmp is None:
         tmp = torch.empty_like(v)
-    _check(_lib().reg_exp_field(_ptr(v), d, int(steps), int(pad), _ptr(tmp), _ptr(out), _stream(v)), "reg_exp_field")
-    return out
+    _check(_lib().reg_exp_field_backward(_ptr(v), d, int(steps), int(pad), _ptr(saved), _ptr(gout), _ptr(tmp),
+                                         _ptr(gv), _stream(v)), "reg_exp_field_backward")
+    return gv
 
 
 def reg_loss(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None):

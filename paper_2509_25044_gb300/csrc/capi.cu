@@ -473,25 +473,92 @@ reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pa
     return cuda_status(launch_compose(a, b, g, pad, 1.0f, w, (cudaStream_t)stream));
 }
 
-reg_status reg_exp_field(const float *v, reg_dims d, int steps, int pad, float *tmp, float *out, void *stream) {
+reg_status reg_exp_field(const float *v, reg_dims d, int steps, int pad, float *tmp, float *out, float *saved,
+                         void *stream) {
     REG_TRY(check_dims(d));
     if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
     if (steps < 0 || steps > 30) return REG_ERR_INVALID_ARG;
     REG_TRY(check_ptr(v));
-    REG_TRY(check_ptr(tmp));
     REG_TRY(check_ptr(out));
+    REG_TRY(check_opt_ptr(saved));
+    if (!saved) REG_TRY(check_ptr(tmp));
     const Dims g = make_dims(d);
-    if (overlap3(out, v, g.n) || overlap3(tmp, v, g.n) || overlap3(out, tmp, g.n)) return REG_ERR_INVALID_ARG;
+    if (overlap3(out, v, g.n)) return REG_ERR_INVALID_ARG;
+    if (!saved && (overlap3(tmp, v, g.n) || overlap3(out, tmp, g.n))) return REG_ERR_INVALID_ARG;
+    if (saved && steps > 1) {
+        const uintptr_t s0 = (uintptr_t)saved, s1 = s0 + sizeof(float) * 3 * (size_t)g.n * (size_t)(steps - 1);
+        for (const float *f : {v, (const float *)out}) {
+            const uintptr_t f0 = (uintptr_t)f, f1 = f0 + sizeof(float) * 3 * (size_t)g.n;
+            if (f0 < s1 && s0 < f1) return REG_ERR_INVALID_ARG;
+        }
+    }
     const cudaStream_t s = (cudaStream_t)stream;
     if (steps == 0)
         return cuda_status(cudaMemcpyAsync(out, v, sizeof(float) * 3 * (size_t)g.n, cudaMemcpyDeviceToDevice, s));
-    // the last of the ping-pong steps must land in out
-    float *dst = (steps % 2) ? out : tmp;
-    REG_CUDA(launch_compose(v, v, g, pad, (float)ldexp(1.0, -steps), dst, s));
-    for (int k = 1; k < steps; ++k) {
-        float *src = dst;
-        dst = (dst == out) ? tmp : out;
-        REG_CUDA(launch_compose(src, src, g, pad, 1.0f, dst, s));
+    // destination of step k (1-based): the last one is out; the others are the
+    // saved slots, or a ping-pong with tmp chosen so that step `steps` lands in out
+    auto dst_of = [&](int k) -> float * {
+        if (k == steps) return out;
+        if (saved) return saved + (size_t)(k - 1) * 3 * (size_t)g.n;
+        return ((steps - k) % 2) ? tmp : out;
+    };
+    const float *src = v;
+    for (int k = 1; k <= steps; ++k) {
+        float *dst = dst_of(k);
+        REG_CUDA(launch_compose(src, src, g, pad, k == 1 ? (float)ldexp(1.0, -steps) : 1.0f, dst, s));
+        src = dst;
+    }
+    return REG_OK;
+}
+
+reg_status reg_compose_fields_backward(const float *a, const float *b, const float *gw, reg_dims d, int pad,
+                                       float *ga, float *gb, void *stream) {
+    REG_TRY(check_dims(d));
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(a));
+    REG_TRY(check_ptr(b));
+    REG_TRY(check_ptr(gw));
+    REG_TRY(check_opt_ptr(ga));
+    REG_TRY(check_ptr(gb));
+    const Dims g = make_dims(d);
+    if (!ga && a != b) return REG_ERR_INVALID_ARG;
+    for (const float *f : {a, b, gw})
+        if (overlap3(gb, f, g.n) || (ga && overlap3(ga, f, g.n))) return REG_ERR_INVALID_ARG;
+    if (ga && overlap3(ga, gb, g.n)) return REG_ERR_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    REG_CUDA(cudaMemsetAsync(gb, 0, sizeof(float) * 3 * (size_t)g.n, s));
+    return cuda_status(launch_compose_backward(a, b, gw, g, pad, 1.0f, ga, gb, s));
+}
+
+reg_status reg_exp_field_backward(const float *v, reg_dims d, int steps, int pad, const float *saved,
+                                  const float *gout, float *tmp, float *gv, void *stream) {
+    REG_TRY(check_dims(d));
+    if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
+    if (steps < 0 || steps > 30) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(v));
+    REG_TRY(check_ptr(gout));
+    REG_TRY(check_ptr(tmp));
+    REG_TRY(check_ptr(gv));
+    if (steps > 1) REG_TRY(check_ptr(saved));
+    const Dims g = make_dims(d);
+    const float *outs[3] = {gout, tmp, gv};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (overlap3(outs[i], outs[j], g.n)) return REG_ERR_INVALID_ARG;
+    if (overlap3(tmp, v, g.n) || overlap3(gv, v, g.n)) return REG_ERR_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * 3 * (size_t)g.n;
+    if (steps == 0) return cuda_status(cudaMemcpyAsync(gv, gout, bytes, cudaMemcpyDeviceToDevice, s));
+    // step k maps u_{k-1} to u_k; its adjoint (both terms, a = b = u_{k-1})
+    // lands in gv for k = 1 and alternates with tmp before that
+    const float *gsrc = gout;
+    for (int k = steps; k >= 1; --k) {
+        float *dst = (k % 2) ? gv : tmp;
+        const float *uin = k == 1 ? v : saved + (size_t)(k - 2) * 3 * (size_t)g.n;
+        REG_CUDA(cudaMemsetAsync(dst, 0, bytes, s));
+        REG_CUDA(launch_compose_backward(uin, uin, gsrc, g, pad, k == 1 ? (float)ldexp(1.0, -steps) : 1.0f,
+                                         nullptr, dst, s));
+        gsrc = dst;
     }
     return REG_OK;
 }

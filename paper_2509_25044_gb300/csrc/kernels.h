@@ -102,6 +102,10 @@ cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, in
 // Field composition w = s a + s b o (id + s a) (w must not alias a or b)
 cudaError_t launch_compose(const float *a, const float *b, const Dims &g, int pad, float scale, float *w,
                            cudaStream_t s);
+// Adjoint of the composition: ga (written; NULL when a == b, gb then gets
+// the whole gradient) and gb (accumulated with atomics: zero it first)
+cudaError_t launch_compose_backward(const float *a, const float *b, const float *gw, const Dims &g, int pad,
+                                    float scale, float *ga, float *gb, cudaStream_t s);
 // Composite sampler backward: g_u = S gX (optional), out[12] = dL/dA
 // (row-major), dL/dt; partials: 12 doubles per block of mi_sweep_grid(g)
 cudaError_t launch_composite_backward(const void *M, int dt, const float *u, const Dims &g, int pad,

@@ -144,6 +144,71 @@ __global__ void __launch_bounds__(TILE_THREADS) compose_kernel(const float *__re
     }
 }
 
+// Adjoint of w = s a + s b o (id + s a) for gw = dL/dw:
+//   ga = s gw + s^2 (grad b)^T gw at the sample point p + s a(p),
+//   gb += s gw scattered onto the 8 corners of that sample with its trilinear
+//         weights (the same padding as the sampler; the transpose of sampling b).
+// SAME (a and b one field): ga is added into gb as well, which then holds the
+// whole gradient.  The scatter uses float atomics, so the order of the
+// additions -- and the last bits of gb -- can vary between runs.
+template <int PAD, bool SAME>
+__global__ void __launch_bounds__(TILE_THREADS)
+    compose_backward_kernel(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ gw,
+                            Dims g, int zc, float s, float *__restrict__ ga, float *__restrict__ gb) {
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc);
+    for (int z = z0; z < z1; ++z) {
+        const long long p = (long long)z * g.nxy + (long long)y * g.nx + x;
+        const float ux = s * __ldg(a + p), uy = s * __ldg(a + g.n + p), uz = s * __ldg(a + 2 * g.n + p);
+        const float w0 = __ldg(gw + p), w1 = __ldg(gw + g.n + p), w2 = __ldg(gw + 2 * g.n + p);
+        float jx[3], jy[3], jz[3];  // d b_d / d phi_k
+#pragma unroll
+        for (int d = 0; d < 3; ++d) (void)sample_grad<float, PAD>(b + d * g.n, g, x, y, z, ux, uy, uz, jx[d], jy[d], jz[d]);
+        const float s2 = s * s;
+        const float gax = fmaf(s2, fmaf(w0, jx[0], fmaf(w1, jx[1], w2 * jx[2])), s * w0);
+        const float gay = fmaf(s2, fmaf(w0, jy[0], fmaf(w1, jy[1], w2 * jy[2])), s * w1);
+        const float gaz = fmaf(s2, fmaf(w0, jz[0], fmaf(w1, jz[1], w2 * jz[2])), s * w2);
+        if (SAME) {
+            atomicAdd(gb + p, gax);
+            atomicAdd(gb + g.n + p, gay);
+            atomicAdd(gb + 2 * g.n + p, gaz);
+        } else {
+            ga[p] = gax;
+            ga[g.n + p] = gay;
+            ga[2 * g.n + p] = gaz;
+        }
+        // the scatter: corner weights of the sample (padding as in the sampler)
+        const Axis X = axis_setup<PAD>(x, ux, g.nx), Y = axis_setup<PAD>(y, uy, g.ny), Z = axis_setup<PAD>(z, uz, g.nz);
+        const float sw[3] = {s * w0, s * w1, s * w2};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+            const float wt = (bx ? X.a : 1.0f - X.a) * (by ? Y.a : 1.0f - Y.a) * (bz ? Z.a : 1.0f - Z.a);
+            const bool valid = (bx ? X.v1 : X.v0) && (by ? Y.v1 : Y.v0) && (bz ? Z.v1 : Z.v0);
+            if (!valid || wt == 0.0f) continue;
+            const long long q = ((long long)(bz ? Z.i1 : Z.i0) * g.ny + (by ? Y.i1 : Y.i0)) * g.nx + (bx ? X.i1 : X.i0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) atomicAdd(gb + d * g.n + q, wt * sw[d]);
+        }
+    }
+}
+
+cudaError_t launch_compose_backward(const float *a, const float *b, const float *gw, const Dims &g, int pad,
+                                    float scale, float *ga, float *gb, cudaStream_t s) {
+    const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
+    with_pad(pad, [&](auto pd) {
+        constexpr int PD = decltype(pd)::value;
+        if (ga)
+            compose_backward_kernel<PD, false><<<grid, block, 0, s>>>(a, b, gw, g, G.zc, scale, ga, gb);
+        else
+            compose_backward_kernel<PD, true><<<grid, block, 0, s>>>(a, b, gw, g, G.zc, scale, ga, gb);
+    });
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compose(const float *a, const float *b, const Dims &g, int pad, float scale, float *w,
                            cudaStream_t s) {
     const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);

@@ -164,6 +164,24 @@ def test_composite_validation(capi):
                                      vp(FAKE), wsl, None, None, None, None) == 1
 
 
+def test_field_composition_validation(capi):
+    L = _lib(capi)
+    vp = ctypes.c_void_p
+    F2 = FAKE << 8
+    # ga == NULL requires a and b to be one field
+    assert L.reg_compose_fields_backward(vp(FAKE), vp(FAKE << 4), vp(FAKE << 6), dims(), 0, None, vp(F2), None) == 1
+    # gb overlapping an input
+    assert L.reg_compose_fields_backward(vp(FAKE), vp(FAKE), vp(FAKE << 6), dims(), 0, None, vp(FAKE + 64),
+                                         None) == 1
+    # steps out of range; backward past one step needs the saved fields
+    assert L.reg_exp_field(vp(FAKE), dims(), 31, 0, vp(FAKE << 4), vp(F2), None, None) == 1
+    assert L.reg_exp_field_backward(vp(FAKE), dims(), 3, 0, None, vp(FAKE << 4), vp(FAKE << 6), vp(F2),
+                                    None) == 1
+    # the gradient buffers must be distinct
+    assert L.reg_exp_field_backward(vp(FAKE), dims(), 1, 0, None, vp(FAKE << 4), vp(FAKE << 4), vp(F2),
+                                    None) == 1
+
+
 def test_product_package_has_no_oracle_dependency():
     """The product path must not import, link or execute the oracle."""
     pkg = os.path.join(ROOT, "paper_2509_25044_gb300")

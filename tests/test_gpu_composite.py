@@ -215,3 +215,39 @@ def test_exp_field_rejects_aliasing(capi):
         capi.reg_exp_field(v, 31)
     with pytest.raises(RuntimeError):
         capi.reg_compose_fields(v, t, out=v)
+
+
+@pytest.mark.parametrize("shape", [(12, 18, 40), (1, 9, 70), (7, 33, 5)])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_compose_backward_matches_oracle(capi, shape, pad):
+    a = field(shape, 3.0, 2.5, 61)
+    b = field(shape, 2.0, 1.5, 62)
+    gw = torch.from_numpy(np.random.default_rng(63).standard_normal((3,) + shape).astype(np.float32))
+    ga, gb = capi.reg_compose_fields_backward(a.to(DEV), b.to(DEV), gw.to(DEV), pad)
+    torch.cuda.synchronize()
+    gar, gbr = O.compose_fields_backward(to64(a), to64(b), to64(gw), pad)
+    assert rel_l2(to64(ga), gar) <= GRAD_RTOL
+    assert rel_l2(to64(gb), gbr) <= GRAD_RTOL
+    # a and b one field: the whole gradient in one buffer
+    ad = a.to(DEV)
+    _, gs = capi.reg_compose_fields_backward(ad, ad, gw.to(DEV), pad, same=True)
+    torch.cuda.synchronize()
+    g1, g2 = O.compose_fields_backward(to64(a), to64(a), to64(gw), pad)
+    assert rel_l2(to64(gs), g1 + g2) <= GRAD_RTOL
+
+
+@pytest.mark.parametrize("steps", [0, 1, 3, 6])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_exp_backward_matches_oracle(capi, steps, pad):
+    shape = (16, 20, 36)
+    v = field(shape, 4.0, 5.0, 64)
+    gout = torch.from_numpy(np.random.default_rng(65).standard_normal((3,) + shape).astype(np.float32))
+    vd = v.to(DEV)
+    saved = torch.empty((max(steps - 1, 1), 3) + shape, device=DEV)
+    out = capi.reg_exp_field(vd, steps, pad, saved=saved)
+    gv = capi.reg_exp_field_backward(vd, steps, gout.to(DEV), saved=saved, pad=pad)
+    torch.cuda.synchronize()
+    assert np.abs(to64(out) - O.exp_field(to64(v), steps, pad)).max() <= 2e-5 * np.abs(to64(v)).max()
+    ref = O.exp_field_backward(to64(v), steps, to64(gout), pad)
+    assert rel_l2(to64(gv), ref) <= 1e-4
+    assert capi.reg_get_device_error() == 0
