@@ -292,6 +292,43 @@ def affine_pipeline(n: int = 192, seed: int = 7, iters: int = 200, lam: float = 
     return row
 
 
+def svf_vs_displacement(config: str = "c0", iters: int = 100, steps_list=(6, 8), lams=(0.0, 2.0)) -> dict:
+    """Displacement-field registration (the fused iteration) against the
+    stationary velocity field form (u = exp(v), scaling and squaring and its
+    backward): final objective, error to the true field, folded voxels and
+    time per iteration, at each regulariser weight."""
+    from . import synth
+    from .register import register_svf
+    dev = torch.device("cuda", torch.cuda.current_device())
+    capi.load()
+    c = synth.CONFIGS[config]
+    d = synth.make(config, device=dev)
+    F, M, ut = d["F"].contiguous(), d["M"].contiguous(), d["u_true"]
+    rows = []
+    err = lambda u: float(((u + ut).norm() / ut.norm()).item())  # M = F o (id + u_true): u* ~ -u_true
+    for lam in lams:
+        if c["kind"] == "lncc":
+            cfg = RegConfig(loss="lncc", window=c["window"], eps=LNCC_EPS, lam=lam, lr=0.1)
+        else:
+            cfg = RegConfig(loss="mi", bins=c["bins"], f_range=d["f_range"], m_range=d["m_range"], lam=lam, lr=0.1)
+        r = Registration(F, M, cfg)
+        res = r.run(iters)
+        fin = r.objective()
+        row = {"lam": lam,
+               "displacement": {"L_final": fin["objective"], "sim_final": fin["sim"],
+                                "fold": r.fold_check()["n_fold"], "rel_err": err(r.current),
+                                "ms_per_iter": res.ms_per_iter}, "svf": []}
+        for steps in steps_list:
+            out = register_svf(F, M, cfg, iters, steps=steps)
+            mn, nf = capi.reg_jacdet_min(out["u"])
+            row["svf"].append({"steps": steps, "L_last": float(out["objective"][-1]),
+                               "sim_last": float(out["sim"][-1]), "fold": int(nf.item()),
+                               "min_det": float(mn.item()), "rel_err": err(out["u"]),
+                               "ms_per_iter": out["ms_per_iter"]})
+        rows.append(row)
+    return {"experiment": "svf_vs_displacement", "config": config, "iters": iters, "rows": rows}
+
+
 def eval_init_pairs(net, n_pairs: int = 8, n: int = 128, seed0: int = 90_000, iters: int = 200, window: int = 7,
                     lam: float = 1.0, lr: float = 0.1, rel_tol: float = 0.01) -> dict:
     """Held-out pairs of the training distribution (seeds never used in
@@ -358,6 +395,9 @@ def main():
     afp = sub.add_parser("affine")
     afp.add_argument("--n", type=int, default=192)
     afp.add_argument("--lam", type=float, default=1.0)
+    svp = sub.add_parser("svf")
+    svp.add_argument("--config", default="c0")
+    svp.add_argument("--iters", type=int, default=100)
     rg = sub.add_parser("regularisers")
     rg.add_argument("--config", default="c0")
     rg.add_argument("--iters", type=int, default=50)
@@ -392,6 +432,9 @@ def main():
         return
     if args.cmd == "affine":
         print(json.dumps(affine_pipeline(args.n, lam=args.lam)))
+        return
+    if args.cmd == "svf":
+        print(json.dumps(svf_vs_displacement(args.config, args.iters)))
         return
     if args.cmd == "regularisers":
         print(json.dumps(regularisers(args.config, args.iters, args.n)))

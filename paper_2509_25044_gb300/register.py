@@ -275,3 +275,49 @@ def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40),
         levels.append({"scale": s, "objective": np.asarray(hist)})
     A_full, t_full = affine_about_centre(A, tc, tuple(F.shape))
     return {"A": A_full, "t": t_full, "tc": tc, "levels": levels}
+
+
+def register_svf(F, M, cfg: RegConfig, iters: int, steps: int = 6, v0=None) -> dict:
+    """Diffeomorphic registration on a stationary velocity field v: each
+    iteration forms u = exp(v) by scaling and squaring on the fused sampler
+    (reg_exp_field, keeping the intermediate fields), takes the similarity
+    gradient dC/du (reg_loss_grad), pulls it back through every squaring step
+    (reg_exp_field_backward), adds lam * dR/dv of the diffusion term on v
+    (reg_regularize) and steps v with Adam (reg_step).  Returns v, u = exp(v),
+    the objective history (C(u) + lam R(v)) and the device time per
+    iteration."""
+    F, M = F.contiguous(), M.contiguous()
+    shape = tuple(F.shape)
+    dev = F.device
+    loss = cfg.loss_desc(F)
+    ws = capi.workspace(loss, F)
+    v = [torch.zeros((3,) + shape, device=dev), torch.zeros((3,) + shape, device=dev)]
+    if v0 is not None:
+        v[0].copy_(v0)
+    m = torch.zeros_like(v[0])
+    s2 = torch.zeros_like(v[0])
+    u = torch.empty_like(v[0])
+    gu = torch.empty_like(v[0])
+    gv = torch.empty_like(v[0])
+    tmp = torch.empty_like(v[0])
+    saved = torch.empty((max(steps - 1, 1), 3) + shape, device=dev)
+    adam = capi.adam_desc(cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps, capi.REG_F32, float(F.numel()))
+    sim = torch.zeros((iters, 2), dtype=torch.float64, device=dev)
+    r = torch.zeros((iters, 2), dtype=torch.float64, device=dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for k in range(iters):
+        a, b = v[k % 2], v[(k + 1) % 2]
+        capi.reg_exp_field(a, steps, cfg.pad, out=u, saved=saved)
+        capi.reg_loss_grad(loss, F, M, u, ws, pad=cfg.pad, sim=sim[k], grad=gu)
+        capi.reg_exp_field_backward(a, steps, gu, saved=saved, pad=cfg.pad, gv=gv, tmp=tmp)
+        capi.reg_regularize(a, cfg.lam, ws, r=r[k], grad=gv)
+        capi.reg_step(a, b, m, s2, gv, adam, k + 1)
+    end.record()
+    torch.cuda.synchronize()
+    vf = v[iters % 2]
+    capi.reg_exp_field(vf, steps, cfg.pad, out=u, saved=saved)
+    h, hr = sim.cpu().numpy()[:, 0], r.cpu().numpy()[:, 0]
+    c = 1.0 - h if cfg.loss == "lncc" else -h
+    return {"v": vf, "u": u, "objective": c + cfg.lam * hr, "sim": h,
+            "ms_per_iter": start.elapsed_time(end) / max(iters, 1)}
