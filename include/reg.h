@@ -285,11 +285,15 @@ REG_API reg_status reg_exp_field_backward(const float *v, reg_dims d, int steps,
  * reg_iterate calls on `stream` (same results bit for bit); only the host
  * work between them is gone, which is what bounds small volumes.
  * iters = 0 does nothing; iters < 0 or t0 < 0 is REG_ERR_INVALID_ARG; u_a
- * and u_b must not overlap. */
+ * and u_b must not overlap.
+ * T (optional, NULL = the plain phi = p + u): a composite transform
+ * (reg_affine); the iterations then optimise u under phi = A p + t + S u with
+ * A, t, S fixed -- the loss gradient S dC/dphi, the diffusion term on u and
+ * Adam, fused as in the plain case. */
 REG_API reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, float *u_a,
                            float *u_b, void *m, void *v, reg_dims d, int pad, float lambda,
                            const reg_adam_desc *adam, int t0, int iters, void *ws, size_t ws_bytes,
-                           double *obj_hist, void *stream);
+                           double *obj_hist, const reg_affine *T, void *stream);
 
 /* Fold check of phi = id + u: min over voxels of det(I + grad u) (central
  * differences, one-sided at the border) and the number of voxels with

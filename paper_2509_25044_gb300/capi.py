@@ -122,7 +122,7 @@ def _lib():
         L.reg_exp_field_backward.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
         L.reg_run.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, RegDims,
                               ctypes.c_int, ctypes.c_float, ctypes.POINTER(RegAdamDesc), ctypes.c_int, ctypes.c_int,
-                              _vp, ctypes.c_size_t, _vp, _vp]
+                              _vp, ctypes.c_size_t, _vp, ctypes.POINTER(RegAffine), _vp]
         for name in EXPORTS:
             if name not in ("reg_version", "reg_status_string"):
                 getattr(L, name).restype = _st
@@ -403,7 +403,7 @@ def reg_iterate(loss: RegLossDesc, F, M, u_in, u_out, m, v, lam: float, adam: Re
 
 
 def reg_run(loss: RegLossDesc, F, M, u_a, u_b, m, v, lam: float, adam: RegAdamDesc, t0: int, iters: int, ws,
-            pad: int = REG_PAD_BORDER, obj_hist=None):
+            pad: int = REG_PAD_BORDER, obj_hist=None, affine: RegAffine | None = None):
     """`iters` fused iterations t0+1..t0+iters in one native call; the last
     iterate ends in u_a (iters even) or u_b (odd).  Returns obj_hist
     [iters][2] = {similarity, R} per iteration."""
@@ -415,7 +415,8 @@ def reg_run(loss: RegLossDesc, F, M, u_a, u_b, m, v, lam: float, adam: RegAdamDe
         obj_hist = torch.empty((max(iters, 1), 2), dtype=torch.float64, device=F.device)
     _check(_lib().reg_run(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u_a), _ptr(u_b), _ptr(m), _ptr(v),
                           d, int(pad), float(lam), ctypes.byref(adam), int(t0), int(iters), _ptr(ws), ws.numel(),
-                          _ptr(obj_hist), _stream(F)), "reg_run")
+                          _ptr(obj_hist), ctypes.byref(affine) if affine is not None else None, _stream(F)),
+           "reg_run")
     return obj_hist
 
 

@@ -198,16 +198,17 @@ AffineT to_affine(const reg_affine &T) {
 
 // sweep 1 of either loss: similarity into sim_out (+ LNCC coefficient fields)
 reg_status run_sweep1(const reg_loss_desc *L, const void *F, const void *M, int img_dt, const float *u,
-                      const Dims &g, int pad, const Ws &w, double *sim_out, bool need_grad, cudaStream_t s) {
+                      const Dims &g, int pad, const Ws &w, double *sim_out, bool need_grad, cudaStream_t s,
+                      const AffineT *aff = nullptr) {
     REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
     if (L->kind == REG_LOSS_LNCC) {
         LnccParams P{L->window / 2, L->eps, L->lncc_grad == REG_LNCC_GRAD_ANTS};
-        REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s));
+        REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s, aff));
         REG_CUDA(launch_lncc_stats(F, w.warped, img_dt, g, P, need_grad ? w.coef : nullptr, w.partials,
                                    w.counters + 0, sim_out, s));
     } else {
         const MiParams P = mi_params(L);
-        REG_CUDA(launch_mi_hist(F, M, img_dt, u, g, pad, P, w.hist, s));
+        REG_CUDA(launch_mi_hist(F, M, img_dt, u, g, pad, P, w.hist, s, aff));
         REG_CUDA(launch_mi_finalize(w.hist, P, g.n, w.gtab, sim_out, s));
     }
     return REG_OK;
@@ -316,9 +317,23 @@ reg_status reg_step(const float *u_in, float *u_out, void *m, void *v, const flo
     return cuda_status(launch_adam(u_in, u_out, m, v, adam->moment_dtype, grad_u, 3 * g.n, S, (cudaStream_t)stream));
 }
 
+// one fused iteration; aff: the composite transform (NULL: phi = p + u)
+static reg_status iterate_impl(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                               const float *u_in, float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
+                               const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
+                               float *grad_out, void *stream, const AffineT *aff);
+
 reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u_in,
                        float *u_out, void *m, void *v, reg_dims d, int pad, float lambda, const reg_adam_desc *adam,
                        int t, void *ws, size_t ws_bytes, double *obj_out, float *grad_out, void *stream) {
+    return iterate_impl(loss, F, M, img_dt, u_in, u_out, m, v, d, pad, lambda, adam, t, ws, ws_bytes, obj_out,
+                        grad_out, stream, nullptr);
+}
+
+static reg_status iterate_impl(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                               const float *u_in, float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
+                               const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
+                               float *grad_out, void *stream, const AffineT *aff) {
     REG_TRY(check_common(loss, F, M, img_dt, u_in, d, pad, ws, ws_bytes));
     REG_TRY(check_adam(adam, t));
     if (!isfinite(lambda)) return REG_ERR_INVALID_ARG;
@@ -336,16 +351,16 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
     const Ws w = carve(ws, g, loss);
     const cudaStream_t s = (cudaStream_t)stream;
     REG_CUDA(mark(0, s));
-    REG_TRY(run_sweep1(loss, F, M, img_dt, u_in, g, pad, w, obj_out, true, s));
+    REG_TRY(run_sweep1(loss, F, M, img_dt, u_in, g, pad, w, obj_out, true, s, aff));
     REG_CUDA(mark(1, s));
     const StepParams S = step_params(adam, t, lambda, g);
     if (loss->kind == REG_LOSS_LNCC) {
         LnccParams P{loss->window / 2, loss->eps, loss->lncc_grad == REG_LNCC_GRAD_ANTS};
         REG_CUDA(launch_lncc_sweep2(F, M, img_dt, u_in, g, pad, P, w.coef, grad_out, true, u_out, m, v,
-                                    adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s));
+                                    adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s, aff));
     } else {
         REG_CUDA(launch_mi_sweep2(F, M, img_dt, u_in, g, pad, mi_params(loss), w.gtab, grad_out, true, u_out, m, v,
-                                  adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s));
+                                  adam->moment_dtype, S, w.partials, w.counters + 1, obj_out + 1, s, aff));
     }
     REG_CUDA(mark(2, s));
     t_events_armed = false;
@@ -354,9 +369,12 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
 
 reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, float *u_a, float *u_b,
                    void *m, void *v, reg_dims d, int pad, float lambda, const reg_adam_desc *adam, int t0, int iters,
-                   void *ws, size_t ws_bytes, double *obj_hist, void *stream) {
+                   void *ws, size_t ws_bytes, double *obj_hist, const reg_affine *T, void *stream) {
     if (iters < 0 || t0 < 0 || (long long)t0 + iters > INT_MAX) return REG_ERR_INVALID_ARG;
+    if (T && !affine_ok(T)) return REG_ERR_INVALID_ARG;
     if (iters == 0) return REG_OK;
+    AffineT A;
+    if (T) A = to_affine(*T);
     // validate once (the per-iteration calls repeat the same checks, which
     // cost nothing next to a launch)
     REG_TRY(check_common(loss, F, M, img_dt, u_a, d, pad, ws, ws_bytes));
@@ -368,8 +386,8 @@ reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int 
     reg_status st = REG_OK;
     for (int k = 0; k < iters && st == REG_OK; ++k) {
         float *a = (k % 2) ? u_b : u_a, *b = (k % 2) ? u_a : u_b;
-        st = reg_iterate(loss, F, M, img_dt, a, b, m, v, d, pad, lambda, adam, t0 + k + 1, ws, ws_bytes,
-                         obj_hist + 2 * (size_t)k, nullptr, stream);
+        st = iterate_impl(loss, F, M, img_dt, a, b, m, v, d, pad, lambda, adam, t0 + k + 1, ws, ws_bytes,
+                          obj_hist + 2 * (size_t)k, nullptr, stream, T ? &A : nullptr);
     }
     t_events_armed = armed;
     return st;

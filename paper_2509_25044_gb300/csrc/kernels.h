@@ -126,8 +126,9 @@ __host__ __device__ inline const float4 *mi_table4(const float *Gtab) {
 cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P, long long N, float *Gtab,
                                double *sim_out, cudaStream_t s);
 // Second MI sweep: adjoint (+ optional diffusion + Adam).  With aff (the
-// composite transform; step must be false, u and grad_out may be NULL):
-// grad_out = S gX and r_out[12] = dC/dA, dC/dt from 12 partials per block.
+// composite transform): without the step (u and grad_out may be NULL)
+// grad_out = S gX and r_out[12] = dC/dA, dC/dt from 12 partials per block;
+// with it, dC/du = S gX feeds the diffusion + Adam update of u.
 cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                              const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                              void *m, void *v, int mdt, const StepParams &S, double *partials,

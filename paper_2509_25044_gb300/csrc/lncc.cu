@@ -305,8 +305,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
     }
 }
 
-// AFF: the composite transform (STEP false; u and grad_out may be NULL);
-// grad_out = S gX and r_out[12] = dC/dA, dC/dt.
+// AFF: the composite transform phi = A p + t + S u.  Without STEP (u and
+// grad_out may be NULL): grad_out = S gX and r_out[12] = dC/dA, dC/dt.  With
+// STEP: dC/du = S gX enters the diffusion + Adam update of u as usual.
 template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
 __global__ void __launch_bounds__(TILE_THREADS)
     lncc_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
@@ -314,7 +315,6 @@ __global__ void __launch_bounds__(TILE_THREADS)
                        float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                        double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
                        unsigned *err, AffineT A) {
-    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     extern __shared__ float smem[];
     __shared__ double red[32];
     const int r = P.r;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 diffusion_ptr<I>(uc, p, nx, hxm, hxp, hym, hyp, zo > 0, zo + 1 < g.nz, cur, prv, nxt, gR, rpart);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], AFF ? A.s[c] * gs[c] : gs[c]);
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
                     (u_out + c * g.n)[p] =
                         adam_fast(cur[c], gt, ld_moment(mc[c], p), ld_moment(vc[c], p), mc[c], vc[c], p, S);
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
     }
-    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
+    if (AFF && !STEP) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -453,7 +453,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                             float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                             double *__restrict__ partials, unsigned *__restrict__ counter,
                             double *__restrict__ r_out, unsigned *err, AffineT A) {
-    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     __shared__ double red[32];
     const int r = P.r;
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -518,7 +517,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                 diffusion_ptr<I>(uc, p, nx, hxm, hxp, hym, hyp, z > 0, z + 1 < g.nz, cur, prv, nxt, gR, rpart);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], AFF ? A.s[c] * gs[c] : gs[c]);
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
                     (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
                 }
@@ -543,7 +542,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
             }
         }
     }
-    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
+    if (AFF && !STEP) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -679,10 +678,19 @@ static cudaError_t launch_lncc_sweep2_ants(const void *F, const void *M, int dt,
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
-            if (aff) {  // the composite form: gradients only, 64-bit offsets
+            if (aff && !step) {  // the composite form: gradients only, 64-bit offsets
                 lncc_sweep2_ants_kernel<T, float, false, PD, long long, true><<<grid, block, 0, s>>>(
                     (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, nullptr, nullptr, nullptr, S,
                     partials, counter, r_out, err, A);
+                return;
+            }
+            if (aff) {  // the composite form with the step
+                with_type(mdt, [&](auto mp) {
+                    using MT = elem_t<decltype(mp)>;
+                    lncc_sweep2_ants_kernel<T, MT, true, PD, long long, true><<<grid, block, 0, s>>>(
+                        (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
+                        partials, counter, r_out, err, A);
+                });
                 return;
             }
             with_index(g, [&](auto ip) {
@@ -724,12 +732,23 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
-            if (aff) {  // the composite form: gradients only, 64-bit offsets
+            if (aff && !step) {  // the composite form: gradients only, 64-bit offsets
                 e = prepare_march(lncc_sweep2_kernel<T, float, false, PD, long long, true>, smem, g, P.r, G, grid);
                 if (e == cudaSuccess)
                     lncc_sweep2_kernel<T, float, false, PD, long long, true><<<grid, block, smem, s>>>(
                         (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, nullptr, nullptr, nullptr, S,
                         partials, counter, r_out, err, A);
+                return;
+            }
+            if (aff) {  // the composite form with the step
+                with_type(mdt, [&](auto mp) {
+                    using MT = elem_t<decltype(mp)>;
+                    e = prepare_march(lncc_sweep2_kernel<T, MT, true, PD, long long, true>, smem, g, P.r, G, grid);
+                    if (e == cudaSuccess)
+                        lncc_sweep2_kernel<T, MT, true, PD, long long, true><<<grid, block, smem, s>>>(
+                            (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m, (MT *)v, S,
+                            partials, counter, r_out, err, A);
+                });
                 return;
             }
             with_index(g, [&](auto ip) {

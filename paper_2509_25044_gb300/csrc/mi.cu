@@ -234,8 +234,9 @@ __global__ void __launch_bounds__(1024) mi_finalize_kernel(const unsigned long l
     }
 }
 
-// AFF: the composite transform (STEP false; u and grad_out may be NULL);
-// grad_out = S gX and r_out[12] = dC/dA, dC/dt.
+// AFF: the composite transform phi = A p + t + S u.  Without STEP (u and
+// grad_out may be NULL): grad_out = S gX and r_out[12] = dC/dA, dC/dt.  With
+// STEP: dC/du = S gX enters the diffusion + Adam update of u as usual.
 template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
 __global__ void __launch_bounds__(TILE_THREADS, 4)
     mi_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
@@ -243,7 +244,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                      double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
                      unsigned *err, AffineT A) {
-    static_assert(!(AFF && STEP), "the composite sweep computes gradients only");
     // G4[m][n] = G'[m][n .. n+3]: one 16-byte shared load per kernel row
     extern __shared__ float4 G4[];  // B * B entries (dynamic)
     __shared__ double red[32];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                 diffusion_ptr<I>(uc, p, nx, hxm, hxp, hym, hyp, z > 0, z + 1 < g.nz, cur, prv, nxt, gR, rpart);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], gs[c]);
+                    const float gt = fmaf(S.lam * S.two_over_n, gR[c], AFF ? A.s[c] * gs[c] : gs[c]);
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
                     (u_out + c * g.n)[p] = adam_fast(cur[c], gt, mcur[c], vcur[c], mc[c], vc[c], p, S);
                 }
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
             }
         }
     }
-    if (AFF) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
+    if (AFF && !STEP) affine_reduce(aacc, x, y, partials, counter, r_out, red, err);
     if (STEP) {
         const double bs = block_sum((double)rpart, red);
         const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -438,11 +438,21 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {
             constexpr int PD = decltype(pd)::value;
-            if (aff) {  // the composite form: gradients only, 64-bit offsets
+            if (aff && !step) {  // the composite form: gradients only, 64-bit offsets
                 if (prepare(mi_sweep2_kernel<T, float, false, PD, long long, true>))
                     mi_sweep2_kernel<T, float, false, PD, long long, true><<<grid, block, smem, s>>>(
                         (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, nullptr, nullptr, nullptr, S,
                         partials, counter, r_out, err, A);
+                return;
+            }
+            if (aff) {  // the composite form with the step
+                with_type(mdt, [&](auto mp) {
+                    using MT = elem_t<decltype(mp)>;
+                    if (prepare(mi_sweep2_kernel<T, MT, true, PD, long long, true>))
+                        mi_sweep2_kernel<T, MT, true, PD, long long, true><<<grid, block, smem, s>>>(
+                            (const T *)F, (const T *)M, u, g, P, G.zc, Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
+                            partials, counter, r_out, err, A);
+                });
                 return;
             }
             with_index(g, [&](auto ip) {

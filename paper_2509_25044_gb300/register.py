@@ -61,9 +61,9 @@ class Registration:
     def __init__(self, F: torch.Tensor, M: torch.Tensor, cfg: RegConfig, u0: torch.Tensor | None = None,
                  affine=None):
         """affine: an optional capi.RegAffine; the deformable field is then
-        optimised under the composite transform phi = A p + t + S u (loss
-        gradient from reg_loss_grad_composite, then the diffusion gradient and
-        Adam as separate launches)."""
+        optimised under the composite transform phi = A p + t + S u (the fused
+        iteration of reg_run; with the smoothing regulariser the composite
+        loss gradient, the smoothing and Adam run as separate launches)."""
         if F.device.type != "cuda":
             raise ValueError("F and M must be CUDA tensors")
         self.F, self.M, self.cfg = F.contiguous(), M.contiguous(), cfg
@@ -83,7 +83,7 @@ class Registration:
         self.t = 0
         self.affine = affine
         self.smoothing = cfg.sigma_grad > 0.0 or cfg.sigma_warp > 0.0
-        self.unfused = self.smoothing or affine is not None
+        self.unfused = self.smoothing
         if self.unfused:
             self.g = torch.empty_like(self.u[0])
             self.tmp = torch.empty_like(self.u[0])
@@ -103,7 +103,7 @@ class Registration:
             # one native call runs all iterations (no host work between them)
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]
             capi.reg_run(self.loss, self.F, self.M, a, b, self.m, self.v, self.cfg.lam, self.adam, self.t, iters,
-                         self.ws, pad=self.cfg.pad, obj_hist=hist)
+                         self.ws, pad=self.cfg.pad, obj_hist=hist, affine=self.affine)
             self.t += iters
         for k in range(iters if self.unfused else 0):
             a, b = self.u[self.t % 2], self.u[(self.t + 1) % 2]

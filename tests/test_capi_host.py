@@ -119,12 +119,16 @@ def test_loss_and_iterate_validation(capi):
     # multi-iteration run: negative counts, overlapping ping-pong buffers; 0 iterations is a no-op
     def run(t0, iters, ub=FAKE << 8):
         return L.reg_run(ctypes.byref(lncc), vp(FAKE), vp(FAKE), 0, vp(FAKE), vp(ub), vp(FAKE), vp(FAKE), dims(), 0,
-                         0.1, ctypes.byref(adam), t0, iters, vp(FAKE), need, vp(FAKE), None)
+                         0.1, ctypes.byref(adam), t0, iters, vp(FAKE), need, vp(FAKE), T, None)
+    T = None
     assert run(0, -1) == 1
     assert run(-1, 5) == 1
     assert run(2 ** 31 - 3, 5) == 1
     assert run(0, 0) == 0
     assert run(0, 3, ub=FAKE + 256) == 1
+    T = ctypes.byref(capi.affine_desc(t=(float("inf"), 0.0, 0.0)))  # a non-finite transform
+    assert run(0, 3) == 1
+    T = None
     badadam = capi.adam_desc(0.1, beta1=1.0)
     assert L.reg_step(vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), vp(FAKE), dims(), ctypes.byref(badadam), 1,
                       None) == 1

@@ -251,3 +251,44 @@ def test_exp_backward_matches_oracle(capi, steps, pad):
     ref = O.exp_field_backward(to64(v), steps, to64(gout), pad)
     assert rel_l2(to64(gv), ref) <= 1e-4
     assert capi.reg_get_device_error() == 0
+
+
+@pytest.mark.parametrize("kind", ["lncc", "lncc_ants", "mi", "mi_hard"])
+def test_run_under_composite_transform_matches_oracle(capi, kind):
+    """reg_run with a composite transform (the fused iteration optimising u
+    under phi = A p + t + S u): the objective history is the oracle's
+    composite similarity and R(u), and the step is Adam on the oracle's
+    gradient S dC/dphi + lam dR/du."""
+    shape = (16, 18, 40)
+    F, M = (mono_images if kind.startswith("lncc") else multimodal_images)(shape, 71)
+    u = field(shape, 3.0, 1.0, 72)
+    A, t, s = _affine(shape, 73, s=(1.0, 1.1, 0.9))
+    loss, spec = _loss(capi, kind, F, M)
+    N = F.numel()
+    gen = torch.Generator().manual_seed(74)
+    m0 = torch.randn((3,) + shape, generator=gen) * 1e-2
+    v0 = m0 ** 2 + torch.rand((3,) + shape, generator=gen) * 1e-4
+    lam, lr = 0.5, 0.1
+    ud, m, v = u.to(DEV), m0.to(DEV), v0.to(DEV)
+    ub = torch.empty_like(ud)
+    adam = capi.adam_desc(lr, grad_scale=float(N))
+    ws = capi.workspace(loss, F.to(DEV))
+    hist = capi.reg_run(loss, F.to(DEV), M.to(DEV), ud, ub, m, v, lam, adam, 2, 1, ws,
+                        affine=_desc(capi, A, t, s)).cpu().numpy()
+    Sr, gur, _, _ = O.similarity_and_grad_composite(to64(F), to64(M), A, t, s, to64(u), spec)
+    R, gR = O.diffusion(to64(u))
+    assert_rel(hist[0, 0], Sr, LOSS_RTOL, "similarity")
+    assert_rel(hist[0, 1], R, 1e-6, "R")
+    ur, _, _ = O.adam(to64(u), to64(m0), to64(v0), gur + lam * gR, 3, lr, grad_scale=N)
+    assert rel_l2(to64(ub) - to64(u), ur - to64(u)) <= 1e-3
+    # the identity transform is the plain fused iteration
+    u1, u2 = torch.empty_like(ud), torch.empty_like(ud)
+    for T, out in ((capi.affine_desc(), u1), (None, u2)):
+        mm, vv = m0.to(DEV), v0.to(DEV)
+        capi.reg_run(loss, F.to(DEV), M.to(DEV), ud, out, mm, vv, lam, adam, 2, 1, ws, affine=T)
+    torch.cuda.synchronize()
+    if kind == "lncc":
+        assert rel_l2(to64(u1) - to64(u), to64(u2) - to64(u)) <= 1e-5
+    else:
+        assert torch.equal(u1, u2)
+    assert capi.reg_get_device_error() == 0
