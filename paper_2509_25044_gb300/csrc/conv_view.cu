@@ -231,10 +231,12 @@ void n_blocks(int N, int &Nb, int &nblocks) {
 
 size_t view_smem_bytes(const ViewGeom &G) { return 2 * (size_t)G.VGB + G.wbytes + 64 + 1024; }
 
-// Tile choice: the largest useful fraction of computed GEMM rows (valid
-// outputs / (MT * 128)), then the fewest brick rows per output row, under
-// 2 CTAs per SM of shared memory (<= 113 KB) and tensor memory (<= 256
-// columns); 1 CTA per SM is the fallback.
+// Tile choice: the largest useful fraction of the GEMM rows the whole launch
+// occupies -- valid outputs / (waves x resident CTAs x MT x 128), so that a
+// last wave that leaves most SMs idle counts against a tile -- then the
+// fewest brick rows per output row, under 2 CTAs per SM of shared memory
+// (<= 113 KB) and tensor memory (<= 256 columns); 1 CTA per SM is the
+// fallback.
 bool choose_geom(const Dims &d, int Cin, int Cout, int N, float slope, ViewGeom &G) {
     if (Cin % VIEW_CK || Cin < VIEW_CK || d.nx + 2 > 256) return false;
     G.nx = d.nx;
@@ -273,10 +275,12 @@ bool choose_geom(const Dims &d, int Cin, int Cout, int N, float slope, ViewGeom 
                 g.VGB = (need * 16 + 1023) / 1024 * 1024;
                 if (view_smem_bytes(g) > smem_cap) continue;
                 const int ty_tiles = (d.ny + Ty - 1) / Ty, tz_tiles = (d.nz + Tz - 1) / Tz;
-                const double valid = (double)d.nx * d.ny * d.nz / ((double)ty_tiles * tz_tiles);
-                const double eff = valid / (g.MT * 128.0);
+                const long long slots = (long long)(pass == 0 ? 2 : 1) * num_sms();
+                const long long ctas = (long long)ty_tiles * tz_tiles * nblocks;
+                const long long waves = (ctas + slots - 1) / slots;
+                const double eff = (double)d.nx * d.ny * d.nz * nblocks / ((double)waves * slots * g.MT * 128.0);
                 const double reuse = (double)(g.By * g.Bz) / (double)(Ty * Tz);
-                const double score = eff - 0.01 * reuse;
+                const double score = eff / (1.0 + 0.01 * reuse);
                 if (score > best) {
                     best = score;
                     bestG = g;
