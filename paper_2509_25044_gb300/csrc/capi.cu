@@ -70,7 +70,7 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
     const long long mi = mi_sweep_grid(g).blocks();
     if (mi > nb) nb = mi;
     if (L && L->kind == REG_LOSS_LNCC) {
-        const long long ln = lncc_grid(g, L->window / 2).blocks();
+        const long long ln = lncc_max_blocks(g);
         if (ln > nb) nb = ln;
     }
     return nb;

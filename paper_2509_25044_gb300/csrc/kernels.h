@@ -88,10 +88,11 @@ struct LnccParams {
 
 // per-kernel grids (used both to launch and to size the workspace)
 MarchGrid mi_sweep_grid(const Dims &g);
-// LNCC window-march grid for a kernel with per_sm CTAs resident per SM (the
-// default, 8 = 2048 threads / 256, bounds every kernel: workspace sizing)
-constexpr int LNCC_MAX_PER_SM = 8;
-MarchGrid lncc_grid(const Dims &g, int r, int per_sm = LNCC_MAX_PER_SM);
+// LNCC window-march grid for a kernel with per_sm CTAs resident per SM, and
+// the most blocks it can have for any residency (workspace sizing)
+constexpr int LNCC_MAX_PER_SM = 8;  // 2048 threads / 256
+MarchGrid lncc_grid(const Dims &g, int r, int per_sm);
+long long lncc_max_blocks(const Dims &g);
 MarchGrid lncc_ants_grid(const Dims &g);
 MarchGrid diffusion_grid(const Dims &g);
 

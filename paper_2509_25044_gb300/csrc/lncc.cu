@@ -28,6 +28,7 @@
 //   fields (exact adjoint, not the ANTs shortcut), then dL/dJ, chained
 //   through the sampler slope to dL/du, optionally fused with the diffusion
 //   gradient and the Adam step.
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.h"
@@ -563,21 +564,35 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
 }
 
 // Every CTA marches zc + 2r planes (its chunk plus the window's warm-up), one
-// plane after the other.  A volume with enough tiles x long chunks (32 planes,
-// or 8r) to give every SM several CTAs keeps them: the warm-up costs at most
-// 2r / 32 of the traffic.  A smaller one would leave the GPU waiting on a few
-// long serial marches, so its z range is cut into as many chunks as one wave
-// of resident CTAs holds (chunk time shrinks with zc; a second wave would add
-// another 2r warm-up planes), down to 2 planes per chunk.
+// plane after the other, so the launch takes about
+//     waves x (zc + 2r)   plane steps,   waves = ceil(tiles x chunks / resident CTAs).
+// The chunk count minimises that (the fewest chunks on ties: less warm-up
+// traffic).  A small volume gets as many chunks as one wave holds; a large one
+// long chunks, cut so that the last wave is not left mostly idle.  At most
+// LNCC_MAX_CHUNKS chunks, at least 2 planes each.
+constexpr long long LNCC_MAX_CHUNKS = 64;
+static long long lncc_chunk_cap(const Dims &g) {
+    const long long half = (g.nz + 1) / 2;
+    return std::max(1LL, std::min(LNCC_MAX_CHUNKS, half));
+}
 MarchGrid lncc_grid(const Dims &g, int r, int per_sm) {
-    const long long target = 12LL * num_sms();
-    const int long_zc = 8 * r > 32 ? 8 * r : 32;
     const long long tiles = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    const long long long_chunks = (g.nz + long_zc - 1) / long_zc;
-    if (tiles * long_chunks >= target) return march_grid(g, target, long_zc);
-    long long chunks = (long long)per_sm * num_sms() / tiles;
-    if (chunks < long_chunks) chunks = long_chunks;
-    return march_grid(g, chunks * tiles, 2);
+    const long long slots = (long long)per_sm * num_sms();
+    long long best_c = 1, best = -1;
+    for (long long c = 1; c <= lncc_chunk_cap(g); ++c) {
+        const long long zc = (g.nz + c - 1) / c, chunks = (g.nz + zc - 1) / zc;
+        const long long waves = (tiles * chunks + slots - 1) / slots;
+        const long long cost = waves * (zc + 2 * r);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_c = c;
+        }
+    }
+    return march_grid(g, best_c * tiles, 1);
+}
+long long lncc_max_blocks(const Dims &g) {
+    const long long tiles = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    return tiles * lncc_chunk_cap(g);
 }
 
 // CTAs of `kernel` (TILE_THREADS threads, `smem` dynamic bytes) resident per
