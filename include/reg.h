@@ -141,8 +141,10 @@ REG_API int reg_version(void);
 REG_API const char *reg_status_string(reg_status s);
 
 /* Bytes of device workspace that reg_loss, reg_loss_grad, reg_regularize,
- * reg_iterate and reg_jacdet_min need for these dims (loss may be NULL for
- * the regulariser / det J alone).  *bytes is a HOST pointer. */
+ * reg_iterate, reg_run and reg_jacdet_min need for these dims (loss may be
+ * NULL for the regulariser / det J alone; LNCC adds 24 bytes per voxel: the
+ * warped image, three adjoint coefficient fields and F's window mean and
+ * variance).  *bytes is a HOST pointer. */
 REG_API reg_status reg_workspace_size(const reg_loss_desc *loss, reg_dims d, size_t *bytes);
 
 /* J = M o (id + u): trilinear warp of M (img_dt) by u (Sec. 2.1, the
@@ -282,8 +284,12 @@ REG_API reg_status reg_exp_field_backward(const float *v, reg_dims d, int steps,
  * the last iterate is in u_a when iters is even and in u_b when it is odd.
  * obj_hist: device double[2 * iters]; entry 2k, 2k + 1 = {similarity,
  * R} at iteration k's input.  The launches are those of `iters`
- * reg_iterate calls on `stream` (same results bit for bit); only the host
- * work between them is gone, which is what bounds small volumes.
+ * reg_iterate calls on `stream` (MI: the same results bit for bit); only the
+ * host work between them is gone, which is what bounds small volumes.  LNCC:
+ * F does not change during the call, so the window mean and variance of F
+ * are formed once, before the first iteration, and every iteration's window
+ * statistics box-sum only J, J^2 and FJ (the results then differ from
+ * reg_iterate's in the last bits).
  * iters = 0 does nothing; iters < 0 or t0 < 0 is REG_ERR_INVALID_ARG; u_a
  * and u_b must not overlap.
  * T (optional, NULL = the plain phi = p + u): a composite transform

@@ -79,7 +79,8 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
 size_t workspace_bytes(const Dims &g, const reg_loss_desc *L) {
     size_t bytes = align256(WS_PARTIALS + sizeof(double) * PARTIALS_PER_BLOCK * (size_t)max_partial_blocks(g, L));
     // LNCC: three coefficient fields and the warped image
-    if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 4 * (size_t)g.n);
+    // LNCC: three coefficient fields, the warped image, F's window mean and variance
+    if (L && L->kind == REG_LOSS_LNCC) bytes = align256(bytes + sizeof(float) * 6 * (size_t)g.n);
     return bytes;
 }
 
@@ -91,6 +92,7 @@ struct Ws {
     double *partials;
     float *coef;   // LNCC: [3][N] adjoint coefficients
     float *warped; // LNCC: [N] warped moving image
+    float *fstat;  // LNCC: [2][N] window mean and variance of F (formed once per reg_run)
 };
 
 Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
@@ -104,6 +106,7 @@ Ws carve(void *ws, const Dims &g, const reg_loss_desc *L) {
     w.coef = (float *)(b + align256(WS_PARTIALS + sizeof(double) * PARTIALS_PER_BLOCK *
                                                (size_t)max_partial_blocks(g, L)));
     w.warped = w.coef + 3 * (size_t)g.n;
+    w.fstat = w.warped + (size_t)g.n;
     return w;
 }
 
@@ -162,6 +165,13 @@ reg_status check_ptr(const void *p) {
 }
 reg_status check_opt_ptr(const void *p) { return p ? check_ptr(p) : REG_OK; }
 
+// whether two [3][n] FP32 fields share any byte
+bool overlap3(const float *a, const float *b, long long n) {
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + sizeof(float) * 3 * (size_t)n;
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + sizeof(float) * 3 * (size_t)n;
+    return a0 < b1 && b0 < a1;
+}
+
 reg_status check_common(const reg_loss_desc *L, const void *F, const void *M, int img_dt, const float *u,
                         reg_dims d, int pad, void *ws, size_t ws_bytes) {
     REG_TRY(check_dims(d));
@@ -199,13 +209,13 @@ AffineT to_affine(const reg_affine &T) {
 // sweep 1 of either loss: similarity into sim_out (+ LNCC coefficient fields)
 reg_status run_sweep1(const reg_loss_desc *L, const void *F, const void *M, int img_dt, const float *u,
                       const Dims &g, int pad, const Ws &w, double *sim_out, bool need_grad, cudaStream_t s,
-                      const AffineT *aff = nullptr) {
+                      const AffineT *aff = nullptr, const float *fstat = nullptr) {
     REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
     if (L->kind == REG_LOSS_LNCC) {
         LnccParams P{L->window / 2, L->eps, L->lncc_grad == REG_LNCC_GRAD_ANTS};
         REG_CUDA(launch_warp(M, img_dt, u, g, pad, w.warped, nullptr, s, aff));
         REG_CUDA(launch_lncc_stats(F, w.warped, img_dt, g, P, need_grad ? w.coef : nullptr, w.partials,
-                                   w.counters + 0, sim_out, s));
+                                   w.counters + 0, sim_out, s, fstat));
     } else {
         const MiParams P = mi_params(L);
         REG_CUDA(launch_mi_hist(F, M, img_dt, u, g, pad, P, w.hist, s, aff));
@@ -317,11 +327,12 @@ reg_status reg_step(const float *u_in, float *u_out, void *m, void *v, const flo
     return cuda_status(launch_adam(u_in, u_out, m, v, adam->moment_dtype, grad_u, 3 * g.n, S, (cudaStream_t)stream));
 }
 
-// one fused iteration; aff: the composite transform (NULL: phi = p + u)
+// one fused iteration; aff: the composite transform (NULL: phi = p + u);
+// fcached: F's LNCC window statistics are already in the workspace
 static reg_status iterate_impl(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
                                const float *u_in, float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
                                const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
-                               float *grad_out, void *stream, const AffineT *aff);
+                               float *grad_out, void *stream, const AffineT *aff, bool fcached = false);
 
 reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u_in,
                        float *u_out, void *m, void *v, reg_dims d, int pad, float lambda, const reg_adam_desc *adam,
@@ -333,7 +344,7 @@ reg_status reg_iterate(const reg_loss_desc *loss, const void *F, const void *M, 
 static reg_status iterate_impl(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
                                const float *u_in, float *u_out, void *m, void *v, reg_dims d, int pad, float lambda,
                                const reg_adam_desc *adam, int t, void *ws, size_t ws_bytes, double *obj_out,
-                               float *grad_out, void *stream, const AffineT *aff) {
+                               float *grad_out, void *stream, const AffineT *aff, bool fcached) {
     REG_TRY(check_common(loss, F, M, img_dt, u_in, d, pad, ws, ws_bytes));
     REG_TRY(check_adam(adam, t));
     if (!isfinite(lambda)) return REG_ERR_INVALID_ARG;
@@ -351,7 +362,7 @@ static reg_status iterate_impl(const reg_loss_desc *loss, const void *F, const v
     const Ws w = carve(ws, g, loss);
     const cudaStream_t s = (cudaStream_t)stream;
     REG_CUDA(mark(0, s));
-    REG_TRY(run_sweep1(loss, F, M, img_dt, u_in, g, pad, w, obj_out, true, s, aff));
+    REG_TRY(run_sweep1(loss, F, M, img_dt, u_in, g, pad, w, obj_out, true, s, aff, fcached ? w.fstat : nullptr));
     REG_CUDA(mark(1, s));
     const StepParams S = step_params(adam, t, lambda, g);
     if (loss->kind == REG_LOSS_LNCC) {
@@ -381,13 +392,27 @@ reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int 
     REG_TRY(check_adam(adam, t0 + 1));
     REG_TRY(check_ptr(u_b));
     REG_TRY(check_ptr(obj_hist));
+    // everything the iterations check, before the first launch
+    if (!isfinite(lambda)) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(m));
+    REG_TRY(check_ptr(v));
+    if (overlap3(u_a, u_b, make_dims(d).n)) return REG_ERR_INVALID_ARG;
     const bool armed = t_events_armed;
     t_events_armed = false;  // the timing hook belongs to single reg_iterate calls
+    // LNCC: F is fixed for the whole run, so its window mean and variance are
+    // formed once here and every iteration box-sums only (J, J^2, FJ)
+    const bool fcached = loss->kind == REG_LOSS_LNCC;
+    if (fcached) {
+        const Dims g = make_dims(d);
+        const Ws w = carve(ws, g, loss);
+        const LnccParams P{loss->window / 2, loss->eps, loss->lncc_grad == REG_LNCC_GRAD_ANTS};
+        REG_CUDA(launch_lncc_fstats(F, img_dt, g, P, w.fstat, (cudaStream_t)stream));
+    }
     reg_status st = REG_OK;
     for (int k = 0; k < iters && st == REG_OK; ++k) {
         float *a = (k % 2) ? u_b : u_a, *b = (k % 2) ? u_a : u_b;
         st = iterate_impl(loss, F, M, img_dt, a, b, m, v, d, pad, lambda, adam, t0 + k + 1, ws, ws_bytes,
-                          obj_hist + 2 * (size_t)k, nullptr, stream, T ? &A : nullptr);
+                          obj_hist + 2 * (size_t)k, nullptr, stream, T ? &A : nullptr, fcached);
     }
     t_events_armed = armed;
     return st;
@@ -472,12 +497,6 @@ reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, con
                                       REG_F32, S, w.partials, w.counters + 2, aout, s, &A));
     }
     return REG_OK;
-}
-
-static bool overlap3(const float *a, const float *b, long long n) {
-    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + sizeof(float) * 3 * (size_t)n;
-    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + sizeof(float) * 3 * (size_t)n;
-    return a0 < b1 && b0 < a1;
 }
 
 reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pad, float *w, void *stream) {

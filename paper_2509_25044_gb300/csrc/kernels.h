@@ -137,8 +137,15 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
 
 // First LNCC sweep: window statistics of F and the warped image J (already
 // in HBM, FP32) -> similarity (+ optional adjoint coefficient fields, [3][N]).
+// fstat (optional): F's window mean and variance ([2][N]) from
+// launch_lncc_fstats, so that only the three sums involving J are formed
 cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims &g, const LnccParams &P, float *coef,
-                              double *partials, unsigned *counter, double *sim_out, cudaStream_t s);
+                              double *partials, unsigned *counter, double *sim_out, cudaStream_t s,
+                              const float *fstat = nullptr);
+// F's window mean and variance (fstat [2][N]): F is fixed during a
+// registration, so a run of iterations forms them once
+cudaError_t launch_lncc_fstats(const void *F, int dt, const Dims &g, const LnccParams &P, float *fstat,
+                               cudaStream_t s);
 // Second LNCC sweep: box sums of the coefficient fields -> adjoint (+ optional
 // diffusion + Adam).  aff as for launch_mi_sweep2.
 cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,

@@ -181,16 +181,30 @@ __device__ __forceinline__ Stage<I> make_stage(const LnccSmem &L, int r, int x0,
     return S;
 }
 
-template <typename T, bool COEF, typename I, int NY>
-__global__ void __launch_bounds__(TILE_THREADS, 3)
+// MODE: LNCC_FULL forms the five box sums of (F, J, F^2, J^2, FJ).
+// LNCC_FCACHED forms the three of (J, J^2, FJ) and reads the window mean and
+// variance of F from fstat ([2][N]; F is fixed during a registration, so they
+// are formed once per run).  LNCC_FSTATS forms the two of (F, F^2) and writes
+// that mean and variance to fstat (no J, no similarity).
+constexpr int LNCC_FULL = 0, LNCC_FCACHED = 1, LNCC_FSTATS = 2;
+template <int MODE>
+__host__ __device__ constexpr int lncc_stats_k() {
+    return MODE == LNCC_FULL ? 5 : (MODE == LNCC_FCACHED ? 3 : 2);
+}
+
+// (the three- and two-sum modes fit 4 CTAs per SM in 64 registers)
+template <typename T, bool COEF, typename I, int NY, int MODE = LNCC_FULL>
+__global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
     lncc_stats_kernel(const T *__restrict__ F, const float *__restrict__ J, Dims g, LnccParams P, int zc,
-                      float *__restrict__ coef, double *__restrict__ partials, unsigned *__restrict__ counter,
-                      double *__restrict__ sim_out, unsigned *err) {
+                      float *__restrict__ coef, float *__restrict__ fstat, double *__restrict__ partials,
+                      unsigned *__restrict__ counter, double *__restrict__ sim_out, unsigned *err) {
+    constexpr int K = lncc_stats_k<MODE>();
+    constexpr bool HAS_J = MODE != LNCC_FSTATS;
     extern __shared__ float smem[];
     __shared__ double red[32];
     __shared__ float shift[2];
     const int r = P.r;
-    const LnccSmem L(r, 5);
+    const LnccSmem L(r, K);
     float *st = smem;
     float *hx = st + L.stage_words();
     float *ring = hx + L.hx_words();
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
         const int cx = min(x0 + TX / 2, g.nx - 1), cy = min(y0 + TY / 2, g.ny - 1), cz = min(z0 + zc / 2, g.nz - 1);
         const I pc = (I)cz * nxy + (I)cy * g.nx + cx;
         shift[0] = ld_vox(F, pc);
-        shift[1] = __ldg(J + pc);
+        shift[1] = HAS_J ? __ldg(J + pc) : 0.0f;
     }
     for (int i = tid; i < L.ring_words(); i += TILE_THREADS) ring[i] = 0.0f;
     __syncthreads();
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
     const float cxy = active ? (float)(win_count(x, r, g.nx) * win_count(y, r, g.ny)) : 1.0f;
     const float inv_n = 1.0f / (float)g.n;
     const int kst = L.RH * L.RWP;
-    const XJobs xj = make_xjobs<5>(L, tid);
+    const XJobs xj = make_xjobs<K>(L, tid);
     const Stage<I> sg = make_stage<NY, I>(L, r, x0, y0, g);
     const I rowstep = (I)TY * g.nx;
     float pf[NY][STAGE_NX], pj[NY][STAGE_NX];
@@ -227,14 +241,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
                 if (qin && (sg.gmask >> (j * STAGE_NX + i) & 1u)) {
                     const I p = qoff + (I)j * rowstep + TX * i;
                     f = ld_vox(F, p) - shF;
-                    jv = __ldg(J + p) - shJ;
+                    if (HAS_J) jv = __ldg(J + p) - shJ;
                 }
                 pf[j][i] = f;
                 pj[j][i] = jv;
             }
     };
     fetch(z0 - r);
-    float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float S[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) S[k] = 0.0f;
     float nsum = 0.0f;
     int slot = 0;
     for (int q = z0 - r; q < z1 + r; ++q) {
@@ -245,32 +261,59 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
                 if (sg.smask >> (j * STAGE_NX + i) & 1u) {
                     const int o = sg.sbase + j * TY * L.RWP + TX * i;
                     const float f = pf[j][i], jv = pj[j][i];
-                    st[o] = f;
-                    st[kst + o] = jv;
-                    st[2 * kst + o] = f * f;
-                    st[3 * kst + o] = jv * jv;
-                    st[4 * kst + o] = f * jv;
+                    if (MODE == LNCC_FULL) {
+                        st[o] = f;
+                        st[kst + o] = jv;
+                        st[2 * kst + o] = f * f;
+                        st[3 * kst + o] = jv * jv;
+                        st[4 * kst + o] = f * jv;
+                    } else if (MODE == LNCC_FCACHED) {
+                        st[o] = jv;
+                        st[kst + o] = jv * jv;
+                        st[2 * kst + o] = f * jv;
+                    } else {
+                        st[o] = f;
+                        st[kst + o] = f * f;
+                    }
                 }
         if (q + 1 < z1 + r) fetch(q + 1);  // in flight during the box sums of plane q
         __syncthreads();
         xpass(st, hx, xj, r);
-        float old[5];
+        float old[K];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) old[k] = ring[(slot * 5 + k) * TILE_THREADS + tid];
+        for (int k = 0; k < K; ++k) old[k] = ring[(slot * K + k) * TILE_THREADS + tid];
         __syncthreads();
-        ypass<5>(hx, ring, slot, L, r, tid);
+        ypass<K>(hx, ring, slot, L, r, tid);
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < 5; ++k) S[k] += ring[(slot * 5 + k) * TILE_THREADS + tid] - old[k];
+        for (int k = 0; k < K; ++k) S[k] += ring[(slot * K + k) * TILE_THREADS + tid] - old[k];
         slot = slot + 1 == L.W ? 0 : slot + 1;
         const int zo = q - r;
         if (active && zo >= z0 && zo < z1) {
             const float c = cxy * (float)win_count(zo, r, g.nz);
             const float ic = 1.0f / c;
-            const float mF = S[0] * ic, mJ = S[1] * ic;
-            const float A = fmaf(S[4], ic, -mF * mJ);
-            const float Bv = fmaxf(fmaf(S[2], ic, -mF * mF), 0.0f);
-            const float Cv = fmaxf(fmaf(S[3], ic, -mJ * mJ), 0.0f);
+            const I p = (I)zo * nxy + (I)y * g.nx + x;
+            if (MODE == LNCC_FSTATS) {
+                const float m = S[0] * ic;
+                fstat[p] = m + shF;
+                (fstat + g.n)[p] = fmaxf(fmaf(S[1], ic, -m * m), 0.0f);
+                continue;
+            }
+            // means of the shifted values; A, B, C the window covariance and variances
+            float mF, mJ, A, Bv, Cv;
+            if (MODE == LNCC_FULL) {
+                mF = S[0] * ic;
+                mJ = S[1] * ic;
+                A = fmaf(S[4], ic, -mF * mJ);
+                Bv = fmaxf(fmaf(S[2], ic, -mF * mF), 0.0f);
+                Cv = fmaxf(fmaf(S[3], ic, -mJ * mJ), 0.0f);
+            } else {
+                mF = __ldg(fstat + p) - shF;
+                Bv = __ldg(fstat + g.n + p);
+                mJ = S[0] * ic;
+                A = fmaf(S[2], ic, -mF * mJ);
+                Cv = fmaxf(fmaf(S[1], ic, -mJ * mJ), 0.0f);
+            }
             const float D = fmaf(Bv, Cv, P.eps);
             float n = 0.0f, aFJ = 0.0f, aJJ = 0.0f;
             if (D > 0.0f) {
@@ -281,7 +324,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
             }
             nsum += n;
             if (COEF) {
-                const I p = (I)zo * nxy + (I)y * g.nx + x;
                 const float aJ = -(aFJ * (mF + shF) + 2.0f * aJJ * (mJ + shJ));
                 coef[p] = aJ;
                 (coef + g.n)[p] = aJJ;
@@ -289,6 +331,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 3)
             }
         }
     }
+    if (MODE == LNCC_FSTATS) return;
     const double bs = block_sum((double)nsum, red);
     const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (tid == 0) partials[bid] = bs;
@@ -649,11 +692,11 @@ static cudaError_t prepare_march(K kernel, size_t smem, const Dims &g, int r, Ma
 }
 
 cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims &g, const LnccParams &P, float *coef,
-                              double *partials, unsigned *counter, double *sim_out, cudaStream_t s) {
+                              double *partials, unsigned *counter, double *sim_out, cudaStream_t s,
+                              const float *fstat) {
     MarchGrid G;
     dim3 grid;
     const dim3 block(TX, TY);
-    const size_t smem = lncc_smem_bytes(P.r, 5);
     unsigned *err = error_word();
     cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {
@@ -662,17 +705,48 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
             using I = elem_t<decltype(ip)>;
             with_stage_rows(P.r, [&](auto ny) {
                 constexpr int NY = decltype(ny)::value;
-                if (coef) {
-                    e = prepare_march(lncc_stats_kernel<T, true, I, NY>, smem, g, P.r, G, grid);
+                auto run = [&](auto kern, int K) {
+                    const size_t smem = lncc_smem_bytes(P.r, K);
+                    e = prepare_march(kern, smem, g, P.r, G, grid);
                     if (e == cudaSuccess)
-                        lncc_stats_kernel<T, true, I, NY><<<grid, block, smem, s>>>(
-                            (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
+                        kern<<<grid, block, smem, s>>>((const T *)F, J, g, P, G.zc, coef, (float *)fstat, partials,
+                                                       counter, sim_out, err);
+                };
+                if (fstat) {  // F's window statistics formed beforehand (launch_lncc_fstats)
+                    if (coef)
+                        run(lncc_stats_kernel<T, true, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
+                    else
+                        run(lncc_stats_kernel<T, false, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
+                } else if (coef) {
+                    run(lncc_stats_kernel<T, true, I, NY>, lncc_stats_k<LNCC_FULL>());
                 } else {
-                    e = prepare_march(lncc_stats_kernel<T, false, I, NY>, smem, g, P.r, G, grid);
-                    if (e == cudaSuccess)
-                        lncc_stats_kernel<T, false, I, NY><<<grid, block, smem, s>>>(
-                            (const T *)F, J, g, P, G.zc, coef, partials, counter, sim_out, err);
+                    run(lncc_stats_kernel<T, false, I, NY>, lncc_stats_k<LNCC_FULL>());
                 }
+            });
+        });
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lncc_fstats(const void *F, int dt, const Dims &g, const LnccParams &P, float *fstat,
+                               cudaStream_t s) {
+    MarchGrid G;
+    dim3 grid;
+    const dim3 block(TX, TY);
+    const size_t smem = lncc_smem_bytes(P.r, lncc_stats_k<LNCC_FSTATS>());
+    cudaError_t e = cudaSuccess;
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_index(g, [&](auto ip) {
+            using I = elem_t<decltype(ip)>;
+            with_stage_rows(P.r, [&](auto ny) {
+                constexpr int NY = decltype(ny)::value;
+                auto kern = lncc_stats_kernel<T, false, I, NY, LNCC_FSTATS>;
+                e = prepare_march(kern, smem, g, P.r, G, grid);
+                if (e == cudaSuccess)
+                    kern<<<grid, block, smem, s>>>((const T *)F, nullptr, g, P, G.zc, nullptr, fstat, nullptr,
+                                                   nullptr, nullptr, nullptr);
             });
         });
     });
