@@ -232,10 +232,11 @@ void n_blocks(int N, int &Nb, int &nblocks) {
 size_t view_smem_bytes(const ViewGeom &G) { return 2 * (size_t)G.VGB + G.wbytes + 64 + 1024; }
 
 // Tile choice: the largest useful fraction of the GEMM rows the whole launch
-// occupies -- valid outputs / (waves x resident CTAs x MT x 128), so that a
-// last wave that leaves most SMs idle counts against a tile -- then the
-// fewest brick rows per output row, under 2 CTAs per SM of shared memory
-// (<= 113 KB) and tensor memory (<= 256 columns); 1 CTA per SM is the
+// occupies -- valid outputs / (waves x resident CTAs x MT x 128), with the
+// residency each tile's shared and tensor memory allow, so that a last wave
+// that leaves most SMs idle counts against a tile -- then the fewest brick
+// rows per output row; tiles need at most 113 KB of shared memory and 256
+// tensor-memory columns (at least 2 CTAs per SM), with 1 CTA per SM as the
 // fallback.
 bool choose_geom(const Dims &d, int Cin, int Cout, int N, float slope, ViewGeom &G) {
     if (Cin % VIEW_CK || Cin < VIEW_CK || d.nx + 2 > 256) return false;
@@ -275,7 +276,12 @@ bool choose_geom(const Dims &d, int Cin, int Cout, int N, float slope, ViewGeom 
                 g.VGB = (need * 16 + 1023) / 1024 * 1024;
                 if (view_smem_bytes(g) > smem_cap) continue;
                 const int ty_tiles = (d.ny + Ty - 1) / Ty, tz_tiles = (d.nz + Tz - 1) / Tz;
-                const long long slots = (long long)(pass == 0 ? 2 : 1) * num_sms();
+                // CTAs resident per SM: 228 KB of shared memory (1 KB reserved per
+                // CTA) and 512 tensor-memory columns per SM, 16 CTAs of 128 threads
+                const long long by_smem = (228LL * 1024) / ((long long)view_smem_bytes(g) + 1024);
+                const long long by_tmem = 512 / g.tmem_cols;
+                const long long per_sm = std::max(1LL, std::min(std::min(by_smem, by_tmem), 16LL));
+                const long long slots = per_sm * num_sms();
                 const long long ctas = (long long)ty_tiles * tz_tiles * nblocks;
                 const long long waves = (ctas + slots - 1) / slots;
                 const double eff = (double)d.nx * d.ny * d.nz * nblocks / ((double)waves * slots * g.MT * 128.0);
