@@ -432,3 +432,34 @@ def test_run_matches_repeated_iterate(capi, kind, iters):
         assert rel_l2(to64(ub) - to64(u0), to64(ua) - to64(u0)) <= 1e-4
         assert rel_l2(to64(mb), to64(ma)) <= 1e-4
     assert capi.reg_get_device_error() == 0
+
+
+# ---------------------------------------------------------------------------
+# degenerate inputs the method has: constant images (zero window variances,
+# a single-bin histogram) and one-voxel volumes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["lncc", "lncc_eps0", "mi"])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 3), (9, 10, 37)])
+def test_constant_and_tiny_volumes_match_oracle(capi, kind, shape):
+    gen = torch.Generator().manual_seed(81)
+    F = torch.full(shape, 0.7)
+    M = torch.rand(shape, generator=gen)
+    u = 0.6 * torch.randn((3,) + shape, generator=gen)
+    if kind == "mi":
+        loss = capi.mi_desc((0.0, 1.0), (0.0, 1.0), 16)
+        spec = O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=(0.0, 1.0), m_range=(0.0, 1.0))
+    else:
+        eps = 0.0 if kind == "lncc_eps0" else 1e-9
+        loss = capi.lncc_desc(3, eps)
+        spec = O.LossSpec(kind=O.LOSS_LNCC, window=3, eps=eps)
+    ws = capi.workspace(loss, F.to(DEV))
+    sim, g = capi.reg_loss_grad(loss, F.to(DEV), M.to(DEV), u.to(DEV), ws)
+    torch.cuda.synchronize()
+    Sr, gr = O.similarity_and_grad(to64(F), to64(M), to64(u), spec)
+    # F constant: every window variance of F is 0, so each n_i is 0 (LNCC), and
+    # the joint histogram has one fixed-image bin, so MI = 0
+    assert abs(Sr) <= 1e-12
+    assert abs(sim.item()) <= 1e-6
+    assert np.all(np.isfinite(to64(g)))
+    np.testing.assert_allclose(to64(g), gr, rtol=0, atol=1e-6 * max(1.0, np.abs(gr).max()))
+    assert capi.reg_get_device_error() == 0
