@@ -155,40 +155,4 @@ __device__ __forceinline__ float adam_fast(float u, float g, float m0, float v0,
     return fmaf(-S.lr_bc1, __fdividef(mn, denom), u);
 }
 
-// The same stencil with the x-neighbours supplied by the caller (a warp
-// holds a row of x, so they come from lane shuffles); hxm / hxp say whether
-// x-1 / x+1 lie inside the volume.
-__device__ __forceinline__ void diffusion_xn(const float *__restrict__ u, const Dims &g, int y, int z, long long p,
-                                             bool hxm, bool hxp, const float cur[3], const float prv[3],
-                                             const float nxt[3], const float xm[3], const float xp[3], float gR[3],
-                                             float &rpart) {
-    const bool hym = y > 0, hyp = y + 1 < g.ny;
-    const bool hzm = z > 0, hzp = z + 1 < g.nz;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float *uc = u + (long long)c * g.n;
-        const float c0 = cur[c];
-        float acc = 0.0f;
-        if (hxp) {
-            const float d = xp[c] - c0;
-            acc -= d;
-            rpart = fmaf(d, d, rpart);
-        }
-        if (hxm) acc += c0 - xm[c];
-        if (hyp) {
-            const float d = __ldg(uc + p + g.nx) - c0;
-            acc -= d;
-            rpart = fmaf(d, d, rpart);
-        }
-        if (hym) acc += c0 - __ldg(uc + p - g.nx);
-        if (hzp) {
-            const float d = nxt[c] - c0;
-            acc -= d;
-            rpart = fmaf(d, d, rpart);
-        }
-        if (hzm) acc += c0 - prv[c];
-        gR[c] = acc;
-    }
-}
-
 }  // namespace regk
