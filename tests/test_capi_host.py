@@ -186,6 +186,15 @@ def test_field_composition_validation(capi):
                                     None) == 1
 
 
+def test_autograd_front_end_is_importable():
+    """The torch.autograd wrappers load without a GPU (they run only on one)."""
+    from paper_2509_25044_gb300 import torch_ops
+    import torch
+    assert issubclass(torch_ops.Warp, torch.autograd.Function)
+    assert callable(torch_ops.LNCCLoss.apply) and callable(torch_ops.MILoss.apply)
+    assert callable(torch_ops.optimize)
+
+
 def test_product_package_has_no_oracle_dependency():
     """The product path must not import, link or execute the oracle."""
     pkg = os.path.join(ROOT, "paper_2509_25044_gb300")
