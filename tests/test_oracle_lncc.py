@@ -176,3 +176,29 @@ def test_ants_gradient_approximates_the_exact_adjoint():
         assert cos > 0.8, (win, cos)
         _, ga2 = O.lncc_grad_ants(F, 3.0 * J - 2.0, win, 0.0)
         np.testing.assert_allclose(3.0 * ga2, ga, rtol=1e-7, atol=1e-12 * np.abs(ga).max())
+
+
+@pytest.mark.parametrize("win", [3, 5])
+def test_brute_force_windows_on_a_tiny_volume(rng, win):
+    """Every voxel's n_i from explicitly extracted windows (truncated at the
+    border, two-pass centred moments, pure numpy) equals the oracle's."""
+    shape = (5, 4, 6)
+    F = rng.standard_normal(shape)
+    J = 0.6 * F + 0.5 * rng.standard_normal(shape)
+    eps = 1e-3
+    r = win // 2
+    nz, ny, nx = shape
+    ref = np.empty(shape)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                sl = (slice(max(z - r, 0), min(z + r + 1, nz)), slice(max(y - r, 0), min(y + r + 1, ny)),
+                      slice(max(x - r, 0), min(x + r + 1, nx)))
+                f, j = F[sl].ravel(), J[sl].ravel()
+                A = np.mean((f - f.mean()) * (j - j.mean()))
+                B = np.mean((f - f.mean()) ** 2)
+                C = np.mean((j - j.mean()) ** 2)
+                ref[z, y, x] = A * A / (B * C + eps)
+    S, n = O.lncc(F, J, win, eps, per_voxel=True)
+    np.testing.assert_allclose(n, ref, rtol=1e-12, atol=1e-14)
+    assert abs(S - ref.mean()) <= 1e-13

@@ -195,3 +195,10 @@ def test_per_point_adjoint_and_pmf_mi_match_the_whole_volume_forms(rng):
     idx = rng.choice(N, 50, replace=False)
     gp = O.mi_adjoint_points(Fh[idx], Jh[idx], N, B, p)
     np.testing.assert_allclose(gp, g[idx], rtol=1e-12, atol=0)
+
+
+def test_kernel_derivative_sums_to_zero():
+    """The derivative of the partition of unity: sum_m beta3'(s - m) = 0 for
+    every s, which is why the -1 term of dMI/dp drops out of the adjoint."""
+    for s in np.linspace(1.0, 9.0, 37):
+        assert abs(sum(O.bspline3_deriv(s - m) for m in range(-2, 14))) <= 1e-15
