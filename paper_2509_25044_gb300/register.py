@@ -172,13 +172,17 @@ def register_multiscale(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 100,
     block means, reg_downsample2, repeated), starting from the previous
     level's field upsampled trilinearly with its displacements scaled
     (reg_nn_field_upsample); Adam restarts at every level.  Scales must be
-    decreasing powers of two ending at 1 and divide the image size.  Returns
-    the full-resolution field, every level's RegResult and the device time of
-    the whole schedule (pyramid and upsampling included)."""
+    decreasing powers of two ending at 1 and divide the image size; u0
+    (optional) is the initial field on the coarsest level's grid, in its
+    voxels.  Returns the full-resolution field, every level's RegResult and
+    the device time of the whole schedule (pyramid and upsampling included)."""
     if list(scales)[-1] != 1 or any(a <= b for a, b in zip(scales, scales[1:])):
         raise ValueError("scales must decrease to 1")
     if len(iters) != len(scales):
         raise ValueError("one iteration count per scale")
+    coarse = (3,) + tuple(n // scales[0] for n in F.shape)
+    if u0 is not None and tuple(u0.shape) != coarse:
+        raise ValueError(f"u0 must be the coarsest level's field, shape {coarse}")
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
     pyr = {1: (F.contiguous(), M.contiguous())}
