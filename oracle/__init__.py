@@ -16,12 +16,11 @@ Conventions: volumes ``[nz, ny, nx]`` (x fastest), displacement ``u`` is
 from __future__ import annotations
 
 import ctypes
-import os
 from dataclasses import dataclass
 
 import numpy as np
 
-from .build import build as _build_lib, lib_path
+from .build import build as _build_lib
 
 PAD_BORDER = 0
 PAD_ZEROS = 1
