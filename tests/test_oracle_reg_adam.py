@@ -13,15 +13,21 @@ def test_diffusion_constant_field_is_zero(rng):
     assert R == 0.0 and not g.any()
 
 
-def test_diffusion_linear_field_closed_form():
-    nz, ny, nx = 5, 6, 7
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("comp", [0, 1, 2])
+def test_diffusion_linear_field_closed_form(axis, comp):
+    """u_comp = a * (coordinate along one axis), the other components 0: only
+    the n_axis - 1 differences along that axis are non-zero, each a, on every
+    line along it; R = a^2 (n_axis - 1) (N / n_axis) / N."""
+    shape = (5, 6, 7)  # nz, ny, nx; axis 0 = x
     a = 0.7
-    x = np.arange(nx, dtype=np.float64)
-    u = np.zeros((3, nz, ny, nx))
-    u[1] = a * x  # y-component varies along x only
+    coords = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    u = np.zeros((3,) + shape)
+    u[comp] = a * coords[2 - axis]
     R, _ = O.diffusion(u)
-    N = nx * ny * nz
-    assert abs(R - a * a * (nx - 1) * ny * nz / N) < 1e-14
+    N = int(np.prod(shape))
+    n_ax = shape[2 - axis]
+    assert abs(R - a * a * (n_ax - 1) * (N // n_ax) / N) < 1e-14
 
 
 def test_diffusion_gradient_is_scaled_neumann_laplacian():
@@ -137,3 +143,26 @@ def test_gaussian_smooth_preserves_constants_and_mass(rng):
     x = np.broadcast_to(np.arange(40, dtype=np.float64), (3, 3, 40)).copy()
     s = O.gaussian_smooth(x, 1.0)
     np.testing.assert_allclose(s[:, :, 8:32], x[:, :, 8:32], rtol=0, atol=1e-12)
+
+
+def test_objective_gradient_is_the_derivative_of_its_total(rng):
+    """The iteration's objective C + lam R (lam != 1): its gradient in u equals
+    central differences of its own total at random components."""
+    from scipy.ndimage import gaussian_filter
+    shape = (6, 7, 8)
+    F = gaussian_filter(rng.standard_normal(shape), 1.0)
+    M = gaussian_filter(rng.standard_normal(shape), 1.0)
+    u = 0.8 * rng.standard_normal((3,) + shape)
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=3, eps=1e-3)
+    lam = 2.5
+    obj = O.objective(F, M, u, spec, lam)
+    assert obj["total"] == obj["loss"] + lam * obj["R"]
+    h = 1e-6
+    for _ in range(16):
+        k = tuple(rng.integers(0, s) for s in u.shape)
+        up = u.copy()
+        up[k] += h
+        um = u.copy()
+        um[k] -= h
+        fd = (O.objective(F, M, up, spec, lam)["total"] - O.objective(F, M, um, spec, lam)["total"]) / (2 * h)
+        assert abs(fd - obj["grad"][k]) <= 1e-6 * (1.0 + abs(fd))

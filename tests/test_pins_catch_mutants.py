@@ -1,0 +1,245 @@
+"""How strong the oracle's pins are: each entry of MUTANTS plants one plausible
+mistake in a copy of the oracle (a flipped sign, a dropped factor or term, a
+wrong index, a transposed operand, a wrong normalisation or border rule), and
+the pin tests (tests/test_oracle_*.py, run against that copy) must fail on
+every one.  The unmodified copy must pass them, so a failure means the pin
+caught the mistake and not that the harness is broken.  The oracle itself is
+never modified: the copies live in a temporary directory, each built with the
+oracle's own build script before its pins run."""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+C = "oracle.c"
+PY = "__init__.py"
+
+# (name, file, text, replacement, occurrence of the text to replace, 1-based)
+MUTANTS = [
+    # trilinear warp and its slope (Eq. interp; Algorithm gridsampler)
+    ("warp: corner weights swapped", C,
+     "w[k] = bb[k] ? a[k] : 1.0 - a[k];", "w[k] = bb[k] ? 1.0 - a[k] : a[k];", 1),
+    ("warp: slope sign flipped", C,
+     "dw[k] = bb[k] ? 1.0 : -1.0;", "dw[k] = bb[k] ? -1.0 : 1.0;", 1),
+    ("warp: x and y of the voxel swapped", C,
+     "const int pc[3] = {x, y, z};", "const int pc[3] = {y, x, z};", 1),
+    ("warp: corner offset taken from another axis's bit", C,
+     "c[k] = i[k] + bb[k];", "c[k] = i[k] + bb[(k + 1) % 3];", 1),
+    ("warp: border slope not flattened outside the volume", C,
+     "slope_ok[k] = (phi >= 0.0 && phi <= (double)(n[k] - 1)) ? 1.0 : 0.0;", "slope_ok[k] = 1.0;", 1),
+    ("warp: border cell not clamped below the last voxel", C,
+     "long f = (long)floor(q);\n                            if (f > n[k] - 2) f = n[k] - 2;",
+     "long f = (long)floor(q);", 1),
+    ("warp: border point clamped one voxel short of the top", C,
+     "if (q > (double)(n[k] - 1)) q = (double)(n[k] - 1);", "if (q > (double)(n[k] - 2)) q = (double)(n[k] - 2);", 1),
+    ("warp adjoint: corner weights swapped", C,
+     "w *= bb[k] ? a[k] : 1.0 - a[k];", "w *= bb[k] ? 1.0 - a[k] : a[k];", 1),
+    ("warp adjoint: scatter to the sampling voxel", C,
+     "gM[lin((int)c[0], (int)c[1], (int)c[2], nx, ny)] += w * g[p];", "gM[p] += w * g[p];", 1),
+    # LNCC (App. fused LNCC, Eqs. lncc-loss, lncc-a..c)
+    ("lncc: window one voxel short on the high side", C,
+     "*hi = c + r > n - 1 ? n - 1 : c + r;", "*hi = c + r > n - 1 ? n - 1 : c + r - 1;", 1),
+    ("lncc: border window not truncated (divides by the full size)", C,
+     "const double muF = sF / cnt, muJ = sJ / cnt;",
+     "cnt = (double)((2 * r + 1) * (2 * r + 1) * (2 * r + 1));\n"
+     "                const double muF = sF / cnt, muJ = sJ / cnt;", 1),
+    ("lncc: covariance not normalised", C, "                A /= cnt;\n", "", 1),
+    ("lncc: F and J variances taken from the same image", C,
+     "C += dj * dj;", "C += df * df;", 1),
+    ("lncc: eps dropped", C,
+     "const double D = B * C + eps;\n                const double ni", "const double D = B * C;\n                const double ni", 1),
+    ("lncc grad: dn/dC sign flipped", C,
+     "const double dndC = -A[i] * A[i] * B[i] / (D * D);", "const double dndC = A[i] * A[i] * B[i] / (D * D);", 1),
+    ("lncc grad: factor 2 of dC/dJ dropped", C,
+     "beta[i] = dLdn * dndC * 2.0 / cnt[i];", "beta[i] = dLdn * dndC / cnt[i];", 1),
+    ("lncc grad: own window's mean used for every window", C,
+     "g += alpha[i] * (F[k] - muF[i]) + beta[i] * (J[k] - muJ[i]);",
+     "g += alpha[i] * (F[k] - muF[k]) + beta[i] * (J[k] - muJ[i]);", 1),
+    ("lncc grad: dn/dA uses B instead of A", C,
+     "const double dndA = 2.0 * A[i] / D;", "const double dndA = 2.0 * B[i] / D;", 1),
+    ("lncc ANTs: window size factor dropped", C,
+     "g = cnt[k] * (alpha * (F[k] - muF[k]) + beta * (J[k] - muJ[k]));",
+     "g = alpha * (F[k] - muF[k]) + beta * (J[k] - muJ[k]);", 1),
+    ("lncc points: factor 2 of dC/dJ dropped", C,
+     "dndC * 2.0 * (J[k] - mJ) / c", "dndC * (J[k] - mJ) / c", 1),
+    # Parzen MI (Sec. 2.2, Eq. mi; Eq. gradientmi-threadn)
+    ("mi: B-spline cubic term sign flipped", C,
+     "return 2.0 / 3.0 - a * a + 0.5 * a * a * a;", "return 2.0 / 3.0 - a * a - 0.5 * a * a * a;", 1),
+    ("mi: B-spline derivative sign convention flipped", C,
+     "const double s = t < 0.0 ? -1.0 : 1.0;", "const double s = t < 0.0 ? 1.0 : -1.0;", 1),
+    ("mi: bin map stretched over all bins", C,
+     "return v * (double)(B - 3) + 1.0;", "return v * (double)(B - 1);", 1),
+    ("mi: joint histogram not divided by N", C,
+     "for (int e = 0; e < BB; ++e) p[e] /= (double)N;", ";", 1),
+    ("mi: moving marginal read transposed", C,
+     "pJ[n] += p[m * B + n];", "pJ[n] += p[n * B + m];", 1),
+    ("mi: log ratio with the wrong marginal bin", C,
+     "if (v > 0.0) mi += v * log(v / (pI[m] * pJ[n]));", "if (v > 0.0) mi += v * log(v / (pI[m] * pJ[m]));", 1),
+    ("mi adjoint: sign flipped", C,
+     "const double scale = -(double)(B - 3) / (double)N;", "const double scale = (double)(B - 3) / (double)N;", 1),
+    ("mi adjoint: bin-map slope dropped", C,
+     "const double scale = -(double)(B - 3) / (double)N;", "const double scale = -1.0 / (double)N;", 1),
+    ("mi adjoint: table read transposed", C,
+     "g += G[m * B + n] * wF[m] * dJ[n];", "g += G[n * B + m] * wF[m] * dJ[n];", 1),
+    ("mi adjoint: kernel derivative argument reversed", C,
+     "dJ[m] = or_bspline3_deriv(sJ - (double)m);", "dJ[m] = or_bspline3_deriv((double)m - sJ);", 1),
+    ("mi adjoint: marginal term kept (log ratio without pJ)", C,
+     "G[m * B + n] = v > 0.0 ? log(v / (pI[m] * pJ[n])) : 0.0;",
+     "G[m * B + n] = v > 0.0 ? log(v / pI[m]) : 0.0;", 1),
+    ("mi of a pmf: moving marginal read transposed", C,
+     "pJ[n] += p[m * B + n];", "pJ[n] += p[n * B + m];", 3),
+    # hard-binned MI (App. fused MI, approximate histogram)
+    ("hard mi: bin truncated instead of rounded", C,
+     "int m = (int)floorf(sb + 0.5f);", "int m = (int)floorf(sb);", 1),
+    ("hard mi: smoothing weights not the B-spline's", C,
+     "const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};", "const double w[3] = {0.25, 0.5, 0.25};", 1),
+    ("hard mi: fixed and moving bins swapped", C,
+     "cnt[hard_bin(F[k], f_lo, f_scale, B) * B + hard_bin(J[k], m_lo, m_scale, B)]",
+     "cnt[hard_bin(J[k], m_lo, m_scale, B) * B + hard_bin(F[k], f_lo, f_scale, B)]", 1),
+    # Gaussian smoothing, downsampling, regulariser, Adam, det J
+    ("gaussian: variance doubled", C,
+     "w[k + r] = exp(-0.5 * (double)k * (double)k / (sigma * sigma));",
+     "w[k + r] = exp(-(double)k * (double)k / (sigma * sigma));", 1),
+    ("gaussian: periodic instead of nearest border", C,
+     "qq = qq < 0 ? 0 : (qq > n[axis] - 1 ? n[axis] - 1 : qq);",
+     "qq = ((qq % n[axis]) + n[axis]) % n[axis];", 1),
+    ("gaussian: one axis skipped", C,
+     "for (int axis = 0; axis < 3; ++axis) {", "for (int axis = 0; axis < 2; ++axis) {", 1),
+    ("downsample: block sum not divided by 8", C,
+     "out[lin(x, y, z, mx, my)] = acc / 8.0;", "out[lin(x, y, z, mx, my)] = acc / 4.0;", 1),
+    ("downsample: y offset taken from dx", C,
+     "in[lin(2 * x + dx, 2 * y + dy, 2 * z + dz, nx, ny)]", "in[lin(2 * x + dx, 2 * y + dx, 2 * z + dz, nx, ny)]", 1),
+    ("diffusion: gradient sign at the lower voxel flipped", C,
+     "gc[p] -= 2.0 * diff / (double)N;", "gc[p] += 2.0 * diff / (double)N;", 1),
+    ("diffusion: z differences dropped", C,
+     "const int step_ok[3] = {nx > 1, ny > 1, nz > 1};", "const int step_ok[3] = {nx > 1, ny > 1, 0};", 1),
+    ("bf16: ties rounded up instead of to even", C,
+     "bits = bits + 0x7fffu + lsb;", "bits = bits + 0x8000u;", 1),
+    ("adam: bias correction dropped", C,
+     "u[i] -= lr * (mn / bc1) / (sqrt(vn / bc2) + eps);", "u[i] -= lr * mn / (sqrt(vn) + eps);", 1),
+    ("adam: gradient scale ignored", C,
+     "const double gs = grad_scale * g[i];", "const double gs = g[i];", 1),
+    ("adam: second moment from the unscaled gradient", C,
+     "(1.0 - b2) * gs * gs;", "(1.0 - b2) * g[i] * g[i];", 1),
+    ("jacdet: cofactor sign flipped", C,
+     "Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +",
+     "Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) -", 1),
+    ("jacdet: identity not added", C,
+     "Jm[c][d] = (c == d ? 1.0 : 0.0) + deriv;", "Jm[c][d] = deriv;", 1),
+    ("jacdet: border difference divided by 2", C,
+     "h = (double)(hi[d] - lo[d]);", "h = 2.0;", 1),
+    # convolutions of the learned initialiser
+    ("conv: x and z taps swapped", C,
+     "const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;",
+     "const int xx = x + t / 9 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t % 3 - 1;", 1),
+    ("conv: bias dropped", C,
+     "double acc = bias ? bias[o] : 0.0;", "double acc = 0.0;", 1),
+    ("conv dgrad: gathered instead of scattered", C,
+     "din[q * Cin + c] += w[((long)o * 27 + t) * Cin + c] * dout[v * Cout + o];",
+     "din[v * Cin + c] += w[((long)o * 27 + t) * Cin + c] * dout[q * Cout + o];", 1),
+    ("conv wgrad: input not shifted by the tap", C,
+     "acc += dout[lin(x, y, z, nx, ny) * Cout + o] * in[q * Cin + c];",
+     "acc += dout[lin(x, y, z, nx, ny) * Cout + o] * in[lin(x, y, z, nx, ny) * Cin + c];", 1),
+    # the chain rule and the composite transform, in the Python layer
+    ("chain: warp slope dropped from the LNCC gradient", PY,
+     "return S, gJ[None] * dJ", "return S, np.repeat(gJ[None], 3, axis=0)", 1),
+    ("chain: normalisation slope dropped from the MI gradient", PY,
+     "return v, (gJh * dJh)[None] * dJ", "return v, gJh[None] * dJ", 2),
+    ("chain: intensity map slope not 1/(hi - lo)", PY,
+     "d = np.where((t >= 0.0) & (t <= 1.0), 1.0 / (hi - lo), 0.0)",
+     "d = np.where((t >= 0.0) & (t <= 1.0), 1.0, 0.0)", 1),
+    ("objective: lambda not applied to the regulariser gradient", PY,
+     "grad=g + lam * gR", "grad=g + gR", 1),
+    ("composite: A applied transposed", PY,
+     'np.einsum("ij,jzyx->izyx", A, X)', 'np.einsum("ji,jzyx->izyx", A, X)', 1),
+    ("composite: S not applied to u", PY,
+     "phi = phi + s[:, None, None, None] * _f64(u)", "phi = phi + _f64(u)", 1),
+    ("composite: dC/dA transposed", PY,
+     'g_A = np.einsum("izyx,jzyx->ij", gX, X)', 'g_A = np.einsum("izyx,jzyx->ji", gX, X)', 1),
+    ("composite: S dropped from dC/du", PY,
+     "return s[:, None, None, None] * gX, g_A, g_t", "return gX, g_A, g_t", 1),
+    ("compose: fields composed in the other order", PY,
+     "return a + np.stack([warp(b[c], a, pad) for c in range(3)])",
+     "return b + np.stack([warp(a[c], b, pad) for c in range(3)])", 1),
+    ("compose backward: slope term dropped", PY,
+     "ga += scale * scale * gw[d][None] * dJ", "pass", 1),
+    ("compose backward: scatter replaced by a gather", PY,
+     "gb[d] = scale * warp_adjoint(gw[d], sa, pad)", "gb[d] = scale * warp(gw[d], -sa, pad)", 1),
+    ("exp: velocity scaled by 2^-(steps-1)", PY,
+     "u = _f64(v) / float(2 ** steps)\n    for _ in range(steps):",
+     "u = _f64(v) / float(2 ** (steps - 1))\n    for _ in range(steps):", 1),
+    ("exp backward: 2^-steps dropped", PY,
+     "return g / float(2 ** steps)", "return g", 1),
+    ("exp backward: scatter term dropped", PY,
+     "g = ga + gb", "g = ga", 1),
+]
+
+
+def _mutate(src: str, text: str, new: str, nth: int) -> str:
+    at = -1
+    for _ in range(nth):
+        at = src.find(text, at + 1)
+        assert at >= 0, f"mutation site not found: {text!r} (occurrence {nth})"
+    return src[:at] + new + src[at + len(text):]
+
+
+def _copy_base(dst: str) -> None:
+    """The pins and a copy of the oracle (its source and its built library)."""
+    import glob
+    from oracle import build as ob
+    ob.build()
+    os.makedirs(os.path.join(dst, "tests"))
+    os.makedirs(os.path.join(dst, "oracle", "_build"))
+    shutil.copy2(os.path.join(ROOT, "pytest.ini"), dst)
+    shutil.copy2(os.path.join(ROOT, "tests", "conftest.py"), os.path.join(dst, "tests"))
+    for f in glob.glob(os.path.join(ROOT, "tests", "test_oracle_*.py")):
+        shutil.copy2(f, os.path.join(dst, "tests"))
+    for f in ("oracle.c", "__init__.py", "build.py"):
+        shutil.copy2(os.path.join(ROOT, "oracle", f), os.path.join(dst, "oracle"))
+    shutil.copy2(ob.lib_path(), os.path.join(dst, "oracle", "_build"))
+
+
+def _env():
+    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
+    env.pop("PYTEST_ADDOPTS", None)
+    return env
+
+
+def _run_pins(d: str) -> subprocess.CompletedProcess:
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "tests"],
+                          cwd=d, env=_env(), capture_output=True, text=True, timeout=600)
+
+
+def _check(base: str, work: str, i: int):
+    name, fname, text, new, nth = MUTANTS[i]
+    d = os.path.join(work, f"m{i:02d}")
+    shutil.copytree(base, d)
+    path = os.path.join(d, "oracle", fname)
+    with open(path) as f:
+        src = f.read()
+    with open(path, "w") as f:
+        f.write(_mutate(src, text, new, nth))
+    if fname == C:
+        # the mutant must compile, so that a failing pin is the pin's doing
+        b = subprocess.run([sys.executable, "-c", "from oracle import build; build.build(force=True)"],
+                           cwd=d, env=_env(), capture_output=True, text=True, timeout=300)
+        if b.returncode != 0:
+            return name, "did not compile: " + b.stderr[-400:]
+    r = _run_pins(d)
+    if r.returncode == 1:
+        return name, None
+    return name, f"pins exited {r.returncode}: " + (r.stdout + r.stderr)[-400:]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    base = str(tmp_path / "base")
+    _copy_base(base)
+    control = _run_pins(base)
+    assert control.returncode == 0, "the unmodified copy fails its pins:\n" + control.stdout[-2000:]
+    with ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as pool:
+        results = list(pool.map(lambda i: _check(base, str(tmp_path), i), range(len(MUTANTS))))
+    survivors = [f"{name}: {why}" for name, why in results if why is not None]
+    assert not survivors, "mistakes no pin caught:\n" + "\n".join(survivors)
