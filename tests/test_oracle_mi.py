@@ -182,6 +182,23 @@ def test_hard_binned_symmetry_and_constant(rng):
     assert abs(a - ref) < 0.1 * ref
 
 
+def test_hard_binned_gradient_uses_the_hard_pmf(rng):
+    """Off the bin centres the two PMFs differ, and the hard-binned gradient
+    is the Parzen adjoint (Eq. gradientmi-threadn) taken with the hard
+    estimator's own PMF, not with the Parzen one."""
+    B = 16
+    F = rng.random((7, 8, 9))
+    J = np.sqrt(F) + 0.1 * rng.random((7, 8, 9))
+    fr, jr = (0.0, 1.0), (0.0, 1.2)
+    _, p_hard = O.mi_hard(F, J, B, fr, jr, with_hist=True)
+    _, g = O.mi_hard_grad(F, J, B, fr, jr)
+    Fh, Jh = O.normalize(F, *fr)[0].ravel(), O.normalize(J, *jr)[0].ravel()
+    ref = O.mi_adjoint_points(Fh, Jh, Fh.size, B, p_hard)
+    np.testing.assert_allclose(g.ravel(), ref, rtol=1e-12, atol=1e-15 * np.abs(ref).max())
+    _, g_parzen = O.mi_grad(Fh, Jh, B)
+    assert np.abs(g.ravel() - g_parzen).max() > 1e-3 * np.abs(g_parzen).max()
+
+
 def test_per_point_adjoint_and_pmf_mi_match_the_whole_volume_forms(rng):
     """The per-voxel adjoint for a given PMF and the MI of a given PMF (used
     for sampled checks of volumes too large for the oracle's own histogram)

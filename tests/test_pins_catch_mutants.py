@@ -35,6 +35,10 @@ MUTANTS = [
      "long f = (long)floor(q);", 1),
     ("warp: border point clamped one voxel short of the top", C,
      "if (q > (double)(n[k] - 1)) q = (double)(n[k] - 1);", "if (q > (double)(n[k] - 2)) q = (double)(n[k] - 2);", 1),
+    ("warp zeros: slope flattened outside the volume", C,
+     "slope_ok[k] = 1.0;\n                        long f = (long)floor(phi);",
+     "slope_ok[k] = (phi >= 0.0 && phi <= (double)(n[k] - 1)) ? 1.0 : 0.0;\n"
+     "                        long f = (long)floor(phi);", 1),
     ("warp adjoint: corner weights swapped", C,
      "w *= bb[k] ? a[k] : 1.0 - a[k];", "w *= bb[k] ? 1.0 - a[k] : a[k];", 1),
     ("warp adjoint: scatter to the sampling voxel", C,
@@ -63,6 +67,9 @@ MUTANTS = [
     ("lncc ANTs: window size factor dropped", C,
      "g = cnt[k] * (alpha * (F[k] - muF[k]) + beta * (J[k] - muJ[k]));",
      "g = alpha * (F[k] - muF[k]) + beta * (J[k] - muJ[k]);", 1),
+    ("lncc ANTs: factor 2 of dC/dJ dropped", C,
+     "const double beta = dLdn * (-A[k] * A[k] * B[k] / (D * D)) * 2.0 / cnt[k];",
+     "const double beta = dLdn * (-A[k] * A[k] * B[k] / (D * D)) / cnt[k];", 1),
     ("lncc points: factor 2 of dC/dJ dropped", C,
      "dndC * 2.0 * (J[k] - mJ) / c", "dndC * (J[k] - mJ) / c", 1),
     # Parzen MI (Sec. 2.2, Eq. mi; Eq. gradientmi-threadn)
@@ -99,10 +106,16 @@ MUTANTS = [
     ("hard mi: fixed and moving bins swapped", C,
      "cnt[hard_bin(F[k], f_lo, f_scale, B) * B + hard_bin(J[k], m_lo, m_scale, B)]",
      "cnt[hard_bin(J[k], m_lo, m_scale, B) * B + hard_bin(F[k], f_lo, f_scale, B)]", 1),
+    ("hard mi grad: paired with the Parzen PMF instead of the hard one", C,
+     "const double mi = or_mi_hard(F, J, N, B, f_lo, f_scale, m_lo, m_scale, p);\n    mi_adjoint(",
+     "const double mi = or_mi_hard(F, J, N, B, f_lo, f_scale, m_lo, m_scale, p);\n"
+     "    or_mi(Fh, Jh, N, B, p);\n    mi_adjoint(", 1),
     # Gaussian smoothing, downsampling, regulariser, Adam, det J
     ("gaussian: variance doubled", C,
      "w[k + r] = exp(-0.5 * (double)k * (double)k / (sigma * sigma));",
      "w[k + r] = exp(-(double)k * (double)k / (sigma * sigma));", 1),
+    ("gaussian: truncated at 3 sigma instead of 4", C,
+     "const int r = (int)(4.0 * sigma + 0.5);", "const int r = (int)(3.0 * sigma + 0.5);", 1),
     ("gaussian: periodic instead of nearest border", C,
      "qq = qq < 0 ? 0 : (qq > n[axis] - 1 ? n[axis] - 1 : qq);",
      "qq = ((qq % n[axis]) + n[axis]) % n[axis];", 1),
@@ -120,6 +133,13 @@ MUTANTS = [
      "bits = bits + 0x7fffu + lsb;", "bits = bits + 0x8000u;", 1),
     ("adam: bias correction dropped", C,
      "u[i] -= lr * (mn / bc1) / (sqrt(vn / bc2) + eps);", "u[i] -= lr * mn / (sqrt(vn) + eps);", 1),
+    ("adam: eps inside the square root", C,
+     "u[i] -= lr * (mn / bc1) / (sqrt(vn / bc2) + eps);", "u[i] -= lr * (mn / bc1) / sqrt(vn / bc2 + eps);", 1),
+    ("adam: update from the rounded moments", C,
+     "u[i] -= lr * (mn / bc1) / (sqrt(vn / bc2) + eps);\n        m[i] = bf16_moments ? or_bf16_round(mn) : mn;\n"
+     "        v[i] = bf16_moments ? or_bf16_round(vn) : vn;",
+     "m[i] = bf16_moments ? or_bf16_round(mn) : mn;\n        v[i] = bf16_moments ? or_bf16_round(vn) : vn;\n"
+     "        u[i] -= lr * (m[i] / bc1) / (sqrt(v[i] / bc2) + eps);", 1),
     ("adam: gradient scale ignored", C,
      "const double gs = grad_scale * g[i];", "const double gs = g[i];", 1),
     ("adam: second moment from the unscaled gradient", C,
@@ -157,6 +177,11 @@ MUTANTS = [
      'np.einsum("ij,jzyx->izyx", A, X)', 'np.einsum("ji,jzyx->izyx", A, X)', 1),
     ("composite: S not applied to u", PY,
      "phi = phi + s[:, None, None, None] * _f64(u)", "phi = phi + _f64(u)", 1),
+    ("composite: translation subtracted", PY,
+     "phi = np.einsum(\"ij,jzyx->izyx\", A, X) + t[:, None, None, None]",
+     "phi = np.einsum(\"ij,jzyx->izyx\", A, X) - t[:, None, None, None]", 1),
+    ("composite: dC/dt averaged instead of summed", PY,
+     "g_t = gX.reshape(3, -1).sum(axis=1)", "g_t = gX.reshape(3, -1).mean(axis=1)", 1),
     ("composite: dC/dA transposed", PY,
      'g_A = np.einsum("izyx,jzyx->ij", gX, X)', 'g_A = np.einsum("izyx,jzyx->ji", gX, X)', 1),
     ("composite: S dropped from dC/du", PY,
@@ -168,6 +193,8 @@ MUTANTS = [
      "ga += scale * scale * gw[d][None] * dJ", "pass", 1),
     ("compose backward: scatter replaced by a gather", PY,
      "gb[d] = scale * warp_adjoint(gw[d], sa, pad)", "gb[d] = scale * warp(gw[d], -sa, pad)", 1),
+    ("compose backward: scale dropped from the direct term", PY,
+     "ga = scale * gw.copy()", "ga = gw.copy()", 1),
     ("exp: velocity scaled by 2^-(steps-1)", PY,
      "u = _f64(v) / float(2 ** steps)\n    for _ in range(steps):",
      "u = _f64(v) / float(2 ** (steps - 1))\n    for _ in range(steps):", 1),
@@ -175,6 +202,8 @@ MUTANTS = [
      "return g / float(2 ** steps)", "return g", 1),
     ("exp backward: scatter term dropped", PY,
      "g = ga + gb", "g = ga", 1),
+    ("exp backward: one squaring too many replayed", PY,
+     "for _ in range(steps - 1):\n        us.append", "for _ in range(steps):\n        us.append", 1),
 ]
 
 
