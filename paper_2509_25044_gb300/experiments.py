@@ -153,8 +153,8 @@ def approx_vs_exact(config: str, variant: str = "ants", iters: int | None = None
     _warm(r1.F, r1.M, r1.cfg, affine=r1.affine)
     res1 = r1.run(iters)
     # the exact form's objective along the approximate run (a replay: the
-    # iteration is deterministic), so both runs are judged by one function
-    judge = Registration(F, M, cfg0)
+    # iteration is deterministic), so both runs are scored by one function
+    exact = Registration(F, M, cfg0)
     rep = Registration(F, M, cfg1)
     trace = []
     for _ in range(iters):
