@@ -55,7 +55,7 @@ typedef enum reg_status {
     REG_ERR_NONFINITE = 6,   /* device error word: a non-finite partial sum was seen */
     REG_ERR_TIMEOUT = 7,     /* device error word: a bounded device wait expired */
     REG_ERR_CUDA = 8,        /* a CUDA runtime call or kernel launch failed */
-    REG_ERR_UNSUPPORTED = 9  /* valid request this build does not implement */
+    REG_ERR_UNSUPPORTED = 9  /* a valid request the library does not implement */
 } reg_status;
 
 typedef enum reg_dtype { REG_F32 = 0, REG_BF16 = 1 } reg_dtype;

@@ -350,7 +350,7 @@ def test_smooth_field_matches_oracle(capi, shape, sigma):
 
 
 def test_smoothing_regularised_registration(capi):
-    """The driver's smoothing path (gradient -> smooth -> Adam -> smooth, no
+    """The registration driver's smoothing path (gradient -> smooth -> Adam -> smooth, no
     diffusion term) decreases the objective and regularises the field: far
     fewer folded voxels than the same run without smoothing."""
     from paper_2509_25044_gb300 import synth
