@@ -204,3 +204,74 @@ def test_product_package_has_no_oracle_dependency():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt and "oracle.c" not in txt, f
+
+
+def test_nn_validation(capi):
+    """The learned initialiser's entry points reject bad shapes, enums, null
+    and misaligned pointers with their documented codes before any launch."""
+    L = capi.nn()
+    vp = ctypes.c_void_p
+    F, U = vp(FAKE), vp(FAKE + 8)  # aligned / misaligned, never dereferenced
+    d = dims()
+    # host-only sizes
+    assert L.reg_nn_conv_kpad(8) == 256 and L.reg_nn_conv_kpad(16) == 448
+    assert L.reg_nn_conv_scratch_bytes(4, 8) == 0
+    assert L.reg_nn_dgrad_scratch_bytes(8, 4) == 0
+    assert L.reg_nn_wgrad_scratch_bytes(dims(0, 4, 4), 8, 16) == 0
+    # forward convolution: (in, Cin, W, bias, Cout, d, epilogue, slope, scratch, bytes, out, stream)
+    fwd = L.reg_nn_conv3d_fwd
+    assert fwd(F, 8, F, F, 8, dims(0, 4, 4), 0, 0.2, None, 0, F, None) == 2
+    assert fwd(F, 12, F, F, 8, d, 0, 0.2, None, 0, F, None) == 2    # Cin % 8
+    assert fwd(F, 136, F, F, 8, d, 0, 0.2, None, 0, F, None) == 2   # Cin > 128
+    assert fwd(F, 8, F, F, 65, d, 2, 0.2, None, 0, F, None) == 2    # Cout > 64
+    assert fwd(F, 8, F, F, 8, d, 3, 0.2, None, 0, F, None) == 1     # epilogue
+    assert fwd(F, 8, F, F, 12, d, 0, 0.2, None, 0, F, None) == 2    # BF16 output needs Cout % 8
+    assert fwd(None, 8, F, F, 8, d, 0, 0.2, None, 0, F, None) == 1
+    assert fwd(U, 8, F, F, 8, d, 0, 0.2, None, 0, F, None) == 4
+    assert fwd(F, 8, F, None, 8, d, 0, 0.2, None, 0, F, None) == 1  # bias required
+    assert fwd(F, 8, F, None, 8, d, 1, 0.2, U, 1 << 20, F, None) == 4
+    # data gradient: (dpre, Cout, W, Cin, d, Wd_scratch, din, stream)
+    dg = L.reg_nn_conv3d_dgrad
+    assert dg(F, 8, F, 8, dims(4, 0, 4), F, F, None) == 2
+    assert dg(F, 12, F, 8, d, F, F, None) == 2
+    assert dg(F, 8, F, 136, d, F, F, None) == 2
+    assert dg(F, 8, F, 8, d, F, U, None) == 4
+    # weight gradient: (in, Cin, dpre, Cout, d, scratch, bytes, dW, stream)
+    wg = L.reg_nn_conv3d_wgrad
+    assert wg(F, 8, F, 8, d, F, 1 << 20, F, None) == 2    # Cout < 16
+    assert wg(F, 8, F, 80, d, F, 1 << 20, F, None) == 2   # Cout > 64
+    assert wg(F, 8, F, 16, d, F, 1 << 20, U, None) == 4
+    # network input: (F, M, img_dt, d, factor, f_lo, f_hi, m_lo, m_hi, out, stream)
+    pp = L.reg_nn_pack_pair
+    assert pp(F, F, capi.REG_F32, d, 3, 0.0, 1.0, 0.0, 1.0, F, None) == 2
+    assert pp(F, F, capi.REG_F32, d, 0, 0.0, 1.0, 0.0, 1.0, F, None) == 2
+    assert pp(F, F, 7, d, 2, 0.0, 1.0, 0.0, 1.0, F, None) == 3
+    assert pp(F, F, capi.REG_F32, d, 2, 1.0, 1.0, 0.0, 1.0, F, None) == 1
+    assert pp(F, F, capi.REG_F32, d, 2, 0.0, 1.0, 0.0, float("nan"), F, None) == 1
+    assert pp(F, F, capi.REG_BF16, d, 2, 0.0, 1.0, 0.0, 1.0, U, None) == 4
+    # element-wise and layout operators
+    assert L.reg_nn_leaky_bwd(F, F, -1, 0.2, F, None) == 1
+    assert L.reg_nn_leaky_bwd(None, F, 16, 0.2, F, None) == 1
+    assert L.reg_nn_bias_grad(F, 0, 8, F, F, None) == 1
+    assert L.reg_nn_bias_grad(F, 64, 65, F, F, None) == 1
+    assert L.reg_nn_bias_grad(F, 64, 8, None, F, None) == 1
+    assert L.reg_nn_avgpool2(F, 8, dims(7, 8, 8), F, 0, None) == 2
+    assert L.reg_nn_avgpool2(F, 0, d, F, 0, None) == 2
+    assert L.reg_nn_avgpool2(None, 8, d, F, 1, None) == 1
+    assert L.reg_nn_upsample2(F, 8, dims(0, 4, 4), F, 0, None) == 2
+    assert L.reg_nn_upsample2(F, 8, d, None, 1, None) == 1
+    assert L.reg_nn_put_channels(F, 8, 64, F, 16, 9, 0, None) == 1   # c0 + Csrc > Cdst
+    assert L.reg_nn_put_channels(F, 8, -1, F, 16, 0, 0, None) == 1
+    assert L.reg_nn_put_channels(F, 8, 64, F, 16, -1, 0, None) == 1
+    assert L.reg_nn_take_channels(F, 16, 9, 64, F, 8, 0, None) == 1  # c0 + Cdst > Csrc
+    assert L.reg_nn_mse(F, F, 64, 2, F, F, F, None) == 1             # Cpad < 3
+    assert L.reg_nn_mse(F, F, 0, 4, F, F, F, None) == 1
+    assert L.reg_nn_mse(F, F, 64, 4, F, F, None, None) == 1
+    assert L.reg_nn_field_down2(F, dims(8, 8, 7), F, None) == 2
+    assert L.reg_nn_field_down2(None, d, F, None) == 1
+    assert L.reg_nn_field_upsample(F, d, 0, F, None) == 2
+    assert L.reg_nn_field_upsample(F, d, 2, None, None) == 1
+    adam = capi.adam_desc(1e-3, 0.9, 0.999, 1e-8, capi.REG_F32, 1.0)
+    assert L.reg_nn_adam(F, F, F, F, 16, ctypes.byref(adam), 0, None, None) == 1
+    assert L.reg_nn_adam(F, F, F, F, 0, ctypes.byref(adam), 1, None, None) == 1
+    assert L.reg_nn_adam(F, F, F, F, 16, None, 1, None, None) == 1
