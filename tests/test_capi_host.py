@@ -275,3 +275,53 @@ def test_nn_validation(capi):
     assert L.reg_nn_adam(F, F, F, F, 16, ctypes.byref(adam), 0, None, None) == 1
     assert L.reg_nn_adam(F, F, F, F, 0, ctypes.byref(adam), 1, None, None) == 1
     assert L.reg_nn_adam(F, F, F, F, 16, None, 1, None, None) == 1
+
+
+def test_auxiliary_entry_points_validation(capi):
+    """Smoothing, downsampling, det J, the allocation-free MI call, the GEMM
+    test hook and the timing-event switch: documented codes, no launch."""
+    L = _lib(capi)
+    vp = ctypes.c_void_p
+    F, F2, U = vp(FAKE), vp(FAKE + 0x100), vp(FAKE + 8)
+    d = dims()
+    # reg_downsample2(in, dt, d, out, stream)
+    assert L.reg_downsample2(F, capi.REG_F32, dims(7, 8, 8), F2, None) == 2
+    assert L.reg_downsample2(F, 7, d, F2, None) == 3
+    assert L.reg_downsample2(F, capi.REG_BF16, d, F, None) == 1   # in place
+    assert L.reg_downsample2(None, capi.REG_F32, d, F2, None) == 1
+    assert L.reg_downsample2(F, capi.REG_F32, d, U, None) == 4
+    # reg_smooth_field(u, d, sigma, tmp, out, stream)
+    assert L.reg_smooth_field(F, d, 0.0, F2, vp(FAKE + 0x200), None) == 1
+    assert L.reg_smooth_field(F, d, 8.0, F2, vp(FAKE + 0x200), None) == 1
+    assert L.reg_smooth_field(F, d, float("nan"), F2, vp(FAKE + 0x200), None) == 1
+    assert L.reg_smooth_field(F, d, 1.0, F, vp(FAKE + 0x200), None) == 1   # u aliases tmp
+    assert L.reg_smooth_field(F, d, 1.0, None, vp(FAKE + 0x200), None) == 1
+    # reg_jacdet_min(u, d, ws, ws_bytes, min_out, nfold_out, stream)
+    assert L.reg_jacdet_min(F, dims(0, 4, 4), None, 0, F2, F2, None) == 2
+    assert L.reg_jacdet_min(U, d, None, 0, F2, F2, None) == 4
+    assert L.reg_jacdet_min(F, d, None, 0, F2, None, None) == 1
+    # reg_debug_gemm_bf16(A, B, C, M, N, K, a_mn_major, b_mn_major, stream)
+    g = L.reg_debug_gemm_bf16
+    assert g(F, F, F, 100, 64, 64, 0, 0, None) == 2   # M % 128
+    assert g(F, F, F, 128, 8, 64, 0, 0, None) == 2    # N < 16
+    assert g(F, F, F, 128, 144, 64, 0, 0, None) == 2  # N > 128
+    assert g(F, F, F, 128, 64, 32, 0, 0, None) == 2   # K % 64
+    assert g(F, F, F, 128, 64, 64, 2, 0, None) == 1
+    # reg_mi_loss_grad_noalloc(loss, F, M, img_dt, u, d, pad, sim_out, grad_u, stream)
+    na = L.reg_mi_loss_grad_noalloc
+    mi = capi.mi_desc((0, 1), (0, 1), 32)
+    assert na(None, F, F, capi.REG_F32, F, d, 0, F, None, None) == 1
+    assert na(ctypes.byref(capi.lncc_desc(7)), F, F, capi.REG_F32, F, d, 0, F, None, None) == 9
+    assert na(ctypes.byref(capi.mi_desc((0, 1), (0, 1), 4)), F, F, capi.REG_F32, F, d, 0, F, None, None) == 2
+    assert na(ctypes.byref(capi.mi_desc((0, 1), (0, 1), 65)), F, F, capi.REG_F32, F, d, 0, F, None, None) == 2
+    assert na(ctypes.byref(capi.mi_desc((1, 1), (0, 1), 32)), F, F, capi.REG_F32, F, d, 0, F, None, None) == 1
+    assert na(ctypes.byref(mi), F, F, 7, F, d, 0, F, None, None) == 3
+    assert na(ctypes.byref(mi), F, F, capi.REG_F32, F, d, 5, F, None, None) == 1
+    assert na(ctypes.byref(mi), F, F, capi.REG_F32, F, dims(0, 4, 4), 0, F, None, None) == 2
+    assert na(ctypes.byref(mi), None, F, capi.REG_F32, F, d, 0, F, None, None) == 1
+    assert na(ctypes.byref(mi), F, F, capi.REG_F32, F, d, 0, F, U, None) == 4
+    # reg_set_timing_events(events, n): three events or (NULL, 0) to disarm
+    assert L.reg_set_timing_events(None, 0) == 0
+    assert L.reg_set_timing_events(None, 3) == 1
+    two = (ctypes.c_void_p * 2)(FAKE, FAKE)
+    assert L.reg_set_timing_events(two, 2) == 1
