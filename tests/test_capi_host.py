@@ -206,6 +206,20 @@ def test_product_package_has_no_oracle_dependency():
                 assert "liboracle" not in txt and "oracle.c" not in txt, f
 
 
+def test_oracle_has_no_product_dependency():
+    """The other direction: the oracle includes only the C standard library
+    and imports nothing of the product package, so the two share no code."""
+    d = os.path.join(ROOT, "oracle")
+    for f in sorted(os.listdir(d)):
+        if not f.endswith((".py", ".c", ".h")):
+            continue
+        txt = open(os.path.join(d, f)).read()
+        assert not re.search(r"^\s*(import|from)\s+paper_2509_25044_gb300", txt, re.M), f
+        assert "libreg" not in txt, f
+        for inc in re.findall(r"#include\s*([<\"][^>\"]+[>\"])", txt):
+            assert inc in ("<math.h>", "<stdint.h>", "<stdlib.h>", "<string.h>", "<stdio.h>"), (f, inc)
+
+
 def test_nn_validation(capi):
     """The learned initialiser's entry points reject bad shapes, enums, null
     and misaligned pointers with their documented codes before any launch."""
