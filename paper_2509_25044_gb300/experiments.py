@@ -159,7 +159,7 @@ def approx_vs_exact(config: str, variant: str = "ants", iters: int | None = None
     trace = []
     for _ in range(iters):
         rep.run(1)
-        trace.append(judge.objective(u=rep.current)["objective"])
+        trace.append(exact.objective(u=rep.current)["objective"])
     k1 = _first_within(trace, Lstar, tol)
     out["approx"] = {"ms_per_iter": res1.ms_per_iter, "iters_to_target": None if k1 is None else k1 + 1,
                      "time_to_target_ms": None if k1 is None else (k1 + 1) * res1.ms_per_iter,
