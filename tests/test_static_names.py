@@ -1,0 +1,51 @@
+"""Static check of the Python sources (CPU): every module compiles, and every
+name a module reads is bound somewhere in it (an assignment, argument,
+import, definition or builtin).  It catches a renamed variable left behind on
+a path no CPU test executes, such as the GPU-only experiment drivers."""
+import ast
+import builtins
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _sources():
+    out = [os.path.join(ROOT, f) for f in ("bench.py", "__graft_entry__.py")]
+    for d in ("paper_2509_25044_gb300", "oracle", "tests"):
+        for f in sorted(os.listdir(os.path.join(ROOT, d))):
+            if f.endswith(".py"):
+                out.append(os.path.join(ROOT, d, f))
+    return out
+
+
+def _bound(tree):
+    names = set(dir(builtins)) | {"__file__", "__name__"}
+    for n in ast.walk(tree):
+        if isinstance(n, (ast.FunctionDef, ast.AsyncFunctionDef, ast.ClassDef)):
+            names.add(n.name)
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            names.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, ast.Name) and isinstance(n.ctx, (ast.Store, ast.Del)):
+            names.add(n.id)
+        elif isinstance(n, ast.arg):
+            names.add(n.arg)
+        elif isinstance(n, (ast.Global, ast.Nonlocal)):
+            names.update(n.names)
+        elif isinstance(n, ast.ExceptHandler) and n.name:
+            names.add(n.name)
+        elif isinstance(n, ast.MatchAs) and n.name:
+            names.add(n.name)
+    return names
+
+
+@pytest.mark.parametrize("path", _sources(), ids=lambda p: os.path.relpath(p, ROOT))
+def test_every_read_name_is_bound(path):
+    src = open(path).read()
+    tree = ast.parse(src, filename=path)
+    compile(tree, path, "exec")
+    bound = _bound(tree)
+    unbound = sorted({(n.id, n.lineno) for n in ast.walk(tree)
+                      if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load) and n.id not in bound})
+    assert not unbound, f"names read but never bound: {unbound}"
