@@ -49,3 +49,43 @@ def test_every_read_name_is_bound(path):
     unbound = sorted({(n.id, n.lineno) for n in ast.walk(tree)
                       if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load) and n.id not in bound})
     assert not unbound, f"names read but never bound: {unbound}"
+
+
+def _module_aliases(tree):
+    """alias -> module name, for imports of this project's own modules."""
+    own = ("paper_2509_25044_gb300", "oracle")
+    out = {}
+    for n in ast.walk(tree):
+        if isinstance(n, ast.Import):
+            for a in n.names:
+                if a.name.split(".")[0] in own and a.asname:
+                    out[a.asname] = a.name
+        elif isinstance(n, ast.ImportFrom) and n.module and n.level == 0 and n.module.split(".")[0] in own:
+            for a in n.names:
+                out[a.asname or a.name] = f"{n.module}.{a.name}"
+        elif isinstance(n, ast.ImportFrom) and n.level == 1:  # from . import x (inside the package)
+            for a in n.names:
+                out[a.asname or a.name] = f"paper_2509_25044_gb300.{a.name}" if n.module is None else None
+    return {k: v for k, v in out.items() if v}
+
+
+@pytest.mark.parametrize("path", _sources(), ids=lambda p: os.path.relpath(p, ROOT))
+def test_attributes_of_own_modules_exist(path):
+    """capi.reg_x, synth.make, O.warp ...: every attribute read from one of the
+    project's modules exists in it."""
+    import importlib
+    import sys
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    tree = ast.parse(open(path).read(), filename=path)
+    missing = []
+    for alias, mod in _module_aliases(tree).items():
+        try:
+            m = importlib.import_module(mod)
+        except ImportError:
+            continue  # a name imported from a module, not a module
+        for n in ast.walk(tree):
+            if (isinstance(n, ast.Attribute) and isinstance(n.value, ast.Name) and n.value.id == alias
+                    and isinstance(n.ctx, ast.Load) and not hasattr(m, n.attr)):
+                missing.append((alias, n.attr, n.lineno))
+    assert not missing, f"attributes that do not exist: {sorted(set(missing))}"
