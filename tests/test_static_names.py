@@ -89,3 +89,48 @@ def test_attributes_of_own_modules_exist(path):
                     and isinstance(n.ctx, ast.Load) and not hasattr(m, n.attr)):
                 missing.append((alias, n.attr, n.lineno))
     assert not missing, f"attributes that do not exist: {sorted(set(missing))}"
+
+
+def _resolve(mod: str):
+    import importlib
+    try:
+        return importlib.import_module(mod)
+    except ImportError:
+        parent, _, name = mod.rpartition(".")
+        return getattr(importlib.import_module(parent), name, None)
+
+
+@pytest.mark.parametrize("path", _sources(), ids=lambda p: os.path.relpath(p, ROOT))
+def test_calls_of_own_functions_fit_their_signatures(path):
+    """Every call of one of the project's Python functions or classes
+    (capi.reg_loss(...), Registration(...)) passes no unknown keyword and no
+    more positional arguments than the signature takes."""
+    import inspect
+    import sys
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    tree = ast.parse(open(path).read(), filename=path)
+    objs = {alias: _resolve(mod) for alias, mod in _module_aliases(tree).items()}
+    bad = []
+    for n in ast.walk(tree):
+        if not isinstance(n, ast.Call):
+            continue
+        f = n.func
+        target = None
+        if isinstance(f, ast.Attribute) and isinstance(f.value, ast.Name) and inspect.ismodule(objs.get(f.value.id)):
+            target = getattr(objs[f.value.id], f.attr, None)
+        elif isinstance(f, ast.Name) and f.id in objs and not inspect.ismodule(objs[f.id]):
+            target = objs[f.id]
+        if not (inspect.isfunction(target) or inspect.isclass(target)):
+            continue
+        if any(isinstance(a, ast.Starred) for a in n.args) or any(k.arg is None for k in n.keywords):
+            continue
+        try:
+            sig = inspect.signature(target)
+        except (TypeError, ValueError):
+            continue
+        try:
+            sig.bind_partial(*[None] * len(n.args), **{k.arg: None for k in n.keywords})
+        except TypeError as e:
+            bad.append((ast.unparse(f), n.lineno, str(e)))
+    assert not bad, f"calls that do not fit: {bad}"
