@@ -339,3 +339,56 @@ def test_auxiliary_entry_points_validation(capi):
     assert L.reg_set_timing_events(None, 3) == 1
     two = (ctypes.c_void_p * 2)(FAKE, FAKE)
     assert L.reg_set_timing_events(two, 2) == 1
+
+
+def _c_params(txt):
+    """name -> (return type, [parameter types]) of every REG_API prototype."""
+    out = {}
+    for ret, name, params in re.findall(r"REG_API\s+([^;{]*?)\b(reg_\w+)\s*\(([^)]*)\)\s*;", txt):
+        params = " ".join(params.split())
+        types = [] if params in ("", "void") else [re.sub(r"\s*\b\w+$", "", p.strip()) for p in params.split(",")]
+        out[name] = (" ".join(ret.split()), types)
+    return out
+
+
+def _kind_of_c(t):
+    t = t.replace("const", "").strip()
+    if "*" in t:
+        return "ptr"
+    return {"int": "i4", "unsigned": "u4", "unsigned int": "u4", "long long": "i8", "unsigned long long": "u8",
+            "size_t": "u8", "float": "f4", "double": "f8", "reg_status": "i4", "reg_dims": "reg_dims"}[" ".join(t.split())]
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    if t.__name__ == "RegDims":
+        return "reg_dims"
+    if t in (ctypes.c_float, ctypes.c_double):
+        return f"f{ctypes.sizeof(t)}"
+    signed = t(-1).value == -1
+    return f"{'i' if signed else 'u'}{ctypes.sizeof(t)}"
+
+
+def test_binding_argtypes_match_the_header(capi):
+    """Every entry point's ctypes signature in the binding has the header's
+    parameter count, and each parameter the same kind (pointer, struct by
+    value, integer or float of the same width and signedness); functions that
+    return size_t or a string declare it."""
+    protos = _c_params(open(os.path.join(ROOT, "include", "reg.h")).read())
+    assert set(protos) == set(header_symbols())
+    capi.load()
+    L = capi.nn()
+    for name, (ret, params) in protos.items():
+        fn = getattr(L, name)
+        argtypes = fn.argtypes or []
+        assert len(argtypes) == len(params), (name, len(argtypes), len(params))
+        for i, (a, p) in enumerate(zip(argtypes, params)):
+            assert _kind_of_ctypes(a) == _kind_of_c(p), (name, i, a, p)
+        if ret == "size_t":
+            assert fn.restype is ctypes.c_size_t, name
+        elif ret == "const char *":
+            assert fn.restype is ctypes.c_char_p, name
+        else:
+            assert ret in ("reg_status", "int"), (name, ret)
+            assert fn.restype in (ctypes.c_int, None) or fn.restype.__name__ == "c_int", name
