@@ -226,6 +226,16 @@ def affine_about_centre(A, tc, shape):
     return A, c - A @ c + np.asarray(tc, dtype=np.float64)
 
 
+def centred_affine_grads(gA, gt, c, s):
+    """Gradients in the centred parameters of phi(p) = A (p - c) + c + tc / s
+    (c the volume centre of the level, s its scale, tc in full-resolution
+    voxels) from those in phi(p) = A p + t: since t = c - A c + tc / s,
+    dC/dA at fixed tc = dC/dA - (dC/dt) c^T and dC/dtc = (dC/dt) / s."""
+    gA = np.asarray(gA, dtype=np.float64).reshape(3, 3)
+    gt = np.asarray(gt, dtype=np.float64).reshape(3)
+    return gA - np.outer(gt, c), gt / s
+
+
 def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40), lr_A: float = 0.01,
                     lr_t: float = 0.3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
                     final_lr: float = 0.1) -> dict:
@@ -265,9 +275,7 @@ def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40),
             h = buf.cpu().numpy()
             sim, gA, gt = h[0], h[2:11].reshape(3, 3), h[11:14]
             hist.append(1.0 - sim if cfg.loss == "lncc" else -sim)
-            # gradients in the centred parameters: dC/dA at fixed tc, dC/dtc
-            gA = gA - np.outer(gt, c)
-            gtc = gt / s
+            gA, gtc = centred_affine_grads(gA, gt, c, s)
             b1, b2 = 1.0 - beta1 ** (k + 1), 1.0 - beta2 ** (k + 1)
             decay = 1.0 - (1.0 - final_lr) * k / max(it - 1, 1)
             mA = beta1 * mA + (1 - beta1) * gA
