@@ -50,3 +50,20 @@ def test_affine_about_centre_is_the_same_map(rng):
     A2, t = affine_about_centre(A, tc, shape)
     p = rng.uniform(0.0, 20.0, (3, 50))
     np.testing.assert_allclose(A2 @ p + t[:, None], A @ (p - c[:, None]) + c[:, None] + tc[:, None], atol=1e-12)
+
+
+def test_multiscale_schedule_is_validated_before_any_launch():
+    """Scales must decrease to 1, one iteration count per scale, and u0 lives
+    on the coarsest level's grid: each is rejected on the host."""
+    import torch
+    from paper_2509_25044_gb300.register import RegConfig, register_multiscale
+    F = M = torch.zeros(16, 16, 16)
+    cfg = RegConfig(loss="lncc")
+    with pytest.raises(ValueError, match="decrease"):
+        register_multiscale(F, M, cfg, scales=(2, 4, 1), iters=(1, 1, 1))
+    with pytest.raises(ValueError, match="decrease"):
+        register_multiscale(F, M, cfg, scales=(4, 2), iters=(1, 1))
+    with pytest.raises(ValueError, match="one iteration count"):
+        register_multiscale(F, M, cfg, scales=(4, 2, 1), iters=(1, 1))
+    with pytest.raises(ValueError, match="coarsest"):
+        register_multiscale(F, M, cfg, scales=(4, 2, 1), iters=(1, 1, 1), u0=torch.zeros(3, 16, 16, 16))
