@@ -24,7 +24,7 @@ class RegConfig:
     ants: bool = False          # LNCC gradient with the ANTs approximation (no second box sum)
     mi_hard: bool = False       # MI with the hard-binned approximate histogram estimator
     bins: int = 32              # MI bins
-    f_range: tuple | None = None
+    f_range: tuple | None = None  # MI intensity ranges; default: each image's own (min, max)
     m_range: tuple | None = None
     lam: float = 0.1            # diffusion weight
     lr: float = 0.1             # Adam step size (voxels)
@@ -36,11 +36,14 @@ class RegConfig:
     sigma_warp: float = 0.0     # > 0: Gaussian smoothing of the field after each step
     pad: int = capi.REG_PAD_BORDER
 
-    def loss_desc(self, F):
+    def loss_desc(self, F, M=None):
         if self.loss == "lncc":
             return capi.lncc_desc(self.window, self.eps, ants=self.ants)
         fr = self.f_range if self.f_range is not None else (float(F.min()), float(F.max()))
-        mr = self.m_range if self.m_range is not None else (0.0, 1.0)
+        if self.m_range is not None:
+            mr = self.m_range
+        else:
+            mr = (float(M.min()), float(M.max())) if M is not None else (0.0, 1.0)
         return capi.mi_desc(fr, mr, self.bins, hard=self.mi_hard)
 
 
@@ -70,7 +73,7 @@ class Registration:
         self.shape = tuple(F.shape)
         self.N = F.numel()
         dev = F.device
-        self.loss = cfg.loss_desc(F)
+        self.loss = cfg.loss_desc(self.F, self.M)
         mt = torch.bfloat16 if cfg.moments == "bf16" else torch.float32
         self.u = [torch.zeros((3,) + self.shape, device=dev), torch.zeros((3,) + self.shape, device=dev)]
         if u0 is not None:
@@ -256,7 +259,7 @@ def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40),
         f, m = pyr[s]
         pyr[2 * s] = (capi.reg_downsample2(f), capi.reg_downsample2(m))
         s *= 2
-    loss = cfg.loss_desc(F)
+    loss = cfg.loss_desc(F, M)
     A = np.eye(3)
     tc = np.zeros(3)
     levels = []
@@ -301,7 +304,7 @@ def register_svf(F, M, cfg: RegConfig, iters: int, steps: int = 6, v0=None) -> d
     F, M = F.contiguous(), M.contiguous()
     shape = tuple(F.shape)
     dev = F.device
-    loss = cfg.loss_desc(F)
+    loss = cfg.loss_desc(F, M)
     ws = capi.workspace(loss, F)
     v = [torch.zeros((3,) + shape, device=dev), torch.zeros((3,) + shape, device=dev)]
     if v0 is not None:

@@ -67,3 +67,14 @@ def test_multiscale_schedule_is_validated_before_any_launch():
         register_multiscale(F, M, cfg, scales=(4, 2, 1), iters=(1, 1))
     with pytest.raises(ValueError, match="coarsest"):
         register_multiscale(F, M, cfg, scales=(4, 2, 1), iters=(1, 1, 1), u0=torch.zeros(3, 16, 16, 16))
+
+
+def test_mi_ranges_default_to_each_images_own():
+    import torch
+    from paper_2509_25044_gb300.register import RegConfig
+    F = torch.linspace(-2.0, 3.0, 64).reshape(4, 4, 4)
+    M = torch.linspace(10.0, 50.0, 64).reshape(4, 4, 4)
+    d = RegConfig(loss="mi", bins=16).loss_desc(F, M)
+    assert (d.f_lo, d.f_hi, d.m_lo, d.m_hi, d.bins) == (-2.0, 3.0, 10.0, 50.0, 16)
+    d = RegConfig(loss="mi", m_range=(0.0, 60.0)).loss_desc(F, M)
+    assert (d.m_lo, d.m_hi) == (0.0, 60.0)
