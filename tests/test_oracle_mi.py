@@ -219,3 +219,53 @@ def test_kernel_derivative_sums_to_zero():
     every s, which is why the -1 term of dMI/dp drops out of the adjoint."""
     for s in np.linspace(1.0, 9.0, 37):
         assert abs(sum(O.bspline3_deriv(s - m) for m in range(-2, 14))) <= 1e-15
+
+
+# ---- the chain through the warp and the intensity map (Sec. 2.2) ------------
+def _smooth_pair(rng, shape=(8, 9, 10)):
+    from scipy.ndimage import gaussian_filter
+    F = gaussian_filter(rng.standard_normal(shape), 1.2)
+    M = np.tanh(F) + 0.3 * gaussian_filter(rng.standard_normal(shape), 1.2)
+    u = 0.7 * rng.standard_normal((3,) + shape)
+    return F, M, u
+
+
+def test_mi_is_invariant_to_an_intensity_map_carried_by_the_range(rng):
+    """Each image is mapped to [0, 1] by its own range, so M' = 3 M + 2 with
+    the range mapped the same way gives the same MI and the same dC/du; the
+    fixed image's range differs from the moving one's."""
+    F, M, u = _smooth_pair(rng)
+    fr = (float(F.min()) - 0.1, float(F.max()) + 0.2)
+    mr = (float(M.min()) - 0.05, float(M.max()) + 0.1)
+    s1, g1 = O.similarity_and_grad(F, M, u, O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=fr, m_range=mr))
+    mr2 = (3 * mr[0] + 2, 3 * mr[1] + 2)
+    s2, g2 = O.similarity_and_grad(F, 3 * M + 2, u, O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=fr, m_range=mr2))
+    assert abs(s1 - s2) <= 1e-12 * abs(s1) and s1 > 0.01
+    np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-10 * np.abs(g1).max())
+
+
+def test_mi_clamps_intensities_outside_the_range(rng):
+    """Intensities outside the stated range count at its ends: with u = 0 (so
+    J = M) the MI of M equals that of M clipped to the range, and voxels
+    outside it get no gradient."""
+    F, M, _ = _smooth_pair(rng)
+    u = np.zeros((3,) + F.shape)
+    fr = (float(F.min()), float(F.max()))
+    lo, hi = np.quantile(M, [0.2, 0.8])
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=fr, m_range=(float(lo), float(hi)))
+    s1, g = O.similarity_and_grad(F, M, u, spec)
+    s2, _ = O.similarity_and_grad(F, np.clip(M, lo, hi), u, spec)
+    assert abs(s1 - s2) <= 1e-12 * abs(s2)
+    outside = (M < lo) | (M > hi)
+    assert outside.sum() > 0.3 * M.size and not g[:, outside].any()
+
+
+def test_objective_of_mi_is_minus_mi():
+    """The MI objective is C = -MI: F = M taking two separated values (MI =
+    ln 2 exactly, see the closed form above) gives loss -ln 2 at u = 0."""
+    a, b = _bin_value(5.0), _bin_value(20.0)
+    F = np.array([a, b] * 256).reshape(8, 8, 8)
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=B, f_range=(0.0, 1.0), m_range=(0.0, 1.0))
+    obj = O.objective(F, F, np.zeros((3, 8, 8, 8)), spec, 0.5)
+    assert abs(obj["loss"] + math.log(2.0)) < 1e-12 and obj["R"] == 0.0
+    assert abs(obj["total"] + math.log(2.0)) < 1e-12

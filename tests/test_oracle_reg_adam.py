@@ -166,3 +166,23 @@ def test_objective_gradient_is_the_derivative_of_its_total(rng):
         um[k] -= h
         fd = (O.objective(F, M, up, spec, lam)["total"] - O.objective(F, M, um, spec, lam)["total"]) / (2 * h)
         assert abs(fd - obj["grad"][k]) <= 1e-6 * (1.0 + abs(fd))
+
+
+def test_first_iteration_moves_each_component_by_lr(rng):
+    """The iteration feeds Adam N times the gradient (per-voxel gradients of
+    a mean over N voxels are O(1/N), far below Adam's eps otherwise): the
+    first step is then lr times the sign of the descent direction, to within
+    lr * eps / |N g|, on every component with |N g| above 0.1."""
+    from scipy.ndimage import gaussian_filter
+    shape = (8, 9, 10)
+    F = gaussian_filter(rng.standard_normal(shape), 1.0)
+    M = gaussian_filter(rng.standard_normal(shape), 1.0)
+    u = 0.5 * rng.standard_normal((3,) + shape)
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=3, eps=1e-3)
+    lr = 0.1
+    z = np.zeros_like(u)
+    out = O.iterate(F, M, u, z, z, 1, spec, lam=0.5, lr=lr)
+    g = out["grad"] * F.size
+    big = np.abs(g) > 0.1
+    assert big.mean() > 0.5
+    np.testing.assert_allclose((u - out["u"])[big], lr * np.sign(g[big]), rtol=0, atol=1e-7 * lr)

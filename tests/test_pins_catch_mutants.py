@@ -171,6 +171,16 @@ MUTANTS = [
     ("chain: intensity map slope not 1/(hi - lo)", PY,
      "d = np.where((t >= 0.0) & (t <= 1.0), 1.0 / (hi - lo), 0.0)",
      "d = np.where((t >= 0.0) & (t <= 1.0), 1.0, 0.0)", 1),
+    ("binding: volume sizes passed to C in z, y, x order", PY,
+     "    nz, ny, nx = vol.shape\n    return nx, ny, nz", "    nz, ny, nx = vol.shape\n    return nz, ny, nx", 1),
+    ("chain: moving image normalised with the fixed image's range", PY,
+     "Jh, dJh = normalize(J, *spec.m_range)", "Jh, dJh = normalize(J, *spec.f_range)", 1),
+    ("chain: intensities not clamped to [0, 1]", PY,
+     "return np.clip(t, 0.0, 1.0), d", "return t, d", 1),
+    ("objective: MI loss taken as 1 - MI", PY,
+     "loss = 1.0 - sim if spec.kind == LOSS_LNCC else -sim", "loss = 1.0 - sim", 1),
+    ("iterate: Adam input not scaled by N", PY,
+     "grad_scale = float(np.prod(np.shape(F)))", "grad_scale = 1.0", 1),
     ("objective: lambda not applied to the regulariser gradient", PY,
      "grad=g + lam * gR", "grad=g + gR", 1),
     ("composite: A applied transposed", PY,
