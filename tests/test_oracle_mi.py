@@ -269,3 +269,23 @@ def test_objective_of_mi_is_minus_mi():
     obj = O.objective(F, F, np.zeros((3, 8, 8, 8)), spec, 0.5)
     assert abs(obj["loss"] + math.log(2.0)) < 1e-12 and obj["R"] == 0.0
     assert abs(obj["total"] + math.log(2.0)) < 1e-12
+
+
+def test_hard_binned_chain_uses_the_hard_pmf(rng):
+    """Through the warp and the intensity map, the hard-binned estimator's
+    dC/du is the Parzen adjoint taken with the hard estimator's own PMF (the
+    pairing its C-level gradient is pinned to), chained by dJh/dJ and the
+    warp's slope; off the bin centres it differs from the Parzen chain."""
+    F, M, u = _smooth_pair(rng)
+    fr = (float(F.min()), float(F.max()))
+    mr = (float(M.min()) - 0.1, float(M.max()) + 0.1)
+    spec = O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=fr, m_range=mr, mi_estimator=1)
+    s, g = O.similarity_and_grad(F, M, u, spec)
+    J, dJ = O.warp(M, u, O.PAD_BORDER, with_grad=True)
+    v, p = O.mi_hard(F, J, 16, fr, mr, with_hist=True)
+    Fh, Jh, dJh = O.normalize(F, *fr)[0], *O.normalize(J, *mr)
+    gJh = O.mi_adjoint_points(Fh.ravel(), Jh.ravel(), F.size, 16, p).reshape(F.shape)
+    assert s == v
+    np.testing.assert_allclose(g, (gJh * dJh)[None] * dJ, rtol=1e-12, atol=1e-15 * np.abs(g).max())
+    _, g_parzen = O.similarity_and_grad(F, M, u, O.LossSpec(kind=O.LOSS_MI, bins=16, f_range=fr, m_range=mr))
+    assert np.abs(g - g_parzen).max() > 1e-3 * np.abs(g_parzen).max()

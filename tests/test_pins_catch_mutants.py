@@ -181,6 +181,11 @@ MUTANTS = [
      "loss = 1.0 - sim if spec.kind == LOSS_LNCC else -sim", "loss = 1.0 - sim", 1),
     ("iterate: Adam input not scaled by N", PY,
      "grad_scale = float(np.prod(np.shape(F)))", "grad_scale = 1.0", 1),
+    ("chain: the exact and ANTs LNCC gradients dispatched the other way round", PY,
+     "(lncc_grad_ants if spec.lncc_grad == 1 else lncc_grad)", "(lncc_grad if spec.lncc_grad == 1 else lncc_grad_ants)", 1),
+    ("chain: the hard-binned estimator's gradient taken from the Parzen PMF", PY,
+     "v, gJh = mi_hard_grad(F, J, spec.bins, spec.f_range, spec.m_range)",
+     "v, gJh = mi_hard(F, J, spec.bins, spec.f_range, spec.m_range), mi_grad(Fh, Jh, spec.bins)[1]", 1),
     ("objective: lambda not applied to the regulariser gradient", PY,
      "grad=g + lam * gR", "grad=g + gR", 1),
     ("composite: A applied transposed", PY,
