@@ -156,6 +156,24 @@ def test_compose_translations_add(rng):
     np.testing.assert_allclose(O.compose_fields(a, b), a + b, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("pad", [O.PAD_BORDER, O.PAD_ZEROS])
+def test_compose_follows_the_padding_mode(pad):
+    """a = an integer shift of +2 voxels along x, b = a constant field c:
+    w(p) = a + b(p + a) is a + c where p + a lies inside the volume; outside
+    it is a + c with BORDER padding and a with ZEROS padding."""
+    shape = (4, 5, 6)
+    a = np.zeros((3,) + shape)
+    a[0] = 2.0
+    c = np.array([0.3, -0.4, 0.5])
+    b = np.ones((3,) + shape) * c[:, None, None, None]
+    w = O.compose_fields(a, b, pad)
+    inside = np.arange(shape[2]) + 2 <= shape[2] - 1
+    ref = a + b
+    if pad == O.PAD_ZEROS:
+        ref[:, :, :, ~inside] = a[:, :, :, ~inside]
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-15)
+
+
 def test_compose_with_linear_field_is_exact(rng):
     """b(p) = B p is linear, so trilinear sampling is exact in the interior:
     w(p) = a(p) + B (p + a(p))."""
@@ -221,16 +239,17 @@ def test_warp_adjoint_of_integer_shift_is_reverse_shift(rng):
     np.testing.assert_array_equal(gM[:, :, :2], 0.0)
 
 
+@pytest.mark.parametrize("pad", [O.PAD_BORDER, O.PAD_ZEROS])
 @pytest.mark.parametrize("scale", [1.0, 0.25])
-def test_compose_backward_matches_differences(rng, scale):
+def test_compose_backward_matches_differences(rng, scale, pad):
     shape = (6, 5, 7)
     a = 0.6 * O.gaussian_smooth(rng.standard_normal((3,) + shape), 1.0) + 0.2 * rng.standard_normal((3,) + shape)
     b = 0.8 * rng.standard_normal((3,) + shape)
     gw = rng.standard_normal((3,) + shape)
-    ga, gb = O.compose_fields_backward(a, b, gw, scale=scale)
+    ga, gb = O.compose_fields_backward(a, b, gw, pad=pad, scale=scale)
 
     def L(a_, b_):
-        w = scale * a_ + np.stack([scale * O.warp(b_[c], scale * a_) for c in range(3)])
+        w = scale * a_ + np.stack([scale * O.warp(b_[c], scale * a_, pad) for c in range(3)])
         return float(np.sum(gw * w))
 
     h = 1e-6

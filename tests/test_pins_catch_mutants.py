@@ -201,6 +201,19 @@ MUTANTS = [
      'g_A = np.einsum("izyx,jzyx->ij", gX, X)', 'g_A = np.einsum("izyx,jzyx->ji", gX, X)', 1),
     ("composite: S dropped from dC/du", PY,
      "return s[:, None, None, None] * gX, g_A, g_t", "return gX, g_A, g_t", 1),
+    ("composite backward: upstream gradient dropped", PY,
+     "return _affine_grads(dJ * _f64(g)[None], s)", "return _affine_grads(dJ, s)", 1),
+    ("compose: padding mode ignored", PY,
+     "return a + np.stack([warp(b[c], a, pad) for c in range(3)])",
+     "return a + np.stack([warp(b[c], a) for c in range(3)])", 1),
+    ("compose backward: padding mode ignored in the scatter", PY,
+     "gb[d] = scale * warp_adjoint(gw[d], sa, pad)", "gb[d] = scale * warp_adjoint(gw[d], sa)", 1),
+    ("exp: one squaring fewer", PY,
+     "    for _ in range(steps):\n        u = compose_fields(u, u, pad)",
+     "    for _ in range(steps - 1):\n        u = compose_fields(u, u, pad)", 1),
+    ("warp: padding mode ignored for the composite sampler", PY,
+     "return warp(M, composite_offset(M.shape, A, t, s, u), pad, with_grad)",
+     "return warp(M, composite_offset(M.shape, A, t, s, u), PAD_BORDER, with_grad)", 1),
     ("compose: fields composed in the other order", PY,
      "return a + np.stack([warp(b[c], a, pad) for c in range(3)])",
      "return b + np.stack([warp(a[c], b, pad) for c in range(3)])", 1),
