@@ -72,6 +72,15 @@ MUTANTS = [
      "const double beta = dLdn * (-A[k] * A[k] * B[k] / (D * D)) / cnt[k];", 1),
     ("lncc points: factor 2 of dC/dJ dropped", C,
      "dndC * 2.0 * (J[k] - mJ) / c", "dndC * (J[k] - mJ) / c", 1),
+    ("lncc points: per-voxel NCC not squared", C,
+     "n_out[s] = D > 0.0 ? A * A / D : 0.0;", "n_out[s] = D > 0.0 ? A / D : 0.0;", 1),
+    ("lncc points: window statistics at the listed voxel for every window", C,
+     "window_stats(F, J, nx, ny, nz, r, xx, yy, zz, eps, &mF, &mJ, &A, &B, &C, &c);",
+     "window_stats(F, J, nx, ny, nz, r, x, y, z, eps, &mF, &mJ, &A, &B, &C, &c);", 1),
+    ("hard mi: PMF not divided by N", C,
+     "p[m * B + n] = acc / (double)N;", "p[m * B + n] = acc;", 1),
+    ("gaussian: weights not normalised", C,
+     "for (int k = 0; k <= 2 * r; ++k) w[k] /= sum;", ";", 1),
     # Parzen MI (Sec. 2.2, Eq. mi; Eq. gradientmi-threadn)
     ("mi: B-spline cubic term sign flipped", C,
      "return 2.0 / 3.0 - a * a + 0.5 * a * a * a;", "return 2.0 / 3.0 - a * a - 0.5 * a * a * a;", 1),
