@@ -144,7 +144,14 @@ def _check(status: int, where: str):
 
 
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Device address of a tensor.  Host tensors are refused here: every entry
+    point reads and writes device memory only, and there is no host path."""
+    if t is None:
+        return None
+    if t.device.type != "cuda":
+        raise ValueError(f"a {t.device.type} tensor was passed where device memory is required "
+                         "(the library runs on the GPU only)")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream(t=None):

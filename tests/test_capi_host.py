@@ -392,3 +392,16 @@ def test_binding_argtypes_match_the_header(capi):
         else:
             assert ret in ("reg_status", "int"), (name, ret)
             assert fn.restype in (ctypes.c_int, None) or fn.restype.__name__ == "c_int", name
+
+
+def test_binding_refuses_host_tensors(capi):
+    """A host tensor never reaches a kernel: the binding refuses it before the
+    call (no host path, no silent copy)."""
+    import torch
+    M = torch.zeros(4, 4, 4)
+    u = torch.zeros(3, 4, 4, 4)
+    with pytest.raises(ValueError, match="device memory"):
+        capi.reg_warp(M, u, J=torch.empty(4, 4, 4))
+    with pytest.raises(ValueError, match="device memory"):
+        capi.ptr(M)
+    assert capi.ptr(None) is None
