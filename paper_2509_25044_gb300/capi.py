@@ -182,6 +182,28 @@ def _need(t, shape, dtype, name):
         raise TypeError(f"{name} dtype {t.dtype} != {dtype}")
 
 
+def _buf(t, numel: int, dtype, name):
+    """A caller-supplied output buffer: contiguous, of the given dtype, with
+    room for the `numel` elements the library writes."""
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} dtype {t.dtype} != {dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements; {numel} are written")
+
+
+def _field(t, vol_shape, name):
+    """A displacement-shaped FP32 field [3][nz][ny][nx] of the given volume."""
+    _need(t, (3,) + tuple(vol_shape), torch.float32, name)
+
+
+def _moments(m, v, vol_shape, adam):
+    mt = torch.bfloat16 if adam.moment_dtype == REG_BF16 else torch.float32
+    _need(m, (3,) + tuple(vol_shape), mt, "m")
+    _need(v, (3,) + tuple(vol_shape), mt, "v")
+
+
 REG_LNCC_GRAD_EXACT, REG_LNCC_GRAD_ANTS = 0, 1
 
 
@@ -233,8 +255,11 @@ def reg_warp(M, u, pad: int = REG_PAD_BORDER, J=None, dJ=None, with_slope: bool 
     _need(u, (3,) + tuple(M.shape), torch.float32, "u")
     if J is None:
         J = torch.empty(M.shape, dtype=torch.float32, device=M.device)
+    _buf(J, M.numel(), torch.float32, "J")
     if with_slope and dJ is None:
         dJ = torch.empty_like(u)
+    if dJ is not None:
+        _buf(dJ, u.numel(), torch.float32, "dJ")
     _check(_lib().reg_warp(_ptr(M), _img_dtype(M), _ptr(u), d, int(pad), _ptr(J), _ptr(dJ), _stream(M)), "reg_warp")
     return (J, dJ) if dJ is not None else J
 
@@ -278,10 +303,15 @@ def reg_loss_grad_composite(loss: RegLossDesc, F, M, T: RegAffine, u=None, ws=No
         ws = workspace(loss, F)
     if sim is None:
         sim = torch.empty(2, dtype=torch.float64, device=F.device)
+    _buf(sim, 1, torch.float64, "sim")
     if need_u and grad_u is None:
         grad_u = torch.empty((3,) + tuple(F.shape), dtype=torch.float32, device=F.device)
+    if need_u:
+        _buf(grad_u, 3 * F.numel(), torch.float32, "grad_u")
     if need_affine and grad_affine is None:
         grad_affine = torch.empty(12, dtype=torch.float64, device=F.device)
+    if need_affine:
+        _buf(grad_affine, 12, torch.float64, "grad_affine")
     _check(_lib().reg_loss_grad_composite(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d,
                                           ctypes.byref(T), int(pad), _ptr(ws), ws.numel(), _ptr(sim),
                                           _ptr(grad_u if need_u else None), _ptr(grad_affine if need_affine else None),
@@ -292,9 +322,11 @@ def reg_loss_grad_composite(loss: RegLossDesc, F, M, T: RegAffine, u=None, ws=No
 def reg_compose_fields(a, b, pad: int = REG_PAD_BORDER, out=None):
     """w = a + b o (id + a) for [3][nz][ny][nx] FP32 fields."""
     d = dims_of(a[0])
+    _field(a, a.shape[1:], "a")
     _need(b, tuple(a.shape), torch.float32, "b")
     if out is None:
         out = torch.empty_like(a)
+    _buf(out, a.numel(), torch.float32, "out")
     _check(_lib().reg_compose_fields(_ptr(a), _ptr(b), d, int(pad), _ptr(out), _stream(a)), "reg_compose_fields")
     return out
 
@@ -303,10 +335,16 @@ def reg_exp_field(v, steps: int, pad: int = REG_PAD_BORDER, out=None, tmp=None, 
     """Scaling and squaring of the velocity field v ([3][nz][ny][nx] FP32);
     saved (optional, [steps - 1][3][nz][ny][nx]) keeps u_1 .. u_{steps-1}."""
     d = dims_of(v[0])
+    _field(v, v.shape[1:], "v")
     if out is None:
         out = torch.empty_like(v)
+    _buf(out, v.numel(), torch.float32, "out")
     if tmp is None and saved is None:
         tmp = torch.empty_like(v)
+    if tmp is not None:
+        _buf(tmp, v.numel(), torch.float32, "tmp")
+    if saved is not None:
+        _buf(saved, max(int(steps) - 1, 0) * v.numel(), torch.float32, "saved")
     _check(_lib().reg_exp_field(_ptr(v), d, int(steps), int(pad), _ptr(tmp), _ptr(out), _ptr(saved), _stream(v)),
            "reg_exp_field")
     return out
@@ -316,6 +354,9 @@ def reg_compose_fields_backward(a, b, gw, pad: int = REG_PAD_BORDER, same: bool 
     """(ga, gb) for gw = dL/dw of w = a + b o (id + a); same=True (a is b):
     returns (None, the whole gradient)."""
     d = dims_of(a[0])
+    _field(a, a.shape[1:], "a")
+    _need(b, tuple(a.shape), torch.float32, "b")
+    _need(gw, tuple(a.shape), torch.float32, "gw")
     ga = None if same else torch.empty_like(a)
     gb = torch.empty_like(b)
     _check(_lib().reg_compose_fields_backward(_ptr(a), _ptr(b), _ptr(gw), d, int(pad), _ptr(ga), _ptr(gb),
@@ -326,10 +367,16 @@ def reg_compose_fields_backward(a, b, gw, pad: int = REG_PAD_BORDER, same: bool 
 def reg_exp_field_backward(v, steps: int, gout, saved=None, pad: int = REG_PAD_BORDER, gv=None, tmp=None):
     """dL/dv of scaling and squaring for gout = dL/d exp(v)."""
     d = dims_of(v[0])
+    _field(v, v.shape[1:], "v")
+    _need(gout, tuple(v.shape), torch.float32, "gout")
+    if saved is not None:
+        _buf(saved, max(int(steps) - 1, 0) * v.numel(), torch.float32, "saved")
     if gv is None:
         gv = torch.empty_like(v)
+    _buf(gv, v.numel(), torch.float32, "gv")
     if tmp is None:
         tmp = torch.empty_like(v)
+    _buf(tmp, v.numel(), torch.float32, "tmp")
     _check(_lib().reg_exp_field_backward(_ptr(v), d, int(steps), int(pad), _ptr(saved), _ptr(gout), _ptr(tmp),
                                          _ptr(gv), _stream(v)), "reg_exp_field_backward")
     return gv
@@ -341,6 +388,7 @@ def reg_loss(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim=None
     _need(u, (3,) + tuple(F.shape), torch.float32, "u")
     if sim is None:
         sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    _buf(sim, 1, torch.float64, "sim")
     _check(_lib().reg_loss(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d, int(pad), _ptr(ws),
                            ws.numel(), _ptr(sim), _stream(F)), "reg_loss")
     return sim
@@ -352,8 +400,10 @@ def reg_loss_grad(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim
     _need(u, (3,) + tuple(F.shape), torch.float32, "u")
     if sim is None:
         sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    _buf(sim, 1, torch.float64, "sim")
     if grad is None:
         grad = torch.empty_like(u)
+    _buf(grad, u.numel(), torch.float32, "grad")
     _check(_lib().reg_loss_grad(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d, int(pad), _ptr(ws),
                                 ws.numel(), _ptr(sim), _ptr(grad), _stream(F)), "reg_loss_grad")
     return sim, grad
@@ -361,8 +411,12 @@ def reg_loss_grad(loss: RegLossDesc, F, M, u, ws, pad: int = REG_PAD_BORDER, sim
 
 def reg_regularize(u, lam: float, ws, r=None, grad=None):
     d = dims_of(u)
+    _field(u, u.shape[1:], "u")
     if r is None:
         r = torch.empty(1, dtype=torch.float64, device=u.device)
+    _buf(r, 1, torch.float64, "r")
+    if grad is not None:
+        _buf(grad, u.numel(), torch.float32, "grad")
     _check(_lib().reg_regularize(_ptr(u), d, float(lam), _ptr(ws), ws.numel(), _ptr(r), _ptr(grad), _stream(u)),
            "reg_regularize")
     return r
@@ -371,10 +425,13 @@ def reg_regularize(u, lam: float, ws, r=None, grad=None):
 def reg_smooth_field(u, sigma: float, out=None, tmp=None):
     """Gaussian smoothing of a [3][nz][ny][nx] FP32 field (out != u)."""
     d = dims_of(u[0])
+    _field(u, u.shape[1:], "u")
     if out is None:
         out = torch.empty_like(u)
+    _buf(out, u.numel(), torch.float32, "out")
     if tmp is None:
         tmp = torch.empty_like(u)
+    _buf(tmp, u.numel(), torch.float32, "tmp")
     _check(_lib().reg_smooth_field(_ptr(u), d, float(sigma), _ptr(tmp), _ptr(out), _stream(u)), "reg_smooth_field")
     return out
 
@@ -390,6 +447,11 @@ def reg_downsample2(img):
 
 def reg_step(u_in, u_out, m, v, grad, adam: RegAdamDesc, t: int):
     d = dims_of(u_in)
+    vol = u_in.shape[1:]
+    _field(u_in, vol, "u_in")
+    _field(u_out, vol, "u_out")
+    _field(grad, vol, "grad")
+    _moments(m, v, vol, adam)
     _check(_lib().reg_step(_ptr(u_in), _ptr(u_out), _ptr(m), _ptr(v), _ptr(grad), d, ctypes.byref(adam), int(t),
                            _stream(u_in)), "reg_step")
     return u_out
@@ -401,8 +463,12 @@ def reg_iterate(loss: RegLossDesc, F, M, u_in, u_out, m, v, lam: float, adam: Re
     _need(M, F.shape, F.dtype, "M")
     _need(u_in, (3,) + tuple(F.shape), torch.float32, "u_in")
     _need(u_out, (3,) + tuple(F.shape), torch.float32, "u_out")
+    _moments(m, v, F.shape, adam)
     if obj is None:
         obj = torch.empty(2, dtype=torch.float64, device=F.device)
+    _buf(obj, 2, torch.float64, "obj")
+    if grad is not None:
+        _buf(grad, 3 * F.numel(), torch.float32, "grad")
     _check(_lib().reg_iterate(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u_in), _ptr(u_out), _ptr(m),
                               _ptr(v), d, int(pad), float(lam), ctypes.byref(adam), int(t), _ptr(ws), ws.numel(),
                               _ptr(obj), _ptr(grad), _stream(F)), "reg_iterate")
@@ -418,8 +484,10 @@ def reg_run(loss: RegLossDesc, F, M, u_a, u_b, m, v, lam: float, adam: RegAdamDe
     _need(M, F.shape, F.dtype, "M")
     _need(u_a, (3,) + tuple(F.shape), torch.float32, "u_a")
     _need(u_b, (3,) + tuple(F.shape), torch.float32, "u_b")
+    _moments(m, v, F.shape, adam)
     if obj_hist is None:
         obj_hist = torch.empty((max(iters, 1), 2), dtype=torch.float64, device=F.device)
+    _buf(obj_hist, 2 * max(int(iters), 0), torch.float64, "obj_hist")
     _check(_lib().reg_run(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u_a), _ptr(u_b), _ptr(m), _ptr(v),
                           d, int(pad), float(lam), ctypes.byref(adam), int(t0), int(iters), _ptr(ws), ws.numel(),
                           _ptr(obj_hist), ctypes.byref(affine) if affine is not None else None, _stream(F)),
@@ -429,10 +497,13 @@ def reg_run(loss: RegLossDesc, F, M, u_a, u_b, m, v, lam: float, adam: RegAdamDe
 
 def reg_jacdet_min(u, out_min=None, out_nfold=None):
     d = dims_of(u)
+    _field(u, u.shape[1:], "u")
     if out_min is None:
         out_min = torch.empty(4, dtype=torch.float32, device=u.device)
+    _buf(out_min, 1, torch.float32, "out_min")
     if out_nfold is None:
         out_nfold = torch.empty(2, dtype=torch.int64, device=u.device)
+    _buf(out_nfold, 1, torch.int64, "out_nfold")
     _check(_lib().reg_jacdet_min(_ptr(u), d, None, 0, _ptr(out_min), _ptr(out_nfold), _stream(u)), "reg_jacdet_min")
     return out_min[:1], out_nfold[:1]
 
@@ -466,8 +537,11 @@ def reg_mi_loss_grad_noalloc(loss: RegLossDesc, F, M, u, pad: int = REG_PAD_BORD
     _need(u, (3,) + tuple(F.shape), torch.float32, "u")
     if sim is None:
         sim = torch.empty(1, dtype=torch.float64, device=F.device)
+    _buf(sim, 1, torch.float64, "sim")
     if with_grad and grad is None:
         grad = torch.empty_like(u)
+    if with_grad:
+        _buf(grad, u.numel(), torch.float32, "grad")
     _check(_lib().reg_mi_loss_grad_noalloc(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d,
                                            int(pad), _ptr(sim), _ptr(grad if with_grad else None), _stream(F)),
            "reg_mi_loss_grad_noalloc")
@@ -476,8 +550,11 @@ def reg_mi_loss_grad_noalloc(loss: RegLossDesc, F, M, u, pad: int = REG_PAD_BORD
 
 def reg_debug_gemm_bf16(A, B, M: int, N: int, K: int, a_mn_major: bool = False, b_mn_major: bool = False, C=None):
     """C = A B^T on the tensor cores (test hook); A, B bf16 in the stated layouts."""
+    _buf(A, int(M) * int(K), torch.bfloat16, "A")
+    _buf(B, int(N) * int(K), torch.bfloat16, "B")
     if C is None:
         C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _buf(C, int(M) * int(N), torch.float32, "C")
     _check(_lib().reg_debug_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(bool(a_mn_major)),
                                       int(bool(b_mn_major)), _stream(A)), "reg_debug_gemm_bf16")
     return C

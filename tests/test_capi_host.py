@@ -405,3 +405,34 @@ def test_binding_refuses_host_tensors(capi):
     with pytest.raises(ValueError, match="device memory"):
         capi.ptr(M)
     assert capi.ptr(None) is None
+
+
+def test_binding_checks_caller_buffers_before_the_call(capi):
+    """Caller-supplied outputs and state are checked for dtype, contiguity
+    and room for what the library writes, before any pointer is taken (so a
+    short buffer is an error, never an out-of-bounds write)."""
+    import torch
+    F = torch.zeros(4, 4, 4)
+    u = torch.zeros(3, 4, 4, 4)
+    lncc = capi.lncc_desc(3, 1e-5)
+    ws = torch.empty(16)
+    with pytest.raises(TypeError, match="sim"):
+        capi.reg_loss(lncc, F, F, u, ws, sim=torch.empty(1, dtype=torch.float32))
+    with pytest.raises(ValueError, match="grad"):
+        capi.reg_loss_grad(lncc, F, F, u, ws, grad=torch.empty(3, 4, 4, 3))
+    adam = capi.adam_desc(0.1)
+    mb = torch.zeros(3, 4, 4, 4, dtype=torch.bfloat16)
+    with pytest.raises(TypeError, match="m dtype"):
+        capi.reg_iterate(lncc, F, F, u, u.clone(), mb, mb.clone(), 0.1, adam, 1, ws)
+    with pytest.raises(ValueError, match="obj_hist"):
+        capi.reg_run(lncc, F, F, u, u.clone(), u.clone(), u.clone(), 0.1, adam, 0, 5, ws,
+                     obj_hist=torch.empty(4, 2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="saved"):
+        capi.reg_exp_field(u, 4, saved=torch.empty(2, 3, 4, 4, 4))
+    with pytest.raises(ValueError, match="contiguous"):
+        capi.reg_compose_fields(u, u, out=torch.empty(4, 4, 4, 3).permute(3, 0, 1, 2))
+    with pytest.raises(ValueError, match="A holds"):
+        capi.reg_debug_gemm_bf16(torch.empty(64, 64, dtype=torch.bfloat16), torch.empty(16, 64, dtype=torch.bfloat16),
+                                 128, 16, 64)
+    with pytest.raises(ValueError, match="shape"):
+        capi.reg_jacdet_min(torch.zeros(2, 4, 4, 4))
