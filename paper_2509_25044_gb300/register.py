@@ -67,8 +67,7 @@ class Registration:
         optimised under the composite transform phi = A p + t + S u (the fused
         iteration of reg_run; with the smoothing regulariser the composite
         loss gradient, the smoothing and Adam run as separate launches)."""
-        if F.device.type != "cuda":
-            raise ValueError("F and M must be CUDA tensors")
+        self._require_device(F)
         self.F, self.M, self.cfg = F.contiguous(), M.contiguous(), cfg
         self.shape = tuple(F.shape)
         self.N = F.numel()
@@ -93,6 +92,11 @@ class Registration:
             self.tmp2 = torch.empty_like(self.u[0])
             self.sim1 = torch.zeros(2, dtype=torch.float64, device=dev)  # 16-byte aligned outputs
             self.r1 = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    @staticmethod
+    def _require_device(F):
+        if F.device.type != "cuda":
+            raise ValueError("F and M must be CUDA tensors")
 
     @property
     def current(self) -> torch.Tensor:

@@ -46,6 +46,9 @@ def fake(monkeypatch):
     monkeypatch.setattr(capi, "_stream", lambda t=None: None)
     monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(capi, "_nn_ready", False)  # the real library's signatures stay untouched
+    from paper_2509_25044_gb300.register import Registration
+    monkeypatch.setattr(Registration, "_require_device", staticmethod(lambda F: None))
     return lib
 
 
@@ -102,3 +105,38 @@ def test_fake_library_leaves_the_checks_in_place(fake):
     with pytest.raises(ValueError, match="grad"):
         capi.reg_loss_grad(capi.lncc_desc(3, 1e-5), F, M, u, torch.empty(0), grad=torch.empty(10))
     assert fake.calls == []
+
+
+def _body(lib):
+    return [c for c in lib.calls if c != "reg_workspace_size"]
+
+
+def test_registration_fused_and_smoothing_paths(fake):
+    from paper_2509_25044_gb300.register import RegConfig, Registration
+    F, M = _pair()
+    r = Registration(F, M, RegConfig(loss="lncc", window=3, moments="bf16"))
+    res = r.run(4)
+    assert _body(fake) == ["reg_run"] and res.objective.shape == (4,) and r.t == 4
+    fake.calls.clear()
+    r.objective()
+    r.fold_check()
+    assert _body(fake) == ["reg_loss", "reg_regularize", "reg_jacdet_min"]
+    fake.calls.clear()
+    r = Registration(F, M, RegConfig(loss="mi", bins=16, sigma_grad=1.0, sigma_warp=0.5))
+    r.run(2)
+    it = ["reg_loss_grad", "reg_regularize", "reg_smooth_field", "reg_step", "reg_smooth_field"]
+    assert _body(fake) == it * 2
+    fake.calls.clear()
+    r = Registration(F, M, RegConfig(loss="lncc", window=3, sigma_grad=1.0), affine=capi.affine_desc())
+    r.run(1)
+    assert _body(fake) == ["reg_loss_grad_composite", "reg_regularize", "reg_smooth_field", "reg_step"]
+
+
+def test_multiscale_driver_orchestration(fake):
+    from paper_2509_25044_gb300.register import RegConfig, register_multiscale
+    F, M = _pair(16)
+    out = register_multiscale(F, M, RegConfig(loss="lncc", window=3), scales=(4, 2, 1), iters=(2, 2, 2))
+    assert _body(fake) == (["reg_downsample2"] * 4 + ["reg_run", "reg_nn_field_upsample", "reg_run",
+                                                       "reg_nn_field_upsample", "reg_run"])
+    assert [lv["shape"] for lv in out["levels"]] == [(4, 4, 4), (8, 8, 8), (16, 16, 16)]
+    assert tuple(out["u"].shape) == (3, 16, 16, 16)
