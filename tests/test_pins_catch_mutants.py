@@ -55,6 +55,12 @@ MUTANTS = [
      "C += dj * dj;", "C += df * df;", 1),
     ("lncc: eps dropped", C,
      "const double D = B * C + eps;\n                const double ni", "const double D = B * C;\n                const double ni", 1),
+    ("lncc: fixed-image window mean taken from the moving image", C,
+     "                            sF += F[k];\n                            sJ += J[k];\n                            cnt += 1.0;",
+     "                            sF += J[k];\n                            sJ += J[k];\n                            cnt += 1.0;", 1),
+    ("lncc grad: dL/dn sign flipped", C,
+     "const double dLdn = -1.0 / (double)N;\n#pragma omp parallel for schedule(static)\n    for (long i = 0;",
+     "const double dLdn = 1.0 / (double)N;\n#pragma omp parallel for schedule(static)\n    for (long i = 0;", 1),
     ("lncc grad: dn/dC sign flipped", C,
      "const double dndC = -A[i] * A[i] * B[i] / (D * D);", "const double dndC = A[i] * A[i] * B[i] / (D * D);", 1),
     ("lncc grad: factor 2 of dC/dJ dropped", C,
@@ -88,6 +94,9 @@ MUTANTS = [
      "const double s = t < 0.0 ? -1.0 : 1.0;", "const double s = t < 0.0 ? 1.0 : -1.0;", 1),
     ("mi: bin map stretched over all bins", C,
      "return v * (double)(B - 3) + 1.0;", "return v * (double)(B - 1);", 1),
+    ("mi: moving bin coordinate from the fixed image", C,
+     "const double sF = bin_coord(Fh[k], B), sJ = bin_coord(Jh[k], B);\n            for (int m = 0; m < B; ++m) {\n                wF[m]",
+     "const double sF = bin_coord(Fh[k], B), sJ = bin_coord(Fh[k], B);\n            for (int m = 0; m < B; ++m) {\n                wF[m]", 1),
     ("mi: joint histogram not divided by N", C,
      "for (int e = 0; e < BB; ++e) p[e] /= (double)N;", ";", 1),
     ("mi: moving marginal read transposed", C,
@@ -153,6 +162,9 @@ MUTANTS = [
      "const double gs = grad_scale * g[i];", "const double gs = g[i];", 1),
     ("adam: second moment from the unscaled gradient", C,
      "(1.0 - b2) * gs * gs;", "(1.0 - b2) * g[i] * g[i];", 1),
+    ("jacdet: difference taken backwards", C,
+     "deriv = (uc[lin(hi[0], hi[1], hi[2], nx, ny)] -\n                                     uc[lin(lo[0], lo[1], lo[2], nx, ny)]) / h;",
+     "deriv = (uc[lin(lo[0], lo[1], lo[2], nx, ny)] -\n                                     uc[lin(hi[0], hi[1], hi[2], nx, ny)]) / h;", 1),
     ("jacdet: cofactor sign flipped", C,
      "Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +",
      "Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) -", 1),
