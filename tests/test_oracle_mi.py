@@ -132,7 +132,7 @@ def test_full_chain_gradient_wrt_u_matches_central_differences(rng):
         vm, _ = O.similarity_and_grad(F, M, um, spec, need_grad=False)
         fd = -(vp - vm) / (2 * h)
         # relative to the entry, with a floor at a tenth of the field's RMS so
-        # that entries near zero are judged on the FD rounding noise scale
+        # that entries near zero are compared on the FD rounding noise scale
         errs.append(abs(g[k] - fd) / (abs(fd) + 0.1 * rms))
     assert max(errs) < 1e-6, errs
 
