@@ -202,3 +202,18 @@ def test_brute_force_windows_on_a_tiny_volume(rng, win):
     S, n = O.lncc(F, J, win, eps, per_voxel=True)
     np.testing.assert_allclose(n, ref, rtol=1e-12, atol=1e-14)
     assert abs(S - ref.mean()) <= 1e-13
+
+
+def test_objective_of_lncc_is_one_minus_s(rng):
+    """The LNCC objective is C = 1 - S: an image against itself (S = 1) at
+    u = 0 gives loss 0, and the regulariser term adds lam R."""
+    F = rng.random((6, 7, 8))
+    spec = O.LossSpec(kind=O.LOSS_LNCC, window=3, eps=0.0)  # no window of random values is flat
+    obj = O.objective(F, F, np.zeros((3, 6, 7, 8)), spec, 0.5)
+    assert abs(obj["loss"]) < 1e-13 and obj["R"] == 0.0 and abs(obj["total"]) < 1e-13
+    u = np.zeros((3, 6, 7, 8))
+    u[0, :, :, 3:] = 0.25  # a step in x: R > 0, and the warp moves J off F
+    obj = O.objective(F, F, u, spec, 0.5)
+    S = O.lncc(F, O.warp(F, u), 3, 0.0)
+    assert abs(obj["loss"] - (1.0 - S)) < 1e-14 and obj["R"] > 0
+    assert abs(obj["total"] - (1.0 - S + 0.5 * obj["R"])) < 1e-14

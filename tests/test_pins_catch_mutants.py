@@ -198,6 +198,8 @@ MUTANTS = [
      "Jh, dJh = normalize(J, *spec.m_range)", "Jh, dJh = normalize(J, *spec.f_range)", 1),
     ("chain: intensities not clamped to [0, 1]", PY,
      "return np.clip(t, 0.0, 1.0), d", "return t, d", 1),
+    ("objective: LNCC loss taken as -S", PY,
+     "loss = 1.0 - sim if spec.kind == LOSS_LNCC else -sim", "loss = -sim", 1),
     ("objective: MI loss taken as 1 - MI", PY,
      "loss = 1.0 - sim if spec.kind == LOSS_LNCC else -sim", "loss = 1.0 - sim", 1),
     ("iterate: Adam input not scaled by N", PY,
