@@ -78,3 +78,16 @@ def test_mi_ranges_default_to_each_images_own():
     assert (d.f_lo, d.f_hi, d.m_lo, d.m_hi, d.bins) == (-2.0, 3.0, 10.0, 50.0, 16)
     d = RegConfig(loss="mi", m_range=(0.0, 60.0)).loss_desc(F, M)
     assert (d.m_lo, d.m_hi) == (0.0, 60.0)
+
+
+def test_experiment_helpers():
+    """Time-to-target takes the first iterate within tol of the target; the
+    workload configurations map to the registration settings they state."""
+    from paper_2509_25044_gb300 import synth
+    from paper_2509_25044_gb300.experiments import LNCC_EPS, _cfg, _first_within
+    assert _first_within([5.0, 3.0, 2.05, 1.0], 2.0, 0.1) == 2
+    assert _first_within([5.0, 3.0], 2.0, 0.1) is None
+    c0 = _cfg(synth.CONFIGS["c0"], {}, "f32", lam_scale=2.0)
+    assert (c0.loss, c0.window, c0.eps, c0.lam, c0.moments) == ("lncc", 7, LNCC_EPS, 0.2, "f32")
+    c1 = _cfg(synth.CONFIGS["c1"], {"f_range": (0.0, 1.0), "m_range": (0.1, 0.9)}, "bf16")
+    assert (c1.loss, c1.bins, c1.m_range, c1.lam, c1.moments) == ("mi", 32, (0.1, 0.9), 0.05, "bf16")
