@@ -89,6 +89,22 @@ def _load():
         lib.or_conv3d_dgrad.restype = None
         lib.or_conv3d_wgrad.argtypes = [_dp, ci, _dp, ci, ci, ci, ci, _dp]
         lib.or_conv3d_wgrad.restype = None
+        cl, cd = ctypes.c_long, ctypes.c_double
+        lib.or_leaky.argtypes = [_dp, cl, cd, _dp]
+        lib.or_leaky_bwd.argtypes = [_dp, _dp, cl, cd, _dp]
+        lib.or_avgpool2.argtypes = [_dp, ci, ci, ci, ci, _dp]
+        lib.or_avgpool2_adjoint.argtypes = [_dp, ci, ci, ci, ci, _dp]
+        lib.or_upsample.argtypes = [_dp, ci, ci, ci, ci, ci, _dp]
+        lib.or_upsample_adjoint.argtypes = [_dp, ci, ci, ci, ci, ci, _dp]
+        lib.or_concat.argtypes = [_dp, ci, _dp, ci, cl, _dp]
+        lib.or_field_down2.argtypes = [_dp, ci, ci, ci, _dp]
+        lib.or_field_upsample.argtypes = [_dp, ci, ci, ci, ci, _dp]
+        lib.or_pack_pair.argtypes = [_dp, _dp, ci, ci, ci, ci, cd, cd, cd, cd, _dp]
+        lib.or_mse.argtypes = [_dp, _dp, cl, _dp]
+        lib.or_mse.restype = cd
+        for f in ("or_leaky", "or_leaky_bwd", "or_avgpool2", "or_avgpool2_adjoint", "or_upsample",
+                  "or_upsample_adjoint", "or_concat", "or_field_down2", "or_field_upsample", "or_pack_pair"):
+            getattr(lib, f).restype = None
         _lib = lib
     return _lib
 
@@ -335,6 +351,100 @@ def conv3d_wgrad(x, dout):
     dw = np.empty((cout, 27, cin))
     _load().or_conv3d_wgrad(_ptr(x), cin, _ptr(dout), cout, nx, ny, nz, _ptr(dw))
     return dw
+
+
+# --------------------------------------------------------------------------
+# the learned initialiser's other operators (channels-last activations
+# [nz, ny, nx, C]; displacement fields [3, nz, ny, nx])
+# --------------------------------------------------------------------------
+def leaky(x, slope: float = 0.2):
+    x = _f64(x)
+    y = np.empty_like(x)
+    _load().or_leaky(_ptr(x), x.size, float(slope), _ptr(y))
+    return y
+
+
+def leaky_bwd(x, dy, slope: float = 0.2):
+    """dL/dx of y = LeakyReLU(x) for the upstream gradient dy."""
+    x, dy = _f64(x), _f64(dy)
+    dx = np.empty_like(x)
+    _load().or_leaky_bwd(_ptr(x), _ptr(dy), x.size, float(slope), _ptr(dx))
+    return dx
+
+
+def avgpool2(x):
+    x = _f64(x)
+    nz, ny, nx, c = x.shape
+    out = np.empty((nz // 2, ny // 2, nx // 2, c))
+    _load().or_avgpool2(_ptr(x), c, nx, ny, nz, _ptr(out))
+    return out
+
+
+def avgpool2_adjoint(g, fine_shape):
+    g = _f64(g)
+    nz, ny, nx = fine_shape
+    c = g.shape[3]
+    out = np.empty((nz, ny, nx, c))
+    _load().or_avgpool2_adjoint(_ptr(g), c, nx, ny, nz, _ptr(out))
+    return out
+
+
+def upsample(x, s: int = 2):
+    x = _f64(x)
+    nz, ny, nx, c = x.shape
+    out = np.empty((s * nz, s * ny, s * nx, c))
+    _load().or_upsample(_ptr(x), c, nx, ny, nz, int(s), _ptr(out))
+    return out
+
+
+def upsample_adjoint(g, s: int = 2):
+    g = _f64(g)
+    nz, ny, nx, c = g.shape
+    out = np.empty((nz // s, ny // s, nx // s, c))
+    _load().or_upsample_adjoint(_ptr(g), c, nx // s, ny // s, nz // s, int(s), _ptr(out))
+    return out
+
+
+def concat(a, b):
+    a, b = _f64(a), _f64(b)
+    V = a.size // a.shape[-1]
+    out = np.empty(a.shape[:-1] + (a.shape[-1] + b.shape[-1],))
+    _load().or_concat(_ptr(a), a.shape[-1], _ptr(b), b.shape[-1], V, _ptr(out))
+    return out
+
+
+def field_down2(u):
+    u = _f64(u)
+    _, nz, ny, nx = u.shape
+    out = np.empty((3, nz // 2, ny // 2, nx // 2))
+    _load().or_field_down2(_ptr(u), nx, ny, nz, _ptr(out))
+    return out
+
+
+def field_upsample(u, s: int):
+    u = _f64(u)
+    _, nz, ny, nx = u.shape
+    out = np.empty((3, s * nz, s * ny, s * nx))
+    _load().or_field_upsample(_ptr(u), nx, ny, nz, int(s), _ptr(out))
+    return out
+
+
+def pack_pair(F, M, factor: int, f_range, m_range):
+    """[nz/f, ny/f, nx/f, 2]: block means of F and M mapped by their ranges."""
+    F, M = _f64(F), _f64(M)
+    nz, ny, nx = F.shape
+    out = np.empty((nz // factor, ny // factor, nx // factor, 2))
+    _load().or_pack_pair(_ptr(F), _ptr(M), nx, ny, nz, int(factor), float(f_range[0]), float(f_range[1]),
+                         float(m_range[0]), float(m_range[1]), _ptr(out))
+    return out
+
+
+def mse(pred, target):
+    """(loss, dloss/dpred) for [3, V] (or [3, ...]) fields."""
+    pred, target = _f64(pred), _f64(target)
+    g = np.empty_like(pred)
+    loss = _load().or_mse(_ptr(pred), _ptr(target), pred.size // 3, _ptr(g))
+    return loss, g
 
 
 # --------------------------------------------------------------------------

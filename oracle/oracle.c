@@ -940,3 +940,180 @@ void or_conv3d_wgrad(const double *in, int Cin, const double *dout, int Cout, in
                 dw[((long)o * 27 + t) * Cin + c] = acc;
             }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The learned initialiser's other operators (the U-Net of the workloads:   */
+/* LeakyReLU 0.2, 2x average pooling down, 2x trilinear upsampling plus     */
+/* channel concat up, and the resampling of its half-resolution output to   */
+/* the registration grid).  Activations are channels-last in[v][C];         */
+/* displacement fields are [3][nz][ny][nx] in voxel units of their grid.    */
+/* ------------------------------------------------------------------------ */
+
+/* LeakyReLU: x for x > 0, slope * x otherwise; its derivative 1 or slope   */
+/* (slope at x = 0).  dx = dy * f'(x).                                       */
+void or_leaky(const double *x, long n, double slope, double *y)
+{
+    for (long i = 0; i < n; ++i) y[i] = x[i] > 0.0 ? x[i] : slope * x[i];
+}
+void or_leaky_bwd(const double *x, const double *dy, long n, double slope, double *dx)
+{
+    for (long i = 0; i < n; ++i) dx[i] = x[i] > 0.0 ? dy[i] : slope * dy[i];
+}
+
+/* 2x average pooling: out[Z][Y][X][c] = mean of in over the 2x2x2 block at */
+/* (2X, 2Y, 2Z); nx, ny, nz (the input's) even.  The adjoint spreads each   */
+/* coarse gradient over its block with weight 1/8.                          */
+void or_avgpool2(const double *in, int C, int nx, int ny, int nz, double *out)
+{
+    const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+    for (int Z = 0; Z < mz; ++Z)
+        for (int Y = 0; Y < my; ++Y)
+            for (int X = 0; X < mx; ++X)
+                for (int c = 0; c < C; ++c) {
+                    double s = 0.0;
+                    for (int dz = 0; dz < 2; ++dz)
+                        for (int dy = 0; dy < 2; ++dy)
+                            for (int dx = 0; dx < 2; ++dx)
+                                s += in[lin(2 * X + dx, 2 * Y + dy, 2 * Z + dz, nx, ny) * C + c];
+                    out[lin(X, Y, Z, mx, my) * C + c] = s / 8.0;
+                }
+}
+void or_avgpool2_adjoint(const double *gout, int C, int nx, int ny, int nz, double *gin)
+{
+    const int mx = nx / 2, my = ny / 2;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                for (int c = 0; c < C; ++c)
+                    gin[lin(x, y, z, nx, ny) * C + c] = gout[lin(x / 2, y / 2, z / 2, mx, my) * C + c] / 8.0;
+}
+
+/* Trilinear upsampling by an integer factor s with voxel-centre alignment: */
+/* the centre of fine voxel f lies at coarse coordinate (f + 1/2) / s - 1/2  */
+/* (x_fine = s x_coarse + (s - 1) / 2).  Along each axis the value is the    */
+/* linear interpolation between the coarse voxels floor(c) and floor(c) + 1, */
+/* both clamped into [0, n - 1] (border).  in: coarse [nzc][nyc][nxc][C],    */
+/* out: fine (s nxc, s nyc, s nzc) x C.                                      */
+static void up_coord(int f, int s, int n, int *i0, int *i1, double *a)
+{
+    const double c = ((double)f + 0.5) / (double)s - 0.5;
+    const double fl = floor(c);
+    *a = c - fl;
+    int lo = (int)fl, hi = (int)fl + 1;
+    *i0 = lo < 0 ? 0 : (lo > n - 1 ? n - 1 : lo);
+    *i1 = hi < 0 ? 0 : (hi > n - 1 ? n - 1 : hi);
+}
+
+void or_upsample(const double *in, int C, int nxc, int nyc, int nzc, int s, double *out)
+{
+    const int nx = s * nxc, ny = s * nyc, nz = s * nzc;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int ix[2], iy[2], iz[2];
+                double ax, ay, az;
+                up_coord(x, s, nxc, &ix[0], &ix[1], &ax);
+                up_coord(y, s, nyc, &iy[0], &iy[1], &ay);
+                up_coord(z, s, nzc, &iz[0], &iz[1], &az);
+                for (int c = 0; c < C; ++c) {
+                    double v = 0.0;
+                    for (int b = 0; b < 8; ++b) {
+                        const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+                        const double w = (bx ? ax : 1.0 - ax) * (by ? ay : 1.0 - ay) * (bz ? az : 1.0 - az);
+                        v += w * in[lin(ix[bx], iy[by], iz[bz], nxc, nyc) * C + c];
+                    }
+                    out[lin(x, y, z, nx, ny) * C + c] = v;
+                }
+            }
+}
+
+/* its adjoint: every fine gradient scattered onto its 8 coarse corners */
+void or_upsample_adjoint(const double *gout, int C, int nxc, int nyc, int nzc, int s, double *gin)
+{
+    const int nx = s * nxc, ny = s * nyc, nz = s * nzc;
+    memset(gin, 0, sizeof(double) * (size_t)nxc * nyc * nzc * C);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int ix[2], iy[2], iz[2];
+                double ax, ay, az;
+                up_coord(x, s, nxc, &ix[0], &ix[1], &ax);
+                up_coord(y, s, nyc, &iy[0], &iy[1], &ay);
+                up_coord(z, s, nzc, &iz[0], &iz[1], &az);
+                for (int c = 0; c < C; ++c)
+                    for (int b = 0; b < 8; ++b) {
+                        const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+                        const double w = (bx ? ax : 1.0 - ax) * (by ? ay : 1.0 - ay) * (bz ? az : 1.0 - az);
+                        gin[lin(ix[bx], iy[by], iz[bz], nxc, nyc) * C + c] += w * gout[lin(x, y, z, nx, ny) * C + c];
+                    }
+            }
+}
+
+/* channel concat of two channels-last volumes of V voxels: out[v] =        */
+/* [a[v][0 .. Ca), b[v][0 .. Cb)]                                            */
+void or_concat(const double *a, int Ca, const double *b, int Cb, long V, double *out)
+{
+    for (long v = 0; v < V; ++v) {
+        for (int c = 0; c < Ca; ++c) out[v * (Ca + Cb) + c] = a[v * Ca + c];
+        for (int c = 0; c < Cb; ++c) out[v * (Ca + Cb) + Ca + c] = b[v * Cb + c];
+    }
+}
+
+/* Displacement resampling between the network's grid and the registration */
+/* grid.  Down: 2x block mean of each channel, halved (the displacement in  */
+/* coarse voxels).  Up: trilinear upsampling by s (as or_upsample),          */
+/* multiplied by s (the displacement in fine voxels).                        */
+void or_field_down2(const double *u, int nx, int ny, int nz, double *out)
+{
+    const int mx = nx / 2, my = ny / 2, mz = nz / 2;
+    const long n = (long)nx * ny * nz, m = (long)mx * my * mz;
+    for (int ch = 0; ch < 3; ++ch) {
+        or_avgpool2(u + ch * n, 1, nx, ny, nz, out + ch * m);
+        for (long i = 0; i < m; ++i) out[ch * m + i] *= 0.5;
+    }
+}
+void or_field_upsample(const double *u, int nxc, int nyc, int nzc, int s, double *out)
+{
+    const long m = (long)nxc * nyc * nzc, n = m * s * s * s;
+    for (int ch = 0; ch < 3; ++ch) {
+        or_upsample(u + ch * m, 1, nxc, nyc, nzc, s, out + ch * n);
+        for (long i = 0; i < n; ++i) out[ch * n + i] *= (double)s;
+    }
+}
+
+/* The network input: F and M averaged over factor^3 blocks, each mapped to */
+/* (v - lo) / (hi - lo); out[v][0] = F, out[v][1] = M at d / factor.         */
+void or_pack_pair(const double *F, const double *M, int nx, int ny, int nz, int factor, double f_lo, double f_hi,
+                  double m_lo, double m_hi, double *out)
+{
+    const int mx = nx / factor, my = ny / factor, mz = nz / factor;
+    const double cnt = (double)factor * factor * factor;
+    for (int Z = 0; Z < mz; ++Z)
+        for (int Y = 0; Y < my; ++Y)
+            for (int X = 0; X < mx; ++X) {
+                double sf = 0.0, sm = 0.0;
+                for (int dz = 0; dz < factor; ++dz)
+                    for (int dy = 0; dy < factor; ++dy)
+                        for (int dx = 0; dx < factor; ++dx) {
+                            const long p = lin(X * factor + dx, Y * factor + dy, Z * factor + dz, nx, ny);
+                            sf += F[p];
+                            sm += M[p];
+                        }
+                const long v = lin(X, Y, Z, mx, my);
+                out[2 * v] = (sf / cnt - f_lo) / (f_hi - f_lo);
+                out[2 * v + 1] = (sm / cnt - m_lo) / (m_hi - m_lo);
+            }
+}
+
+/* The training loss: mean over the 3 channels and V voxels of              */
+/* (pred - target)^2, and its gradient 2 (pred - target) / (3 V).           */
+double or_mse(const double *pred, const double *target, long V, double *grad)
+{
+    double s = 0.0;
+    for (long i = 0; i < 3 * V; ++i) {
+        const double d = pred[i] - target[i];
+        s += d * d;
+        if (grad) grad[i] = 2.0 * d / (3.0 * (double)V);
+    }
+    return s / (3.0 * (double)V);
+}

@@ -144,13 +144,24 @@ def _check(status: int, where: str):
 
 
 def _ptr(t):
-    """Device address of a tensor.  Host tensors are refused here: every entry
-    point reads and writes device memory only, and there is no host path."""
+    """Device address of a tensor, taken only after three checks:
+    - it is contiguous: the library indexes every array densely from its
+      dims, so an expanded or strided view would be read past its storage;
+    - it is device memory: every entry point reads and writes device memory
+      only, and there is no host path;
+    - it lives on the current CUDA device, where the library launches its
+      kernels (select another GPU with torch.cuda.device / set_device)."""
     if t is None:
         return None
+    if not t.is_contiguous():
+        raise ValueError("a non-contiguous tensor was passed: every array must be dense and contiguous")
     if t.device.type != "cuda":
         raise ValueError(f"a {t.device.type} tensor was passed where device memory is required "
                          "(the library runs on the GPU only)")
+    cur = torch.cuda.current_device()
+    if t.device.index is not None and t.device.index != cur:
+        raise ValueError(f"a tensor on {t.device} was passed while cuda:{cur} is the current device "
+                         "(the library launches on the current device)")
     return ctypes.c_void_p(t.data_ptr())
 
 

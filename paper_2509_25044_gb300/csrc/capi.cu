@@ -69,6 +69,10 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
     long long nb = diffusion_grid(g).blocks();
     const long long mi = mi_sweep_grid(g).blocks();
     if (mi > nb) nb = mi;
+    if (mi_tma_ok(g)) {
+        const long long mt = mi_tma_sweep_grid(g).blocks();
+        if (mt > nb) nb = mt;
+    }
     if (L && L->kind == REG_LOSS_LNCC) {
         const long long ln = lncc_max_blocks(g);
         if (ln > nb) nb = ln;

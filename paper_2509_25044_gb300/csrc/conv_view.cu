@@ -54,6 +54,26 @@ bool make_map_bf16_4d(CUtensorMap *map, const void *base, const uint64_t dims[4]
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+bool make_map(CUtensorMap *map, const void *base, int dt, int rank, const uint64_t *dims, const uint32_t *box) {
+    const EncodeTiled fn = encode_fn();
+    if (!fn || rank < 1 || rank > 5) return false;
+    const uint64_t es = dt == REG_BF16 ? 2 : 4;
+    cuuint64_t gdim[5], gstride[4];
+    cuuint32_t bx[5], estr[5];
+    uint64_t stride = es;
+    for (int i = 0; i < rank; ++i) {
+        gdim[i] = dims[i];
+        bx[i] = box[i];
+        estr[i] = 1;
+        if (i > 0) gstride[i - 1] = stride;
+        stride *= dims[i];
+    }
+    return fn(map, dt == REG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+              (cuuint32_t)rank, const_cast<void *>(base), gdim, gstride, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace tma
 
 namespace {
@@ -545,10 +565,12 @@ cudaError_t launch_conv_view(const void *in, int Cin, const void *W, int rows, i
     if (e != cudaSuccess) return e;
     const size_t smem = view_smem_bytes(G);
     const dim3 grid((unsigned)(G.tiles_y * ((d.nz + G.Tz - 1) / G.Tz)), (unsigned)nblocks);
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     auto run = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            kern<<<grid, VIEW_THREADS, smem, s>>>(map, (const __nv_bfloat16 *)Wt_scratch, bias, out, G, error_word());
+            kern<<<grid, VIEW_THREADS, smem, s>>>(map, (const __nv_bfloat16 *)Wt_scratch, bias, out, G, err);
     };
     switch (epi) {
         case EPI_BIAS_LEAKY_BF16: run(conv_view_kernel<EPI_BIAS_LEAKY_BF16>); break;
@@ -582,7 +604,9 @@ cudaError_t launch_conv_wgrad_view(const void *in, int Cin, const void *dpre, in
     cudaError_t e = cudaFuncSetAttribute(conv_wgrad_view_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    conv_wgrad_view_kernel<<<grid, VIEW_THREADS, smem, s>>>(xmap, dmap, G, part, error_word());
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
+    conv_wgrad_view_kernel<<<grid, VIEW_THREADS, smem, s>>>(xmap, dmap, G, part, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int K = 27 * Cin, total = Cout * Kpad;

@@ -134,6 +134,17 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                              const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                              void *m, void *v, int mdt, const StepParams &S, double *partials,
                              unsigned *counter, double *r_out, cudaStream_t s, const AffineT *aff = nullptr);
+// The TMA-staged form of the plain second sweep (mi_tma.cu), used by
+// launch_mi_sweep2 when mi_tma_ok(g) and there is no composite transform;
+// cudaErrorNotSupported if a tensor map cannot be built (the caller then
+// runs the plain kernel).  Its grid has mi_tma_sweep_grid(g).blocks() CTAs
+// (one partial each).
+bool mi_tma_ok(const Dims &g);
+MarchGrid mi_tma_sweep_grid(const Dims &g);
+cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
+                                 const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
+                                 void *m, void *v, int mdt, const StepParams &S, double *partials,
+                                 unsigned *counter, double *r_out, cudaStream_t s);
 
 // First LNCC sweep: window statistics of F and the warped image J (already
 // in HBM, FP32) -> similarity (+ optional adjoint coefficient fields, [3][N]).

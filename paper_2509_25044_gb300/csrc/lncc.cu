@@ -698,6 +698,7 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
     dim3 grid;
     const dim3 block(TX, TY);
     unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
@@ -762,6 +763,7 @@ static cudaError_t launch_lncc_sweep2_ants(const void *F, const void *M, int dt,
     const MarchGrid G = lncc_ants_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     const AffineT A = aff ? *aff : AffineT{};
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
@@ -816,6 +818,7 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
     const dim3 block(TX, TY);
     const size_t smem = lncc_smem_bytes(P.r, 3);
     unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;

@@ -21,47 +21,11 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "mi_common.cuh"
 
 namespace regk {
 
-// Cubic B-spline weights of the 4 bins around bin coordinate s in [1, B-2]:
-// bins i0-1 .. i0+2 with i0 = min(floor(s), B-3), fraction f = s - i0.
-__device__ __forceinline__ int bspline_weights(float s, int B, float w[4]) {
-    int i0 = (int)floorf(s);
-    i0 = min(max(i0, 1), B - 3);
-    const float f = s - (float)i0;
-    const float f2 = f * f, f3 = f2 * f, g = 1.0f - f;
-    w[0] = g * g * g * (1.0f / 6.0f);
-    w[1] = (3.0f * f3 - 6.0f * f2 + 4.0f) * (1.0f / 6.0f);
-    w[2] = (-3.0f * f3 + 3.0f * f2 + 3.0f * f + 1.0f) * (1.0f / 6.0f);
-    w[3] = f3 * (1.0f / 6.0f);
-    return i0;
-}
-
-// derivatives of the same 4 weights with respect to s
-__device__ __forceinline__ int bspline_dweights(float s, int B, float d[4]) {
-    int i0 = (int)floorf(s);
-    i0 = min(max(i0, 1), B - 3);
-    const float f = s - (float)i0;
-    const float g = 1.0f - f;
-    d[0] = -0.5f * g * g;
-    d[1] = 1.5f * f * f - 2.0f * f;
-    d[2] = -1.5f * f * f + f + 0.5f;
-    d[3] = 0.5f * f * f;
-    return i0;
-}
-
-__device__ __forceinline__ float to_bin(float v, float lo, float scale, int B) {
-    const float t = fminf(fmaxf((v - lo) * scale, 0.0f), 1.0f);
-    return fmaf(t, (float)(B - 3), 1.0f);
-}
-
-// Shared histogram of one CTA: copies private copies, copy c used by the
-// lanes with lane % copies == c, each copy padded by one word so that the
-// same bin of different copies falls in different banks.  With 32 copies
-// (B <= 32) the 32 lanes of one atomic instruction never share an address.
 constexpr int HIST_TX = 32, HIST_TY = 32, HIST_THREADS = HIST_TX * HIST_TY;
-__host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 32 : (B <= 45 ? 16 : 8); }
 // A copy serves (32 / copies) lanes of each of the 32 warps, one voxel per
 // lane and plane, so after this many planes a CTA adds its copies to the
 // global histogram and clears them (MI_MAX_COPY_VOXELS keeps the 32-bit
@@ -69,7 +33,6 @@ __host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 32 : (B 
 __host__ __device__ constexpr int hist_batch_planes(int B) {
     return MI_MAX_COPY_VOXELS / (32 * (32 / hist_copies(B)));
 }
-size_t mi_hist_smem_bytes(int B) { return sizeof(unsigned) * (size_t)hist_copies(B) * ((size_t)B * B + 1); }
 
 // Persistent CTAs (one per SM): the volume is cut into 32 x 32 columns, the
 // (column, plane) pairs are numbered column-major and each CTA takes one
@@ -77,13 +40,7 @@ size_t mi_hist_smem_bytes(int B) { return sizeof(unsigned) * (size_t)hist_copies
 // Each thread marches its (x, y) column through the planes of its range,
 // with F and u of the next plane requested before the current plane is
 // computed, and adds the 16 fixed-point products of its voxel's B-spline
-// weights to its copy.  The products are rounded by one FFMA against
-// 2^23 (exact round-to-nearest of wf * wj * MI_FIXED_SCALE, which is below
-// 2^22), so the bins are sums of integers and the histogram does not depend
-// on the order of the atomics (deterministic).
-// nearest bin of bin coordinate s (the hard-binned estimator's rule)
-__device__ __forceinline__ int nearest_bin(float s, int B) { return min(max((int)floorf(s + 0.5f), 1), B - 2); }
-
+// weights to its copy (hist_add_parzen).
 template <typename T, int PAD, typename I, bool HARD, bool AFF>
 __global__ void __launch_bounds__(HIST_THREADS, 1)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
@@ -100,7 +57,6 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
     const I nxy = (I)g.nxy;
     const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
     const int batch = hist_batch_planes(B);
-    constexpr float MAGIC = 8388608.0f;  // 2^23: ulp 1 in [2^23, 2^24)
     for (long long b0 = beg; b0 < end; b0 += batch) {
         const long long b1 = min(end, b0 + batch);
         for (long long pos = b0; pos < b1;) {
@@ -138,18 +94,7 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
                     const int mJ = nearest_bin(to_bin(jv, P.m_lo, P.m_scale, B), B);
                     atomicAdd(shc + mF * B + mJ, 1u);
                 } else {
-                    float wf[4], wj[4];
-                    const int iF = bspline_weights(to_bin(fv, P.f_lo, P.f_scale, B), B, wf) - 1;
-                    const int iJ = bspline_weights(to_bin(jv, P.m_lo, P.m_scale, B), B, wj) - 1;
-                    unsigned *row = shc + iF * B + iJ;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const float sa = wf[a] * MI_FIXED_SCALE;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            atomicAdd(row + b, __float_as_uint(fmaf(sa, wj[b], MAGIC)) - 0x4B000000u);
-                        row += B;
-                    }
+                    hist_add_parzen(shc, B, to_bin(fv, P.f_lo, P.f_scale, B), to_bin(jv, P.m_lo, P.m_scale, B));
                 }
                 fv = fn;
                 ux = nx0;
@@ -414,7 +359,9 @@ cudaError_t launch_mi_finalize(const unsigned long long *hist, const MiParams &P
     // Parzen bins hold fixed-point weight (MI_FIXED_SCALE per unit); hard bins hold counts
     const double inv_total = 1.0 / ((P.hard ? 1.0 : (double)MI_FIXED_SCALE) * (double)N);
     const double gscale = -(double)(P.bins - 3) * (double)P.m_scale / (double)N;
-    mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, P.hard, inv_total, gscale, Gtab, sim_out, error_word());
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
+    mi_finalize_kernel<<<1, 1024, 0, s>>>(hist, P.bins, P.hard, inv_total, gscale, Gtab, sim_out, err);
     return cudaGetLastError();
 }
 
@@ -422,10 +369,17 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                              const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                              void *m, void *v, int mdt, const StepParams &S, double *partials,
                              unsigned *counter, double *r_out, cudaStream_t s, const AffineT *aff) {
+    // the TMA-staged form (mi_tma.cu), same arithmetic, where its tensor maps apply
+    if (!aff && mi_tma_ok(g)) {
+        const cudaError_t e = launch_mi_sweep2_tma(F, M, dt, u, g, pad, P, Gtab, grad_out, step, u_out, m, v, mdt,
+                                                   S, partials, counter, r_out, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const MarchGrid G = mi_sweep_grid(g);
     const AffineT A = aff ? *aff : AffineT{};
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     const size_t smem = sizeof(float4) * (size_t)P.bins * P.bins;
     cudaError_t e = cudaSuccess;
     // the G table exceeds the default 48 KiB of dynamic shared memory only for B > 55

@@ -1,0 +1,350 @@
+// mi_tma.cu -- the second MI sweep (Sec. 2.2, Eq. gradientmi-threadn; App.
+// fused MI), fused with the diffusion gradient and Adam, with every streamed
+// array staged in shared memory by the Tensor Memory Accelerator.
+//
+// The plain sweep (mi.cu) loads u, F, m and v itself, one plane ahead in
+// registers, and spends most of its issue slots on those loads and their
+// 64-bit addresses; at gigavoxel sizes its loads are too few in flight to
+// cover DRAM latency.  Here a CTA owns a 32 x 8 voxel tile and marches it
+// through a chunk of z-planes with warp specialisation:
+//
+//   producer (one elected thread of warp 8): for each plane, one tiled TMA
+//     copy of u with the diffusion stencil's halo (x0-4 .. x0+35, y0-1 ..
+//     y0+8, all 3 channels; zero outside the volume) into a ring of SW_NU
+//     plane slots, and one copy each of F, m and v (the tile, 3 channels for
+//     m and v) into a ring of SW_NS slots.  Each slot's mbarrier completes on
+//     the copies' byte count; the producer refills a slot once the 8
+//     consumer warps have released it (a second mbarrier per slot).
+//   consumers (warps 0-7, one row of the tile each, one voxel per lane): u at
+//     z-1, z, z+1 and the 4 in-plane neighbours, F, m and v come from shared
+//     memory; only the 8 corner gathers of the trilinear sampler go to
+//     global memory.  The per-voxel arithmetic (sampler, B-spline weights,
+//     16-term adjoint, diffusion, Adam) is that of mi.cu term for term, so
+//     both paths give the same bits for u', m, v and the gradient.
+//
+// Every wait is bounded: a wait that expires latches REG_ERR_TIMEOUT in the
+// device error word, the CTA stops issuing and consuming, waits (bounded)
+// for the copies it has in flight and returns.
+#include <algorithm>
+
+#include "kernels.h"
+#include "mi_common.cuh"
+#include "tma.cuh"
+
+namespace regk {
+
+namespace {
+
+constexpr int SW_TX = 32, SW_TY = 8;                                 // tile: one warp per row
+constexpr int SW_UX = SW_TX + 8, SW_UY = SW_TY + 2, SW_UC = SW_UX * SW_UY;  // u box: x0-4 .., y0-1 ..
+constexpr int SW_NU = 5;   // u plane slots: z-1, z, z+1 in use, two in flight
+constexpr int SW_NS = 3;   // F / m / v plane slots
+constexpr int SW_WARPS = SW_TY + 1;
+constexpr int SW_THREADS = 32 * SW_WARPS;
+constexpr uint32_t SW_UBYTES = 3u * SW_UC * sizeof(float);
+
+__host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) & ~(size_t)127; }
+
+// dynamic shared memory: the adjoint table, the two rings, the mbarriers
+struct SwLayout {
+    size_t u, f, m, v, bar, total, fslot, mslot;
+    __host__ __device__ SwLayout(int B, int fbytes, int mbytes) {
+        fslot = al128((size_t)SW_TX * SW_TY * fbytes);
+        mslot = al128((size_t)3 * SW_TX * SW_TY * mbytes);
+        u = al128(sizeof(float4) * (size_t)B * B);
+        f = u + SW_NU * al128(SW_UBYTES);
+        m = f + SW_NS * fslot;
+        v = m + SW_NS * mslot;
+        bar = v + SW_NS * mslot;
+        total = bar + sizeof(uint64_t) * 2 * (SW_NU + SW_NS);
+    }
+};
+
+__device__ __forceinline__ float sm_val(const float *p, int i) { return p[i]; }
+__device__ __forceinline__ float sm_val(const __nv_bfloat16 *p, int i) { return __bfloat162float(p[i]); }
+
+}  // namespace
+
+template <typename T, typename MT, bool STEP, int PAD, typename I>
+__global__ void __launch_bounds__(SW_THREADS, 3)
+    mi_sweep2_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
+                         const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap vmap,
+                         const T *__restrict__ M, Dims g, MiParams P, int zc, const float *__restrict__ Gtab,
+                         float *__restrict__ grad_out, float *__restrict__ u_out, MT *__restrict__ m,
+                         MT *__restrict__ v, StepParams S, double *__restrict__ partials,
+                         unsigned *__restrict__ counter, double *__restrict__ r_out, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ volatile int abort_flag;
+    constexpr int FB = (int)sizeof(T), MB = STEP ? (int)sizeof(MT) : 0;
+    const int B = P.bins, BB = B * B;
+    const SwLayout L(B, FB, MB);
+    float4 *G4 = reinterpret_cast<float4 *>(smem);
+    uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + L.bar);
+    uint64_t *empty_u = full_u + SW_NU, *full_s = empty_u + SW_NU, *empty_s = full_s + SW_NS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float4 *T4 = mi_table4(Gtab);
+    for (int i = tid; i < BB; i += SW_THREADS) G4[i] = __ldg(T4 + i);
+    if (tid == 0) {
+        for (int s = 0; s < SW_NU; ++s) {
+            umma::mbar_init(full_u + s, 1);
+            umma::mbar_init(empty_u + s, SW_TY);
+        }
+        for (int s = 0; s < SW_NS; ++s) {
+            umma::mbar_init(full_s + s, 1);
+            umma::mbar_init(empty_s + s, SW_TY);
+        }
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    const int x0 = blockIdx.x * SW_TX, y0 = blockIdx.y * SW_TY;
+    const int z0 = blockIdx.z * zc, z1 = min(g.nz, z0 + zc), nzc = z1 - z0;
+    double rsum = 0.0;
+    if (warp == SW_TY) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            const uint32_t sbytes = (uint32_t)(SW_TX * SW_TY * FB + 2 * 3 * SW_TX * SW_TY * MB);
+            int ju = 0, ks = 0;  // u planes / F,m,v planes issued
+            for (int j = 0; j < nzc + 2 && !abort_flag; ++j) {
+                const int su = j % SW_NU;
+                if (j >= SW_NU && !umma::mbar_wait(empty_u + su, ((j / SW_NU) - 1) & 1)) {
+                    latch_error(err, REG_ERR_TIMEOUT);
+                    abort_flag = 1;
+                    break;
+                }
+                tma::expect_tx(full_u + su, SW_UBYTES);
+                tma::load_4d(smem + L.u + su * al128(SW_UBYTES), &umap, x0 - 4, y0 - 1, z0 - 1 + j, 0, full_u + su);
+                ju = j + 1;
+                const int k = j - 1;
+                if (k < 0 || k >= nzc) continue;
+                const int ss = k % SW_NS;
+                if (k >= SW_NS && !umma::mbar_wait(empty_s + ss, ((k / SW_NS) - 1) & 1)) {
+                    latch_error(err, REG_ERR_TIMEOUT);
+                    abort_flag = 1;
+                    break;
+                }
+                tma::expect_tx(full_s + ss, sbytes);
+                tma::load_3d(smem + L.f + ss * L.fslot, &fmap, x0, y0, z0 + k, full_s + ss);
+                if (STEP) {
+                    tma::load_4d(smem + L.m + ss * L.mslot, &mmap, x0, y0, z0 + k, 0, full_s + ss);
+                    tma::load_4d(smem + L.v + ss * L.mslot, &vmap, x0, y0, z0 + k, 0, full_s + ss);
+                }
+                ks = k + 1;
+            }
+            // copies still in flight (only after an abort) land before the CTA exits
+            for (int j = std::max(0, ju - SW_NU); j < ju; ++j) umma::mbar_wait(full_u + j % SW_NU, (j / SW_NU) & 1);
+            for (int k = std::max(0, ks - SW_NS); k < ks; ++k) umma::mbar_wait(full_s + k % SW_NS, (k / SW_NS) & 1);
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int x = x0 + lane, y = y0 + warp;
+        const bool in = x < g.nx && y < g.ny;
+        const bool hxm = x > 0, hxp = x + 1 < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
+        const I nxy = (I)g.nxy;
+        I p = (I)z0 * nxy + (I)y * g.nx + x;
+        const int o = (warp + 1) * SW_UX + lane + 4;  // (x, y) in a u channel slot
+        const int t = warp * SW_TX + lane;            // (x, y) in an F / m / v slot
+        float racc = 0.0f;
+        for (int zi = 0; zi < nzc; ++zi, p += nxy) {
+            const int z = z0 + zi;
+            bool ok = true;
+            if (zi == 0) ok = umma::mbar_wait(full_u, 0) && umma::mbar_wait(full_u + 1, 0);
+            const int jn = zi + 2;
+            ok = ok && umma::mbar_wait(full_u + jn % SW_NU, (jn / SW_NU) & 1) &&
+                 umma::mbar_wait(full_s + zi % SW_NS, (zi / SW_NS) & 1);
+            if (!ok || abort_flag) {
+                latch_error(err, REG_ERR_TIMEOUT);
+                abort_flag = 1;
+                break;
+            }
+            const float *Up = reinterpret_cast<const float *>(smem + L.u + (zi % SW_NU) * al128(SW_UBYTES));
+            const float *Uc = reinterpret_cast<const float *>(smem + L.u + ((zi + 1) % SW_NU) * al128(SW_UBYTES));
+            const float *Un = reinterpret_cast<const float *>(smem + L.u + (jn % SW_NU) * al128(SW_UBYTES));
+            const T *Fs = reinterpret_cast<const T *>(smem + L.f + (zi % SW_NS) * L.fslot);
+            if (in) {
+                const float cur[3] = {Uc[o], Uc[SW_UC + o], Uc[2 * SW_UC + o]};
+                float sx, sy, sz;
+                const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
+                float wf[4], dj[4];
+                const int iF = bspline_weights(to_bin(sm_val(Fs, t), P.f_lo, P.f_scale, B), B, wf) - 1;
+                const float tj = (jv - P.m_lo) * P.m_scale;
+                const int iJ = bspline_dweights(to_bin(jv, P.m_lo, P.m_scale, B), B, dj) - 1;
+                float gj = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 r = G4[(iF + a) * B + iJ];
+                    const float tt = fmaf(r.x, dj[0], fmaf(r.y, dj[1], fmaf(r.z, dj[2], r.w * dj[3])));
+                    gj = fmaf(wf[a], tt, gj);
+                }
+                if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
+                const float gs[3] = {gj * sx, gj * sy, gj * sz};
+                if (STEP) {
+                    const MT *Ms = reinterpret_cast<const MT *>(smem + L.m + (zi % SW_NS) * L.mslot);
+                    const MT *Vs = reinterpret_cast<const MT *>(smem + L.v + (zi % SW_NS) * L.mslot);
+                    const bool hzm = z > 0, hzp = z + 1 < g.nz;
+                    float rpart = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        // diffusion gradient, same terms and order as diffusion_ptr
+                        const float *U = Uc + c * SW_UC;
+                        const float c0 = cur[c];
+                        float acc = 0.0f;
+                        if (hxp) {
+                            const float d = U[o + 1] - c0;
+                            acc -= d;
+                            rpart = fmaf(d, d, rpart);
+                        }
+                        if (hxm) acc += c0 - U[o - 1];
+                        if (hyp) {
+                            const float d = U[o + SW_UX] - c0;
+                            acc -= d;
+                            rpart = fmaf(d, d, rpart);
+                        }
+                        if (hym) acc += c0 - U[o - SW_UX];
+                        if (hzp) {
+                            const float d = Un[c * SW_UC + o] - c0;
+                            acc -= d;
+                            rpart = fmaf(d, d, rpart);
+                        }
+                        if (hzm) acc += c0 - Up[c * SW_UC + o];
+                        const float gt = fmaf(S.lam * S.two_over_n, acc, gs[c]);
+                        if (grad_out) (grad_out + c * g.n)[p] = gt;
+                        const float m0 = sm_val(Ms, c * SW_TX * SW_TY + t);
+                        const float v0 = sm_val(Vs, c * SW_TX * SW_TY + t);
+                        (u_out + c * g.n)[p] = adam_fast(c0, gt, m0, v0, m + c * g.n, v + c * g.n, p, S);
+                    }
+                    racc += rpart;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                umma::mbar_arrive(empty_u + zi % SW_NU);
+                umma::mbar_arrive(empty_s + zi % SW_NS);
+            }
+            if ((zi & 15) == 15) {
+                rsum += (double)racc;
+                racc = 0.0f;
+            }
+        }
+        rsum += (double)racc;
+    }
+    if (STEP) {
+        const double bs = block_sum(rsum, red);
+        const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (tid == 0) partials[bid] = bs;
+        if (arrive_last(counter)) {
+            const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+            double acc = 0.0;
+            for (long long i = tid; i < nb; i += SW_THREADS) acc += __ldcg(partials + i);
+            const double tot = block_sum(acc, red);
+            if (tid == 0) {
+                const double R = tot / (double)g.n;
+                if (!isfinite(R)) latch_error(err, REG_ERR_NONFINITE);
+                r_out[0] = R;
+                *counter = 0u;
+            }
+        }
+    }
+}
+
+// The TMA path needs every tensor-map stride to be a multiple of 16 bytes
+// (BF16 rows: nx % 8 == 0) and no composite transform.
+bool mi_tma_ok(const Dims &g) { return g.nx % 8 == 0; }
+
+// Grid: 32 x 8 tiles; the z-chunk count minimises (waves of resident CTAs) x
+// (planes per CTA + 3), the 3 being each CTA's start-up (its adjoint table
+// and the two planes its stencil reads beyond the chunk).
+MarchGrid mi_tma_sweep_grid(const Dims &g) {
+    MarchGrid G;
+    G.tiles_x = (g.nx + SW_TX - 1) / SW_TX;
+    G.tiles_y = (g.ny + SW_TY - 1) / SW_TY;
+    static int per_sm = 0;  // 0 until the occupancy calculator has answered
+    int n = per_sm;
+    if (n == 0) {
+        // residency of the FP32 instantiation with 32 bins (every instantiation
+        // has the same register budget; only larger tables take more shared
+        // memory); the grid must not depend on the call's bin count, since it
+        // also sizes the workspace
+        const SwLayout L(32, 4, 4);
+        auto kern = mi_sweep2_tma_kernel<float, float, true, REG_PAD_BORDER, int>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, SW_THREADS, L.total) == cudaSuccess && n > 0)
+            per_sm = n;
+        else
+            n = 1;
+    }
+    const long long tiles = (long long)G.tiles_x * G.tiles_y;
+    const long long slots = (long long)n * num_sms();
+    long long best_c = 1;
+    double best = -1.0;
+    for (long long c = 1; c <= std::min<long long>(g.nz, 256); ++c) {
+        const long long zc = (g.nz + c - 1) / c;
+        if ((g.nz + zc - 1) / zc != c) continue;
+        const long long waves = (tiles * c + slots - 1) / slots;
+        const double cost = (double)waves * (double)(zc + 3);
+        if (best < 0.0 || cost < best) {
+            best = cost;
+            best_c = c;
+        }
+    }
+    G.zc = (int)((g.nz + best_c - 1) / best_c);
+    G.chunks = (int)((g.nz + G.zc - 1) / G.zc);
+    return G;
+}
+
+cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
+                                 const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
+                                 void *m, void *v, int mdt, const StepParams &S, double *partials,
+                                 unsigned *counter, double *r_out, cudaStream_t s) {
+    CUtensorMap umap, fmap, mmap, vmap;
+    const uint64_t d4[4] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz, 3};
+    const uint64_t d3[3] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
+    const uint32_t ubox[4] = {SW_UX, SW_UY, 1, 3}, sbox4[4] = {SW_TX, SW_TY, 1, 3}, sbox3[3] = {SW_TX, SW_TY, 1};
+    if (!tma::make_map(&umap, u, REG_F32, 4, d4, ubox) || !tma::make_map(&fmap, F, dt, 3, d3, sbox3))
+        return cudaErrorNotSupported;
+    if (step) {
+        if (!tma::make_map(&mmap, m, mdt, 4, d4, sbox4) || !tma::make_map(&vmap, v, mdt, 4, d4, sbox4))
+            return cudaErrorNotSupported;
+    } else {
+        mmap = umap;  // unused without the step
+        vmap = umap;
+    }
+    const MarchGrid G = mi_tma_sweep_grid(g);
+    const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
+    cudaError_t e = cudaSuccess;
+    with_type(dt, [&](auto tp) {
+        using T = elem_t<decltype(tp)>;
+        with_pad(pad, [&](auto pd) {
+            constexpr int PD = decltype(pd)::value;
+            with_index(g, [&](auto ip) {
+                using I = elem_t<decltype(ip)>;
+                auto go = [&](auto kern, auto *mp, bool st) {
+                    using MT = std::remove_pointer_t<decltype(mp)>;
+                    const size_t smem =
+                        SwLayout(P.bins, (int)sizeof(T), st ? (int)sizeof(MT) : 0).total;
+                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return;
+                    kern<<<grid, SW_THREADS, smem, s>>>(umap, fmap, mmap, vmap, (const T *)M, g, P, G.zc, Gtab,
+                                                        grad_out, u_out, (MT *)m, (MT *)v, S, partials, counter,
+                                                        r_out, err);
+                };
+                if (!step)
+                    go(mi_sweep2_tma_kernel<T, float, false, PD, I>, (float *)nullptr, false);
+                else if (mdt == REG_BF16)
+                    go(mi_sweep2_tma_kernel<T, __nv_bfloat16, true, PD, I>, (__nv_bfloat16 *)nullptr, true);
+                else
+                    go(mi_sweep2_tma_kernel<T, float, true, PD, I>, (float *)nullptr, true);
+            });
+        });
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace regk

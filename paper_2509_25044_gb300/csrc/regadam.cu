@@ -1,15 +1,24 @@
 // regadam.cu -- diffusion regulariser, Adam step, Jacobian-determinant fold
 // check, the device error word and the bounded-wait test hook.
+#include <mutex>
+
 #include "kernels.h"
 
 namespace regk {
 
 __device__ unsigned int g_reg_error = 0u;
 
+// The word's device address, looked up once per device (with that device
+// current) under a lock; nullptr when the runtime cannot give it, which the
+// launchers turn into an error return.  The cache outlives a
+// cudaDeviceReset: a process that resets a device must not call the library
+// on it again.
 unsigned *error_word() {
+    static std::mutex lock;
     static unsigned *cached[64] = {nullptr};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> guard(lock);
     if (!cached[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_reg_error) != cudaSuccess) return nullptr;
@@ -112,9 +121,10 @@ cudaError_t launch_diffusion(const float *u, const Dims &g, float lam, float *gr
                              unsigned *counter, double *r_out, cudaStream_t s) {
     const MarchGrid G = diffusion_grid(g);
     const float scale = (float)((double)lam * 2.0 / (double)g.n);
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     diffusion_kernel<<<dim3(G.tiles_x, G.tiles_y, G.chunks), dim3(TX, TY), 0, s>>>(u, g, G.zc, scale, grad,
-                                                                                   partials, counter, r_out,
-                                                                                   error_word());
+                                                                                   partials, counter, r_out, err);
     return cudaGetLastError();
 }
 
@@ -234,7 +244,9 @@ __global__ void wait_flag_kernel(const unsigned *flag, unsigned expect, unsigned
 }
 
 cudaError_t launch_wait_flag(const unsigned *flag, unsigned expect, unsigned long long timeout_ns, cudaStream_t s) {
-    wait_flag_kernel<<<1, 1, 0, s>>>(flag, expect, timeout_ns, error_word());
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
+    wait_flag_kernel<<<1, 1, 0, s>>>(flag, expect, timeout_ns, err);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,17 @@ __device__ __forceinline__ void load_4d(void *smem_dst, const CUtensorMap *map, 
         : "memory");
 }
 
+// box of a 3-D tiled tensor map at (c0 innermost, c1, c2) -> shared memory,
+// same rules as load_4d
+__device__ __forceinline__ void load_3d(void *smem_dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                        uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(umma::smem_addr(smem_dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(umma::smem_addr(mbar))
+        : "memory");
+}
+
 // contiguous bytes global -> shared (both 16-byte aligned, bytes % 16 == 0)
 __device__ __forceinline__ void load_bulk(void *smem_dst, const void *src, uint32_t bytes, uint64_t *mbar) {
     asm volatile(
@@ -46,6 +57,13 @@ __device__ __forceinline__ void load_bulk(void *smem_dst, const void *src, uint3
 // (dims[0] * 2 bytes a multiple of 16) and the given box.  Returns false if
 // the driver entry point is missing or rejects the description.
 bool make_map_bf16_4d(CUtensorMap *map, const void *base, const uint64_t dims[4], const uint32_t box[4]);
+
+// Host: a tiled tensor map of rank 3 or 4 over a dense FP32 (dt = REG_F32) or
+// BF16 (REG_BF16) array, dims[0] innermost, no swizzle, zero fill outside the
+// array.  Every stride (dims[0] * element size, ...) must be a multiple of 16
+// bytes and box[0] * element size a multiple of 16.  Returns false if the
+// driver entry point is missing or rejects the description.
+bool make_map(CUtensorMap *map, const void *base, int dt, int rank, const uint64_t *dims, const uint32_t *box);
 
 }  // namespace tma
 }  // namespace regk

@@ -99,6 +99,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase) {
     return false;
 }
 
+// one arrival on an mbarrier (its count was set by mbar_init)
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // make generic-proxy shared-memory writes visible to the tensor core (async proxy)

@@ -72,11 +72,13 @@ size_t gemm_smem_bytes() { return sizeof(GemmShared) + 1024; }
 
 cudaError_t launch_gemm_test(const void *A, const void *B, float *C, int M, int N, int K, int a_mn, int b_mn,
                              cudaStream_t s) {
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     const size_t smem = gemm_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(gemm_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     gemm_test_kernel<<<M / GEMM_M, GEMM_THREADS, smem, s>>>((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, C, M,
-                                                            N, K, a_mn, b_mn, error_word());
+                                                            N, K, a_mn, b_mn, err);
     return cudaGetLastError();
 }
 
@@ -274,6 +276,8 @@ __global__ void repack_dgrad_kernel(const __nv_bfloat16 *__restrict__ W, int Cou
 
 cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, const float *bias, int Cout, int N,
                             const Dims &d, int epi, float slope, void *out, cudaStream_t s) {
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     const size_t smem = gemm_smem_bytes();
     ConvGeom g{d.nx, d.ny, d.nz, d.n};
     const unsigned grid = (unsigned)((d.n + GEMM_M - 1) / GEMM_M);
@@ -285,7 +289,7 @@ cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, co
             if (e != cudaSuccess) return e;
             conv_fwd_kernel<EPI_BIAS_LEAKY_BF16><<<grid, GEMM_THREADS, smem, s>>>(
                 (const __nv_bfloat16 *)in, Cin, (const __nv_bfloat16 *)W, Kpad, bias, Cout, N, g, slope, out,
-                error_word());
+                err);
             break;
         case EPI_PLAIN_BF16:
             e = cudaFuncSetAttribute(conv_fwd_kernel<EPI_PLAIN_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -293,7 +297,7 @@ cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, co
             if (e != cudaSuccess) return e;
             conv_fwd_kernel<EPI_PLAIN_BF16><<<grid, GEMM_THREADS, smem, s>>>(
                 (const __nv_bfloat16 *)in, Cin, (const __nv_bfloat16 *)W, Kpad, bias, Cout, N, g, slope, out,
-                error_word());
+                err);
             break;
         default:
             e = cudaFuncSetAttribute(conv_fwd_kernel<EPI_BIAS_F32_SOA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -301,7 +305,7 @@ cudaError_t launch_conv_fwd(const void *in, int Cin, const void *W, int Kpad, co
             if (e != cudaSuccess) return e;
             conv_fwd_kernel<EPI_BIAS_F32_SOA><<<grid, GEMM_THREADS, smem, s>>>(
                 (const __nv_bfloat16 *)in, Cin, (const __nv_bfloat16 *)W, Kpad, bias, Cout, N, g, slope, out,
-                error_word());
+                err);
     }
     return cudaGetLastError();
 }
@@ -315,6 +319,8 @@ int wgrad_splits(const Dims &d) {
 
 cudaError_t launch_conv_wgrad(const void *in, int Cin, const void *dpre, int Cout, const Dims &d, float *part,
                               float *dW, int Kpad, cudaStream_t s) {
+    unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     const size_t smem = gemm_smem_bytes();
     ConvGeom g{d.nx, d.ny, d.nz, d.n};
     const int K = 27 * Cin;
@@ -327,7 +333,7 @@ cudaError_t launch_conv_wgrad(const void *in, int Cin, const void *dpre, int Cou
     if (e != cudaSuccess) return e;
     conv_wgrad_kernel<<<dim3(mtiles, splits), GEMM_THREADS, smem, s>>>((const __nv_bfloat16 *)in, Cin,
                                                                        (const __nv_bfloat16 *)dpre, Cout, g, vps, part,
-                                                                       Mrows, error_word());
+                                                                       Mrows, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int total = Cout * Kpad;

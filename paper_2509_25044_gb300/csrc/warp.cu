@@ -110,6 +110,7 @@ cudaError_t launch_composite_backward(const void *M, int dt, const float *u, con
     const MarchGrid G = march_grid(g, 8LL * num_sms() * 4, 1);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks), block(TX, TY);
     unsigned *err = error_word();
+    if (!err) return cudaErrorInvalidDevice;
     with_type(dt, [&](auto tp) {
         using T = elem_t<decltype(tp)>;
         with_pad(pad, [&](auto pd) {

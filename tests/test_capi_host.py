@@ -436,3 +436,32 @@ def test_binding_checks_caller_buffers_before_the_call(capi):
                                  128, 16, 64)
     with pytest.raises(ValueError, match="shape"):
         capi.reg_jacdet_min(torch.zeros(2, 4, 4, 4))
+    # the fixed image sets the dims: an expanded (strided) F is refused before
+    # its pointer is taken, in the workspace and the no-workspace entry points
+    Fx = torch.zeros(1, 1, 1).expand(4, 4, 4)
+    mi = capi.mi_desc((0.0, 1.0), (0.0, 1.0), 16)
+    with pytest.raises(ValueError, match="contiguous"):
+        capi.reg_loss_grad(lncc, Fx, F, u, ws)
+    with pytest.raises(ValueError, match="contiguous"):
+        capi.reg_mi_loss_grad_noalloc(mi, Fx, F, u)
+    with pytest.raises(ValueError, match="contiguous"):
+        capi.reg_iterate(mi, Fx, F, u, u.clone(), u.clone(), u.clone(), 0.1, adam, 1, ws)
+
+
+def test_binding_refuses_tensors_off_the_current_device(capi, monkeypatch):
+    """A tensor on another GPU than the current one (where the library
+    launches) is refused before its address is taken."""
+    import torch
+
+    class Fake:  # a contiguous CUDA tensor on device 1 (no GPU needed)
+        device = torch.device("cuda", 1)
+
+        def is_contiguous(self):
+            return True
+
+        def data_ptr(self):
+            raise AssertionError("the address of a tensor on another device was taken")
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    with pytest.raises(ValueError, match="current device"):
+        capi._ptr(Fake())

@@ -303,6 +303,28 @@ def test_iterate_matches_oracle(capi, kind, shape):
     np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
 
 
+# Rows of whole 4-voxel quads take the vector sweeps (a thread per quad, x
+# neighbours from adjacent lanes, memory loads at each warp's 128-voxel edge):
+# rows that span several warps with a partial last one, ragged y and z, both
+# moment types.
+@pytest.mark.parametrize("kind", ["mi", "mi_hard"])
+@pytest.mark.parametrize("shape,mdt", [((9, 11, 260), 0), ((6, 70, 132), 1), ((5, 3, 4), 0)])
+def test_iterate_quad_rows_match_oracle(capi, kind, shape, mdt):
+    c = _iterate_case(capi, kind, shape, mdt=mdt, t=2, seed=91)
+    ref = O.objective(to64(c["F"]), to64(c["M"]), to64(c["u"]), c["spec"], 0.1)
+    assert_rel(c["obj"][0].item(), ref["sim"], LOSS_RTOL, "similarity")
+    assert_rel(c["obj"][1].item(), ref["R"], 1e-6, "R")
+    assert rel_l2(to64(c["g"]), ref["grad"]) <= GRAD_RTOL
+    ur, mr, vr = O.adam(to64(c["u"]), to64(c["m0"]), to64(c["v0"]), to64(c["g"]), 2, 0.1, grad_scale=c["N"],
+                        bf16_moments=bool(mdt))
+    np.testing.assert_allclose(to64(c["uo"]), ur, atol=1e-5, rtol=0)
+    if mdt:  # BF16 moments: one BF16 ulp of the oracle's RNE-rounded moments, plus the FP32 rounding
+        # of b1 m + (1 - b1) g where the two terms (|m| < 0.05) cancel: 2 * 2^-24 * 0.05 < 1e-8
+        np.testing.assert_allclose(to64(c["m"]), mr, rtol=2 ** -7, atol=1e-8)
+    else:
+        np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
+
+
 @pytest.mark.parametrize("kind", ["lncc", "mi"])
 def test_iterate_is_deterministic(capi, kind):
     a = _iterate_case(capi, kind, (40, 33, 37), seed=71)
