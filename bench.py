@@ -1,13 +1,17 @@
 """Benchmark: one fused registration iteration (warp + similarity fwd/bwd +
 diffusion regulariser + Adam) on synthetic volumes, through the C ABI.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c4] [--impl ours|reference]
 
-Default workload (c1): 192^3 FP32 multimodal pair, 32-bin cubic B-spline
-Parzen MI, diffusion lambda = 0.05, Adam.  A step is one iteration over the
-whole volume.  Prints one JSON line (rank 0).  With N > 1 (torchrun), every
-rank registers its own independent pair (replicas, weak scaling); only the
-timing is reduced across ranks.
+Default workload (c4): 1280^3 (2.1 G voxels) BF16-stored multimodal pair,
+32-bin cubic B-spline Parzen MI, diffusion lambda = 0.05, Adam with BF16
+moments -- the largest workload that fits one GPU.  A step is one iteration
+over the whole volume.  The 192^3 MI (c1) and 512^3 LNCC (c2) workloads are
+timed after it as sub-records, each with its own roofline, and the BF16
+storage form is compared with plain FP32 on time to solution (c2).  Prints
+one JSON line (rank 0).  With N > 1 (torchrun), every rank registers its own
+independent pair (replicas, weak scaling); only the timing is reduced across
+ranks.
 """
 from __future__ import annotations
 
@@ -31,16 +35,6 @@ WORKLOADS = {
     "c2": "512^3 BF16-stored mono-modal pair, LNCC 9^3, diffusion lambda 0.1, Adam (BF16 moments)",
     "c4": "1280^3 BF16-stored multimodal phantom pair, 32-bin Parzen MI, diffusion lambda 0.05, Adam (BF16 moments)",
 }
-# algorithmic bytes per voxel of one iteration (each compulsory tensor moved once)
-#   sweep 1: F, M (one gather counted once), u;  LNCC also writes 3 FP32 coefficient fields
-#   sweep 2: F, M, u (12 B), m, v (3 components each) read; u' (12 B), m, v written;
-#            LNCC also reads the coefficient fields
-def bytes_per_voxel(kind, img_bytes, mom_bytes):
-    s1 = 2 * img_bytes + 12 + (12 if kind == "lncc" else 0)
-    s2 = 2 * img_bytes + 12 + 12 + 2 * (2 * 3 * mom_bytes) + (12 if kind == "lncc" else 0)
-    return s1, s2
-
-
 def csrc_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2509_25044_gb300", "csrc")
@@ -153,19 +147,30 @@ def max_over_ranks(x, world, device):
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): the FP64 oracle as it stands
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg_name: str, budget_s: float = 20.0):
-    """A bounded sample of the workload for the oracle: z-slabs of the same
-    volume, grown until one iteration takes a few seconds."""
-    import numpy as np
-    from paper_2509_25044_gb300 import synth
-    d = synth.make(cfg_name) if cfg_name in ("c0", "c1") else synth.make(cfg_name, n=128)
-    c = d["config"]
-    F, M = d["F"].double().numpy(), d["M"].double().numpy()
-    u = (-0.5 * d["u_true"]).double().numpy()
-    return c, F, M, u, d
+_SAMPLES = {}
 
 
-def time_oracle_iteration(cfg_name: str, nz: int | None = None):
+def oracle_sample(cfg_name: str):
+    """The oracle's bounded sample of a workload: the workload itself for the
+    192^3 and 64^3 ones; for the 512^3 and 1280^3 ones the same recipe at
+    128^3 (the FP64 oracle would need 15 GB / 235 GB for them).  Generated
+    once per process."""
+    if cfg_name not in _SAMPLES:
+        from paper_2509_25044_gb300 import synth
+        d = synth.make(cfg_name) if cfg_name in ("c0", "c1") else synth.make(cfg_name, n=128)
+        F, M = d["F"].double().numpy(), d["M"].double().numpy()
+        u = (-0.5 * d["u_true"]).double().numpy()
+        _SAMPLES[cfg_name] = (d["config"], F, M, u, d)
+    c, F, M, u, d = _SAMPLES[cfg_name]
+    return c, F, M, u.copy(), d
+
+
+def sample_name(cfg_name: str) -> str:
+    return f"the {cfg_name} workload" if cfg_name in ("c0", "c1") else f"the {cfg_name} recipe at 128^3"
+
+
+def time_oracle_iteration(cfg_name: str, nz: int | None = None, reps: int = 1):
+    """(voxels per iteration, seconds per iteration) of the FP64 oracle."""
     import numpy as np
     import oracle as O
     c, F, M, u, d = oracle_sample(cfg_name)
@@ -178,8 +183,9 @@ def time_oracle_iteration(cfg_name: str, nz: int | None = None):
     m = np.zeros_like(u)
     v = np.zeros_like(u)
     t0 = time.perf_counter()
-    O.iterate(F, M, u, m, v, 1, spec, c["lam"], c["lr"], bf16_moments=(c["dtype"] == "bf16"))
-    dt = time.perf_counter() - t0
+    for _ in range(reps):
+        O.iterate(F, M, u, m, v, 1, spec, c["lam"], c["lr"], bf16_moments=(c["dtype"] == "bf16"))
+    dt = (time.perf_counter() - t0) / reps
     return F.size, dt
 
 
@@ -191,16 +197,32 @@ def oracle_threads():
 
 
 def cpu_baseline(cfg_name: str):
-    n_vox, dt = time_oracle_iteration(cfg_name)
-    return {"value": n_vox / dt / 1e9, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"one full FP64 oracle iteration of the {cfg_name} workload ({n_vox} voxels, {dt:.1f} s)"}
+    """The FP64 oracle as it stands on the host cores: all of them (this
+    process), and one (a child process started with OMP_NUM_THREADS=1, since
+    OpenMP fixes its thread count when the library loads)."""
+    n_vox, dt = time_oracle_iteration(cfg_name, reps=3)
+    rec = {"value": n_vox / dt / 1e9, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+           "sample": f"three full FP64 oracle iterations of {sample_name(cfg_name)} ({n_vox} voxels, "
+                     f"{dt:.2f} s each)"}
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, bench; n, dt = bench.time_oracle_iteration(%r); print(json.dumps([n, dt]))" % cfg_name)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+        n1, dt1 = json.loads(r.stdout.strip().splitlines()[-1])
+        rec["single_thread"] = {"value": n1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                                "sample": f"one FP64 oracle iteration of {sample_name(cfg_name)} "
+                                          f"({n1} voxels, {dt1:.2f} s)"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        rec["single_thread"] = {"value": None, "error": str(e)[:200]}
+    return rec
 
 
 def run_reference(args):
     rank, world, local = setup_dist(args.gpus)
     if rank != 0:
         return
-    # each step: one FP64 oracle iteration on a z-slab sample of the same workload
+    # each step: one FP64 oracle iteration on the bounded sample of the workload
     cfg = args.config
     nz = 48 if cfg == "c1" else None
     for _ in range(args.warmup):
@@ -211,7 +233,8 @@ def run_reference(args):
         tot_vox += n
         tot_t += dt
     value = tot_vox / tot_t / 1e9
-    sample = f"z-slab of {nz} planes of the {cfg} volume per step" if nz else f"full {cfg} volume per step"
+    sample = (f"z-slab of {nz} planes of the {cfg} volume per step" if nz else
+              f"{sample_name(cfg)} per step")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -225,30 +248,43 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args):
-    import torch
-    rank, world, local = setup_dist(args.gpus)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2509_25044_gb300 import build, capi, synth
-    if rank == 0 or world == 1:
-        build.build()
-    barrier(world)
-    capi.load()
+def alg_bytes(kind: str, bf16: bool):
+    """Algorithmic bytes per voxel, each compulsory tensor moved once (images
+    and Adam moments share the storage type in every workload):
+      MI, two sweeps (the joint histogram is global): sweep 1 reads F, M, u;
+        sweep 2 reads F, M, u, m, v and writes u', m, v -> 20 + 80 (FP32),
+        16 + 52 (BF16);
+      LNCC, one iteration: F, M, u, m, v read, u', m, v written -> 80 (FP32),
+        52 (BF16); intermediates the library keeps between its own kernels
+        are not counted."""
+    ib = 2 if bf16 else 4
+    step = 2 * ib + 12 + 12 + 2 * (2 * 3 * ib)
+    if kind == "mi":
+        return 2 * ib + 12, step
+    return None, step
 
-    cfg = synth.CONFIGS[args.config]
+
+def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", mi_estimator="parzen"):
+    """K timed iterations (after W untimed ones) of workload `name` through
+    reg_iterate, with per-sweep CUDA events on every timed iteration; with
+    e2e, a second pass through the public call with the inputs copied from
+    pinned host memory every step and the result read back."""
+    import torch
+    from paper_2509_25044_gb300 import capi, synth
+    cfg = synth.CONFIGS[name]
     kind = cfg["kind"]
     bf16 = cfg["dtype"] == "bf16"
-    d = synth.make(args.config, device=dev, seed=cfg["seed"] + 1000 * rank, n=args.n)
+    d = synth.make(name, device=dev, seed=cfg["seed"] + 1000 * rank, n=n)
     F = d["F"].to(torch.bfloat16 if bf16 else torch.float32).contiguous()
     M = d["M"].to(torch.bfloat16 if bf16 else torch.float32).contiguous()
+    f_range, m_range = d.get("f_range"), d.get("m_range")
+    del d
     shape = tuple(F.shape)
     N = F.numel()
-    del d["u_true"]
     if kind == "lncc":
-        loss = capi.lncc_desc(cfg["window"], 1e-9, ants=args.lncc_grad == "ants")
+        loss = capi.lncc_desc(cfg["window"], 1e-9, ants=lncc_grad == "ants")
     else:
-        loss = capi.mi_desc(d["f_range"], d["m_range"], cfg["bins"], hard=args.mi_estimator == "hard")
+        loss = capi.mi_desc(f_range, m_range, cfg["bins"], hard=mi_estimator == "hard")
     mdt = capi.REG_BF16 if bf16 else capi.REG_F32
     mtype = torch.bfloat16 if bf16 else torch.float32
     u = [torch.zeros((3,) + shape, device=dev), torch.zeros((3,) + shape, device=dev)]
@@ -259,30 +295,29 @@ def run_ours(args):
     adam = capi.adam_desc(cfg["lr"], moment_dtype=mdt, grad_scale=float(N))
     lam = cfg["lam"]
     stream = torch.cuda.current_stream(dev)
-
     step_no = [0]
 
-    def step():
+    def step(Fd=F, Md=M):
         step_no[0] += 1
         a, b = u[(step_no[0] - 1) % 2], u[step_no[0] % 2]
-        capi.reg_iterate(loss, F, M, a, b, m, v, lam, adam, step_no[0], ws, obj=obj)
+        capi.reg_iterate(loss, Fd, Md, a, b, m, v, lam, adam, step_no[0], ws, obj=obj)
+        return b
 
-    for _ in range(args.warmup):
+    for _ in range(W):
         step()
     torch.cuda.synchronize()
     if capi.reg_get_device_error() != 0:
-        raise RuntimeError("device error during warm-up")
+        raise RuntimeError(f"device error during the warm-up of {name}")
 
     # ---- timed region: K iterations, per-sweep events on every iteration ----
-    K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for trip in evs:  # torch creates the CUDA event on its first record
-        for e in trip:
-            e.record(stream)
+        for ev in trip:
+            ev.record(stream)
     start.record(stream)
     end.record(stream)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
     barrier(world)
@@ -299,98 +334,158 @@ def run_ours(args):
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     ms_max = max_over_ranks(ms, world, dev)
-    s1 = [e[0].elapsed_time(e[1]) for e in evs]
-    s2 = [e[1].elapsed_time(e[2]) for e in evs]
+    s1 = [ev[0].elapsed_time(ev[1]) for ev in evs]
+    s2 = [ev[1].elapsed_time(ev[2]) for ev in evs]
     err = capi.reg_get_device_error()
     objv = obj.cpu().tolist()
+    b1, b2 = alg_bytes(kind, bf16)
+    peak, peak_kind = read_peaks()
+    t1, t2 = statistics.median(s1), statistics.median(s2)
+    mean1, mean2 = sum(s1) / K, sum(s2) / K
+    it_ms = ms_max / K
+    if kind == "mi":
+        # the second sweep dominates; sweep 1 is the histogram
+        kname = "mi_sweep2_tma" if (shape[2] % 8 == 0) else "mi_sweep2"
+        ach = b2 * N / (mean2 * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "algorithmic_bytes_per_voxel": b2, "traffic": read_traffic(kname, name)}
+        sweeps = {"sweep1_median_ms": t1, "sweep2_median_ms": t2,
+                  "sweep1_GBps": b1 * N / (mean1 * 1e-3) / 1e9, "sweep2_GBps": ach,
+                  "sweep1_frac": b1 * N / (mean1 * 1e-3) / 1e9 / peak,
+                  "iteration_GBps": (b1 + b2) * N / (it_ms * 1e-3) / 1e9,
+                  "iteration_frac": (b1 + b2) * N / (it_ms * 1e-3) / 1e9 / peak}
+    else:
+        # one LNCC iteration is the unit: its kernels (warp, window statistics,
+        # adjoint + step) together against the single-sweep bytes
+        ach = b2 * N / (it_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "lncc iteration (all kernels)", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_voxel": b2,
+                "traffic": None}
+        sweeps = {"warp_and_statistics_median_ms": t1, "adjoint_and_step_median_ms": t2}
+    roof["peak_source"] = (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                           else "fallback 6.8 TB/s")
+    out = {"name": name, "n": shape[0], "voxels": N, "steps": K, "warmup": W, "ms_per_step": it_ms,
+           "value": world * N * K / (ms_max * 1e-3) / 1e9, "roofline": roof, "sweeps": sweeps, "clocks": clk,
+           "objective_last": objv, "device_error": err, "wall_s": wall, "bf16": bf16, "kind": kind}
 
-    # ---- end to end: host (pinned) images in, objective out, every step ----
-    # Every step copies its own F and M from pinned host memory and reads its
-    # objective back.  The copies run on their own stream into two device
-    # buffers, so step k + 1's inputs arrive while step k computes; events
-    # order each copy after the compute that last read its buffer, and each
-    # compute after its inputs' copy.
-    Fh = F.cpu().pin_memory()
-    Mh = M.cpu().pin_memory()
-    objh = torch.zeros(2, dtype=torch.float64).pin_memory()
-    Fd2 = [torch.empty_like(F), torch.empty_like(F)]
-    Md2 = [torch.empty_like(M), torch.empty_like(M)]
-    cstream = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    consumed = [torch.cuda.Event(), torch.cuda.Event()]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Ke = max(1, min(K, 200))
+    if e2e:
+        # ---- end to end: pinned host images in, objective out every step; the
+        # final field u' read back into pinned host memory at the end ----
+        # The copies run on their own stream into two device buffers, so step
+        # k + 1's inputs arrive while step k computes; events order each copy
+        # after the compute that last read its buffer.
+        Fh = F.cpu().pin_memory()
+        Mh = M.cpu().pin_memory()
+        objh = torch.zeros(2, dtype=torch.float64).pin_memory()
+        uh = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
+        Fd2 = [torch.empty_like(F), torch.empty_like(F)]
+        Md2 = [torch.empty_like(M), torch.empty_like(M)]
+        cstream = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        consumed = [torch.cuda.Event(), torch.cuda.Event()]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Ke = max(1, min(K, 200))
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cstream.wait_event(e0)
+
+        def h2d(k):
+            i = k % 2
+            with torch.cuda.stream(cstream):
+                if k >= 2:
+                    cstream.wait_event(consumed[i])
+                Fd2[i].copy_(Fh, non_blocking=True)
+                Md2[i].copy_(Mh, non_blocking=True)
+                copied[i].record(cstream)
+
+        h2d(0)
+        last = None
+        for k in range(Ke):
+            if k + 1 < Ke:
+                h2d(k + 1)
+            i = k % 2
+            stream.wait_event(copied[i])
+            last = step(Fd2[i], Md2[i])
+            consumed[i].record(stream)
+            objh.copy_(obj, non_blocking=True)
+        uh.copy_(last, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        ib = 2 if bf16 else 4
+        out["e2e"] = {"value": world * N * Ke / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": 2 * N * ib, "d2h_bytes_per_step": 16 + 12 * N / Ke,
+                      "steps": Ke,
+                      "note": "per step: pinned host F, M -> device (a copy stream, two device buffers: step k+1's "
+                              "copy overlaps step k's compute), one iteration, objective (16 B) -> pinned host; "
+                              f"after the last step the field u' ({12 * N} B) -> pinned host, counted per step "
+                              f"over the {Ke} steps"}
+        del Fh, Mh, uh, Fd2, Md2
+    return out
+
+
+def time_to_solution_record(n=None):
+    """BF16 storage form vs plain FP32 on the 512^3 LNCC workload (c2):
+    iterations and time to the FP32 run's progress target
+    L <= L* + 0.01 (L0 - L*), final objective, fold check."""
+    from paper_2509_25044_gb300 import experiments
+    r = experiments.time_to_loss("c2", iters=None, eval_every=10, n=n, lam_scale=20.0)
+    keep = ("ms_per_iter", "iters_to_target", "iters_to_target_upper", "time_to_target_ms", "final",
+            "final_on_fp32_images", "final_rel_to_fp32_final", "fold")
+    return {"workload": WORKLOADS["c2"] + f" at {r['n']}^3, lambda {r['lam']:g} (the objective's weight)",
+            "iters": r["iters"], "target": r["target"],
+            "fp32": {k: r["fp32"][k] for k in keep if k in r["fp32"]},
+            "bf16": {k: r["bf16"][k] for k in keep if k in r["bf16"]},
+            "speedup_bf16_vs_fp32": r.get("speedup_bf16_vs_fp32")}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = setup_dist(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2509_25044_gb300 import build, capi
+    if rank == 0 or world == 1:
+        build.build()
     barrier(world)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    cstream.wait_event(e0)
+    capi.load()
 
-    def h2d(k):
-        i = k % 2
-        with torch.cuda.stream(cstream):
-            if k >= 2:
-                cstream.wait_event(consumed[i])
-            Fd2[i].copy_(Fh, non_blocking=True)
-            Md2[i].copy_(Mh, non_blocking=True)
-            copied[i].record(cstream)
-
-    h2d(0)
-    for k in range(Ke):
-        if k + 1 < Ke:
-            h2d(k + 1)
-        i = k % 2
-        stream.wait_event(copied[i])
-        step_no[0] += 1
-        a, b = u[(step_no[0] - 1) % 2], u[step_no[0] % 2]
-        capi.reg_iterate(loss, Fd2[i], Md2[i], a, b, m, v, lam, adam, step_no[0], ws, obj=obj)
-        consumed[i].record(stream)
-        objh.copy_(obj, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-
+    K, W = args.steps, args.warmup
+    head = measure(args.config, K, W, dev, rank, world, n=args.n, e2e=True, lncc_grad=args.lncc_grad,
+                   mi_estimator=args.mi_estimator)
+    torch.cuda.empty_cache()
+    subs = {}
+    if not args.no_subs:
+        for name in [c for c in args.subs.split(",") if c and c != args.config]:
+            r = measure(name, min(K, 100) if name != "c2" else min(K, 30), max(3, min(W, 5)), dev, rank, world)
+            subs[name] = {k: r[k] for k in ("n", "voxels", "steps", "ms_per_step", "value", "roofline", "sweeps",
+                                            "clocks")}
+            subs[name]["workload"] = WORKLOADS[name]
+            torch.cuda.empty_cache()
     if rank != 0:
         return
-    value = world * N * K / (ms_max * 1e-3) / 1e9
-    e2e_value = world * N * Ke / (e2e_ms * 1e-3) / 1e9
-    ib = 2 if bf16 else 4  # images and Adam moments share the storage type in every workload
-    b1, b2 = bytes_per_voxel(kind, ib, ib)
-    peak, peak_kind = read_peaks()
-    t2 = statistics.median(s2)
-    t1 = statistics.median(s1)
-    ach2 = b2 * N / (sum(s2) / K * 1e-3) / 1e9
-    ach1 = b1 * N / (sum(s1) / K * 1e-3) / 1e9
-    dom = "sweep2" if t2 >= t1 else "sweep1"
-    kname = {("mi", "sweep2"): "mi_sweep2", ("mi", "sweep1"): "mi_hist", ("lncc", "sweep2"): "lncc_sweep2",
-             ("lncc", "sweep1"): "lncc_stats"}[(kind, dom)]
-    if kind == "lncc" and args.lncc_grad == "ants" and dom == "sweep2":
-        kname = "lncc_sweep2_ants"
-    ach = ach2 if dom == "sweep2" else ach1
+    kind = head["kind"]
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f32" if bf16 else "f32", "data": "synthetic",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32" if head["bf16"] else "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config] + (", ANTs gradient approximation"
                                                          if kind == "lncc" and args.lncc_grad == "ants" else "")
                    + (", hard-binned histogram" if kind == "mi" and args.mi_estimator == "hard" else ""),
-                   "name": args.config, "n": shape[0],
+                   "name": args.config, "n": head["n"], "voxels": head["voxels"],
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": f"inputs larger than L2 (working set {(b1 + b2) * N / 1e9:.2f} GB/iteration > 129 MB)"},
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s",
-                     "frac": ach / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                     if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "algorithmic_bytes_per_voxel": b2 if dom == "sweep2" else b1,
-                     "traffic": read_traffic(kname, args.config)},
-        "sweeps_ms": {"sweep1_median": t1, "sweep2_median": t2,
-                      "sweep1_GBps": ach1, "sweep2_GBps": ach2,
-                      "iteration_GBps": (b1 + b2) * N / (ms_max / K * 1e-3) / 1e9},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * ib, "d2h_bytes_per_step": 16,
-                "note": "per step: pinned host F, M -> device (a copy stream, two device buffers: "
-                        "step k+1's copy overlaps step k's compute), one iteration, objective -> host"},
+                   "l2": "inputs larger than L2 (the iteration streams "
+                         f"{head['voxels'] * (68 if head['bf16'] else 100) / 1e9:.1f} GB > 129 MB)"},
+        "roofline": head["roofline"], "sweeps": head["sweeps"], "e2e": head["e2e"],
         "gpu_launches": 3 * K,  # MI: histogram, finalize, sweep 2; LNCC: warp, window statistics, sweep 2
-        "clocks": clk,
-        "objective_last": objv, "device_error": err, "wall_s": wall,
+        "clocks": head["clocks"], "objective_last": head["objective_last"], "device_error": head["device_error"],
+        "wall_s": head["wall_s"],
     }
+    if subs:
+        out["workloads"] = subs
+    if world == 1 and not args.no_ttl:
+        out["time_to_solution"] = time_to_solution_record(args.ttl_n)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.config)
     if not args.no_unet:
@@ -463,9 +558,13 @@ def unet_tensor_core(dev, peak):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--config", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--subs", default="c1,c2", help="further workloads timed as sub-records (comma-separated)")
+    ap.add_argument("--no-subs", action="store_true")
+    ap.add_argument("--no-ttl", action="store_true", help="skip the BF16 vs FP32 time-to-solution record")
+    ap.add_argument("--ttl-n", type=int, default=None, help="grid size of the time-to-solution record (512)")
     ap.add_argument("--n", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -153,9 +153,12 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
             const int jn = zi + 2;
             ok = ok && umma::mbar_wait(full_u + jn % SW_NU, (jn / SW_NU) & 1) &&
                  umma::mbar_wait(full_s + zi % SW_NS, (zi / SW_NS) & 1);
-            if (!ok || abort_flag) {
-                latch_error(err, REG_ERR_TIMEOUT);
-                abort_flag = 1;
+            // the warp leaves together (its lanes meet at __syncwarp below)
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
+                if (lane == 0) {
+                    latch_error(err, REG_ERR_TIMEOUT);
+                    abort_flag = 1;
+                }
                 break;
             }
             const float *Up = reinterpret_cast<const float *>(smem + L.u + (zi % SW_NU) * al128(SW_UBYTES));
@@ -310,8 +313,7 @@ cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const flo
         if (!tma::make_map(&mmap, m, mdt, 4, d4, sbox4) || !tma::make_map(&vmap, v, mdt, 4, d4, sbox4))
             return cudaErrorNotSupported;
     } else {
-        mmap = umap;  // unused without the step
-        vmap = umap;
+        mmap = vmap = umap;  // unused without the step
     }
     const MarchGrid G = mi_tma_sweep_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);

@@ -162,31 +162,47 @@ __device__ __forceinline__ void gather8_interior(const T *M, const Dims &g, cons
     v[7] = ld_vox(q3, 1);
 }
 
-// value only
-template <typename T, int PAD, typename I = long long>
-__device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
-                                        float uz) {
+// A value-only sample split in two: gather_corners issues the 8 corner
+// loads and sets the fractions, interp_corners interpolates them.  A caller
+// can gather one sample before it interpolates another (software
+// pipelining); sample() is the two back to back.
+struct Corners {
     float c[8];
     float ax, ay, az;
+};
+template <typename T, int PAD, typename I = long long>
+__device__ __forceinline__ void gather_corners(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
+                                               float uz, Corners &k) {
     Cell cell;
     if (interior_cell(g, x, y, z, ux, uy, uz, cell)) {
-        gather8_interior<T, I>(M, g, cell, c);
-        ax = cell.ax;
-        ay = cell.ay;
-        az = cell.az;
+        gather8_interior<T, I>(M, g, cell, k.c);
+        k.ax = cell.ax;
+        k.ay = cell.ay;
+        k.az = cell.az;
     } else {
         const Axis X = axis_setup<PAD>(x, ux, g.nx);
         const Axis Y = axis_setup<PAD>(y, uy, g.ny);
         const Axis Z = axis_setup<PAD>(z, uz, g.nz);
-        gather8<T, PAD, I>(M, g, X, Y, Z, c);
-        ax = X.a;
-        ay = Y.a;
-        az = Z.a;
+        gather8<T, PAD, I>(M, g, X, Y, Z, k.c);
+        k.ax = X.a;
+        k.ay = Y.a;
+        k.az = Z.a;
     }
-    const float e00 = lerp1(ax, c[0], c[1]), e10 = lerp1(ax, c[2], c[3]);
-    const float e01 = lerp1(ax, c[4], c[5]), e11 = lerp1(ax, c[6], c[7]);
-    const float f0 = lerp1(ay, e00, e10), f1 = lerp1(ay, e01, e11);
-    return lerp1(az, f0, f1);
+}
+__device__ __forceinline__ float interp_corners(const Corners &k) {
+    const float e00 = lerp1(k.ax, k.c[0], k.c[1]), e10 = lerp1(k.ax, k.c[2], k.c[3]);
+    const float e01 = lerp1(k.ax, k.c[4], k.c[5]), e11 = lerp1(k.ax, k.c[6], k.c[7]);
+    const float f0 = lerp1(k.ay, e00, e10), f1 = lerp1(k.ay, e01, e11);
+    return lerp1(k.az, f0, f1);
+}
+
+// value only
+template <typename T, int PAD, typename I = long long>
+__device__ __forceinline__ float sample(const T *M, const Dims &g, int x, int y, int z, float ux, float uy,
+                                        float uz) {
+    Corners k;
+    gather_corners<T, PAD, I>(M, g, x, y, z, ux, uy, uz, k);
+    return interp_corners(k);
 }
 
 // value and slope dJ/dphi

@@ -172,6 +172,34 @@ MUTANTS = [
      "Jm[c][d] = (c == d ? 1.0 : 0.0) + deriv;", "Jm[c][d] = deriv;", 1),
     ("jacdet: border difference divided by 2", C,
      "h = (double)(hi[d] - lo[d]);", "h = 2.0;", 1),
+    # the learned initialiser's other operators
+    ("leaky: slope applied to the positive side", C,
+     "y[i] = x[i] > 0.0 ? x[i] : slope * x[i];", "y[i] = x[i] > 0.0 ? slope * x[i] : x[i];", 1),
+    ("leaky backward: derivative 1 on the negative side", C,
+     "dx[i] = x[i] > 0.0 ? dy[i] : slope * dy[i];", "dx[i] = dy[i];", 1),
+    ("avgpool: divided by 4", C,
+     "out[lin(X, Y, Z, mx, my) * C + c] = s / 8.0;", "out[lin(X, Y, Z, mx, my) * C + c] = s / 4.0;", 1),
+    ("avgpool: block not offset in z", C,
+     "s += in[lin(2 * X + dx, 2 * Y + dy, 2 * Z + dz, nx, ny) * C + c];",
+     "s += in[lin(2 * X + dx, 2 * Y + dy, 2 * Z, nx, ny) * C + c];", 1),
+    ("avgpool adjoint: weight 1 instead of 1/8", C,
+     "gout[lin(x / 2, y / 2, z / 2, mx, my) * C + c] / 8.0;", "gout[lin(x / 2, y / 2, z / 2, mx, my) * C + c];", 1),
+    ("upsample: corner-aligned instead of voxel-centre coordinates", C,
+     "const double c = ((double)f + 0.5) / (double)s - 0.5;", "const double c = (double)f / (double)s;", 1),
+    ("upsample: the two corner weights swapped along x", C,
+     "const double w = (bx ? ax : 1.0 - ax)", "const double w = (bx ? 1.0 - ax : ax)", 1),
+    ("upsample adjoint: corner weights swapped along y", C,
+     "(by ? ay : 1.0 - ay) * (bz ? az : 1.0 - az);\n                        gin",
+     "(by ? 1.0 - ay : ay) * (bz ? az : 1.0 - az);\n                        gin", 1),
+    ("concat: b written over a's channels", C,
+     "out[v * (Ca + Cb) + Ca + c] = b[v * Cb + c];", "out[v * (Ca + Cb) + c] = b[v * Cb + c];", 1),
+    ("field down2: displacement not halved", C, "out[ch * m + i] *= 0.5;", "out[ch * m + i] *= 1.0;", 1),
+    ("field upsample: displacement not rescaled", C, "out[ch * n + i] *= (double)s;", "out[ch * n + i] *= 1.0;", 1),
+    ("pack pair: F normalised by M's range", C,
+     "out[2 * v] = (sf / cnt - f_lo) / (f_hi - f_lo);", "out[2 * v] = (sf / cnt - f_lo) / (m_hi - m_lo);", 1),
+    ("mse: gradient without the factor 2", C,
+     "if (grad) grad[i] = 2.0 * d / (3.0 * (double)V);", "if (grad) grad[i] = d / (3.0 * (double)V);", 1),
+    ("mse: mean over V instead of 3V", C, "return s / (3.0 * (double)V);", "return s / (double)V;", 1),
     # convolutions of the learned initialiser
     ("conv: x and z taps swapped", C,
      "const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;",
