@@ -28,7 +28,14 @@
  *    partials found on the device are latched in a device error word, read
  *    (and cleared) by reg_get_device_error().  No kernel traps or asserts.
  *  - Determinism: identical inputs give bitwise-identical outputs
- *    (fixed-order FP64 reductions, integer MI histograms).
+ *    (fixed-order FP64 reductions, integer MI histograms), except where an
+ *    entry point's own comment says otherwise (the scatters of
+ *    reg_compose_fields_backward and reg_exp_field_backward).
+ *  - Device set-up: the library looks up the device address of its error
+ *    word (and reg_mi_loss_grad_noalloc that of its scratch array) once per
+ *    device, the first time it is used with that device current.  A process
+ *    that calls cudaDeviceReset must not use the library on that device
+ *    afterwards.
  */
 #ifndef REG_H
 #define REG_H
@@ -326,7 +333,9 @@ REG_API reg_status reg_get_device_error(void *stream);
  *     counts do not fit and return REG_ERR_SHAPE; a non-MI descriptor returns
  *     REG_ERR_UNSUPPORTED.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address; make that first call before any stream capture.
+ *     array's device address and keeps it for the life of the process (so
+ *     not across a cudaDeviceReset); make that first call before any stream
+ *     capture.
  *   - Every call shares the one array (it keeps the previous call's
  *     contents; the histogram is cleared at the start of each call), so calls
  *     that may overlap on the GPU -- different streams, or several host

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "checks.h"
 #include "kernels.h"
 
 using namespace regk;
@@ -26,33 +27,6 @@ constexpr size_t PARTIALS_PER_BLOCK = 12;  // the composite sweeps reduce dC/dA,
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
-
-reg_status check_dims(reg_dims d) {
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return REG_ERR_SHAPE;
-    if (d.nx > (1 << 20) || d.ny > (1 << 19) || d.nz > (1 << 16)) return REG_ERR_SHAPE;
-    const long long n = (long long)d.nx * d.ny * d.nz;
-    if (n > (1LL << 36)) return REG_ERR_SHAPE;
-    return REG_OK;
-}
-
-reg_status check_loss(const reg_loss_desc *L) {
-    if (!L) return REG_ERR_INVALID_ARG;
-    if (L->kind == REG_LOSS_LNCC) {
-        if (L->window < 3 || L->window > 2 * MAX_RADIUS + 1 || (L->window & 1) == 0) return REG_ERR_SHAPE;
-        if (!(L->eps >= 0.0f) || !isfinite(L->eps)) return REG_ERR_INVALID_ARG;
-        if (L->lncc_grad != REG_LNCC_GRAD_EXACT && L->lncc_grad != REG_LNCC_GRAD_ANTS) return REG_ERR_INVALID_ARG;
-        return REG_OK;
-    }
-    if (L->kind == REG_LOSS_MI) {
-        if (L->bins < 8 || L->bins > MAX_BINS) return REG_ERR_SHAPE;
-        if (!isfinite(L->f_lo) || !isfinite(L->f_hi) || !isfinite(L->m_lo) || !isfinite(L->m_hi))
-            return REG_ERR_INVALID_ARG;
-        if (!(L->f_hi > L->f_lo) || !(L->m_hi > L->m_lo)) return REG_ERR_INVALID_ARG;
-        if (L->mi_estimator != REG_MI_PARZEN && L->mi_estimator != REG_MI_HARD) return REG_ERR_INVALID_ARG;
-        return REG_OK;
-    }
-    return REG_ERR_INVALID_ARG;
-}
 
 reg_status check_adam(const reg_adam_desc *A, int t) {
     if (!A) return REG_ERR_INVALID_ARG;

@@ -16,6 +16,7 @@
 // with that device current; host code never uses the symbol itself.
 #include <mutex>
 
+#include "checks.h"
 #include "kernels.h"
 
 using namespace regk;
@@ -23,6 +24,8 @@ using namespace regk;
 namespace {
 
 constexpr int kNoallocMaxBins = 64;
+// the kernels index a histogram and tables of up to MAX_BINS x MAX_BINS entries
+static_assert(kNoallocMaxBins <= MAX_BINS, "the scratch must hold the largest histogram the kernels write");
 constexpr size_t kHistBytes = sizeof(unsigned long long) * kNoallocMaxBins * kNoallocMaxBins;  // 32 KiB
 constexpr size_t kGtabBytes = MI_TABLE_BYTES;  // 80 KiB: G' and its 4-wide rows
 constexpr size_t kScratchBytes = kHistBytes + kGtabBytes;
@@ -60,15 +63,14 @@ extern "C" reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const 
                                                const float *u, reg_dims d, int pad, double *sim_out,
                                                float *grad_u, void *stream) {
     if (!loss || loss->kind != REG_LOSS_MI) return loss ? REG_ERR_UNSUPPORTED : REG_ERR_INVALID_ARG;
-    // the scratch holds a bins x bins histogram and table: larger counts do not fit
-    if (loss->bins < 8 || loss->bins > kNoallocMaxBins) return REG_ERR_SHAPE;
-    if (!isfinite(loss->f_lo) || !isfinite(loss->f_hi) || !isfinite(loss->m_lo) || !isfinite(loss->m_hi) ||
-        !(loss->f_hi > loss->f_lo) || !(loss->m_hi > loss->m_lo))
-        return REG_ERR_INVALID_ARG;
-    if (loss->mi_estimator != REG_MI_PARZEN && loss->mi_estimator != REG_MI_HARD) return REG_ERR_INVALID_ARG;
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > (1 << 20) || d.ny > (1 << 19) || d.nz > (1 << 16) ||
-        (long long)d.nx * d.ny * d.nz > (1LL << 36))
-        return REG_ERR_SHAPE;
+    // the same descriptor and dims checks as the workspace entry points; the
+    // scratch holds a bins x bins histogram and table, so no count beyond the
+    // array's fits
+    reg_status st = check_loss(loss);
+    if (st != REG_OK) return st;
+    if (loss->bins > kNoallocMaxBins) return REG_ERR_SHAPE;
+    st = check_dims(d);
+    if (st != REG_OK) return st;
     if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
     if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
     if (!F || !M || !u || !sim_out) return REG_ERR_INVALID_ARG;
@@ -76,7 +78,7 @@ extern "C" reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const 
         return REG_ERR_ALIGN;
 
     unsigned char *scratch = nullptr;
-    const reg_status st = scratch_address(&scratch);
+    st = scratch_address(&scratch);
     if (st != REG_OK) return st;
     unsigned long long *hist = (unsigned long long *)scratch;
     float *gtab = (float *)(scratch + kHistBytes);

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle as O
-from _util import GRAD_RTOL, LOSS_RTOL, assert_rel, rel_l2, to64
+from _util import GRAD_RTOL, LOSS_RTOL, assert_bf16_drift, assert_rel, rel_l2, to64
 from paper_2509_25044_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -81,15 +81,16 @@ def test_c2_lncc_bf16_512_sampled(capi):
     Fv, Mv = to64(Fb.float()), to64(Mb.float())
     J, dJ = O.warp(Mv, u64, O.PAD_BORDER, with_grad=True)
     gJ, _ = O.lncc_grad_points(Fv, J, 9, 1e-5, pts)
-    assert rel_l2(ggpu, gJ[None, :] * dJ.reshape(3, -1)[:, pts]) <= GRAD_RTOL
+    gbf = gJ[None, :] * dJ.reshape(3, -1)[:, pts]
+    assert rel_l2(ggpu, gbf) <= GRAD_RTOL
     del J, dJ, Fv, Mv
     # Against the FP32 images the difference is the BF16 rounding of the
     # inputs themselves (2^-9 relative per voxel, comparable to the 0.02 noise
-    # that sets the local variances here), not arithmetic: it is measured and
-    # bounded loosely, the bar above is the parity bar.
+    # that sets the local variances here), not arithmetic: it may not exceed
+    # the oracle's own drift between the two inputs.
     J, dJ = O.warp(M32, u64, O.PAD_BORDER, with_grad=True)
     gJ, _ = O.lncc_grad_points(F32, J, 9, 1e-5, pts)
-    assert rel_l2(ggpu, gJ[None, :] * dJ.reshape(3, -1)[:, pts]) <= 0.2
+    assert_bf16_drift(ggpu, gbf, gJ[None, :] * dJ.reshape(3, -1)[:, pts], "c2 512^3 BF16")
 
 
 def test_c4_mi_bf16_1280_sampled(capi):
