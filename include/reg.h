@@ -245,6 +245,46 @@ REG_API reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void
                                            size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
                                            void *stream);
 
+/* As reg_loss_grad_composite, with the transform read from DEVICE memory:
+ * T_dev holds 15 floats in the layout of reg_affine (A row-major, t, s),
+ * for instance written by reg_affine_adam_step, so that an optimiser running
+ * on the device can feed the next evaluation without a round trip through
+ * the host.  The kernels read T_dev; its entries are not checked on the host
+ * and must be finite. */
+REG_API reg_status reg_loss_grad_composite_dev(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                               const float *u, reg_dims d, const float *T_dev, int pad, void *ws,
+                                               size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
+                                               void *stream);
+
+/* One Adam step of the affine stage (the optimiser state m1, m2 of Sec. 3.1
+ * applied to the 12 parameters of phi(p) = A (p - c) + c + tc / s, the map
+ * about the centre c of a pyramid level of scale s, tc in voxels of the
+ * finest grid), on one device thread in FP64:
+ *   gA = dC/dA - (dC/dt) c^T,  gtc = (dC/dt) / s,
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2  (per parameter),
+ *   A  -= decay lr_A   mhat / (sqrt(vhat) + eps),
+ *   tc -= decay lr_t s mhat / (sqrt(vhat) + eps),
+ * with bias correction 1 - beta^(k+1) and decay = 1 - (1 - final_lr) k /
+ * max(iters - 1, 1) (the steps shrink linearly to final_lr of their value over
+ * the level).  grad_affine: device double[12] as reg_loss_grad_composite
+ * writes it (dC/dA row-major, dC/dt) for the transform T_dev held; sim: device
+ * double[1], its similarity.  state: device double[36] = A (9), tc (3), m_A
+ * (9), v_A (9), m_t (3), v_t (3), updated in place (the caller sets A = I,
+ * tc = 0 and the moments to 0 to start, the moments again at a new level).
+ * T_dev: device float[15], overwritten with the next transform (A, t = c - A c
+ * + tc / s, s = 1).  obj_out (device double[1], may be NULL) receives the
+ * objective at the input transform: 1 - S (LNCC) or -MI.  k >= 0 is the
+ * step's index within its level. */
+typedef struct reg_affine_adam_desc {
+    double lr_A, lr_t, beta1, beta2, eps, final_lr;
+    int iters;          /* steps in this level (for the decay) */
+    double scale;       /* s: the level's voxel size in voxels of the finest grid */
+    double centre[3];   /* c: the level's volume centre (voxels of that level, x, y, z) */
+    int loss_kind;      /* reg_loss_kind of the objective recorded in obj_out */
+} reg_affine_adam_desc;
+REG_API reg_status reg_affine_adam_step(const double *grad_affine, const double *sim, double *state, float *T_dev,
+                                        const reg_affine_adam_desc *desc, int k, double *obj_out, void *stream);
+
 /* Composition of displacement fields (the fused sampler applied to a
  * 3-channel field): (id + w) = (id + b) o (id + a), i.e.
  *     w(p) = a(p) + b(p + a(p)),

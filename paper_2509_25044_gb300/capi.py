@@ -31,7 +31,8 @@ EXPORTS = ("reg_version", "reg_status_string", "reg_workspace_size", "reg_warp",
            "reg_debug_wait_flag", "reg_set_timing_events", "reg_mi_loss_grad_noalloc",
            "reg_debug_gemm_bf16", "reg_smooth_field", "reg_downsample2", "reg_run", "reg_warp_composite",
            "reg_warp_composite_backward", "reg_loss_grad_composite", "reg_compose_fields", "reg_exp_field",
-           "reg_compose_fields_backward", "reg_exp_field_backward")
+           "reg_compose_fields_backward", "reg_exp_field_backward", "reg_loss_grad_composite_dev",
+           "reg_affine_adam_step")
 
 
 class RegError(RuntimeError):
@@ -53,6 +54,14 @@ class RegLossDesc(ctypes.Structure):
 class RegAdamDesc(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("moment_dtype", ctypes.c_int), ("grad_scale", ctypes.c_float)]
+
+
+class RegAffineAdamDesc(ctypes.Structure):
+    """The affine stage's Adam step (reg_affine_adam_step)."""
+    _fields_ = [("lr_A", ctypes.c_double), ("lr_t", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("final_lr", ctypes.c_double),
+                ("iters", ctypes.c_int), ("scale", ctypes.c_double), ("centre", ctypes.c_double * 3),
+                ("loss_kind", ctypes.c_int)]
 
 
 class RegAffine(ctypes.Structure):
@@ -116,6 +125,11 @@ def _lib():
                                                   _vp, ctypes.c_size_t, _vp]
         L.reg_loss_grad_composite.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp, RegDims,
                                               _aff, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]
+        L.reg_loss_grad_composite_dev.argtypes = [ctypes.POINTER(RegLossDesc), _vp, _vp, ctypes.c_int, _vp,
+                                                  RegDims, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp,
+                                                  _vp]
+        L.reg_affine_adam_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(RegAffineAdamDesc), ctypes.c_int, _vp,
+                                           _vp]
         L.reg_compose_fields.argtypes = [_vp, _vp, RegDims, ctypes.c_int, _vp, _vp]
         L.reg_exp_field.argtypes = [_vp, RegDims, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.reg_compose_fields_backward.argtypes = [_vp, _vp, _vp, RegDims, ctypes.c_int, _vp, _vp, _vp]
@@ -328,6 +342,61 @@ def reg_loss_grad_composite(loss: RegLossDesc, F, M, T: RegAffine, u=None, ws=No
                                           _ptr(grad_u if need_u else None), _ptr(grad_affine if need_affine else None),
                                           _stream(F)), "reg_loss_grad_composite")
     return sim, (grad_u if need_u else None), (grad_affine if need_affine else None)
+
+
+def reg_loss_grad_composite_dev(loss: RegLossDesc, F, M, T_dev, u=None, ws=None, pad: int = REG_PAD_BORDER,
+                                need_u: bool = True, need_affine: bool = True, sim=None, grad_u=None,
+                                grad_affine=None):
+    """As reg_loss_grad_composite with the transform in device memory (T_dev:
+    float32[15], the reg_affine layout A, t, s)."""
+    d = dims_of(F)
+    _need(M, F.shape, F.dtype, "M")
+    _buf(T_dev, 15, torch.float32, "T_dev")
+    if u is not None:
+        _need(u, (3,) + tuple(F.shape), torch.float32, "u")
+    if ws is None:
+        ws = workspace(loss, F)
+    if sim is None:
+        sim = torch.empty(2, dtype=torch.float64, device=F.device)
+    _buf(sim, 1, torch.float64, "sim")
+    if need_u and grad_u is None:
+        grad_u = torch.empty((3,) + tuple(F.shape), dtype=torch.float32, device=F.device)
+    if need_u:
+        _buf(grad_u, 3 * F.numel(), torch.float32, "grad_u")
+    if need_affine and grad_affine is None:
+        grad_affine = torch.empty(12, dtype=torch.float64, device=F.device)
+    if need_affine:
+        _buf(grad_affine, 12, torch.float64, "grad_affine")
+    _check(_lib().reg_loss_grad_composite_dev(ctypes.byref(loss), _ptr(F), _ptr(M), _img_dtype(F), _ptr(u), d,
+                                              _ptr(T_dev), int(pad), _ptr(ws), ws.numel(), _ptr(sim),
+                                              _ptr(grad_u if need_u else None),
+                                              _ptr(grad_affine if need_affine else None), _stream(F)),
+           "reg_loss_grad_composite_dev")
+    return sim, (grad_u if need_u else None), (grad_affine if need_affine else None)
+
+
+def affine_adam_desc(lr_A, lr_t, iters, scale, centre, loss_kind, beta1=0.9, beta2=0.999, eps=1e-8,
+                     final_lr=0.1) -> RegAffineAdamDesc:
+    d = RegAffineAdamDesc(float(lr_A), float(lr_t), float(beta1), float(beta2), float(eps), float(final_lr),
+                          int(iters), float(scale))
+    for i in range(3):
+        d.centre[i] = float(centre[i])
+    d.loss_kind = int(loss_kind)
+    return d
+
+
+def reg_affine_adam_step(grad_affine, sim, state, T_dev, desc: RegAffineAdamDesc, k: int, obj=None):
+    """One device Adam step of the affine stage (state float64[36], T_dev
+    float32[15] updated in place; obj float64[1] or None receives the
+    objective at the input transform)."""
+    _buf(grad_affine, 12, torch.float64, "grad_affine")
+    _buf(sim, 1, torch.float64, "sim")
+    _buf(state, 36, torch.float64, "state")
+    _buf(T_dev, 15, torch.float32, "T_dev")
+    if obj is not None:
+        _buf(obj, 1, torch.float64, "obj")
+    _check(_lib().reg_affine_adam_step(_ptr(grad_affine), _ptr(sim), _ptr(state), _ptr(T_dev), ctypes.byref(desc),
+                                       int(k), _ptr(obj), _stream(state)), "reg_affine_adam_step")
 
 
 def reg_compose_fields(a, b, pad: int = REG_PAD_BORDER, out=None):

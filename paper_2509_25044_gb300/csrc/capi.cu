@@ -433,15 +433,17 @@ reg_status reg_warp_composite_backward(const void *M, int img_dt, const float *u
                                                  grad_affine ? grad_affine : w.scratch, s));
 }
 
-reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
-                                   const float *u, reg_dims d, const reg_affine *T, int pad, void *ws,
-                                   size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
-                                   void *stream) {
+namespace {
+// the composite similarity and gradients for a transform given by value or,
+// through A.dev, in device memory (arguments other than the transform are
+// checked here)
+reg_status loss_grad_composite(const reg_loss_desc *loss, const void *F, const void *M, int img_dt, const float *u,
+                               reg_dims d, const AffineT &A, int pad, void *ws, size_t ws_bytes, double *sim_out,
+                               float *grad_u, double *grad_affine, void *stream) {
     REG_TRY(check_dims(d));
     REG_TRY(check_loss(loss));
     if (img_dt != REG_F32 && img_dt != REG_BF16) return REG_ERR_DTYPE;
     if (pad != REG_PAD_BORDER && pad != REG_PAD_ZEROS) return REG_ERR_INVALID_ARG;
-    if (!affine_ok(T)) return REG_ERR_INVALID_ARG;
     REG_TRY(check_ptr(F));
     REG_TRY(check_ptr(M));
     REG_TRY(check_opt_ptr(u));
@@ -453,7 +455,6 @@ reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, con
     if (ws_bytes < workspace_bytes(g, loss)) return REG_ERR_WORKSPACE;
     const Ws w = carve(ws, g, loss);
     const cudaStream_t s = (cudaStream_t)stream;
-    const AffineT A = to_affine(*T);
     const bool need_grad = grad_u || grad_affine;
     double *aout = grad_affine ? grad_affine : w.scratch;
     REG_CUDA(cudaMemsetAsync(w.hist, 0, WS_ZERO_BYTES, s));
@@ -475,6 +476,58 @@ reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, con
                                       REG_F32, S, w.partials, w.counters + 2, aout, s, &A));
     }
     return REG_OK;
+}
+}  // namespace
+
+reg_status reg_loss_grad_composite(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                   const float *u, reg_dims d, const reg_affine *T, int pad, void *ws,
+                                   size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
+                                   void *stream) {
+    if (!affine_ok(T)) return REG_ERR_INVALID_ARG;
+    return loss_grad_composite(loss, F, M, img_dt, u, d, to_affine(*T), pad, ws, ws_bytes, sim_out, grad_u,
+                               grad_affine, stream);
+}
+
+reg_status reg_loss_grad_composite_dev(const reg_loss_desc *loss, const void *F, const void *M, int img_dt,
+                                       const float *u, reg_dims d, const float *T_dev, int pad, void *ws,
+                                       size_t ws_bytes, double *sim_out, float *grad_u, double *grad_affine,
+                                       void *stream) {
+    REG_TRY(check_ptr(T_dev));
+    AffineT A{};
+    A.dev = T_dev;
+    return loss_grad_composite(loss, F, M, img_dt, u, d, A, pad, ws, ws_bytes, sim_out, grad_u, grad_affine, stream);
+}
+
+reg_status reg_affine_adam_step(const double *grad_affine, const double *sim, double *state, float *T_dev,
+                                const reg_affine_adam_desc *desc, int k, double *obj_out, void *stream) {
+    if (!desc || k < 0 || desc->iters < 1) return REG_ERR_INVALID_ARG;
+    const double vals[] = {desc->lr_A, desc->lr_t, desc->eps, desc->final_lr, desc->scale,
+                           desc->centre[0], desc->centre[1], desc->centre[2]};
+    for (double v : vals)
+        if (!isfinite(v)) return REG_ERR_INVALID_ARG;
+    if (!(desc->lr_A > 0.0) || !(desc->lr_t > 0.0) || !(desc->eps >= 0.0) || !(desc->scale > 0.0))
+        return REG_ERR_INVALID_ARG;
+    if (!(desc->beta1 >= 0.0 && desc->beta1 < 1.0) || !(desc->beta2 >= 0.0 && desc->beta2 < 1.0))
+        return REG_ERR_INVALID_ARG;
+    if (desc->loss_kind != REG_LOSS_LNCC && desc->loss_kind != REG_LOSS_MI) return REG_ERR_INVALID_ARG;
+    REG_TRY(check_ptr(grad_affine));
+    REG_TRY(check_ptr(sim));
+    REG_TRY(check_ptr(state));
+    REG_TRY(check_ptr(T_dev));
+    REG_TRY(check_opt_ptr(obj_out));
+    AffineAdam P;
+    P.lr_A = desc->lr_A;
+    P.lr_t = desc->lr_t;
+    P.b1 = desc->beta1;
+    P.b2 = desc->beta2;
+    P.eps = desc->eps;
+    P.scale = desc->scale;
+    for (int i = 0; i < 3; ++i) P.c[i] = desc->centre[i];
+    P.bc1 = 1.0 - pow(desc->beta1, (double)(k + 1));
+    P.bc2 = 1.0 - pow(desc->beta2, (double)(k + 1));
+    P.decay = 1.0 - (1.0 - desc->final_lr) * (double)k / (double)(desc->iters > 1 ? desc->iters - 1 : 1);
+    P.lncc = desc->loss_kind == REG_LOSS_LNCC;
+    return cuda_status(launch_affine_adam(grad_affine, sim, state, T_dev, P, obj_out, (cudaStream_t)stream));
 }
 
 reg_status reg_compose_fields(const float *a, const float *b, reg_dims d, int pad, float *w, void *stream) {

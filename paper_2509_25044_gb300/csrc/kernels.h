@@ -165,6 +165,16 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                                double *partials, unsigned *counter, double *r_out, cudaStream_t s,
                                const AffineT *aff = nullptr);
 
+// One Adam step on the 12 parameters of an affine map about a centre,
+// phi(p) = A (p - c) + c + tc / s, on one device thread (reg_affine_adam_step)
+struct AffineAdam {
+    double lr_A, lr_t, b1, b2, eps, scale, c[3];
+    double bc1, bc2, decay;  // bias corrections 1 - beta^(k+1) and the step's decay factor
+    int lncc;                // the objective recorded: 1 - S (LNCC) or -MI
+};
+cudaError_t launch_affine_adam(const double *grad_affine, const double *sim, double *state, float *T_dev,
+                               const AffineAdam &P, double *obj_out, cudaStream_t s);
+
 cudaError_t launch_diffusion(const float *u, const Dims &g, float lam, float *grad, double *partials,
                              unsigned *counter, double *r_out, cudaStream_t s);
 cudaError_t launch_adam(const float *u_in, float *u_out, void *m, void *v, int mdt, const float *grad,

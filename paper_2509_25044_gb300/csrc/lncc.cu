@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
                        LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
                        float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                        double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
-                       unsigned *err, AffineT A) {
+                       unsigned *err, AffineT Ain) {
+    const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     extern __shared__ float smem[];
     __shared__ double red[32];
     const int r = P.r;
@@ -496,7 +497,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                             LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
                             float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                             double *__restrict__ partials, unsigned *__restrict__ counter,
-                            double *__restrict__ r_out, unsigned *err, AffineT A) {
+                            double *__restrict__ r_out, unsigned *err, AffineT Ain) {
+    const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     __shared__ double red[32];
     const int r = P.r;
     const int tid = threadIdx.y * TX + threadIdx.x;

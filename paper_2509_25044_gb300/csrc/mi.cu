@@ -44,8 +44,9 @@ __host__ __device__ constexpr int hist_batch_planes(int B) {
 template <typename T, int PAD, typename I, bool HARD, bool AFF>
 __global__ void __launch_bounds__(HIST_THREADS, 1)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
-                   int tiles_x, long long total, AffineT A, unsigned long long *__restrict__ hist) {
+                   int tiles_x, long long total, AffineT Ain, unsigned long long *__restrict__ hist) {
     extern __shared__ unsigned sh[];
+    const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     const int B = P.bins, BB = B * B;
     const int copies = hist_copies(B), pitch = BB + 1;
     const int tid = threadIdx.y * HIST_TX + threadIdx.x;
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
                      MiParams P, int zc, const float *__restrict__ Gtab, float *__restrict__ grad_out,
                      float *__restrict__ u_out, MT *__restrict__ m, MT *__restrict__ v, StepParams S,
                      double *__restrict__ partials, unsigned *__restrict__ counter, double *__restrict__ r_out,
-                     unsigned *err, AffineT A) {
+                     unsigned *err, AffineT Ain) {
+    const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     // G4[m][n] = G'[m][n .. n+3]: one 16-byte shared load per kernel row
     extern __shared__ float4 G4[];  // B * B entries (dynamic)
     __shared__ double red[32];

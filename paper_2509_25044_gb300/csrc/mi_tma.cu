@@ -146,13 +146,21 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
         const int o = (warp + 1) * SW_UX + lane + 4;  // (x, y) in a u channel slot
         const int t = warp * SW_TX + lane;            // (x, y) in an F / m / v slot
         float racc = 0.0f;
+        // ring slots of u at z-1, z, z+1 and of F / m / v at z, rotated once per
+        // plane, and the parity each slot's next completion will have
+        int su0 = 0, su1 = 1, su2 = 2, ss = 0;
+        uint32_t uphase = 0u, sphase = 0u;
         for (int zi = 0; zi < nzc; ++zi, p += nxy) {
             const int z = z0 + zi;
             bool ok = true;
-            if (zi == 0) ok = umma::mbar_wait(full_u, 0) && umma::mbar_wait(full_u + 1, 0);
-            const int jn = zi + 2;
-            ok = ok && umma::mbar_wait(full_u + jn % SW_NU, (jn / SW_NU) & 1) &&
-                 umma::mbar_wait(full_s + zi % SW_NS, (zi / SW_NS) & 1);
+            if (zi == 0) {
+                ok = umma::mbar_wait(full_u, 0) && umma::mbar_wait(full_u + 1, 0);
+                uphase = 3u;
+            }
+            ok = ok && umma::mbar_wait(full_u + su2, (uphase >> su2) & 1u) &&
+                 umma::mbar_wait(full_s + ss, (sphase >> ss) & 1u);
+            uphase ^= 1u << su2;
+            sphase ^= 1u << ss;
             // the warp leaves together (its lanes meet at __syncwarp below)
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) {
                 if (lane == 0) {
@@ -161,10 +169,10 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
                 }
                 break;
             }
-            const float *Up = reinterpret_cast<const float *>(smem + L.u + (zi % SW_NU) * al128(SW_UBYTES));
-            const float *Uc = reinterpret_cast<const float *>(smem + L.u + ((zi + 1) % SW_NU) * al128(SW_UBYTES));
-            const float *Un = reinterpret_cast<const float *>(smem + L.u + (jn % SW_NU) * al128(SW_UBYTES));
-            const T *Fs = reinterpret_cast<const T *>(smem + L.f + (zi % SW_NS) * L.fslot);
+            const float *Up = reinterpret_cast<const float *>(smem + L.u + su0 * al128(SW_UBYTES));
+            const float *Uc = reinterpret_cast<const float *>(smem + L.u + su1 * al128(SW_UBYTES));
+            const float *Un = reinterpret_cast<const float *>(smem + L.u + su2 * al128(SW_UBYTES));
+            const T *Fs = reinterpret_cast<const T *>(smem + L.f + ss * L.fslot);
             if (in) {
                 const float cur[3] = {Uc[o], Uc[SW_UC + o], Uc[2 * SW_UC + o]};
                 float sx, sy, sz;
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
                 if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
                 const float gs[3] = {gj * sx, gj * sy, gj * sz};
                 if (STEP) {
-                    const MT *Ms = reinterpret_cast<const MT *>(smem + L.m + (zi % SW_NS) * L.mslot);
-                    const MT *Vs = reinterpret_cast<const MT *>(smem + L.v + (zi % SW_NS) * L.mslot);
+                    const MT *Ms = reinterpret_cast<const MT *>(smem + L.m + ss * L.mslot);
+                    const MT *Vs = reinterpret_cast<const MT *>(smem + L.v + ss * L.mslot);
                     const bool hzm = z > 0, hzp = z + 1 < g.nz;
                     float rpart = 0.0f;
 #pragma unroll
@@ -225,9 +233,13 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
             }
             __syncwarp();
             if (lane == 0) {
-                umma::mbar_arrive(empty_u + zi % SW_NU);
-                umma::mbar_arrive(empty_s + zi % SW_NS);
+                umma::mbar_arrive(empty_u + su0);  // u at z - 1 is no longer needed
+                umma::mbar_arrive(empty_s + ss);
             }
+            su0 = su1;
+            su1 = su2;
+            su2 = su2 + 1 == SW_NU ? 0 : su2 + 1;
+            ss = ss + 1 == SW_NS ? 0 : ss + 1;
             if ((zi & 15) == 15) {
                 rsum += (double)racc;
                 racc = 0.0f;

@@ -252,7 +252,26 @@ struct AffineT {
     float am[9];  // A - I, row-major: row i is output axis i (x, y, z)
     float t[3];   // translation, voxels
     float s[3];   // S = diag(s)
+    // when set, the transform is read on the device instead: 15 floats in the
+    // layout of reg_affine (A row-major, t, s), written by an earlier kernel
+    const float *dev = nullptr;
 };
+// The transform a kernel applies: its by-value parameter, or the device copy
+// that parameter points to (A - I formed in FP32, the same rounding as the
+// host's (float)((double)A - 1) of a float A).
+__device__ __forceinline__ AffineT resolve_affine(const AffineT &A) {
+    if (A.dev == nullptr) return A;
+    AffineT r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r.am[i] = __ldg(A.dev + i) - (i % 4 == 0 ? 1.0f : 0.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        r.t[i] = __ldg(A.dev + 9 + i);
+        r.s[i] = __ldg(A.dev + 12 + i);
+    }
+    r.dev = nullptr;
+    return r;
+}
 __device__ __forceinline__ void composite_disp(const AffineT &T, int x, int y, int z, float &ux, float &uy,
                                                float &uz) {
     const float fx = (float)x, fy = (float)y, fz = (float)z;

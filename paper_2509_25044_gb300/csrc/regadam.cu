@@ -250,4 +250,49 @@ cudaError_t launch_wait_flag(const unsigned *flag, unsigned expect, unsigned lon
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Adam on the 12 parameters of the affine stage (the optimiser state m1, m2 of
+// Sec. 3.1 for phi(p) = A (p - c) + c + tc / s), in FP64 on one thread, fed by
+// the fixed-order sums dC/dA, dC/dt of the composite sweeps:
+//   dC/dA at fixed tc = dC/dA - (dC/dt) c^T,   dC/dtc = (dC/dt) / s,
+// then Adam with bias correction, the step scaled by `decay`, tc's step by s
+// (tc is in voxels of the finest grid).  state: A (9), tc (3), m_A (9),
+// v_A (9), m_t (3), v_t (3).  T_dev receives the next transform in the layout
+// of reg_affine: A, t = c - A c + tc / s, s = 1.
+// ---------------------------------------------------------------------------
+__global__ void affine_adam_kernel(const double *__restrict__ ga, const double *__restrict__ sim,
+                                   double *__restrict__ st, float *__restrict__ T, AffineAdam P,
+                                   double *__restrict__ obj) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (obj) obj[0] = P.lncc ? 1.0 - sim[0] : -sim[0];
+    double *A = st, *tc = st + 9, *mA = st + 12, *vA = st + 21, *mt = st + 30, *vt = st + 33;
+    const double gt[3] = {ga[9], ga[10], ga[11]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const int e = 3 * i + j;
+            const double g = ga[e] - gt[i] * P.c[j];
+            mA[e] = P.b1 * mA[e] + (1.0 - P.b1) * g;
+            vA[e] = P.b2 * vA[e] + (1.0 - P.b2) * g * g;
+            A[e] -= P.decay * P.lr_A * (mA[e] / P.bc1) / (sqrt(vA[e] / P.bc2) + P.eps);
+        }
+    for (int i = 0; i < 3; ++i) {
+        const double g = gt[i] / P.scale;
+        mt[i] = P.b1 * mt[i] + (1.0 - P.b1) * g;
+        vt[i] = P.b2 * vt[i] + (1.0 - P.b2) * g * g;
+        tc[i] -= P.decay * P.lr_t * P.scale * (mt[i] / P.bc1) / (sqrt(vt[i] / P.bc2) + P.eps);
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double Ac = A[3 * i] * P.c[0] + A[3 * i + 1] * P.c[1] + A[3 * i + 2] * P.c[2];
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = (float)A[3 * i + j];
+        T[9 + i] = (float)(P.c[i] - Ac + tc[i] / P.scale);
+        T[12 + i] = 1.0f;
+    }
+}
+
+cudaError_t launch_affine_adam(const double *grad_affine, const double *sim, double *state, float *T_dev,
+                               const AffineAdam &P, double *obj_out, cudaStream_t s) {
+    affine_adam_kernel<<<1, 32, 0, s>>>(grad_affine, sim, state, T_dev, P, obj_out);
+    return cudaGetLastError();
+}
+
 }  // namespace regk

@@ -12,8 +12,9 @@ namespace regk {
 
 template <typename T, bool SLOPE, int PAD, bool AFF>
 __global__ void __launch_bounds__(TILE_THREADS) warp_kernel(const T *__restrict__ M, const float *__restrict__ u,
-                                                            Dims g, int zc, AffineT A, float *__restrict__ J,
+                                                            Dims g, int zc, AffineT Ain, float *__restrict__ J,
                                                             float *__restrict__ dJ) {
+    const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
@@ -71,10 +72,11 @@ cudaError_t launch_warp(const void *M, int dt, const float *u, const Dims &g, in
 // dL/dt are reduced in a fixed order.
 template <typename T, int PAD>
 __global__ void __launch_bounds__(TILE_THREADS)
-    composite_backward_kernel(const T *__restrict__ M, const float *__restrict__ u, Dims g, int zc, AffineT A,
+    composite_backward_kernel(const T *__restrict__ M, const float *__restrict__ u, Dims g, int zc, AffineT Ain,
                               const float *__restrict__ gin, float *__restrict__ g_u, double *__restrict__ partials,
                               unsigned *__restrict__ counter, double *__restrict__ out, unsigned *err) {
     __shared__ double red[32];
+    const AffineT A = resolve_affine(Ain);
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     AffineAcc acc;

@@ -245,18 +245,25 @@ def centred_affine_grads(gA, gt, c, s):
 
 def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40), lr_A: float = 0.01,
                     lr_t: float = 0.3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-                    final_lr: float = 0.1) -> dict:
+                    final_lr: float = 0.1, on_device: bool = True) -> dict:
     """Affine stage of the paper's pipeline: phi(p) = A (p - c) + c + tc about
     the volume centre, optimised by Adam over the 12 parameters at each scale
     of a 2x block-mean pyramid, with the similarity and dC/dA, dC/dt from the
-    composite sampler (reg_loss_grad_composite, u = 0).  tc is kept in voxels
-    of the full-resolution grid; at scale s it is tc / s.  The 12-parameter
-    bookkeeping runs on the host (one 112-byte read per iteration).  The
-    step sizes decay linearly to final_lr of their value over each level: a
-    constant Adam step leaves A jittering by about lr_A, a motion of lr_A
-    times the radius at the volume's edge.  Returns
-    A, t of the full-resolution map (phi = A p + t), tc, and the objective
-    history per level."""
+    composite sampler (u = 0).  tc is kept in voxels of the full-resolution
+    grid; at scale s it is tc / s.  The step sizes decay linearly to final_lr
+    of their value over each level: a constant Adam step leaves A jittering by
+    about lr_A, a motion of lr_A times the radius at the volume's edge.
+
+    on_device (default): each iteration is two launches -- the composite
+    similarity and gradients with the transform read from device memory
+    (reg_loss_grad_composite_dev) and the 12-parameter Adam step on the
+    device (reg_affine_adam_step), which writes the next transform; the host
+    reads the state once per level.  on_device=False runs the same Adam on
+    the host (one 112-byte read per iteration).  Returns A, t of the
+    full-resolution map (phi = A p + t), tc, and the objective history per
+    level."""
+    if on_device:
+        return _register_affine_device(F, M, cfg, scales, iters, lr_A, lr_t, beta1, beta2, eps, final_lr)
     pyr = {1: (F.contiguous(), M.contiguous())}
     s = 1
     while s < scales[0]:
@@ -292,6 +299,44 @@ def register_affine(F, M, cfg: RegConfig, scales=(4, 2, 1), iters=(100, 60, 40),
             A = A - decay * lr_A * (mA / b1) / (np.sqrt(vA / b2) + eps)
             tc = tc - decay * lr_t * s * (mt / b1) / (np.sqrt(vt / b2) + eps)
         levels.append({"scale": s, "objective": np.asarray(hist)})
+    A_full, t_full = affine_about_centre(A, tc, tuple(F.shape))
+    return {"A": A_full, "t": t_full, "tc": tc, "levels": levels}
+
+
+def _register_affine_device(F, M, cfg, scales, iters, lr_A, lr_t, beta1, beta2, eps, final_lr) -> dict:
+    pyr = {1: (F.contiguous(), M.contiguous())}
+    s = 1
+    while s < scales[0]:
+        f, m = pyr[s]
+        pyr[2 * s] = (capi.reg_downsample2(f), capi.reg_downsample2(m))
+        s *= 2
+    loss = cfg.loss_desc(F, M)
+    dev = F.device
+    state = torch.zeros(36, dtype=torch.float64, device=dev)  # A, tc, m_A, v_A, m_t, v_t
+    state[0:9] = torch.eye(3, dtype=torch.float64, device=dev).reshape(9)
+    T = torch.zeros(15, dtype=torch.float32, device=dev)
+    buf = torch.zeros(14, dtype=torch.float64, device=dev)  # sim (2), dC/dA (9), dC/dt (3)
+    kind = capi.REG_LOSS_LNCC if cfg.loss == "lncc" else capi.REG_LOSS_MI
+    levels = []
+    for s, it in zip(scales, iters):
+        f, m = pyr[s]
+        shape = tuple(f.shape)
+        c = _centre(shape)
+        ws = capi.workspace(loss, f)
+        st = state.cpu().numpy()  # A and tc carried over from the previous level (one read per level)
+        A, tc = st[0:9].reshape(3, 3), st[9:12]
+        state[12:36] = 0.0  # fresh moments for the level
+        t0 = c - A @ c + tc / s
+        T.copy_(torch.tensor(np.concatenate([A.reshape(9), t0, np.ones(3)]), dtype=torch.float32))
+        desc = capi.affine_adam_desc(lr_A, lr_t, it, s, c, kind, beta1, beta2, eps, final_lr)
+        hist = torch.zeros((it, 2), dtype=torch.float64, device=dev)  # 16-byte rows: every entry aligned
+        for k in range(it):
+            capi.reg_loss_grad_composite_dev(loss, f, m, T, None, ws, pad=cfg.pad, need_u=False, sim=buf[0:2],
+                                             grad_affine=buf[2:14])
+            capi.reg_affine_adam_step(buf[2:14], buf[0:1], state, T, desc, k, obj=hist[k])
+        levels.append({"scale": s, "objective": hist[:, 0].cpu().numpy()})
+    st = state.cpu().numpy()
+    A, tc = st[0:9].reshape(3, 3), st[9:12]
     A_full, t_full = affine_about_centre(A, tc, tuple(F.shape))
     return {"A": A_full, "t": t_full, "tc": tc, "levels": levels}
 

@@ -67,14 +67,19 @@ def test_svf_driver_orchestration(fake):
     assert out["objective"].shape == (3,) and tuple(out["u"].shape) == (3, 8, 8, 8)
 
 
-def test_affine_driver_orchestration(fake):
+@pytest.mark.parametrize("on_device", [True, False])
+def test_affine_driver_orchestration(fake, on_device):
     from paper_2509_25044_gb300.register import RegConfig, register_affine
     F, M = _pair(16)
     cfg = RegConfig(loss="mi", bins=16)
-    out = register_affine(F, M, cfg, scales=(4, 2, 1), iters=(3, 2, 1))
+    out = register_affine(F, M, cfg, scales=(4, 2, 1), iters=(3, 2, 1), on_device=on_device)
     body = [c for c in fake.calls if c != "reg_workspace_size"]
-    # the pyramid (F and M at 2x and 4x), then one composite gradient per iteration
-    assert body == ["reg_downsample2"] * 4 + ["reg_loss_grad_composite"] * 6
+    # the pyramid (F and M at 2x and 4x), then per iteration one composite
+    # gradient (on the device: with the transform in device memory, followed
+    # by the device Adam step that writes the next transform)
+    per_iter = (["reg_loss_grad_composite_dev", "reg_affine_adam_step"] if on_device
+                else ["reg_loss_grad_composite"])
+    assert body == ["reg_downsample2"] * 4 + per_iter * 6
     assert [lv["scale"] for lv in out["levels"]] == [4, 2, 1]
     assert out["A"].shape == (3, 3) and out["t"].shape == (3,)
 
