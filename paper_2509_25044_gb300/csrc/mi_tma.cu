@@ -35,7 +35,8 @@ namespace regk {
 
 namespace {
 
-constexpr int SW_TX = 32, SW_TY = 8;                                 // tile: one warp per row
+constexpr int SW_VL = 2;                                             // voxels per lane (an x pair)
+constexpr int SW_TX = 32 * SW_VL, SW_TY = 8;                         // tile: one warp per row
 constexpr int SW_UX = SW_TX + 8, SW_UY = SW_TY + 2, SW_UC = SW_UX * SW_UY;  // u box: x0-4 .., y0-1 ..
 constexpr int SW_NU = 5;   // u plane slots: z-1, z, z+1 in use, two in flight
 constexpr int SW_NS = 3;   // F / m / v plane slots
@@ -60,13 +61,21 @@ struct SwLayout {
     }
 };
 
-__device__ __forceinline__ float sm_val(const float *p, int i) { return p[i]; }
-__device__ __forceinline__ float sm_val(const __nv_bfloat16 *p, int i) { return __bfloat162float(p[i]); }
+// two consecutive elements (8-byte aligned FP32 / 4-byte aligned BF16) as floats, and their stores
+__device__ __forceinline__ float2 ld_pair(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+__device__ __forceinline__ void st_pair(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+// round-to-nearest-even of each element, as __float2bfloat16_rn
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
 
 }  // namespace
 
 template <typename T, typename MT, bool STEP, int PAD, typename I>
-__global__ void __launch_bounds__(SW_THREADS, 3)
+__global__ void __launch_bounds__(SW_THREADS, 2)
     mi_sweep2_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
                          const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap vmap,
                          const T *__restrict__ M, Dims g, MiParams P, int zc, const float *__restrict__ Gtab,
@@ -138,13 +147,15 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
         }
     } else {
         // ---------------- consumers ----------------
-        const int x = x0 + lane, y = y0 + warp;
+        // lane: the x pair (x, x + 1); the pair is wholly inside or outside the
+        // volume (nx % 8 == 0, x even)
+        const int x = x0 + SW_VL * lane, y = y0 + warp;
         const bool in = x < g.nx && y < g.ny;
-        const bool hxm = x > 0, hxp = x + 1 < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
+        const bool hxl = x > 0, hxr = x + SW_VL < g.nx, hym = y > 0, hyp = y + 1 < g.ny;
         const I nxy = (I)g.nxy;
         I p = (I)z0 * nxy + (I)y * g.nx + x;
-        const int o = (warp + 1) * SW_UX + lane + 4;  // (x, y) in a u channel slot
-        const int t = warp * SW_TX + lane;            // (x, y) in an F / m / v slot
+        const int o = (warp + 1) * SW_UX + SW_VL * lane + 4;  // (x, y) in a u channel slot (even: 8-byte aligned)
+        const int t = warp * SW_TX + SW_VL * lane;            // (x, y) in an F / m / v slot
         float racc = 0.0f;
         // ring slots of u at z-1, z, z+1 and of F / m / v at z, rotated once per
         // plane, and the parity each slot's next completion will have
@@ -174,22 +185,37 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
             const float *Un = reinterpret_cast<const float *>(smem + L.u + su2 * al128(SW_UBYTES));
             const T *Fs = reinterpret_cast<const T *>(smem + L.f + ss * L.fslot);
             if (in) {
-                const float cur[3] = {Uc[o], Uc[SW_UC + o], Uc[2 * SW_UC + o]};
-                float sx, sy, sz;
-                const float jv = sample_grad<T, PAD, I>(M, g, x, y, z, cur[0], cur[1], cur[2], sx, sy, sz);
-                float wf[4], dj[4];
-                const int iF = bspline_weights(to_bin(sm_val(Fs, t), P.f_lo, P.f_scale, B), B, wf) - 1;
-                const float tj = (jv - P.m_lo) * P.m_scale;
-                const int iJ = bspline_dweights(to_bin(jv, P.m_lo, P.m_scale, B), B, dj) - 1;
-                float gj = 0.0f;
+                float cur[3][SW_VL];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float4 r = G4[(iF + a) * B + iJ];
-                    const float tt = fmaf(r.x, dj[0], fmaf(r.y, dj[1], fmaf(r.z, dj[2], r.w * dj[3])));
-                    gj = fmaf(wf[a], tt, gj);
+                for (int c = 0; c < 3; ++c) {
+                    const float2 q = ld_pair(Uc + c * SW_UC + o);
+                    cur[c][0] = q.x;
+                    cur[c][1] = q.y;
                 }
-                if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
-                const float gs[3] = {gj * sx, gj * sy, gj * sz};
+                const float2 fq = ld_pair(Fs + t);
+                const float fv[SW_VL] = {fq.x, fq.y};
+                float gs[3][SW_VL];
+#pragma unroll
+                for (int e = 0; e < SW_VL; ++e) {
+                    float sx, sy, sz;
+                    const float jv = sample_grad<T, PAD, I>(M, g, x + e, y, z, cur[0][e], cur[1][e], cur[2][e], sx,
+                                                            sy, sz);
+                    float wf[4], dj[4];
+                    const int iF = bspline_weights(to_bin(fv[e], P.f_lo, P.f_scale, B), B, wf) - 1;
+                    const float tj = (jv - P.m_lo) * P.m_scale;
+                    const int iJ = bspline_dweights(to_bin(jv, P.m_lo, P.m_scale, B), B, dj) - 1;
+                    float gj = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float4 r = G4[(iF + a) * B + iJ];
+                        const float tt = fmaf(r.x, dj[0], fmaf(r.y, dj[1], fmaf(r.z, dj[2], r.w * dj[3])));
+                        gj = fmaf(wf[a], tt, gj);
+                    }
+                    if (!(tj >= 0.0f && tj <= 1.0f)) gj = 0.0f;  // intensity clamp is flat
+                    gs[0][e] = gj * sx;
+                    gs[1][e] = gj * sy;
+                    gs[2][e] = gj * sz;
+                }
                 if (STEP) {
                     const MT *Ms = reinterpret_cast<const MT *>(smem + L.m + ss * L.mslot);
                     const MT *Vs = reinterpret_cast<const MT *>(smem + L.v + ss * L.mslot);
@@ -197,38 +223,58 @@ __global__ void __launch_bounds__(SW_THREADS, 3)
                     float rpart = 0.0f;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        // diffusion gradient, same terms and order as diffusion_ptr
                         const float *U = Uc + c * SW_UC;
-                        const float c0 = cur[c];
-                        float acc = 0.0f;
-                        if (hxp) {
-                            const float d = U[o + 1] - c0;
-                            acc -= d;
-                            rpart = fmaf(d, d, rpart);
+                        const float2 yp = ld_pair(U + o + SW_UX), ym = ld_pair(U + o - SW_UX);
+                        const float2 zp = ld_pair(Un + c * SW_UC + o), zm = ld_pair(Up + c * SW_UC + o);
+                        const float xl = U[o - 1], xr = U[o + SW_VL];
+                        const float ypv[SW_VL] = {yp.x, yp.y}, ymv[SW_VL] = {ym.x, ym.y};
+                        const float zpv[SW_VL] = {zp.x, zp.y}, zmv[SW_VL] = {zm.x, zm.y};
+                        const float2 m2 = ld_pair(Ms + c * SW_TX * SW_TY + t), v2 = ld_pair(Vs + c * SW_TX * SW_TY + t);
+                        const float m0[SW_VL] = {m2.x, m2.y}, v0[SW_VL] = {v2.x, v2.y};
+                        float uo[SW_VL], mo[SW_VL], vo[SW_VL], gt[SW_VL];
+#pragma unroll
+                        for (int e = 0; e < SW_VL; ++e) {
+                            // diffusion gradient, same terms and order as diffusion_ptr
+                            const float c0 = cur[c][e];
+                            const bool hxm = e > 0 || hxl, hxp = e < SW_VL - 1 || hxr;
+                            const float xm = e > 0 ? cur[c][e - 1] : xl;
+                            const float xp = e < SW_VL - 1 ? cur[c][e + 1] : xr;
+                            float acc = 0.0f;
+                            if (hxp) {
+                                const float d = xp - c0;
+                                acc -= d;
+                                rpart = fmaf(d, d, rpart);
+                            }
+                            if (hxm) acc += c0 - xm;
+                            if (hyp) {
+                                const float d = ypv[e] - c0;
+                                acc -= d;
+                                rpart = fmaf(d, d, rpart);
+                            }
+                            if (hym) acc += c0 - ymv[e];
+                            if (hzp) {
+                                const float d = zpv[e] - c0;
+                                acc -= d;
+                                rpart = fmaf(d, d, rpart);
+                            }
+                            if (hzm) acc += c0 - zmv[e];
+                            gt[e] = fmaf(S.lam * S.two_over_n, acc, gs[c][e]);
+                            // Adam, term for term as adam_fast
+                            const float gg = S.gscale * gt[e];
+                            mo[e] = fmaf(S.b1, m0[e], (1.0f - S.b1) * gg);
+                            vo[e] = fmaf(S.b2, v0[e], (1.0f - S.b2) * gg * gg);
+                            const float denom = fmaf(sqrt_approx(vo[e]), S.rsqrt_bc2, S.eps);
+                            uo[e] = fmaf(-S.lr_bc1, __fdividef(mo[e], denom), c0);
                         }
-                        if (hxm) acc += c0 - U[o - 1];
-                        if (hyp) {
-                            const float d = U[o + SW_UX] - c0;
-                            acc -= d;
-                            rpart = fmaf(d, d, rpart);
-                        }
-                        if (hym) acc += c0 - U[o - SW_UX];
-                        if (hzp) {
-                            const float d = Un[c * SW_UC + o] - c0;
-                            acc -= d;
-                            rpart = fmaf(d, d, rpart);
-                        }
-                        if (hzm) acc += c0 - Up[c * SW_UC + o];
-                        const float gt = fmaf(S.lam * S.two_over_n, acc, gs[c]);
-                        if (grad_out) (grad_out + c * g.n)[p] = gt;
-                        const float m0 = sm_val(Ms, c * SW_TX * SW_TY + t);
-                        const float v0 = sm_val(Vs, c * SW_TX * SW_TY + t);
-                        (u_out + c * g.n)[p] = adam_fast(c0, gt, m0, v0, m + c * g.n, v + c * g.n, p, S);
+                        if (grad_out) st_pair(grad_out + c * g.n + p, gt[0], gt[1]);
+                        st_pair(u_out + c * g.n + p, uo[0], uo[1]);
+                        st_pair(m + c * g.n + p, mo[0], mo[1]);
+                        st_pair(v + c * g.n + p, vo[0], vo[1]);
                     }
                     racc += rpart;
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) (grad_out + c * g.n)[p] = gs[c];
+                    for (int c = 0; c < 3; ++c) st_pair(grad_out + c * g.n + p, gs[c][0], gs[c][1]);
                 }
             }
             __syncwarp();

@@ -301,13 +301,13 @@ def test_iterate_matches_oracle(capi, kind, shape):
     np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
 
 
-# Rows of whole 4-voxel quads take the vector sweeps (a thread per quad, x
-# neighbours from adjacent lanes, memory loads at each warp's 128-voxel edge):
-# rows that span several warps with a partial last one, ragged y and z, both
-# moment types.
+# Rows with nx % 8 == 0 take the TMA-staged MI sweep (64 x 8 tiles, an x pair
+# per lane, the diffusion halo from the staged box): rows that span several
+# tiles with a partial last one, ragged y and z, both moment types; rows with
+# nx % 8 != 0 the plain sweep.
 @pytest.mark.parametrize("kind", ["mi", "mi_hard"])
-@pytest.mark.parametrize("shape,mdt", [((9, 11, 260), 0), ((6, 70, 132), 1), ((5, 3, 4), 0)])
-def test_iterate_quad_rows_match_oracle(capi, kind, shape, mdt):
+@pytest.mark.parametrize("shape,mdt", [((9, 11, 264), 0), ((6, 70, 136), 1), ((5, 3, 8), 0), ((7, 9, 132), 1)])
+def test_iterate_tile_rows_match_oracle(capi, kind, shape, mdt):
     c = _iterate_case(capi, kind, shape, mdt=mdt, t=2, seed=91)
     ref = O.objective(to64(c["F"]), to64(c["M"]), to64(c["u"]), c["spec"], 0.1)
     assert_rel(c["obj"][0].item(), ref["sim"], LOSS_RTOL, "similarity")
