@@ -260,11 +260,22 @@ class UNet:
     # ---- inference: initial field at the registration grid ---------------------
     def predict_init(self, F, M, f_range, m_range) -> torch.Tensor:
         """u0 for a pair of size n (n a multiple of the network input size):
-        average-pool to the input grid, run the network, upsample the 64^3
-        output to n^3 and rescale it to n^3 voxel units."""
+        average-pool to the input grid, scale each image by its range on that
+        grid (f_range, m_range are the ranges at n^3), run the network,
+        upsample the 64^3 output to n^3 and rescale it to n^3 voxel units."""
         n = F.shape[0]
         factor = n // self.n[0]
         self.pack(F, M, factor, f_range, m_range)
+        if factor > 1:
+            # the network learned on images scaled by the range of the grid it
+            # sees; pooling narrows that range (the noise averages out), so
+            # measure it on the pooled grid (channels in units of the given
+            # ranges) and pack again
+            lo, hi = torch.aminmax(self.a["x0"][:, :2].float(), dim=0)
+            lo, hi = lo.tolist(), hi.tolist()
+            fw, mw = f_range[1] - f_range[0], m_range[1] - m_range[0]
+            self.pack(F, M, factor, (f_range[0] + lo[0] * fw, f_range[0] + hi[0] * fw),
+                      (m_range[0] + lo[1] * mw, m_range[0] + hi[1] * mw))
         u_half = self.forward()
         up = n // self.n[1]
         out = torch.empty((3,) + tuple(F.shape), dtype=torch.float32, device=self.dev)
@@ -273,14 +284,16 @@ class UNet:
         return out
 
 
-def training_pair(n: int, seed: int, device) -> dict:
+def training_pair(n: int, seed: int, device, noise: float = 0.02) -> dict:
     """One training pair at n^3 made with the library's own warp: a blob
-    image B (sigma scaled to the grid) with N(0, 0.02^2) noise as M, a random
+    image B (sigma scaled to the grid) with N(0, noise^2) noise as M, a random
     smooth field v_true (sigma ~ U[4,12], max |v| ~ U(0,10]) and F = M o (id +
     v_true), so that v_true is the displacement the registration of M onto F
     recovers (the noise is part of the texture and moves with it, as in the
-    mono-modal workloads).  Random numbers come from torch's Philox generator
-    on the device, seeded with `seed`."""
+    mono-modal workloads).  noise = 0.02 is the workloads' acquisition noise
+    at the grid itself; a pair that the network sees after 4^3 average
+    pooling (the 512^3 workload at 128^3) carries 0.02 / 8.  Random numbers
+    come from torch's Philox generator on the device, seeded with `seed`."""
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     s = n / 64.0
@@ -289,6 +302,6 @@ def training_pair(n: int, seed: int, device) -> dict:
     sigma = 4.0 + 8.0 * float(u01[0])
     mx = 10.0 * (1.0 - float(u01[1]))  # in (0, 10]
     v = synth.smooth_field((n, n, n), sigma, mx, gen=gen, device=device)
-    M = B.add_(torch.randn((n, n, n), generator=gen, device=device, dtype=torch.float32), alpha=0.02)
+    M = B.add_(torch.randn((n, n, n), generator=gen, device=device, dtype=torch.float32), alpha=noise)
     F = capi.reg_warp(M, v)
     return dict(F=F, M=M, v=v)
