@@ -69,20 +69,20 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
             const int y = (int)(tile / tiles_x) * HIST_TY + threadIdx.y;
             if (x >= g.nx || y >= g.ny) continue;
             I p = (I)z0 * nxy + (I)y * g.nx + x;
-            float fv = ld_vox(F, p), ux = 0.0f, uy = 0.0f, uz = 0.0f;
+            float fv = ld_vox_cs(F, p), ux = 0.0f, uy = 0.0f, uz = 0.0f;
             if (has_u) {
-                ux = __ldg(u0 + p);
-                uy = __ldg(u1 + p);
-                uz = __ldg(u2 + p);
+                ux = __ldcs(u0 + p);
+                uy = __ldcs(u1 + p);
+                uz = __ldcs(u2 + p);
             }
             for (int z = z0; z < z1; ++z, p += nxy) {
                 float fn = 0.0f, nx0 = 0.0f, nx1 = 0.0f, nx2 = 0.0f;
                 if (z + 1 < z1) {
-                    fn = ld_vox(F, p + nxy);
+                    fn = ld_vox_cs(F, p + nxy);
                     if (has_u) {
-                        nx0 = __ldg(u0 + p + nxy);
-                        nx1 = __ldg(u1 + p + nxy);
-                        nx2 = __ldg(u2 + p + nxy);
+                        nx0 = __ldcs(u0 + p + nxy);
+                        nx1 = __ldcs(u1 + p + nxy);
+                        nx2 = __ldcs(u2 + p + nxy);
                     }
                 }
                 float qx = ux, qy = uy, qz = uz;

@@ -42,6 +42,17 @@ __device__ __forceinline__ float ld_vox(const __nv_bfloat16 *p, I i) {
     return __bfloat162float(__ldg(p + i));
 }
 
+// streaming loads (read once: evict first, so that they do not push the
+// reused gather lines of M out of L1)
+template <typename I>
+__device__ __forceinline__ float ld_vox_cs(const float *p, I i) {
+    return __ldcs(p + i);
+}
+template <typename I>
+__device__ __forceinline__ float ld_vox_cs(const __nv_bfloat16 *p, I i) {
+    return __bfloat162float(__ldcs(p + i));
+}
+
 __device__ __forceinline__ void store_vox(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_vox(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 

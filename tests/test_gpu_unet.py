@@ -311,3 +311,43 @@ def test_unet_training_reduces_loss(capi):
     # loss roughly halves within 80 epochs
     assert losses[-1] < 0.6 * losses[0], [round(v, 4) for v in losses]
     assert np.mean(losses[-5:]) < 0.7 * np.mean(losses[:5]), [round(v, 4) for v in losses]
+
+
+def test_predict_init_scales_each_image_by_its_pooled_range(capi):
+    """A pair larger than the network input is pooled first; the network then
+    sees each image scaled by the range of the pooled grid (the scaling it was
+    trained with), not by the range of the full-resolution image, whose noise
+    tails pooling removes.  The packed input must equal the oracle's pack of
+    the same pair with the pooled ranges the oracle computes."""
+    from paper_2509_25044_gb300.unet import UNet
+    rng = np.random.default_rng(29)
+    n_in, factor = 32, 2
+    shape = (n_in * factor,) * 3
+    # a smooth ramp under heavy noise: pooling narrows the range markedly
+    ramp = np.linspace(0.0, 1.0, shape[2])[None, None, :]
+    F = (ramp + rng.normal(0.0, 0.3, shape)).astype(np.float32)
+    M = (1.0 - ramp + rng.normal(0.0, 0.2, shape)).astype(np.float32)
+    fr, mr = (float(F.min()), float(F.max())), (float(M.min()), float(M.max()))
+    net = UNet(n_in=n_in, seed=0, device=DEV)
+    net.predict_init(torch.from_numpy(F).to(DEV), torch.from_numpy(M).to(DEV), fr, mr)
+    torch.cuda.synchronize()
+    got = net.a["x0"].double().cpu().numpy().reshape((n_in,) * 3 + (16,))[..., :2]
+
+    pF = O.avgpool2(F[..., None])[..., 0]
+    pM = O.avgpool2(M[..., None])[..., 0]
+    pr = [(float(pF.min()), float(pF.max())), (float(pM.min()), float(pM.max()))]
+    assert pr[0][1] - pr[0][0] < 0.8 * (fr[1] - fr[0])  # the case exercises a narrower pooled range
+    ref = O.pack_pair(F, M, factor, pr[0], pr[1])
+    # The pooled range is read back from the first (full-range) pack, whose
+    # values are BF16: its ends carry 2^-9 |e| of the full width, e in units of
+    # it.  A packed value y moves by at most that over the pooled width.  Then
+    # the pack's own bar: one BF16 rounding, and an FP32 8-term block mean.
+    bars = []
+    for c, (full, pooled) in enumerate(zip((fr, mr), pr)):
+        fw, pw = full[1] - full[0], pooled[1] - pooled[0]
+        ends = max(abs(pooled[0] - full[0]), abs(pooled[1] - full[0])) / fw
+        bars.append(2.0 ** -9 * ends * fw / pw * (1 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref[..., c])
+                    + 16 * 2.0 ** -24 * (np.abs(ref[..., c]) + 2.0 * max(abs(full[0]), abs(full[1])) / pw))
+    for c in range(2):
+        err = np.abs(got[..., c] - ref[..., c])
+        assert (err <= bars[c]).all(), (c, float((err - bars[c]).max()))
