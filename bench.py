@@ -265,10 +265,11 @@ def alg_bytes(kind: str, bf16: bool):
 
 
 def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", mi_estimator="parzen"):
-    """K timed iterations (after W untimed ones) of workload `name` through
-    reg_iterate, with per-sweep CUDA events on every timed iteration; with
-    e2e, a second pass through the public call with the inputs copied from
-    pinned host memory every step and the result read back."""
+    """K timed iterations (after W untimed ones) of workload `name` in one
+    reg_run call (the library's multi-iteration entry point), with CUDA events
+    around each iteration's sweeps; with e2e, a second pass through
+    reg_iterate with the inputs copied from pinned host memory every step and
+    the result read back."""
     import torch
     from paper_2509_25044_gb300 import capi, synth
     cfg = synth.CONFIGS[name]
@@ -295,26 +296,33 @@ def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", 
     adam = capi.adam_desc(cfg["lr"], moment_dtype=mdt, grad_scale=float(N))
     lam = cfg["lam"]
     stream = torch.cuda.current_stream(dev)
-    step_no = [0]
+    cur, t = [0], [0]  # u[cur] holds the current iterate; t iterations done
+    hist = torch.zeros((max(K, W, 1), 2), dtype=torch.float64, device=dev)
+
+    def run(iters):
+        capi.reg_run(loss, F, M, u[cur[0]], u[1 - cur[0]], m, v, lam, adam, t[0], iters, ws, obj_hist=hist[:iters])
+        t[0] += iters
+        cur[0] = (cur[0] + iters) % 2
 
     def step(Fd=F, Md=M):
-        step_no[0] += 1
-        a, b = u[(step_no[0] - 1) % 2], u[step_no[0] % 2]
-        capi.reg_iterate(loss, Fd, Md, a, b, m, v, lam, adam, step_no[0], ws, obj=obj)
+        t[0] += 1
+        a, b = u[cur[0]], u[1 - cur[0]]
+        capi.reg_iterate(loss, Fd, Md, a, b, m, v, lam, adam, t[0], ws, obj=obj)
+        cur[0] = 1 - cur[0]
         return b
 
-    for _ in range(W):
-        step()
+    if W > 0:
+        run(W)
     torch.cuda.synchronize()
     if capi.reg_get_device_error() != 0:
         raise RuntimeError(f"device error during the warm-up of {name}")
 
-    # ---- timed region: K iterations, per-sweep events on every iteration ----
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    # ---- timed region: one reg_run call of K iterations, events around each
+    # iteration's sweeps ----
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for trip in evs:  # torch creates the CUDA event on its first record
-        for ev in trip:
-            ev.record(stream)
+    for ev in evs:  # torch creates the CUDA event on its first record
+        ev.record(stream)
     start.record(stream)
     end.record(stream)
     clocks = ClockSampler(dev.index or 0)
@@ -324,9 +332,8 @@ def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", 
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     start.record(stream)
-    for k in range(K):
-        capi.reg_set_timing_events(evs[k])
-        step()
+    capi.reg_set_timing_events(evs)
+    run(K)
     end.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -334,10 +341,10 @@ def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", 
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     ms_max = max_over_ranks(ms, world, dev)
-    s1 = [ev[0].elapsed_time(ev[1]) for ev in evs]
-    s2 = [ev[1].elapsed_time(ev[2]) for ev in evs]
+    s1 = [evs[3 * k].elapsed_time(evs[3 * k + 1]) for k in range(K)]
+    s2 = [evs[3 * k + 1].elapsed_time(evs[3 * k + 2]) for k in range(K)]
     err = capi.reg_get_device_error()
-    objv = obj.cpu().tolist()
+    objv = hist[K - 1].cpu().tolist()
     b1, b2 = alg_bytes(kind, bf16)
     peak, peak_kind = read_peaks()
     t1, t2 = statistics.median(s1), statistics.median(s2)
@@ -366,7 +373,8 @@ def measure(name, K, W, dev, rank, world, n=None, e2e=False, lncc_grad="exact", 
                            else "fallback 6.8 TB/s")
     out = {"name": name, "n": shape[0], "voxels": N, "steps": K, "warmup": W, "ms_per_step": it_ms,
            "value": world * N * K / (ms_max * 1e-3) / 1e9, "roofline": roof, "sweeps": sweeps, "clocks": clk,
-           "objective_last": objv, "device_error": err, "wall_s": wall, "bf16": bf16, "kind": kind}
+           "objective_last": objv, "device_error": err, "wall_s": wall, "bf16": bf16, "kind": kind,
+           "gpu_launches": 3 * K + (1 if kind == "lncc" else 0)}
 
     if e2e:
         # ---- end to end: pinned host images in, objective out every step; the
@@ -478,7 +486,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (the iteration streams "
                          f"{head['voxels'] * (68 if head['bf16'] else 100) / 1e9:.1f} GB > 129 MB)"},
         "roofline": head["roofline"], "sweeps": head["sweeps"], "e2e": head["e2e"],
-        "gpu_launches": 3 * K,  # MI: histogram, finalize, sweep 2; LNCC: warp, window statistics, sweep 2
+        # MI: histogram, finalize, step; LNCC: warp, window statistics, step,
+        # plus F's window statistics once per reg_run call
+        "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"], "objective_last": head["objective_last"], "device_error": head["device_error"],
         "wall_s": head["wall_s"],
     }

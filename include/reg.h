@@ -391,7 +391,10 @@ REG_API reg_status reg_mi_loss_grad_noalloc(const reg_loss_desc *loss, const voi
  * caller's CUDA events (cudaEvent_t passed as void*) on its stream:
  * events[0] before the first sweep, events[1] between the sweeps (after the
  * MI finalisation), events[2] after the second sweep; then the hook clears
- * itself.  n must be 3 (or 0 with events == NULL to clear).  Lets a caller
+ * itself.  With n = 3 * iters events the next reg_run call of `iters`
+ * iterations takes them instead: events[3k .. 3k + 2] for iteration k, at
+ * the same points.  A reg_run call of another length leaves the hook armed.  n must be a positive multiple
+ * of 3 (at most 3 * 2^20), or 0 with events == NULL to clear.  Lets a caller
  * time each sweep inside a long run without synchronising. */
 REG_API reg_status reg_set_timing_events(void *const *events, int n);
 

@@ -598,12 +598,15 @@ def reg_debug_wait_flag(flag, expect: int, timeout_ns: int):
 
 
 def reg_set_timing_events(events):
-    """Arm the timing hook with three torch.cuda.Event objects (or None to clear)."""
+    """Arm the timing hook with torch.cuda.Event objects (or None to clear):
+    three for the next reg_iterate, or three per iteration (flat, iteration
+    k's at 3k .. 3k + 2) for the next reg_run of that many iterations."""
     if events is None:
         _check(_lib().reg_set_timing_events(None, 0), "reg_set_timing_events")
         return
-    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
-    _check(_lib().reg_set_timing_events(arr, 3), "reg_set_timing_events")
+    events = list(events)
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(_lib().reg_set_timing_events(arr, len(events)), "reg_set_timing_events")
 
 
 def reg_mi_loss_grad_noalloc(loss: RegLossDesc, F, M, u, pad: int = REG_PAD_BORDER, sim=None, grad=None,

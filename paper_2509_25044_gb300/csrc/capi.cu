@@ -6,6 +6,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "checks.h"
 #include "kernels.h"
 
@@ -114,12 +117,15 @@ StepParams step_params(const reg_adam_desc *A, int t, float lam, const Dims &g) 
     return S;
 }
 
-thread_local cudaEvent_t t_events[3] = {nullptr, nullptr, nullptr};
+// the timing hook: 3 events for one reg_iterate call, or 3 per iteration
+// of a reg_run call; t_base selects the iteration's three
+thread_local std::vector<cudaEvent_t> t_events;
 thread_local bool t_events_armed = false;
+thread_local size_t t_base = 0;
 
 cudaError_t mark(int i, cudaStream_t s) {
-    if (!t_events_armed || !t_events[i]) return cudaSuccess;
-    return cudaEventRecord(t_events[i], s);
+    if (!t_events_armed || t_base + i >= t_events.size() || !t_events[t_base + i]) return cudaSuccess;
+    return cudaEventRecord(t_events[t_base + i], s);
 }
 
 reg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? REG_OK : REG_ERR_CUDA; }
@@ -375,8 +381,11 @@ reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int 
     REG_TRY(check_ptr(m));
     REG_TRY(check_ptr(v));
     if (overlap3(u_a, u_b, make_dims(d).n)) return REG_ERR_INVALID_ARG;
+    // the timing hook: this call takes it when it holds three events per
+    // iteration, else leaves it armed for the next reg_iterate call
     const bool armed = t_events_armed;
-    t_events_armed = false;  // the timing hook belongs to single reg_iterate calls
+    const bool per_iter = armed && t_events.size() == 3 * (size_t)iters;
+    t_events_armed = false;
     // LNCC: F is fixed for the whole run, so its window mean and variance are
     // formed once here and every iteration box-sums only (J, J^2, FJ)
     const bool fcached = loss->kind == REG_LOSS_LNCC;
@@ -388,11 +397,16 @@ reg_status reg_run(const reg_loss_desc *loss, const void *F, const void *M, int 
     }
     reg_status st = REG_OK;
     for (int k = 0; k < iters && st == REG_OK; ++k) {
+        if (per_iter) {
+            t_events_armed = true;
+            t_base = 3 * (size_t)k;
+        }
         float *a = (k % 2) ? u_b : u_a, *b = (k % 2) ? u_a : u_b;
         st = iterate_impl(loss, F, M, img_dt, a, b, m, v, d, pad, lambda, adam, t0 + k + 1, ws, ws_bytes,
                           obj_hist + 2 * (size_t)k, nullptr, stream, T ? &A : nullptr, fcached);
     }
-    t_events_armed = armed;
+    t_base = 0;
+    t_events_armed = per_iter ? false : armed;
     return st;
 }
 
@@ -666,8 +680,9 @@ reg_status reg_set_timing_events(void *const *events, int n) {
         t_events_armed = false;
         return REG_OK;
     }
-    if (n != 3 || !events) return REG_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i) t_events[i] = (cudaEvent_t)events[i];
+    if (n < 3 || n % 3 || n > 3 * (1 << 20) || !events) return REG_ERR_INVALID_ARG;
+    t_events.assign((cudaEvent_t *)events, (cudaEvent_t *)events + n);
+    t_base = 0;
     t_events_armed = true;
     return REG_OK;
 }

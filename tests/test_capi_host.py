@@ -334,11 +334,17 @@ def test_auxiliary_entry_points_validation(capi):
     assert na(ctypes.byref(mi), F, F, capi.REG_F32, F, dims(0, 4, 4), 0, F, None, None) == 2
     assert na(ctypes.byref(mi), None, F, capi.REG_F32, F, d, 0, F, None, None) == 1
     assert na(ctypes.byref(mi), F, F, capi.REG_F32, F, d, 0, F, U, None) == 4
-    # reg_set_timing_events(events, n): three events or (NULL, 0) to disarm
+    # reg_set_timing_events(events, n): a positive multiple of three events
+    # (three per reg_run iteration) or (NULL, 0) to disarm
     assert L.reg_set_timing_events(None, 0) == 0
     assert L.reg_set_timing_events(None, 3) == 1
     two = (ctypes.c_void_p * 2)(FAKE, FAKE)
     assert L.reg_set_timing_events(two, 2) == 1
+    four = (ctypes.c_void_p * 4)(FAKE, FAKE, FAKE, FAKE)
+    assert L.reg_set_timing_events(four, 4) == 1
+    six = (ctypes.c_void_p * 6)(*([FAKE] * 6))
+    assert L.reg_set_timing_events(six, 6) == 0  # armed (no call records them) ...
+    assert L.reg_set_timing_events(None, 0) == 0  # ... and cleared
 
 
 def _c_params(txt):

@@ -454,6 +454,48 @@ def test_run_matches_repeated_iterate(capi, kind, iters):
     assert capi.reg_get_device_error() == 0
 
 
+@pytest.mark.parametrize("shape,img,bf16_moments,hard", [
+    ((20, 24, 64), torch.bfloat16, True, False),   # the TMA step with BF16 images and moments
+    ((7, 9, 136), torch.bfloat16, True, False),    # ragged rows and tiles
+    ((20, 24, 64), torch.float32, False, False),   # the TMA step in FP32
+    ((20, 24, 64), torch.bfloat16, True, True),    # hard-binned histogram
+    ((256, 256, 256), torch.bfloat16, True, False),  # chunks of 128 planes
+])
+def test_run_matches_repeated_iterate_mi_forms(capi, shape, img, bf16_moments, hard):
+    """reg_run gives the objectives, iterates and moments of as many
+    reg_iterate calls bit for bit in every MI form the bench times: BF16 and
+    FP32 images and moments on the TMA step, the hard-binned estimator, and a
+    volume whose CTAs take long chunks (the histogram is exact fixed point,
+    so nothing depends on the order of its additions)."""
+    iters = 3
+    gen = torch.Generator(device=DEV).manual_seed(23)
+    F = torch.rand(shape, generator=gen, device=DEV).to(img)
+    M = torch.rand(shape, generator=gen, device=DEV).to(img)
+    u0 = 0.4 * torch.randn((3,) + shape, generator=gen, device=DEV)
+    loss = capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32, hard=hard)
+    mt = torch.bfloat16 if bf16_moments else torch.float32
+    adam = capi.adam_desc(0.05, moment_dtype=capi.REG_BF16 if bf16_moments else capi.REG_F32,
+                          grad_scale=float(F.numel()))
+    ws = capi.workspace(loss, F)
+    outs = []
+    for native in (False, True):
+        u = [u0.clone(), torch.zeros_like(u0)]
+        m = torch.zeros((3,) + shape, dtype=mt, device=DEV)
+        v = torch.zeros((3,) + shape, dtype=mt, device=DEV)
+        hist = torch.zeros((iters, 2), dtype=torch.float64, device=DEV)
+        if native:
+            capi.reg_run(loss, F, M, u[0], u[1], m, v, 0.5, adam, 0, iters, ws, obj_hist=hist)
+        else:
+            for k in range(iters):
+                capi.reg_iterate(loss, F, M, u[k % 2], u[(k + 1) % 2], m, v, 0.5, adam, k + 1, ws, obj=hist[k])
+        torch.cuda.synchronize()
+        outs.append((u[iters % 2], m, v, hist))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    assert not torch.equal(outs[0][0], u0)  # the iterations moved u
+    assert capi.reg_get_device_error() == 0
+
+
 # ---------------------------------------------------------------------------
 # degenerate inputs the method has: constant images (zero window variances,
 # a single-bin histogram) and one-voxel volumes
