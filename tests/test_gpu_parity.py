@@ -412,7 +412,7 @@ def test_downsample2_rejects_odd_and_aliasing(capi):
     assert st != 0
 
 
-@pytest.mark.parametrize("kind", ["lncc", "mi"])
+@pytest.mark.parametrize("kind", ["lncc", "lncc_ants", "mi"])
 @pytest.mark.parametrize("iters", [1, 4, 5])
 def test_run_matches_repeated_iterate(capi, kind, iters):
     """reg_run (all iterations in one native call) gives the iterates and
@@ -424,7 +424,8 @@ def test_run_matches_repeated_iterate(capi, kind, iters):
     gen = torch.Generator().manual_seed(11)
     F = torch.rand(shape, generator=gen).to(DEV)
     M = torch.rand(shape, generator=gen).to(DEV)
-    loss = capi.lncc_desc(5, 1e-9) if kind == "lncc" else capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32)
+    loss = (capi.lncc_desc(5, 1e-9, ants=kind == "lncc_ants") if kind.startswith("lncc")
+            else capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32))
     adam = capi.adam_desc(0.05)
     ws = capi.workspace(loss, F)
     outs = []
