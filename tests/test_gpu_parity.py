@@ -455,6 +455,37 @@ def test_run_matches_repeated_iterate(capi, kind, iters):
     assert capi.reg_get_device_error() == 0
 
 
+@pytest.mark.parametrize("shape,img,bins,hard,pad", [
+    ((37, 45, 72), torch.bfloat16, 32, False, 0),   # ragged 32 x 32 columns in x and y
+    ((37, 45, 72), torch.float32, 32, True, 1),     # hard-binned, zero padding
+    ((9, 7, 8), torch.float32, 16, False, 1),       # one column, 16 copies
+    ((400, 310, 256), torch.bfloat16, 32, False, 0),  # copies flushed every 256 planes, many times per CTA
+    ((400, 310, 256), torch.bfloat16, 64, False, 0),  # 8 copies
+])
+def test_identity_composite_histogram_equals_plain_histogram(capi, shape, img, bins, hard, pad):
+    """The composite form with the identity transform (phi = I p + 0 + 1 u =
+    p + u exactly, 64-bit offsets) forms the same fixed-point joint histogram,
+    bit for bit, as the plain form, over ragged tiles, both estimators and
+    pads, and volumes whose persistent CTAs flush their 32-bit copies many
+    times."""
+    gen = torch.Generator(device=DEV).manual_seed(bins + shape[0])
+    F = torch.rand(shape, generator=gen, device=DEV).to(img)
+    M = torch.rand(shape, generator=gen, device=DEV).to(img)
+    u = 1.5 * torch.randn((3,) + shape, generator=gen, device=DEV)
+    loss = capi.mi_desc((0.0, 1.0), (0.0, 1.0), bins, hard=hard)
+    ws_plain, ws_comp = capi.workspace(loss, F), capi.workspace(loss, F)
+    s_plain = capi.reg_loss(loss, F, M, u, ws_plain, pad=pad)
+    s_comp, _, _ = capi.reg_loss_grad_composite(loss, F, M, capi.affine_desc(), u=u, ws=ws_comp, pad=pad,
+                                                need_u=False, need_affine=False)
+    torch.cuda.synchronize()
+    n = bins * bins * 8  # the workspace starts with the u64 joint histogram
+    h_plain, h_comp = ws_plain[:n].view(torch.int64), ws_comp[:n].view(torch.int64)
+    assert int(h_plain.sum()) > 0
+    assert torch.equal(h_plain, h_comp)
+    assert float(s_plain[0]) == float(s_comp[0])
+    assert capi.reg_get_device_error() == 0
+
+
 @pytest.mark.parametrize("shape,img,bf16_moments,hard", [
     ((20, 24, 64), torch.bfloat16, True, False),   # the TMA step with BF16 images and moments
     ((7, 9, 136), torch.bfloat16, True, False),    # ragged rows and tiles
