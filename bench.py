@@ -499,7 +499,7 @@ def run_ours(args):
         # recipe at 512^3, whose sweeps sit nearer the bandwidth roofline
         out["time_to_solution"] = {"lncc_c2": time_to_solution_record("c2", args.ttl_n),
                                    "mi_c1_recipe": time_to_solution_record("c1", args.ttl_n or 512,
-                                                                           lam_scale=40.0)}
+                                                                           lam_scale=100.0)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.config)
     if not args.no_unet:

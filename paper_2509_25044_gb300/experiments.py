@@ -441,15 +441,21 @@ def main():
     li.add_argument("--eval-lam", type=float, default=2.0, help="regulariser weight of the evaluation runs")
     li.add_argument("--train-noise", type=float, default=0.02,
                     help="noise of the training pairs (0.0025: a 512^3 pair as the network sees it, pooled 4^3)")
+    li.add_argument("--train-kind", default="mono", choices=["mono", "multi"],
+                    help="mono-modal blob pairs (LNCC workloads) or two-modality phantoms (MI workloads)")
+    li.add_argument("--train-smooth", type=float, default=1.0, help="smoothing of the two-modality phantoms")
+    li.add_argument("--eval-moments", default="f32", choices=["f32", "bf16"], help="Adam moments of the evaluation")
     args = ap.parse_args()
     if args.cmd == "learned-init":
-        tr, net = train_init(args.pairs, args.epochs, lr=args.lr, out_path=args.save, noise=args.train_noise)
+        tr, net = train_init(args.pairs, args.epochs, lr=args.lr, out_path=args.save, noise=args.train_noise,
+                             kind=args.train_kind, smooth=args.train_smooth)
         print(json.dumps(tr), flush=True)
         if args.eval_pairs > 0:
             print(json.dumps(eval_init_pairs(net, n_pairs=args.eval_pairs, lam=args.eval_lam)), flush=True)
         if args.eval_config != "none":
-            print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=args.eval_lam / 0.1)),
-                  flush=True)
+            lam_scale = args.eval_lam / synth.CONFIGS[args.eval_config]["lam"]
+            print(json.dumps(eval_init(net, args.eval_config, n=args.eval_n, lam_scale=lam_scale,
+                                       moments=args.eval_moments)), flush=True)
         return
     if args.cmd == "multiscale":
         its = tuple(int(x) for x in args.ms_iters.split(","))
@@ -476,13 +482,16 @@ def main():
 # learned initialiser: training and evaluation
 # ---------------------------------------------------------------------------
 def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 2e-4, seed0: int = 10_000,
-               out_path: str | None = None, log_every: int = 200, noise: float = 0.02) -> dict:
+               out_path: str | None = None, log_every: int = 200, noise: float = 0.02, kind: str = "mono",
+               smooth: float = 1.0) -> dict:
     """Train the U-Net on n_pairs seeded pairs made with the library's warp
-    (targets: the known fields pooled to n/2), with acquisition noise `noise`
-    (training_pair).  Pairs are generated once and kept on the device (packed
-    inputs + targets)."""
+    (targets: the known fields pooled to n/2), with acquisition noise `noise`:
+    mono-modal blob pairs (training_pair) or, kind="multi", the MI workloads'
+    two-modality phantoms smoothed at `smooth` (multimodal_training_pair).
+    Pairs are generated once and kept on the device (packed inputs +
+    targets)."""
     import time
-    from .unet import UNet, training_pair
+    from .unet import UNet, multimodal_training_pair, training_pair
     dev = torch.device("cuda", torch.cuda.current_device())
     capi.load()
     net = UNet(n_in=n, seed=0, device=dev)
@@ -490,7 +499,8 @@ def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 2
     t0 = time.perf_counter()
     xs, ts = [], []
     for i in range(n_pairs):
-        p = training_pair(n, seed0 + i, dev, noise=noise)
+        p = (multimodal_training_pair(n, seed0 + i, dev, noise=noise, smooth=smooth) if kind == "multi"
+             else training_pair(n, seed0 + i, dev, noise=noise))
         # images kept as BF16 (the network sees them in BF16 anyway); packed per step
         xs.append((p["F"].to(torch.bfloat16), p["M"].to(torch.bfloat16),
                    (float(p["F"].min()), float(p["F"].max())), (float(p["M"].min()), float(p["M"].max()))))
@@ -519,7 +529,8 @@ def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 2
     train_ms = ev0.elapsed_time(ev1)
     # baseline: predicting zero
     zero = float(np.mean([float((t ** 2).mean().item()) for t in ts[:200]]))
-    out = {"experiment": "train_init", "n_pairs": n_pairs, "epochs": epochs, "n": n, "lr": lr,
+    out = {"experiment": "train_init", "kind": kind, "n_pairs": n_pairs, "epochs": epochs, "n": n, "lr": lr,
+           "noise": noise,
            "pair_generation_s": gen_s, "train_ms": train_ms, "ms_per_pair_step": train_ms / (epochs * n_pairs),
            "loss_per_epoch": hist, "zero_prediction_loss": zero, "device_error": capi.reg_get_device_error()}
     if out_path:
@@ -529,21 +540,26 @@ def train_init(n_pairs: int = 2000, epochs: int = 4, n: int = 128, lr: float = 2
 
 
 def eval_init(net, config: str = "c2", iters: int | None = None, lam_scale: float = 10.0, n: int | None = None,
-              rel_tol: float = 0.01) -> dict:
+              rel_tol: float = 0.01, moments: str = "f32") -> dict:
     """Registration of a held-out pair from zero and from the network's
     initial field: iterations (and time) for the learned-init run to reach
     the zero-init run's final objective within 1 % of the zero-init run's
-    total decrease; fold checks of both."""
+    total decrease; fold checks of both.  The zero-init run is released
+    before the learned-init one starts (gigavoxel pairs)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     d = synth.make(config, device=dev, n=n)
     c = d["config"]
     iters = iters or c["iters"]
     F, M = d["F"].contiguous(), d["M"].contiguous()
-    cfg = _cfg(c, d, "f32", lam_scale)
+    cfg = _cfg(c, d, moments, lam_scale)
+    err = lambda u: float(((u + d["u_true"]).norm() / d["u_true"].norm()).item())
     r0 = Registration(F, M, cfg)
     _warm(r0.F, r0.M, r0.cfg, affine=r0.affine)
     res0 = r0.run(iters)
     fin0 = r0.objective()
+    fold0, err0 = r0.fold_check(), err(r0.current)
+    del r0
+    torch.cuda.empty_cache()
     L0, Lstar = float(res0.objective[0]), fin0["objective"]
     tol = rel_tol * max(L0 - Lstar, 0.0)
     ranges = (float(F.min()), float(F.max())), (float(M.min()), float(M.max()))
@@ -562,10 +578,10 @@ def eval_init(net, config: str = "c2", iters: int | None = None, lam_scale: floa
     tr1 = np.append(res1.objective[1:], fin1["objective"])
     k0 = _first_within(tr0, Lstar, tol)
     k1 = _first_within(tr1, Lstar, tol)
-    err = lambda u: float(((u + d["u_true"]).norm() / d["u_true"].norm()).item())
     out = {"experiment": "eval_init", "config": config, "n": F.shape[0], "iters": iters, "lam": cfg.lam,
+           "moments": moments,
            "zero_init": {"objective_start": L0, "objective_final": Lstar, "iters_to_target": None if k0 is None else k0 + 1,
-                         "ms_per_iter": res0.ms_per_iter, "fold": r0.fold_check(), "rel_err_vs_inverse_true": err(r0.current)},
+                         "ms_per_iter": res0.ms_per_iter, "fold": fold0, "rel_err_vs_inverse_true": err0},
            "learned_init": {"objective_start": float(res1.objective[0]), "objective_final": fin1["objective"],
                             "iters_to_target": None if k1 is None else k1 + 1, "ms_per_iter": res1.ms_per_iter,
                             "init_ms": init_ms, "fold": r1.fold_check(), "rel_err_vs_inverse_true": err(r1.current),

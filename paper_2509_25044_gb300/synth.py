@@ -204,6 +204,24 @@ def mono_pair(n: int, seed: int, blob_sigma=(2.0, 8.0), field_sigma=4.0, max_dis
     return dict(F=F, M=M, u_true=u_true, seed=seed, rng="philox" if gpu_rng else "pcg64")
 
 
+def label_images(shape, n_labels: int, noise_std: float, smooth_sigma: float, rng=None, gen=None, device="cpu"):
+    """Two modalities of one phantom: an n_labels ellipsoid map painted through
+    a random intensity table (U[0,1] per label) and through a second random
+    table that is not monotone in the first, each with N(0, noise_std^2) and
+    Gaussian smoothing at smooth_sigma.  Returns (first, second), aligned."""
+    lab = ellipsoid_labels(shape, n_labels, rng=rng, gen=gen, device=device)
+    tF = _uniform(rng, gen, 0.0, 1.0, n_labels + 1, device)
+    while True:
+        tM = _uniform(rng, gen, 0.0, 1.0, n_labels + 1, device)
+        order = np.argsort(tF)
+        d = np.diff(tM[order])
+        if (d > 0).any() and (d < 0).any():
+            break
+    F = _paint(lab, tF, noise_std, smooth_sigma, rng=rng, gen=gen)
+    M = _paint(lab, tM, noise_std, smooth_sigma, rng=rng, gen=gen)
+    return F, M
+
+
 def multimodal_pair(n: int, seed: int, field_sigma=6.0, max_disp=5.0, n_labels=6, device="cpu",
                     gpu_rng: bool = False):
     """Multi-modal phantom pair: a 6-label ellipsoid map; F paints the labels
@@ -216,17 +234,7 @@ def multimodal_pair(n: int, seed: int, field_sigma=6.0, max_disp=5.0, n_labels=6
     if gpu_rng:
         gen = torch.Generator(device=device)
         gen.manual_seed(seed)
-    lab = ellipsoid_labels(shape, n_labels, rng=rng, gen=gen, device=device)
-    tF = _uniform(rng, gen, 0.0, 1.0, n_labels + 1, device)
-    while True:
-        tM = _uniform(rng, gen, 0.0, 1.0, n_labels + 1, device)
-        order = np.argsort(tF)
-        d = np.diff(tM[order])
-        if (d > 0).any() and (d < 0).any():
-            break
-    F = _paint(lab, tF, 0.03, 1.0, rng=rng, gen=gen)
-    M0 = _paint(lab, tM, 0.03, 1.0, rng=rng, gen=gen)
-    del lab
+    F, M0 = label_images(shape, n_labels, 0.03, 1.0, rng=rng, gen=gen, device=device)
     u_true = smooth_field(shape, field_sigma, max_disp, rng=rng, gen=gen, device=device)
     M = _sample_trilinear(M0, u_true)
     del M0

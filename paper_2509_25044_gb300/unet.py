@@ -284,6 +284,26 @@ class UNet:
         return out
 
 
+def multimodal_training_pair(n: int, seed: int, device, noise: float = 0.03, smooth: float = 1.0) -> dict:
+    """One multi-modal training pair at n^3 (the MI workloads' phantoms): a
+    6-label ellipsoid map painted twice, through two intensity tables that
+    are not monotone in each other, each with N(0, noise^2) and Gaussian
+    smoothing at `smooth` (synth.label_images); a random smooth field v_true
+    (sigma ~ U[4,12], max |v| ~ U(0,10]); F = F0 o (id + v_true) with the
+    library's warp and M the second painting, aligned with F0, so that
+    registering M onto F recovers v_true itself.  Random numbers come from
+    torch's Philox generator on the device, seeded with `seed`."""
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    F0, M = synth.label_images((n, n, n), 6, noise, smooth, gen=gen, device=device)
+    u01 = torch.rand(2, generator=gen, device=device, dtype=torch.float64).cpu().numpy()
+    sigma = 4.0 + 8.0 * float(u01[0])
+    mx = 10.0 * (1.0 - float(u01[1]))  # in (0, 10]
+    v = synth.smooth_field((n, n, n), sigma, mx, gen=gen, device=device)
+    F = capi.reg_warp(F0.contiguous(), v)
+    return dict(F=F, M=M.contiguous(), v=v)
+
+
 def training_pair(n: int, seed: int, device, noise: float = 0.02) -> dict:
     """One training pair at n^3 made with the library's own warp: a blob
     image B (sigma scaled to the grid) with N(0, noise^2) noise as M, a random
