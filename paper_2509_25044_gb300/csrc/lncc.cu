@@ -193,7 +193,8 @@ __host__ __device__ constexpr int lncc_stats_k() {
 }
 
 // (the three- and two-sum modes fit 4 CTAs per SM in 64 registers)
-template <typename T, bool COEF, typename I, int NY, int MODE = LNCC_FULL>
+// (R as in lncc_sweep2_kernel: the window radius compiled in when >= 0)
+template <typename T, bool COEF, typename I, int NY, int MODE = LNCC_FULL, int R = -1>
 __global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
     lncc_stats_kernel(const T *__restrict__ F, const float *__restrict__ J, Dims g, LnccParams P, int zc,
                       float *__restrict__ coef, float *__restrict__ fstat, double *__restrict__ partials,
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
     extern __shared__ float smem[];
     __shared__ double red[32];
     __shared__ float shift[2];
-    const int r = P.r;
+    const int r = R >= 0 ? R : P.r;
     const LnccSmem L(r, K);
     float *st = smem;
     float *hx = st + L.stage_words();
@@ -352,7 +353,9 @@ __global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
 // AFF: the composite transform phi = A p + t + S u.  Without STEP (u and
 // grad_out may be NULL): grad_out = S gX and r_out[12] = dC/dA, dC/dt.  With
 // STEP: dC/du = S gX enters the diffusion + Adam update of u as usual.
-template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false>
+// R >= 0: the window radius fixed at compile time (the index arithmetic of
+// the staging and the x pass folds to constants); R < 0: P.r.
+template <typename T, typename MT, bool STEP, int PAD, typename I, bool AFF = false, int R = -1>
 __global__ void __launch_bounds__(TILE_THREADS)
     lncc_sweep2_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g,
                        LnccParams P, int zc, const float *__restrict__ coef, float *__restrict__ grad_out,
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const AffineT A = AFF ? resolve_affine(Ain) : Ain;
     extern __shared__ float smem[];
     __shared__ double red[32];
-    const int r = P.r;
+    const int r = R >= 0 ? R : P.r;
     const LnccSmem L(r, 3);
     float *st = smem;
     float *hx = st + L.stage_words();
@@ -716,7 +719,12 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
                                                        counter, sim_out, err);
                 };
                 if (fstat) {  // F's window statistics formed beforehand (launch_lncc_fstats)
-                    if (coef)
+                    // the workloads' windows (7^3, 9^3) with their radius compiled in
+                    if (coef && P.r == 4 && NY == 2)
+                        run(lncc_stats_kernel<T, true, I, 2, LNCC_FCACHED, 4>, lncc_stats_k<LNCC_FCACHED>());
+                    else if (coef && P.r == 3 && NY == 2)
+                        run(lncc_stats_kernel<T, true, I, 2, LNCC_FCACHED, 3>, lncc_stats_k<LNCC_FCACHED>());
+                    else if (coef)
                         run(lncc_stats_kernel<T, true, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
                     else
                         run(lncc_stats_kernel<T, false, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
@@ -857,11 +865,20 @@ cudaError_t launch_lncc_sweep2(const void *F, const void *M, int dt, const float
                 }
                 with_type(mdt, [&](auto mp) {
                     using MT = elem_t<decltype(mp)>;
-                    e = prepare_march(lncc_sweep2_kernel<T, MT, true, PD, I>, smem, g, P.r, G, grid);
-                    if (e == cudaSuccess)
-                        lncc_sweep2_kernel<T, MT, true, PD, I><<<grid, block, smem, s>>>(
-                            (const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out, u_out, (MT *)m,
-                            (MT *)v, S, partials, counter, r_out, err, A);
+                    auto go = [&](auto kern) {
+                        e = prepare_march(kern, smem, g, P.r, G, grid);
+                        if (e == cudaSuccess)
+                            kern<<<grid, block, smem, s>>>((const T *)F, (const T *)M, u, g, P, G.zc, coef, grad_out,
+                                                           u_out, (MT *)m, (MT *)v, S, partials, counter, r_out, err,
+                                                           A);
+                    };
+                    // the windows of the workloads (7^3, 9^3) with their radius compiled in
+                    if (P.r == 4)
+                        go(lncc_sweep2_kernel<T, MT, true, PD, I, false, 4>);
+                    else if (P.r == 3)
+                        go(lncc_sweep2_kernel<T, MT, true, PD, I, false, 3>);
+                    else
+                        go(lncc_sweep2_kernel<T, MT, true, PD, I>);
                 });
             });
         });
