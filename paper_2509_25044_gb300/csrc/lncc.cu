@@ -728,6 +728,10 @@ cudaError_t launch_lncc_stats(const void *F, const float *J, int dt, const Dims 
                         run(lncc_stats_kernel<T, true, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
                     else
                         run(lncc_stats_kernel<T, false, I, NY, LNCC_FCACHED>, lncc_stats_k<LNCC_FCACHED>());
+                } else if (coef && P.r == 4 && NY == 2) {
+                    run(lncc_stats_kernel<T, true, I, 2, LNCC_FULL, 4>, lncc_stats_k<LNCC_FULL>());
+                } else if (coef && P.r == 3 && NY == 2) {
+                    run(lncc_stats_kernel<T, true, I, 2, LNCC_FULL, 3>, lncc_stats_k<LNCC_FULL>());
                 } else if (coef) {
                     run(lncc_stats_kernel<T, true, I, NY>, lncc_stats_k<LNCC_FULL>());
                 } else {

@@ -41,13 +41,15 @@ __host__ __device__ constexpr int hist_batch_planes(int B) {
 // with F and u of the next plane requested before the current plane is
 // computed, and adds the 16 fixed-point products of its voxel's B-spline
 // weights to its copy (hist_add_parzen).
-template <typename T, int PAD, typename I, bool HARD, bool AFF>
+// BT > 0: the bin count compiled in (the bin and copy address arithmetic folds
+// to constants); BT = 0: P.bins.
+template <typename T, int PAD, typename I, bool HARD, bool AFF, int BT = 0>
 __global__ void __launch_bounds__(HIST_THREADS, 1)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
                    int tiles_x, long long total, AffineT Ain, unsigned long long *__restrict__ hist) {
     extern __shared__ unsigned sh[];
     const AffineT A = AFF ? resolve_affine(Ain) : Ain;
-    const int B = P.bins, BB = B * B;
+    const int B = BT > 0 ? BT : P.bins, BB = B * B;
     const int copies = hist_copies(B), pitch = BB + 1;
     const int tid = threadIdx.y * HIST_TX + threadIdx.x;
     for (int i = tid; i < copies * pitch; i += HIST_THREADS) sh[i] = 0u;
@@ -345,7 +347,11 @@ cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u,
             }
             with_index(g, [&](auto ip) {
                 using I = elem_t<decltype(ip)>;
-                if (P.hard)
+                // the workloads' 32 bins compiled in
+                if (P.bins == 32)
+                    P.hard ? run(mi_hist_kernel<T, PD, I, true, false, 32>)
+                           : run(mi_hist_kernel<T, PD, I, false, false, 32>);
+                else if (P.hard)
                     run(mi_hist_kernel<T, PD, I, true, false>);
                 else
                     run(mi_hist_kernel<T, PD, I, false, false>);

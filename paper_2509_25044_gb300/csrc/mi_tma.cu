@@ -74,7 +74,9 @@ __device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
 
 }  // namespace
 
-template <typename T, typename MT, bool STEP, int PAD, typename I>
+// BT > 0: the bin count compiled in (table and ring offsets fold to
+// constants); BT = 0: P.bins.
+template <typename T, typename MT, bool STEP, int PAD, typename I, int BT = 0>
 __global__ void __launch_bounds__(SW_THREADS, 2)
     mi_sweep2_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
                          const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap vmap,
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2)
     __shared__ double red[32];
     __shared__ volatile int abort_flag;
     constexpr int FB = (int)sizeof(T), MB = STEP ? (int)sizeof(MT) : 0;
-    const int B = P.bins, BB = B * B;
+    const int B = BT > 0 ? BT : P.bins, BB = B * B;
     const SwLayout L(B, FB, MB);
     float4 *G4 = reinterpret_cast<float4 *>(smem);
     uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -394,10 +396,15 @@ cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const flo
                                                         grad_out, u_out, (MT *)m, (MT *)v, S, partials, counter,
                                                         r_out, err);
                 };
+                // the step with the workloads' 32 bins compiled in
                 if (!step)
                     go(mi_sweep2_tma_kernel<T, float, false, PD, I>, (float *)nullptr, false);
+                else if (mdt == REG_BF16 && P.bins == 32)
+                    go(mi_sweep2_tma_kernel<T, __nv_bfloat16, true, PD, I, 32>, (__nv_bfloat16 *)nullptr, true);
                 else if (mdt == REG_BF16)
                     go(mi_sweep2_tma_kernel<T, __nv_bfloat16, true, PD, I>, (__nv_bfloat16 *)nullptr, true);
+                else if (P.bins == 32)
+                    go(mi_sweep2_tma_kernel<T, float, true, PD, I, 32>, (float *)nullptr, true);
                 else
                     go(mi_sweep2_tma_kernel<T, float, true, PD, I>, (float *)nullptr, true);
             });
