@@ -386,12 +386,27 @@ __global__ void __launch_bounds__(TILE_THREADS)
     float cur[3] = {0.f, 0.f, 0.f}, prv[3] = {0.f, 0.f, 0.f}, nxt[3] = {0.f, 0.f, 0.f};
     const bool has_u = !AFF || u != nullptr;  // the composite form may omit u
     AffineAcc aacc;
-    if (active && has_u) {
+    // the output stage's own operands, one output plane ahead (they land
+    // while the plane's box sums run): F, m, v at the next output voxel and
+    // u two planes ahead (u at z + 1 is the diffusion stencil's)
+    float fq = 0.0f, mq[3] = {0.f, 0.f, 0.f}, vq[3] = {0.f, 0.f, 0.f}, nx2[3] = {0.f, 0.f, 0.f};
+    if (active) {
         const I p = (I)z0 * nxy + col;
+        fq = ld_vox(F, p);
+        if (has_u) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cur[c] = __ldg(uc[c] + p);
-            if (STEP && z0 > 0) prv[c] = __ldg(uc[c] + p - nxy);
+            for (int c = 0; c < 3; ++c) {
+                cur[c] = __ldg(uc[c] + p);
+                if (STEP && z0 > 0) prv[c] = __ldg(uc[c] + p - nxy);
+                if (z0 + 1 < g.nz) nxt[c] = __ldg(uc[c] + p + nxy);
+            }
+        }
+        if (STEP) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                mq[c] = ld_moment(mc[c], p);
+                vq[c] = ld_moment(vc[c], p);
+            }
         }
     }
     __syncthreads();
@@ -432,14 +447,30 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const int zo = q - r;
         if (active && zo >= z0 && zo < z1) {
             const I p = (I)zo * nxy + col;
-            if (zo + 1 < g.nz && has_u) {
+            const float fv = fq;
+            float m0[3], v0[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) nxt[c] = __ldg(uc[c] + p + nxy);
+            for (int c = 0; c < 3; ++c) {
+                m0[c] = mq[c];
+                v0[c] = vq[c];
+            }
+            if (zo + 1 < z1) {
+                fq = ld_vox(F, p + nxy);
+                if (STEP) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        mq[c] = ld_moment(mc[c], p + nxy);
+                        vq[c] = ld_moment(vc[c], p + nxy);
+                    }
+                }
+                if (zo + 2 < g.nz && has_u) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) nx2[c] = __ldg(uc[c] + p + 2 * nxy);
+                }
             }
             float sx, sy, sz, qx = cur[0], qy = cur[1], qz = cur[2];
             if (AFF) composite_disp(A, x, y, zo, qx, qy, qz);
             const float jv = sample_grad<T, PAD, I>(M, g, x, y, zo, qx, qy, qz, sx, sy, sz);
-            const float fv = ld_vox(F, p);
             const float gj = fmaf(fv, Sa[2], fmaf(2.0f * jv, Sa[1], Sa[0]));
             const float gs[3] = {gj * sx, gj * sy, gj * sz};
             if (STEP) {
@@ -449,8 +480,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 for (int c = 0; c < 3; ++c) {
                     const float gt = fmaf(S.lam * S.two_over_n, gR[c], AFF ? A.s[c] * gs[c] : gs[c]);
                     if (grad_out) (grad_out + c * g.n)[p] = gt;
-                    (u_out + c * g.n)[p] =
-                        adam_fast(cur[c], gt, ld_moment(mc[c], p), ld_moment(vc[c], p), mc[c], vc[c], p, S);
+                    (u_out + c * g.n)[p] = adam_fast(cur[c], gt, m0[c], v0[c], mc[c], vc[c], p, S);
                 }
             } else if (AFF) {
                 aacc.add(gs[0], gs[1], gs[2], zo);
@@ -466,6 +496,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             for (int c = 0; c < 3; ++c) {
                 prv[c] = cur[c];
                 cur[c] = nxt[c];
+                nxt[c] = nx2[c];
             }
         }
     }
