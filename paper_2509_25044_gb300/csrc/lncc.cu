@@ -254,6 +254,14 @@ __global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
     for (int k = 0; k < K; ++k) S[k] = 0.0f;
     float nsum = 0.0f;
     int slot = 0;
+    // F's cached window mean and variance at the next output voxel, loaded
+    // one output plane ahead
+    float fm_q = 0.0f, fv_q = 0.0f;
+    if (MODE == LNCC_FCACHED && active) {
+        const I p0 = (I)z0 * nxy + (I)y * g.nx + x;
+        fm_q = __ldg(fstat + p0);
+        fv_q = __ldg(fstat + g.n + p0);
+    }
     for (int q = z0 - r; q < z1 + r; ++q) {
 #pragma unroll
         for (int j = 0; j < NY; ++j)
@@ -309,8 +317,12 @@ __global__ void __launch_bounds__(TILE_THREADS, MODE == LNCC_FULL ? 3 : 4)
                 Bv = fmaxf(fmaf(S[2], ic, -mF * mF), 0.0f);
                 Cv = fmaxf(fmaf(S[3], ic, -mJ * mJ), 0.0f);
             } else {
-                mF = __ldg(fstat + p) - shF;
-                Bv = __ldg(fstat + g.n + p);
+                mF = fm_q - shF;
+                Bv = fv_q;
+                if (zo + 1 < z1) {
+                    fm_q = __ldg(fstat + p + nxy);
+                    fv_q = __ldg(fstat + g.n + p + nxy);
+                }
                 mJ = S[0] * ic;
                 A = fmaf(S[2], ic, -mF * mJ);
                 Cv = fmaxf(fmaf(S[1], ic, -mJ * mJ), 0.0f);
