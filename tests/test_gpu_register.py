@@ -184,3 +184,40 @@ def test_affine_stage_on_the_device_matches_the_host_optimiser():
     for lh, ld in zip(h["levels"], d["levels"]):
         np.testing.assert_allclose(ld["objective"], lh["objective"], rtol=1e-6, atol=1e-9)
     assert times[True] < times[False]
+
+
+def test_run_records_three_events_per_iteration():
+    """The timing hook armed with three events per iteration is taken by a
+    reg_run call of that many iterations: each iteration's events are recorded
+    in order (first sweep, second sweep), the spans add up to no more than the
+    whole call, and the hook is spent afterwards (a second call records
+    nothing new)."""
+    from paper_2509_25044_gb300 import capi
+    capi.load()
+    n, iters = 48, 4
+    gen = torch.Generator(device=DEV).manual_seed(2)
+    F = torch.rand((n, n, n), generator=gen, device=DEV)
+    M = torch.rand((n, n, n), generator=gen, device=DEV)
+    loss = capi.mi_desc((0.0, 1.0), (0.0, 1.0), 32)
+    adam = capi.adam_desc(0.05, grad_scale=float(F.numel()))
+    ws = capi.workspace(loss, F)
+    u = [torch.zeros((3, n, n, n), device=DEV) for _ in range(2)]
+    m, v = torch.zeros_like(u[0]), torch.zeros_like(u[0])
+    s = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * iters)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(s)
+    capi.reg_set_timing_events(evs)
+    capi.reg_run(loss, F, M, u[0], u[1], m, v, 0.5, adam, 0, iters, ws)
+    end.record(s)
+    torch.cuda.synchronize()
+    spans = [evs[k].elapsed_time(evs[k + 1]) for k in range(3 * iters - 1)]
+    assert all(t >= 0.0 for t in spans)  # recorded, in stream order
+    assert sum(spans) <= start.elapsed_time(end) + 1e-3
+    assert evs[0].elapsed_time(evs[-1]) > 0.0
+    # spent: a further call does not re-record the events
+    last = evs[-1].elapsed_time(end)
+    capi.reg_run(loss, F, M, u[0], u[1], m, v, 0.5, adam, iters, iters, ws)
+    torch.cuda.synchronize()
+    assert evs[-1].elapsed_time(end) == last
+    assert capi.reg_get_device_error() == 0
