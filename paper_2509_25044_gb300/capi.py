@@ -605,6 +605,9 @@ def reg_set_timing_events(events):
         _check(_lib().reg_set_timing_events(None, 0), "reg_set_timing_events")
         return
     events = list(events)
+    for e in events:
+        if not e.cuda_event:  # torch creates the CUDA event on its first record
+            e.record()
     arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
     _check(_lib().reg_set_timing_events(arr, len(events)), "reg_set_timing_events")
 

@@ -5,22 +5,23 @@
 // The plain sweep (mi.cu) loads u, F, m and v itself, one plane ahead in
 // registers, and spends most of its issue slots on those loads and their
 // 64-bit addresses; at gigavoxel sizes its loads are too few in flight to
-// cover DRAM latency.  Here a CTA owns a 32 x 8 voxel tile and marches it
-// through a chunk of z-planes with warp specialisation:
+// cover DRAM latency.  Here a CTA owns a SW_TX x SW_TY voxel tile (an x pair
+// per lane, one warp per row) and marches it through a chunk of z-planes with
+// warp specialisation:
 //
-//   producer (one elected thread of warp 8): for each plane, one tiled TMA
-//     copy of u with the diffusion stencil's halo (x0-4 .. x0+35, y0-1 ..
-//     y0+8, all 3 channels; zero outside the volume) into a ring of SW_NU
-//     plane slots, and one copy each of F, m and v (the tile, 3 channels for
-//     m and v) into a ring of SW_NS slots.  Each slot's mbarrier completes on
-//     the copies' byte count; the producer refills a slot once the 8
-//     consumer warps have released it (a second mbarrier per slot).
-//   consumers (warps 0-7, one row of the tile each, one voxel per lane): u at
-//     z-1, z, z+1 and the 4 in-plane neighbours, F, m and v come from shared
-//     memory; only the 8 corner gathers of the trilinear sampler go to
-//     global memory.  The per-voxel arithmetic (sampler, B-spline weights,
-//     16-term adjoint, diffusion, Adam) is that of mi.cu term for term, so
-//     both paths give the same bits for u', m, v and the gradient.
+//   producer (one elected thread of warp SW_TY): for each plane, one tiled
+//     TMA copy of u with the diffusion stencil's halo (x0-4 .. x0+SW_TX+3,
+//     y0-1 .. y0+SW_TY, all 3 channels; zero outside the volume) into a ring
+//     of SW_NU plane slots, and one copy each of F, m and v (the tile, 3
+//     channels for m and v) into a ring of SW_NS slots.  Each slot's mbarrier
+//     completes on the copies' byte count; the producer refills a slot once
+//     the SW_TY consumer warps have released it (a second mbarrier per slot).
+//   consumers (warps 0 .. SW_TY-1, one row of the tile each, two voxels per
+//     lane): u at z-1, z, z+1 and the 4 in-plane neighbours, F, m and v come
+//     from shared memory; only the 8 corner gathers of the trilinear sampler
+//     go to global memory.  The per-voxel arithmetic (sampler, B-spline
+//     weights, 16-term adjoint, diffusion, Adam) is that of mi.cu term for
+//     term, so both paths give the same bits for u', m, v and the gradient.
 //
 // Every wait is bounded: a wait that expires latches REG_ERR_TIMEOUT in the
 // device error word, the CTA stops issuing and consuming, waits (bounded)
@@ -36,7 +37,7 @@ namespace regk {
 namespace {
 
 constexpr int SW_VL = 2;                                             // voxels per lane (an x pair)
-constexpr int SW_TX = 32 * SW_VL, SW_TY = 8;                         // tile: one warp per row
+constexpr int SW_TX = 32 * SW_VL, SW_TY = 9;                         // tile: one warp per row
 constexpr int SW_UX = SW_TX + 8, SW_UY = SW_TY + 2, SW_UC = SW_UX * SW_UY;  // u box: x0-4 .., y0-1 ..
 constexpr int SW_NU = 5;   // u plane slots: z-1, z, z+1 in use, two in flight
 constexpr int SW_NS = 3;   // F / m / v plane slots
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2)
 // (BF16 rows: nx % 8 == 0) and no composite transform.
 bool mi_tma_ok(const Dims &g) { return g.nx % 8 == 0; }
 
-// Grid: 32 x 8 tiles; the z-chunk count minimises (waves of resident CTAs) x
+// Grid: SW_TX x SW_TY tiles; the z-chunk count minimises (waves of resident CTAs) x
 // (planes per CTA + 3), the 3 being each CTA's start-up (its adjoint table
 // and the two planes its stencil reads beyond the chunk).
 MarchGrid mi_tma_sweep_grid(const Dims &g) {

@@ -206,13 +206,15 @@ def test_run_records_three_events_per_iteration():
     s = torch.cuda.current_stream()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * iters)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capi.reg_set_timing_events(evs)  # creates the events (a first record) and arms the hook
     start.record(s)
-    capi.reg_set_timing_events(evs)
     capi.reg_run(loss, F, M, u[0], u[1], m, v, 0.5, adam, 0, iters, ws)
     end.record(s)
     torch.cuda.synchronize()
+    # every event was recorded by the call (after `start`), in stream order
+    assert all(start.elapsed_time(e) >= 0.0 for e in evs)
     spans = [evs[k].elapsed_time(evs[k + 1]) for k in range(3 * iters - 1)]
-    assert all(t >= 0.0 for t in spans)  # recorded, in stream order
+    assert all(t >= 0.0 for t in spans)
     assert sum(spans) <= start.elapsed_time(end) + 1e-3
     assert evs[0].elapsed_time(evs[-1]) > 0.0
     # spent: a further call does not re-record the events
