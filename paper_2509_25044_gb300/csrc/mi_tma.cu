@@ -37,11 +37,12 @@ namespace regk {
 namespace {
 
 constexpr int SW_VL = 2;                                             // voxels per lane (an x pair)
-constexpr int SW_TX = 32 * SW_VL, SW_TY = 9;                         // tile: one warp per row
+constexpr int SW_TX = 32 * SW_VL, SW_TY = 20;                        // tile: one warp per row
 constexpr int SW_UX = SW_TX + 8, SW_UY = SW_TY + 2, SW_UC = SW_UX * SW_UY;  // u box: x0-4 .., y0-1 ..
 constexpr int SW_NU = 5;   // u plane slots: z-1, z, z+1 in use, two in flight
 constexpr int SW_NS = 3;   // F / m / v plane slots
 constexpr int SW_WARPS = SW_TY + 1;
+constexpr int SW_CTAS = SW_TY <= 9 ? 2 : 1;  // resident CTAs per SM the register budget allows
 constexpr int SW_THREADS = 32 * SW_WARPS;
 constexpr uint32_t SW_UBYTES = 3u * SW_UC * sizeof(float);
 
@@ -78,7 +79,7 @@ __device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
 // BT > 0: the bin count compiled in (table and ring offsets fold to
 // constants); BT = 0: P.bins.
 template <typename T, typename MT, bool STEP, int PAD, typename I, int BT = 0>
-__global__ void __launch_bounds__(SW_THREADS, 2)
+__global__ void __launch_bounds__(SW_THREADS, SW_CTAS)
     mi_sweep2_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
                          const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap vmap,
                          const T *__restrict__ M, Dims g, MiParams P, int zc, const float *__restrict__ Gtab,
@@ -375,6 +376,16 @@ cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const flo
             return cudaErrorNotSupported;
     } else {
         mmap = vmap = umap;  // unused without the step
+    }
+    // the rings and the adjoint table must fit one CTA's shared memory (large
+    // bin counts with FP32 moments do not: the plain sweep takes those)
+    {
+        int dev = 0, optin = 0;
+        const size_t need = SwLayout(P.bins, dt == REG_BF16 ? 2 : 4, step ? (mdt == REG_BF16 ? 2 : 4) : 0).total;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            need + 1024 > (size_t)optin)
+            return cudaErrorNotSupported;
     }
     const MarchGrid G = mi_tma_sweep_grid(g);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);

@@ -301,7 +301,7 @@ def test_iterate_matches_oracle(capi, kind, shape):
     np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
 
 
-# Rows with nx % 8 == 0 take the TMA-staged MI sweep (64 x 9 tiles, an x pair
+# Rows with nx % 8 == 0 take the TMA-staged MI sweep (64 x 20 tiles, an x pair
 # per lane, the diffusion halo from the staged box): rows that span several
 # tiles with a partial last one, ragged y and z, both moment types; rows with
 # nx % 8 != 0 the plain sweep.
