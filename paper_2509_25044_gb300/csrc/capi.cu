@@ -47,7 +47,7 @@ long long max_partial_blocks(const Dims &g, const reg_loss_desc *L) {
     const long long mi = mi_sweep_grid(g).blocks();
     if (mi > nb) nb = mi;
     if (mi_tma_ok(g)) {
-        const long long mt = mi_tma_sweep_grid(g).blocks();
+        const long long mt = mi_tma_max_blocks(g);
         if (mt > nb) nb = mt;
     }
     if (L && L->kind == REG_LOSS_LNCC) {

@@ -136,11 +136,14 @@ cudaError_t launch_mi_sweep2(const void *F, const void *M, int dt, const float *
                              unsigned *counter, double *r_out, cudaStream_t s, const AffineT *aff = nullptr);
 // The TMA-staged form of the plain second sweep (mi_tma.cu), used by
 // launch_mi_sweep2 when mi_tma_ok(g) and there is no composite transform;
-// cudaErrorNotSupported if a tensor map cannot be built (the caller then
-// runs the plain kernel).  Its grid has mi_tma_sweep_grid(g).blocks() CTAs
-// (one partial each).
+// cudaErrorNotSupported if a tensor map cannot be built or its rings do not
+// fit a CTA's shared memory (the caller then runs the plain kernel).  Its
+// tiles are 64 x ty voxels (ty = 31 or 20, by what fits); its grid has
+// mi_tma_sweep_grid(g, ty).blocks() CTAs (one partial each), at most
+// mi_tma_max_blocks(g).
 bool mi_tma_ok(const Dims &g);
-MarchGrid mi_tma_sweep_grid(const Dims &g);
+MarchGrid mi_tma_sweep_grid(const Dims &g, int ty);
+long long mi_tma_max_blocks(const Dims &g);
 cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                                  const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                                  void *m, void *v, int mdt, const StepParams &S, double *partials,

@@ -5,18 +5,18 @@
 // The plain sweep (mi.cu) loads u, F, m and v itself, one plane ahead in
 // registers, and spends most of its issue slots on those loads and their
 // 64-bit addresses; at gigavoxel sizes its loads are too few in flight to
-// cover DRAM latency.  Here a CTA owns a SW_TX x SW_TY voxel tile (an x pair
-// per lane, one warp per row) and marches it through a chunk of z-planes with
-// warp specialisation:
+// cover DRAM latency.  Here a CTA owns a 64 x TY voxel tile (an x pair per
+// lane, one warp per row; TY = 31 or 20, SwShape) and marches it through a
+// chunk of z-planes with warp specialisation:
 //
-//   producer (one elected thread of warp SW_TY): for each plane, one tiled
-//     TMA copy of u with the diffusion stencil's halo (x0-4 .. x0+SW_TX+3,
-//     y0-1 .. y0+SW_TY, all 3 channels; zero outside the volume) into a ring
-//     of SW_NU plane slots, and one copy each of F, m and v (the tile, 3
+//   producer (one elected thread of warp TY): for each plane, one tiled TMA
+//     copy of u with the diffusion stencil's halo (x0-4 .. x0+67, y0-1 ..
+//     y0+TY, all 3 channels; zero outside the volume) into a ring of
+//     SwShape::nu plane slots, and one copy each of F, m and v (the tile, 3
 //     channels for m and v) into a ring of SW_NS slots.  Each slot's mbarrier
 //     completes on the copies' byte count; the producer refills a slot once
-//     the SW_TY consumer warps have released it (a second mbarrier per slot).
-//   consumers (warps 0 .. SW_TY-1, one row of the tile each, two voxels per
+//     the TY consumer warps have released it (a second mbarrier per slot).
+//   consumers (warps 0 .. TY-1, one row of the tile each, two voxels per
 //     lane): u at z-1, z, z+1 and the 4 in-plane neighbours, F, m and v come
 //     from shared memory; only the 8 corner gathers of the trilinear sampler
 //     go to global memory.  The per-voxel arithmetic (sampler, B-spline
@@ -36,30 +36,40 @@ namespace regk {
 
 namespace {
 
-constexpr int SW_VL = 2;                                             // voxels per lane (an x pair)
-constexpr int SW_TX = 32 * SW_VL, SW_TY = 20;                        // tile: one warp per row
-constexpr int SW_UX = SW_TX + 8, SW_UY = SW_TY + 2, SW_UC = SW_UX * SW_UY;  // u box: x0-4 .., y0-1 ..
-constexpr int SW_NU = 5;   // u plane slots: z-1, z, z+1 in use, two in flight
-constexpr int SW_NS = 3;   // F / m / v plane slots
-constexpr int SW_WARPS = SW_TY + 1;
-constexpr int SW_CTAS = SW_TY <= 9 ? 2 : 1;  // resident CTAs per SM the register budget allows
-constexpr int SW_THREADS = 32 * SW_WARPS;
-constexpr uint32_t SW_UBYTES = 3u * SW_UC * sizeof(float);
+constexpr int SW_VL = 2;          // voxels per lane (an x pair)
+constexpr int SW_TX = 32 * SW_VL;  // tile width; one warp per tile row
+constexpr int SW_UX = SW_TX + 8;   // u box: x0-4 .. x0+SW_TX+3
+constexpr int SW_NS = 3;           // F / m / v plane slots
+
+// Two tile heights, one CTA per SM each: 31 rows (1024 threads at 64
+// registers) where its rings fit a CTA's shared memory (BF16 images and
+// moments), else 20 rows (672 threads at 80 registers).  More consumer warps
+// cover more of the corner gathers' latency.
+template <int TY>
+struct SwShape {
+    static constexpr int uy = TY + 2;                  // u box rows: y0-1 .. y0+TY
+    static constexpr int uc = SW_UX * uy;              // one u channel of the box
+    static constexpr int threads = 32 * (TY + 1);      // TY consumer warps + the producer
+    static constexpr int nu = TY >= 31 ? 4 : 5;        // u plane slots: z-1, z, z+1 in use, the rest in flight
+    static constexpr uint32_t ubytes = 3u * uc * sizeof(float);
+};
 
 __host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) & ~(size_t)127; }
 
 // dynamic shared memory: the adjoint table, the two rings, the mbarriers
+template <int TY>
 struct SwLayout {
     size_t u, f, m, v, bar, total, fslot, mslot;
     __host__ __device__ SwLayout(int B, int fbytes, int mbytes) {
-        fslot = al128((size_t)SW_TX * SW_TY * fbytes);
-        mslot = al128((size_t)3 * SW_TX * SW_TY * mbytes);
+        using SH = SwShape<TY>;
+        fslot = al128((size_t)SW_TX * TY * fbytes);
+        mslot = al128((size_t)3 * SW_TX * TY * mbytes);
         u = al128(sizeof(float4) * (size_t)B * B);
-        f = u + SW_NU * al128(SW_UBYTES);
+        f = u + SH::nu * al128(SH::ubytes);
         m = f + SW_NS * fslot;
         v = m + SW_NS * mslot;
         bar = v + SW_NS * mslot;
-        total = bar + sizeof(uint64_t) * 2 * (SW_NU + SW_NS);
+        total = bar + sizeof(uint64_t) * 2 * (SH::nu + SW_NS);
     }
 };
 
@@ -78,8 +88,8 @@ __device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
 
 // BT > 0: the bin count compiled in (table and ring offsets fold to
 // constants); BT = 0: P.bins.
-template <typename T, typename MT, bool STEP, int PAD, typename I, int BT = 0>
-__global__ void __launch_bounds__(SW_THREADS, SW_CTAS)
+template <int TY, typename T, typename MT, bool STEP, int PAD, typename I, int BT = 0>
+__global__ void __launch_bounds__(SwShape<TY>::threads, 1)
     mi_sweep2_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
                          const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap vmap,
                          const T *__restrict__ M, Dims g, MiParams P, int zc, const float *__restrict__ Gtab,
@@ -90,8 +100,12 @@ __global__ void __launch_bounds__(SW_THREADS, SW_CTAS)
     __shared__ double red[32];
     __shared__ volatile int abort_flag;
     constexpr int FB = (int)sizeof(T), MB = STEP ? (int)sizeof(MT) : 0;
+    constexpr int SW_TY = TY, SW_UY = SwShape<TY>::uy, SW_UC = SwShape<TY>::uc, SW_NU = SwShape<TY>::nu;
+    constexpr int SW_THREADS = SwShape<TY>::threads;
+    constexpr uint32_t SW_UBYTES = SwShape<TY>::ubytes;
+    (void)SW_UY;
     const int B = BT > 0 ? BT : P.bins, BB = B * B;
-    const SwLayout L(B, FB, MB);
+    const SwLayout<TY> L(B, FB, MB);
     float4 *G4 = reinterpret_cast<float4 *>(smem);
     uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + L.bar);
     uint64_t *empty_u = full_u + SW_NU, *full_s = empty_u + SW_NU, *empty_s = full_s + SW_NS;
@@ -320,25 +334,36 @@ __global__ void __launch_bounds__(SW_THREADS, SW_CTAS)
 // (BF16 rows: nx % 8 == 0) and no composite transform.
 bool mi_tma_ok(const Dims &g) { return g.nx % 8 == 0; }
 
-// Grid: SW_TX x SW_TY tiles; the z-chunk count minimises (waves of resident CTAs) x
-// (planes per CTA + 3), the 3 being each CTA's start-up (its adjoint table
+// Grid of 64 x ty tiles; the z-chunk count minimises (waves of resident CTAs)
+// x (planes per CTA + 3), the 3 being each CTA's start-up (its adjoint table
 // and the two planes its stencil reads beyond the chunk).
-MarchGrid mi_tma_sweep_grid(const Dims &g) {
+MarchGrid mi_tma_sweep_grid(const Dims &g, int ty) {
     MarchGrid G;
     G.tiles_x = (g.nx + SW_TX - 1) / SW_TX;
-    G.tiles_y = (g.ny + SW_TY - 1) / SW_TY;
-    static int per_sm = 0;  // 0 until the occupancy calculator has answered
-    int n = per_sm;
+    G.tiles_y = (g.ny + ty - 1) / ty;
+    static int per_sm[2] = {0, 0};  // 0 until the occupancy calculator has answered
+    const int k = ty >= 31 ? 1 : 0;
+    int n = per_sm[k];
     if (n == 0) {
-        // residency of the FP32 instantiation with 32 bins (every instantiation
-        // has the same register budget; only larger tables take more shared
-        // memory); the grid must not depend on the call's bin count, since it
-        // also sizes the workspace
-        const SwLayout L(32, 4, 4);
-        auto kern = mi_sweep2_tma_kernel<float, float, true, REG_PAD_BORDER, int>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, SW_THREADS, L.total) == cudaSuccess && n > 0)
-            per_sm = n;
+        // residency with 32 bins (the instantiations of one shape share its
+        // register budget; only larger tables take more shared memory); the
+        // grid must not depend on the call's bin count, since it also sizes
+        // the workspace
+        auto query = [&](auto kern, size_t total, int threads) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, total) != cudaSuccess || n < 1) {
+                (void)cudaGetLastError();
+                n = 0;
+            }
+        };
+        if (k == 1)
+            query(mi_sweep2_tma_kernel<31, __nv_bfloat16, __nv_bfloat16, true, REG_PAD_BORDER, int>,
+                  SwLayout<31>(32, 2, 2).total, SwShape<31>::threads);
+        else
+            query(mi_sweep2_tma_kernel<20, float, float, true, REG_PAD_BORDER, int>, SwLayout<20>(32, 4, 4).total,
+                  SwShape<20>::threads);
+        if (n > 0)
+            per_sm[k] = n;
         else
             n = 1;
     }
@@ -361,14 +386,36 @@ MarchGrid mi_tma_sweep_grid(const Dims &g) {
     return G;
 }
 
+long long mi_tma_max_blocks(const Dims &g) {
+    return std::max(mi_tma_sweep_grid(g, 20).blocks(), mi_tma_sweep_grid(g, 31).blocks());
+}
+
 cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                                  const MiParams &P, const float *Gtab, float *grad_out, bool step, float *u_out,
                                  void *m, void *v, int mdt, const StepParams &S, double *partials,
                                  unsigned *counter, double *r_out, cudaStream_t s) {
+    // the taller tile where its rings and the adjoint table fit one CTA's
+    // shared memory, else the shorter; neither (large bin counts with FP32
+    // images and moments): the plain sweep
+    const int fb = dt == REG_BF16 ? 2 : 4, mb = step ? (mdt == REG_BF16 ? 2 : 4) : 0;
+    int ty = 0;
+    {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return cudaErrorNotSupported;
+        if (SwLayout<31>(P.bins, fb, mb).total + 1024 <= (size_t)optin)
+            ty = 31;
+        else if (SwLayout<20>(P.bins, fb, mb).total + 1024 <= (size_t)optin)
+            ty = 20;
+        else
+            return cudaErrorNotSupported;
+    }
     CUtensorMap umap, fmap, mmap, vmap;
     const uint64_t d4[4] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz, 3};
     const uint64_t d3[3] = {(uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
-    const uint32_t ubox[4] = {SW_UX, SW_UY, 1, 3}, sbox4[4] = {SW_TX, SW_TY, 1, 3}, sbox3[3] = {SW_TX, SW_TY, 1};
+    const uint32_t ubox[4] = {SW_UX, (uint32_t)ty + 2, 1, 3}, sbox4[4] = {SW_TX, (uint32_t)ty, 1, 3},
+                   sbox3[3] = {SW_TX, (uint32_t)ty, 1};
     if (!tma::make_map(&umap, u, REG_F32, 4, d4, ubox) || !tma::make_map(&fmap, F, dt, 3, d3, sbox3))
         return cudaErrorNotSupported;
     if (step) {
@@ -377,51 +424,47 @@ cudaError_t launch_mi_sweep2_tma(const void *F, const void *M, int dt, const flo
     } else {
         mmap = vmap = umap;  // unused without the step
     }
-    // the rings and the adjoint table must fit one CTA's shared memory (large
-    // bin counts with FP32 moments do not: the plain sweep takes those)
-    {
-        int dev = 0, optin = 0;
-        const size_t need = SwLayout(P.bins, dt == REG_BF16 ? 2 : 4, step ? (mdt == REG_BF16 ? 2 : 4) : 0).total;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            need + 1024 > (size_t)optin)
-            return cudaErrorNotSupported;
-    }
-    const MarchGrid G = mi_tma_sweep_grid(g);
+    const MarchGrid G = mi_tma_sweep_grid(g, ty);
     const dim3 grid(G.tiles_x, G.tiles_y, G.chunks);
     unsigned *err = error_word();
     if (!err) return cudaErrorInvalidDevice;
     cudaError_t e = cudaSuccess;
-    with_type(dt, [&](auto tp) {
-        using T = elem_t<decltype(tp)>;
-        with_pad(pad, [&](auto pd) {
-            constexpr int PD = decltype(pd)::value;
-            with_index(g, [&](auto ip) {
-                using I = elem_t<decltype(ip)>;
-                auto go = [&](auto kern, auto *mp, bool st) {
-                    using MT = std::remove_pointer_t<decltype(mp)>;
-                    const size_t smem =
-                        SwLayout(P.bins, (int)sizeof(T), st ? (int)sizeof(MT) : 0).total;
-                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                    if (e != cudaSuccess) return;
-                    kern<<<grid, SW_THREADS, smem, s>>>(umap, fmap, mmap, vmap, (const T *)M, g, P, G.zc, Gtab,
-                                                        grad_out, u_out, (MT *)m, (MT *)v, S, partials, counter,
-                                                        r_out, err);
-                };
-                // the step with the workloads' 32 bins compiled in
-                if (!step)
-                    go(mi_sweep2_tma_kernel<T, float, false, PD, I>, (float *)nullptr, false);
-                else if (mdt == REG_BF16 && P.bins == 32)
-                    go(mi_sweep2_tma_kernel<T, __nv_bfloat16, true, PD, I, 32>, (__nv_bfloat16 *)nullptr, true);
-                else if (mdt == REG_BF16)
-                    go(mi_sweep2_tma_kernel<T, __nv_bfloat16, true, PD, I>, (__nv_bfloat16 *)nullptr, true);
-                else if (P.bins == 32)
-                    go(mi_sweep2_tma_kernel<T, float, true, PD, I, 32>, (float *)nullptr, true);
-                else
-                    go(mi_sweep2_tma_kernel<T, float, true, PD, I>, (float *)nullptr, true);
+    auto shape = [&](auto tyc) {
+        constexpr int TY = decltype(tyc)::value;
+        with_type(dt, [&](auto tp) {
+            using T = elem_t<decltype(tp)>;
+            with_pad(pad, [&](auto pd) {
+                constexpr int PD = decltype(pd)::value;
+                with_index(g, [&](auto ip) {
+                    using I = elem_t<decltype(ip)>;
+                    auto go = [&](auto kern, auto *mp, bool st) {
+                        using MT = std::remove_pointer_t<decltype(mp)>;
+                        const size_t smem = SwLayout<TY>(P.bins, (int)sizeof(T), st ? (int)sizeof(MT) : 0).total;
+                        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                        if (e != cudaSuccess) return;
+                        kern<<<grid, SwShape<TY>::threads, smem, s>>>(umap, fmap, mmap, vmap, (const T *)M, g, P, G.zc,
+                                                                      Gtab, grad_out, u_out, (MT *)m, (MT *)v, S,
+                                                                      partials, counter, r_out, err);
+                    };
+                    // the step with the workloads' 32 bins compiled in
+                    if (!step)
+                        go(mi_sweep2_tma_kernel<TY, T, float, false, PD, I>, (float *)nullptr, false);
+                    else if (mdt == REG_BF16 && P.bins == 32)
+                        go(mi_sweep2_tma_kernel<TY, T, __nv_bfloat16, true, PD, I, 32>, (__nv_bfloat16 *)nullptr, true);
+                    else if (mdt == REG_BF16)
+                        go(mi_sweep2_tma_kernel<TY, T, __nv_bfloat16, true, PD, I>, (__nv_bfloat16 *)nullptr, true);
+                    else if (P.bins == 32)
+                        go(mi_sweep2_tma_kernel<TY, T, float, true, PD, I, 32>, (float *)nullptr, true);
+                    else
+                        go(mi_sweep2_tma_kernel<TY, T, float, true, PD, I>, (float *)nullptr, true);
+                });
             });
         });
-    });
+    };
+    if (ty == 31)
+        shape(IC<31>{});
+    else
+        shape(IC<20>{});
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
