@@ -301,10 +301,11 @@ def test_iterate_matches_oracle(capi, kind, shape):
     np.testing.assert_allclose(to64(c["m"]), mr, rtol=1e-5, atol=1e-7)
 
 
-# Rows with nx % 8 == 0 take the TMA-staged MI sweep (64 x 20 tiles, an x pair
-# per lane, the diffusion halo from the staged box): rows that span several
-# tiles with a partial last one, ragged y and z, both moment types; rows with
-# nx % 8 != 0 the plain sweep.
+# Rows with nx % 8 == 0 take the TMA-staged MI sweep (an x pair per lane, the
+# diffusion halo from the staged box; 64 x 31 tiles with BF16 moments, whose
+# rings fit beside FP32 images, 64 x 20 with FP32 moments): rows that span
+# several tiles with a partial last one, ragged y and z, both moment types;
+# rows with nx % 8 != 0 the plain sweep.
 @pytest.mark.parametrize("kind", ["mi", "mi_hard"])
 @pytest.mark.parametrize("shape,mdt", [((9, 11, 264), 0), ((6, 70, 136), 1), ((5, 3, 8), 0), ((7, 9, 132), 1)])
 def test_iterate_tile_rows_match_oracle(capi, kind, shape, mdt):
