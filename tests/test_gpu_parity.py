@@ -255,7 +255,7 @@ def test_jacdet_matches_oracle(capi):
 # ---------------------------------------------------------------------------
 # fused iteration
 # ---------------------------------------------------------------------------
-def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
+def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61, bins=32):
     if kind in ("lncc", "lncc_ants"):
         F, M = mono_images(shape, seed)
         ants = kind == "lncc_ants"
@@ -266,8 +266,8 @@ def _iterate_case(capi, kind, shape, dtype=torch.float32, mdt=0, t=1, seed=61):
         fr = (float(F.min()), float(F.max()))
         mr = (float(M.min()), float(M.max()))
         hard = kind == "mi_hard"
-        loss = capi.mi_desc(fr, mr, 32, hard=hard)
-        spec = O.LossSpec(kind=O.LOSS_MI, bins=32, f_range=fr, m_range=mr, mi_estimator=int(hard))
+        loss = capi.mi_desc(fr, mr, bins, hard=hard)
+        spec = O.LossSpec(kind=O.LOSS_MI, bins=bins, f_range=fr, m_range=mr, mi_estimator=int(hard))
     u = field(shape, 3.0, 2.0, seed + 1)
     N = int(np.prod(shape))
     gen = torch.Generator().manual_seed(seed)
@@ -484,6 +484,27 @@ def test_identity_composite_histogram_equals_plain_histogram(capi, shape, img, b
     assert int(h_plain.sum()) > 0
     assert torch.equal(h_plain, h_comp)
     assert float(s_plain[0]) == float(s_comp[0])
+    assert capi.reg_get_device_error() == 0
+
+
+# 64 bins on rows the TMA sweep takes: its 64 x 31 tile's rings and table do
+# not fit a CTA's shared memory, so the 64 x 20 tile runs (BF16 moments) or,
+# with FP32 images and moments, neither fits and the plain sweep runs.
+@pytest.mark.parametrize("dtype,mdt", [(torch.float32, 0), (torch.float32, 1), (torch.bfloat16, 1)])
+def test_iterate_64_bins_on_tma_rows_matches_oracle(capi, dtype, mdt):
+    shape = (6, 45, 136)
+    c = _iterate_case(capi, "mi", shape, dtype=dtype, mdt=mdt, t=2, seed=93, bins=64)
+    if dtype == torch.bfloat16:
+        F, M = bf16_values(c["F"]), bf16_values(c["M"])
+    else:
+        F, M = c["F"], c["M"]
+    ref = O.objective(to64(F), to64(M), to64(c["u"]), c["spec"], 0.1)
+    assert_rel(c["obj"][0].item(), ref["sim"], LOSS_RTOL, "similarity")
+    assert_rel(c["obj"][1].item(), ref["R"], 1e-6, "R")
+    assert rel_l2(to64(c["g"]), ref["grad"]) <= GRAD_RTOL
+    ur, mr, vr = O.adam(to64(c["u"]), to64(c["m0"]), to64(c["v0"]), to64(c["g"]), 2, 0.1, grad_scale=c["N"],
+                        bf16_moments=bool(mdt))
+    np.testing.assert_allclose(to64(c["uo"]), ur, atol=1e-5, rtol=0)
     assert capi.reg_get_device_error() == 0
 
 
