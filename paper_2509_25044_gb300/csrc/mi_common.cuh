@@ -22,6 +22,21 @@ __device__ __forceinline__ int bspline_weights(float s, int B, float w[4]) {
     return i0;
 }
 
+// The same weights times c6 / (1/6): with c6 = (1/6) 2^20 (exactly RN(1/6)
+// times a power of two) they are the weights times 2^20, bit for bit, in
+// one multiply each instead of two.
+__device__ __forceinline__ int bspline_weights_times(float s, int B, float c6, float w[4]) {
+    int i0 = (int)floorf(s);
+    i0 = min(max(i0, 1), B - 3);
+    const float f = s - (float)i0;
+    const float f2 = f * f, f3 = f2 * f, g = 1.0f - f;
+    w[0] = g * g * g * c6;
+    w[1] = (3.0f * f3 - 6.0f * f2 + 4.0f) * c6;
+    w[2] = (-3.0f * f3 + 3.0f * f2 + 3.0f * f + 1.0f) * c6;
+    w[3] = f3 * c6;
+    return i0;
+}
+
 // derivatives of the same 4 weights with respect to s
 __device__ __forceinline__ int bspline_dweights(float s, int B, float d[4]) {
     int i0 = (int)floorf(s);
@@ -59,13 +74,14 @@ inline size_t mi_hist_smem_bytes(int B) {
 // order of the atomics (deterministic).
 __device__ __forceinline__ void hist_add_parzen(unsigned *shc, int B, float sF, float sJ) {
     constexpr float MAGIC = 8388608.0f;  // 2^23: ulp 1 in [2^23, 2^24)
-    float wf[4], wj[4];
-    const int iF = bspline_weights(sF, B, wf) - 1;
+    float sf[4], wj[4];
+    // the fixed-image weights already times MI_FIXED_SCALE (a power of two)
+    const int iF = bspline_weights_times(sF, B, (1.0f / 6.0f) * MI_FIXED_SCALE, sf) - 1;
     const int iJ = bspline_weights(sJ, B, wj) - 1;
     unsigned *row = shc + iF * B + iJ;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const float sa = wf[a] * MI_FIXED_SCALE;
+        const float sa = sf[a];
 #pragma unroll
         for (int b = 0; b < 4; ++b) atomicAdd(row + b, __float_as_uint(fmaf(sa, wj[b], MAGIC)) - 0x4B000000u);
         row += B;
