@@ -25,18 +25,33 @@
 
 namespace regk {
 
-constexpr int HIST_TX = 32, HIST_TY = 32, HIST_THREADS = HIST_TX * HIST_TY;
-// A copy serves (32 / copies) lanes of each of the 32 warps, one voxel per
-// lane and plane, so after this many planes a CTA adds its copies to the
-// global histogram and clears them (MI_MAX_COPY_VOXELS keeps the 32-bit
-// bins from wrapping).
-__host__ __device__ constexpr int hist_batch_planes(int B) {
-    return MI_MAX_COPY_VOXELS / (32 * (32 / hist_copies(B)));
+constexpr int HIST_TX = 32;
+// Two CTA shapes.  With the workloads' 32 bins compiled in: 32 x 24 columns,
+// 768 threads at 40 registers and 24 copies of 4 KB (lanes 0-7 share theirs
+// with lanes 24-31, the voxels x and x + 24 of a row), two CTAs per SM, so
+// 48 warps cover the corner gathers' latency where one 1024-thread CTA
+// holding 32 copies gives 32.  Otherwise: 32 x 32 columns, 1024 threads at
+// 64 registers, hist_copies(B) copies, one CTA per SM.
+template <int BT>
+struct HistShape {
+    static constexpr bool pair = BT == 32;
+    static constexpr int ty = pair ? 24 : 32;  // rows = warps
+    static constexpr int threads = HIST_TX * ty;
+    static constexpr int per_sm = pair ? 2 : 1;
+};
+__host__ __device__ constexpr int hist_copies_of(int B, bool pair) { return pair ? 24 : hist_copies(B); }
+// A copy serves at most ceil(32 / copies) lanes of each of the `warps`
+// warps, one voxel per lane and plane, so after this many planes a CTA adds
+// its copies to the global histogram and clears them (MI_MAX_COPY_VOXELS
+// keeps the 32-bit bins from wrapping).
+__host__ __device__ constexpr int hist_batch_planes(int copies, int warps) {
+    return MI_MAX_COPY_VOXELS / (warps * ((32 + copies - 1) / copies));
 }
 
-// Persistent CTAs (one per SM): the volume is cut into 32 x 32 columns, the
-// (column, plane) pairs are numbered column-major and each CTA takes one
-// contiguous range of them, so the work is balanced to within one plane.
+// Persistent CTAs (HistShape::per_sm per SM): the volume is cut into 32 x ty
+// columns, the (column, plane) pairs are numbered column-major and each CTA
+// takes one contiguous range of them, so the work is balanced to within one
+// plane.
 // Each thread marches its (x, y) column through the planes of its range,
 // with F and u of the next plane requested before the current plane is
 // computed, and adds the 16 fixed-point products of its voxel's B-spline
@@ -44,22 +59,23 @@ __host__ __device__ constexpr int hist_batch_planes(int B) {
 // BT > 0: the bin count compiled in (the bin and copy address arithmetic folds
 // to constants); BT = 0: P.bins.
 template <typename T, int PAD, typename I, bool HARD, bool AFF, int BT = 0>
-__global__ void __launch_bounds__(HIST_THREADS, 1)
+__global__ void __launch_bounds__(HistShape<BT>::threads, HistShape<BT>::per_sm)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
                    int tiles_x, long long total, AffineT Ain, unsigned long long *__restrict__ hist) {
     extern __shared__ unsigned sh[];
     const AffineT A = AFF ? resolve_affine(Ain) : Ain;
+    using Sh = HistShape<BT>;
     const int B = BT > 0 ? BT : P.bins, BB = B * B;
-    const int copies = hist_copies(B), pitch = BB + 1;
+    const int copies = hist_copies_of(B, Sh::pair), pitch = BB + 1;
     const int tid = threadIdx.y * HIST_TX + threadIdx.x;
-    for (int i = tid; i < copies * pitch; i += HIST_THREADS) sh[i] = 0u;
+    for (int i = tid; i < copies * pitch; i += Sh::threads) sh[i] = 0u;
     __syncthreads();
     unsigned *shc = sh + (threadIdx.x % copies) * pitch;
     const float *u0 = u, *u1 = u + g.n, *u2 = u + 2 * g.n;
     const bool has_u = !AFF || u != nullptr;  // the composite form may omit u
     const I nxy = (I)g.nxy;
     const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
-    const int batch = hist_batch_planes(B);
+    const int batch = hist_batch_planes(copies, Sh::ty);
     for (long long b0 = beg; b0 < end; b0 += batch) {
         const long long b1 = min(end, b0 + batch);
         for (long long pos = b0; pos < b1;) {
@@ -68,7 +84,7 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
             const int z1 = (int)min((long long)g.nz, (long long)z0 + (b1 - pos));
             pos += z1 - z0;
             const int x = (int)(tile % tiles_x) * HIST_TX + threadIdx.x;
-            const int y = (int)(tile / tiles_x) * HIST_TY + threadIdx.y;
+            const int y = (int)(tile / tiles_x) * Sh::ty + threadIdx.y;
             if (x >= g.nx || y >= g.ny) continue;
             I p = (I)z0 * nxy + (I)y * g.nx + x;
             float fv = ld_vox_cs(F, p), ux = 0.0f, uy = 0.0f, uz = 0.0f;
@@ -106,7 +122,7 @@ __global__ void __launch_bounds__(HIST_THREADS, 1)
             }
         }
         __syncthreads();
-        for (int i = tid; i < BB; i += HIST_THREADS) {
+        for (int i = tid; i < BB; i += Sh::threads) {
             unsigned long long v = 0;
             for (int c = 0; c < copies; ++c) {
                 v += sh[c * pitch + i];
@@ -321,12 +337,17 @@ MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 16LL * num_sms(), 
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                            const MiParams &P, unsigned long long *hist, cudaStream_t s, const AffineT *aff) {
-    const int tiles_x = (g.nx + HIST_TX - 1) / HIST_TX, tiles_y = (g.ny + HIST_TY - 1) / HIST_TY;
+    // the shape of the instantiation dispatched below (HistShape<32> for the
+    // 32-bin non-composite forms)
+    const bool pair = !aff && P.bins == 32;
+    const int ty = pair ? HistShape<32>::ty : HistShape<0>::ty;
+    const int tiles_x = (g.nx + HIST_TX - 1) / HIST_TX, tiles_y = (g.ny + ty - 1) / ty;
     const long long total = (long long)tiles_x * tiles_y * g.nz;
     if (total <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<long long>(num_sms(), total);
-    const dim3 block(HIST_TX, HIST_TY);
-    const size_t smem = mi_hist_smem_bytes(P.bins);
+    const int per_sm = pair ? HistShape<32>::per_sm : HistShape<0>::per_sm;
+    const unsigned grid = (unsigned)std::min<long long>((long long)per_sm * num_sms(), total);
+    const dim3 block(HIST_TX, ty);
+    const size_t smem = sizeof(unsigned) * (size_t)hist_copies_of(P.bins, pair) * ((size_t)P.bins * P.bins + 1);
     const AffineT A = aff ? *aff : AffineT{};
     cudaError_t e = cudaSuccess;
     with_type(dt, [&](auto tp) {

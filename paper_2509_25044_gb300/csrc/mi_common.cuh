@@ -61,11 +61,11 @@ __device__ __forceinline__ int nearest_bin(float s, int B) { return min(max((int
 // Shared histogram of one CTA: `copies` private copies, copy c used by the
 // lanes with lane % copies == c, each copy padded by one word so that the
 // same bin of different copies falls in different banks.  With 32 copies
-// (B <= 32) the 32 lanes of one atomic instruction never share an address.
+// the 32 lanes of one atomic instruction never share an address; with
+// fewer, two lanes of a copy do when their voxels fall in the same bins
+// (the two adds then serialise; the integer sums are the same).  The count
+// for the 1024-thread CTA shape, whose copies fill about 131 KB:
 __host__ __device__ constexpr int hist_copies(int B) { return B <= 32 ? 32 : (B <= 45 ? 16 : 8); }
-inline size_t mi_hist_smem_bytes(int B) {
-    return sizeof(unsigned) * (size_t)hist_copies(B) * ((size_t)B * B + 1);
-}
 
 // Adds the 16 fixed-point products of a voxel's 4 + 4 B-spline weights to a
 // copy of the histogram.  Each product is rounded by one FFMA against 2^23

@@ -457,10 +457,10 @@ def test_run_matches_repeated_iterate(capi, kind, iters):
 
 
 @pytest.mark.parametrize("shape,img,bins,hard,pad", [
-    ((37, 45, 72), torch.bfloat16, 32, False, 0),   # ragged 32 x 32 columns in x and y
+    ((37, 45, 72), torch.bfloat16, 32, False, 0),   # ragged columns in x and y (32 x 24 and 32 x 32)
     ((37, 45, 72), torch.float32, 32, True, 1),     # hard-binned, zero padding
     ((9, 7, 8), torch.float32, 16, False, 1),       # one column, 16 copies
-    ((400, 310, 256), torch.bfloat16, 32, False, 0),  # copies flushed every 256 planes, many times per CTA
+    ((400, 310, 256), torch.bfloat16, 32, False, 0),  # copies flushed every 170 / 256 planes, many times per CTA
     ((400, 310, 256), torch.bfloat16, 64, False, 0),  # 8 copies
 ])
 def test_identity_composite_histogram_equals_plain_histogram(capi, shape, img, bins, hard, pad):
@@ -468,7 +468,10 @@ def test_identity_composite_histogram_equals_plain_histogram(capi, shape, img, b
     p + u exactly, 64-bit offsets) forms the same fixed-point joint histogram,
     bit for bit, as the plain form, over ragged tiles, both estimators and
     pads, and volumes whose persistent CTAs flush their 32-bit copies many
-    times."""
+    times.  With 32 bins the two forms also run different CTA shapes (the
+    plain one two 768-thread CTAs per SM with 24 copies, the composite one
+    1024-thread CTA with 32), so this also checks that the shape leaves the
+    integer sums alone."""
     gen = torch.Generator(device=DEV).manual_seed(bins + shape[0])
     F = torch.rand(shape, generator=gen, device=DEV).to(img)
     M = torch.rand(shape, generator=gen, device=DEV).to(img)
