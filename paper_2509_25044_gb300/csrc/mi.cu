@@ -26,15 +26,17 @@
 namespace regk {
 
 constexpr int HIST_TX = 32;
-// Two CTA shapes.  With the workloads' 32 bins compiled in: 32 x 24 columns,
-// 768 threads at 40 registers and 24 copies of 4 KB (lanes 0-7 share theirs
-// with lanes 24-31, the voxels x and x + 24 of a row), two CTAs per SM, so
-// 48 warps cover the corner gathers' latency where one 1024-thread CTA
-// holding 32 copies gives 32.  Otherwise: 32 x 32 columns, 1024 threads at
-// 64 registers, hist_copies(B) copies, one CTA per SM.
-template <int BT>
+// Two CTA shapes.  BF16 images with the workloads' 32 bins compiled in:
+// 32 x 24 columns, 768 threads at 40 registers and 24 copies of 4 KB (lanes
+// 0-7 share theirs with lanes 24-31, the voxels x and x + 24 of a row), two
+// CTAs per SM, so 48 warps cover the corner gathers' latency where one
+// 1024-thread CTA holding 32 copies gives 32.  Otherwise: 32 x 32 columns,
+// 1024 threads at 64 registers, hist_copies(B) copies, one CTA per SM (FP32
+// images gather twice the bytes, and the two CTAs' copies leave too little
+// L1 for them).
+template <int BT, typename T>
 struct HistShape {
-    static constexpr bool pair = BT == 32;
+    static constexpr bool pair = BT == 32 && sizeof(T) == 2;
     static constexpr int ty = pair ? 24 : 32;  // rows = warps
     static constexpr int threads = HIST_TX * ty;
     static constexpr int per_sm = pair ? 2 : 1;
@@ -59,12 +61,12 @@ __host__ __device__ constexpr int hist_batch_planes(int copies, int warps) {
 // BT > 0: the bin count compiled in (the bin and copy address arithmetic folds
 // to constants); BT = 0: P.bins.
 template <typename T, int PAD, typename I, bool HARD, bool AFF, int BT = 0>
-__global__ void __launch_bounds__(HistShape<BT>::threads, HistShape<BT>::per_sm)
+__global__ void __launch_bounds__(HistShape<BT, T>::threads, HistShape<BT, T>::per_sm)
     mi_hist_kernel(const T *__restrict__ F, const T *__restrict__ M, const float *__restrict__ u, Dims g, MiParams P,
                    int tiles_x, long long total, AffineT Ain, unsigned long long *__restrict__ hist) {
     extern __shared__ unsigned sh[];
     const AffineT A = AFF ? resolve_affine(Ain) : Ain;
-    using Sh = HistShape<BT>;
+    using Sh = HistShape<BT, T>;
     const int B = BT > 0 ? BT : P.bins, BB = B * B;
     const int copies = hist_copies_of(B, Sh::pair), pitch = BB + 1;
     const int tid = threadIdx.y * HIST_TX + threadIdx.x;
@@ -337,14 +339,16 @@ MarchGrid mi_sweep_grid(const Dims &g) { return march_grid(g, 16LL * num_sms(), 
 
 cudaError_t launch_mi_hist(const void *F, const void *M, int dt, const float *u, const Dims &g, int pad,
                            const MiParams &P, unsigned long long *hist, cudaStream_t s, const AffineT *aff) {
-    // the shape of the instantiation dispatched below (HistShape<32> for the
-    // 32-bin non-composite forms)
-    const bool pair = !aff && P.bins == 32;
-    const int ty = pair ? HistShape<32>::ty : HistShape<0>::ty;
+    // the shape of the instantiation dispatched below (the two-CTA shape for
+    // the 32-bin non-composite forms on BF16 images)
+    using Pair = HistShape<32, __nv_bfloat16>;
+    using Single = HistShape<0, float>;
+    const bool pair = !aff && P.bins == 32 && dt == REG_BF16;
+    const int ty = pair ? Pair::ty : Single::ty;
     const int tiles_x = (g.nx + HIST_TX - 1) / HIST_TX, tiles_y = (g.ny + ty - 1) / ty;
     const long long total = (long long)tiles_x * tiles_y * g.nz;
     if (total <= 0) return cudaSuccess;
-    const int per_sm = pair ? HistShape<32>::per_sm : HistShape<0>::per_sm;
+    const int per_sm = pair ? Pair::per_sm : Single::per_sm;
     const unsigned grid = (unsigned)std::min<long long>((long long)per_sm * num_sms(), total);
     const dim3 block(HIST_TX, ty);
     const size_t smem = sizeof(unsigned) * (size_t)hist_copies_of(P.bins, pair) * ((size_t)P.bins * P.bins + 1);

@@ -468,10 +468,10 @@ def test_identity_composite_histogram_equals_plain_histogram(capi, shape, img, b
     p + u exactly, 64-bit offsets) forms the same fixed-point joint histogram,
     bit for bit, as the plain form, over ragged tiles, both estimators and
     pads, and volumes whose persistent CTAs flush their 32-bit copies many
-    times.  With 32 bins the two forms also run different CTA shapes (the
-    plain one two 768-thread CTAs per SM with 24 copies, the composite one
-    1024-thread CTA with 32), so this also checks that the shape leaves the
-    integer sums alone."""
+    times.  With 32 bins on BF16 images the two forms also run different CTA
+    shapes (the plain one two 768-thread CTAs per SM with 24 copies, the
+    composite one 1024-thread CTA with 32), so this also checks that the
+    shape leaves the integer sums alone."""
     gen = torch.Generator(device=DEV).manual_seed(bins + shape[0])
     F = torch.rand(shape, generator=gen, device=DEV).to(img)
     M = torch.rand(shape, generator=gen, device=DEV).to(img)
